@@ -1,0 +1,269 @@
+"""CPU oracle for the CityGaussian hot path -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package.  It wraps ``oracle.c`` (plain single-threaded C, compiled by
+``oracle/build.py``) through ctypes; it shares no code with the CUDA library.
+
+Two builds exist: ``f32`` (the parity build: every value in FP32, operation order as
+documented in oracle.c) and ``f64`` (values and decisions in FP64, used for the
+finite-difference pins).  In both, the key path that decides integers (culls, radius,
+tile rect, depth bits) is FP32.
+
+Paper passages: Eq. 1 and Sec. 3.1 (projection, SH colour, depth-sorted alpha blending,
+differentiable rendering); Eq. 7 and Sec. 3.3.2 (MAD block bounds, block frustum test,
+camera block, distance-based level, concatenation).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import numpy as np
+
+from . import build as _build
+
+F_CULL_NEAR, F_CULL_DET, F_CLAMP_X, F_CLAMP_Y = 1, 2, 4, 8
+F_CLAMP_RGB = (16, 32, 64)
+
+
+class OrcCamera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("campos", C.c_float * 3),
+                ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class OrcConfig(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("near_z", C.c_float), ("bg", C.c_float * 3)]
+
+
+def make_camera(cam):
+    c = OrcCamera()
+    c.R[:] = [float(v) for v in np.asarray(cam["R"], dtype=np.float32).reshape(9)]
+    c.t[:] = [float(v) for v in np.asarray(cam["t"], dtype=np.float32)]
+    c.campos[:] = [float(v) for v in np.asarray(cam["campos"], dtype=np.float32)]
+    c.fx, c.fy, c.cx, c.cy = cam["fx"], cam["fy"], cam["cx"], cam["cy"]
+    c.width, c.height = cam["width"], cam["height"]
+    return c
+
+
+def make_config(tile=16, near_z=0.2, bg=(0.0, 0.0, 0.0)):
+    c = OrcConfig()
+    c.tile = tile
+    c.near_z = near_z
+    c.bg[:] = list(bg)
+    return c
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+_LIBS = {}
+
+
+def lib(real="f32"):
+    if real not in _LIBS:
+        _build.build()
+        L = C.CDLL(_build.lib_path(real))
+        vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+        L.orc_project.restype = i64
+        L.orc_project.argtypes = [i64, vp, vp, vp, vp, i32, vp, vp] + [vp] * 9
+        L.orc_emit_keys.restype = i64
+        L.orc_emit_keys.argtypes = [i64, vp, vp, vp, i32, vp, vp, i64]
+        L.orc_sort_pairs.argtypes = [i64, vp, vp]
+        L.orc_tile_ranges.argtypes = [i64, vp, i32, vp]
+        L.orc_composite.restype = i64
+        L.orc_composite.argtypes = [i64, vp, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.orc_composite_brute.argtypes = [i64, vp, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp]
+        L.orc_composite_backward.argtypes = [i64, vp, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
+        L.orc_project_backward.argtypes = [i64, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.orc_l1.argtypes = [i64, vp, vp, vp, vp]
+        L.orc_block_bounds.argtypes = [i32, i32, vp, vp, vp, C.c_double, vp]
+        L.orc_lod_select.argtypes = [i32, i32, vp, vp, vp, vp, C.c_float, vp, vp]
+        L.orc_concat.restype = i64
+        L.orc_concat.argtypes = [i32, i32, vp, vp, vp, vp]
+        L.orc_sh_basis.argtypes = [i64, vp, i32, vp, vp]
+        L.orc_real_bytes.restype = i32
+        _LIBS[real] = L
+    return _LIBS[real]
+
+
+def _dtype(real):
+    return np.float32 if real == "f32" else np.float64
+
+
+def _scene_arrays(scene, real, idx=None):
+    dt = _dtype(real)
+    mo, sc, q, sh = scene["mean_opac"], scene["scale"], scene["quat"], scene["sh"]
+    if idx is not None:
+        mo, sc, q, sh = mo[idx], sc[idx], q[idx], sh[:, idx]
+    return (np.ascontiguousarray(mo, dtype=dt), np.ascontiguousarray(sc, dtype=dt),
+            np.ascontiguousarray(q, dtype=dt), np.ascontiguousarray(sh, dtype=dt))
+
+
+def project(scene, cam, cfg=None, real="f32", idx=None, arrays=None):
+    """Per-Gaussian projection records (Eq. 1's proj) and tile rects."""
+    cfg = cfg or make_config()
+    L = lib(real)
+    dt = _dtype(real)
+    mo, sc, q, sh = arrays if arrays is not None else _scene_arrays(scene, real, idx)
+    n = mo.shape[0]
+    out = {
+        "depth": np.zeros(n, np.float32), "radius": np.zeros(n, np.int32), "rect": np.zeros((n, 4), np.int32),
+        "tiles_touched": np.zeros(n, np.int64), "xy": np.zeros((n, 2), dt), "cov2d": np.zeros((n, 3), dt),
+        "conic": np.zeros((n, 3), dt), "rgb": np.zeros((n, 3), dt), "flags": np.zeros(n, np.int32),
+    }
+    c = make_camera(cam)
+    k = L.orc_project(n, _p(mo), _p(sc), _p(q), _p(sh), scene["sh_degree"], C.byref(c), C.byref(cfg),
+                      _p(out["depth"]), _p(out["radius"]), _p(out["rect"]), _p(out["tiles_touched"]),
+                      _p(out["xy"]), _p(out["cov2d"]), _p(out["conic"]), _p(out["rgb"]), _p(out["flags"]))
+    out["n_entries"] = int(k)
+    out["arrays"] = (mo, sc, q, sh)
+    return out
+
+
+def tiles_xy(cam, tile):
+    return (cam["width"] + tile - 1) // tile, (cam["height"] + tile - 1) // tile
+
+
+def bin_and_sort(pr, cam, cfg=None, real="f32"):
+    """(tile | depth bits, index) keys, sorted, and per-tile ranges."""
+    cfg = cfg or make_config()
+    L = lib(real)
+    tx, ty = tiles_xy(cam, cfg.tile)
+    k = pr["n_entries"]
+    keys = np.zeros(max(k, 1), np.uint64)
+    vals = np.zeros(max(k, 1), np.uint32)
+    n = pr["depth"].shape[0]
+    got = L.orc_emit_keys(n, _p(pr["depth"]), _p(pr["rect"]), _p(pr["tiles_touched"]), tx, _p(keys), _p(vals), k)
+    assert got == k
+    unsorted = (keys[:k].copy(), vals[:k].copy())
+    L.orc_sort_pairs(k, _p(keys), _p(vals))
+    ranges = np.zeros((tx * ty, 2), np.int64)
+    L.orc_tile_ranges(k, _p(keys), tx * ty, _p(ranges))
+    return {"keys": keys[:k], "vals": vals[:k], "ranges": ranges, "unsorted": unsorted}
+
+
+def composite(pr, srt, cam, cfg=None, real="f32", tile_mask=None):
+    cfg = cfg or make_config()
+    L = lib(real)
+    dt = _dtype(real)
+    W, H = cam["width"], cam["height"]
+    mo = pr["arrays"][0]
+    n = mo.shape[0]
+    out = {"image": np.zeros((3, H, W), dt), "final_T": np.zeros((H, W), dt),
+           "n_contrib": np.zeros((H, W), np.int32), "n_visited": np.zeros((H, W), np.int32),
+           "ambiguous": np.zeros((H, W), np.uint8)}
+    h = C.c_uint64(0)
+    tm = None if tile_mask is None else np.ascontiguousarray(tile_mask, dtype=np.uint8)
+    vals = srt["vals"] if srt["vals"].size else np.zeros(1, np.uint32)
+    pairs = L.orc_composite(n, _p(pr["xy"]), _p(pr["conic"]), _p(mo), _p(pr["rgb"]), _p(vals),
+                            _p(srt["ranges"]), W, H, C.byref(cfg), _p(tm), _p(out["image"]), _p(out["final_T"]),
+                            _p(out["n_contrib"]), _p(out["n_visited"]), _p(out["ambiguous"]), C.byref(h))
+    out["pairs"] = int(pairs)
+    out["hash"] = int(h.value)
+    return out
+
+
+def render(scene, cam, cfg=None, real="f32", idx=None, tile_mask=None):
+    """Full forward: project, bin, sort, range, composite.  ``idx`` selects a subset (LoD)."""
+    cfg = cfg or make_config()
+    pr = project(scene, cam, cfg, real, idx)
+    srt = bin_and_sort(pr, cam, cfg, real)
+    out = composite(pr, srt, cam, cfg, real, tile_mask)
+    out["proj"] = pr
+    out["sort"] = srt
+    return out
+
+
+def composite_brute(pr, cam, cfg=None, real="f32"):
+    cfg = cfg or make_config()
+    L = lib(real)
+    dt = _dtype(real)
+    W, H = cam["width"], cam["height"]
+    mo = pr["arrays"][0]
+    img = np.zeros((3, H, W), dt)
+    T = np.zeros((H, W), dt)
+    L.orc_composite_brute(mo.shape[0], _p(pr["xy"]), _p(pr["conic"]), _p(mo), _p(pr["rgb"]), _p(pr["depth"]),
+                          _p(pr["flags"]), W, H, C.byref(cfg), _p(img), _p(T))
+    return img, T
+
+
+def render_backward(scene, cam, dL_dimage, cfg=None, real="f32", idx=None, fwd=None):
+    """Analytic gradient of sum(dL_dimage * image) w.r.t. every Gaussian attribute."""
+    cfg = cfg or make_config()
+    L = lib(real)
+    dt = _dtype(real)
+    if fwd is None:
+        fwd = render(scene, cam, cfg, real, idx)
+    pr, srt = fwd["proj"], fwd["sort"]
+    mo, sc, q, sh = pr["arrays"]
+    n = mo.shape[0]
+    W, H = cam["width"], cam["height"]
+    g2 = {"xy": np.zeros((n, 2), dt), "conic": np.zeros((n, 3), dt), "opac": np.zeros(n, dt),
+          "rgb": np.zeros((n, 3), dt)}
+    gimg = np.ascontiguousarray(dL_dimage, dtype=dt)
+    vals = srt["vals"] if srt["vals"].size else np.zeros(1, np.uint32)
+    L.orc_composite_backward(n, _p(pr["xy"]), _p(pr["conic"]), _p(mo), _p(pr["rgb"]), _p(vals), _p(srt["ranges"]),
+                             W, H, C.byref(cfg), _p(gimg), _p(g2["xy"]), _p(g2["conic"]), _p(g2["opac"]),
+                             _p(g2["rgb"]))
+    g = {"mean": np.zeros((n, 3), dt), "scale": np.zeros((n, 3), dt), "quat": np.zeros((n, 4), dt),
+         "opac": np.zeros(n, dt), "sh": np.zeros_like(sh)}
+    c = make_camera(cam)
+    L.orc_project_backward(n, _p(mo), _p(sc), _p(q), _p(sh), scene["sh_degree"], C.byref(c), C.byref(cfg),
+                           _p(pr["tiles_touched"]), _p(g2["xy"]), _p(g2["conic"]), _p(g2["opac"]), _p(g2["rgb"]),
+                           _p(g["mean"]), _p(g["scale"]), _p(g["quat"]), _p(g["opac"]), _p(g["sh"]))
+    g["screen"] = g2
+    g["fwd"] = fwd
+    return g
+
+
+def l1(img, target, real="f32"):
+    L = lib(real)
+    dt = _dtype(real)
+    a = np.ascontiguousarray(img, dtype=dt)
+    b = np.ascontiguousarray(target, dtype=dt)
+    grad = np.zeros_like(a)
+    loss = C.c_double(0)
+    L.orc_l1(a.size, _p(a), _p(b), _p(grad), C.byref(loss))
+    return loss.value, grad
+
+
+def block_bounds(scene, n_mad=4.0):
+    lo = np.ascontiguousarray(scene["level_offset"], np.int64)
+    lc = np.ascontiguousarray(scene["level_count"], np.int64)
+    nb, nl = lo.shape
+    out = np.zeros((nb, 6), np.float32)
+    mo = np.ascontiguousarray(scene["mean_opac"], np.float32)
+    lib("f64").orc_block_bounds(nb, nl, _p(lo), _p(lc), _p(mo), float(n_mad), _p(out))
+    return out
+
+
+def lod_select(scene, aabb, cam, dist=(200.0, 600.0), near_z=0.2):
+    lc = np.ascontiguousarray(scene["level_count"], np.int64)
+    nb, nl = lc.shape
+    lev = np.zeros(nb, np.int8)
+    c = make_camera(cam)
+    d = np.asarray(dist, np.float64)
+    cell = np.ascontiguousarray(scene["block_cell"], np.float32)
+    lib("f64").orc_lod_select(nb, nl, _p(lc), _p(np.ascontiguousarray(aabb, np.float32)), _p(cell), C.byref(c),
+                              near_z, _p(d), _p(lev))
+    return lev
+
+
+def concat(scene, level):
+    lo = np.ascontiguousarray(scene["level_offset"], np.int64)
+    lc = np.ascontiguousarray(scene["level_count"], np.int64)
+    nb, nl = lo.shape
+    lev = np.ascontiguousarray(level, np.int8)
+    total = int(sum(lc[b, lev[b]] for b in range(nb) if lev[b] >= 0))
+    out = np.zeros(max(total, 1), np.int64)
+    m = lib("f64").orc_concat(nb, nl, _p(lo), _p(lc), _p(lev), _p(out))
+    return out[:m]
+
+
+def sh_basis(dirs, deg=3, real="f64", with_grad=False):
+    dt = _dtype(real)
+    d = np.ascontiguousarray(dirs, dtype=dt).reshape(-1, 3)
+    out = np.zeros((d.shape[0], 16), dt)
+    dout = np.zeros((d.shape[0], 16, 3), dt) if with_grad else None
+    lib(real).orc_sh_basis(d.shape[0], _p(d), deg, _p(out), _p(dout))
+    return (out, dout) if with_grad else out
