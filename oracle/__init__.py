@@ -94,7 +94,7 @@ def _scene_arrays(scene, real, idx=None):
     dt = _dtype(real)
     mo, sc, q, sh = scene["mean_opac"], scene["scale"], scene["quat"], scene["sh"]
     if idx is not None:
-        mo, sc, q, sh = mo[idx], sc[idx], q[idx], sh[:, idx]
+        mo, sc, q, sh = mo[idx], sc[idx], q[idx], sh[idx]
     return (np.ascontiguousarray(mo, dtype=dt), np.ascontiguousarray(sc, dtype=dt),
             np.ascontiguousarray(q, dtype=dt), np.ascontiguousarray(sh, dtype=dt))
 

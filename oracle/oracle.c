@@ -158,7 +158,7 @@ void orc_sh_basis(int64_t n, const REAL* dirs, int32_t deg, REAL* out /*[n][16]*
 
 /* View-dependent colour c_k from the SH features f_k in R^{3x16} (Sec. 3.1):
  * raw = sum_k Y_k(dir) f_k + 0.5, clamped at 0 per channel.  Returns clamp bits. */
-static int colour(const REAL mean[3], const REAL* campos, const REAL* sh, int64_t n, int64_t i, int deg,
+static int colour(const REAL mean[3], const REAL* campos, const REAL* sh, int64_t i, int deg,
                   REAL rgb[3], REAL dirv[3], REAL* len_out, REAL raw[3])
 {
     REAL d0 = mean[0] - campos[0], d1 = mean[1] - campos[1], d2 = mean[2] - campos[2];
@@ -170,8 +170,8 @@ static int colour(const REAL mean[3], const REAL* campos, const REAL* sh, int64_
     int nc = (deg + 1) * (deg + 1);
     int clamp = 0;
     for (int ch = 0; ch < 3; ch++) {
-        REAL acc = Y[0] * sh[(0 * 3 + ch) * n + i];
-        for (int k = 1; k < nc; k++) acc = acc + Y[k] * sh[(k * 3 + ch) * n + i];
+        REAL acc = Y[0] * sh[(i * nc + 0) * 3 + ch];
+        for (int k = 1; k < nc; k++) acc = acc + Y[k] * sh[(i * nc + k) * 3 + ch];
         acc = acc + (REAL)0.5;
         raw[ch] = acc;
         if (acc < 0) { rgb[ch] = 0; clamp |= (F_CLAMP_R << ch); }
@@ -240,7 +240,7 @@ int64_t orc_project(int64_t n, const REAL* mean_opac, const REAL* scale, const R
         cov2d[3 * i] = pr.A; cov2d[3 * i + 1] = pr.B; cov2d[3 * i + 2] = pr.C;
         for (int a = 0; a < 3; a++) conic[3 * i + a] = pr.conic[a];
         REAL dirv[3], raw[3];
-        fl |= colour(mr, cr.campos, sh, n, i, sh_degree, &rgb[3 * i], dirv, NULL, raw);
+        fl |= colour(mr, cr.campos, sh, i, sh_degree, &rgb[3 * i], dirv, NULL, raw);
         flags[i] = fl;
     }
     return total;
@@ -532,7 +532,7 @@ void orc_project_backward(int64_t n, const REAL* mean_opac, const REAL* scale, c
 
         /* colour -> SH coefficients and view direction */
         REAL rgbv[3], dirv[3], raw[3], len;
-        int cl = colour(mr, cr.campos, sh, n, i, sh_degree, rgbv, dirv, &len, raw);
+        int cl = colour(mr, cr.campos, sh, i, sh_degree, rgbv, dirv, &len, raw);
         REAL Y[16], dY[16][3];
         sh_basis(dirv[0], dirv[1], dirv[2], sh_degree, Y, dY);
         REAL gdir[3] = {0, 0, 0};
@@ -540,8 +540,8 @@ void orc_project_backward(int64_t n, const REAL* mean_opac, const REAL* scale, c
             if (cl & (F_CLAMP_R << ch)) continue;
             REAL gc = g_rgb[3 * i + ch];
             for (int k = 0; k < nc; k++) {
-                g_sh[(int64_t)(k * 3 + ch) * n + i] += Y[k] * gc;
-                for (int a = 0; a < 3; a++) gdir[a] += gc * sh[(int64_t)(k * 3 + ch) * n + i] * dY[k][a];
+                g_sh[(i * nc + k) * 3 + ch] += Y[k] * gc;
+                for (int a = 0; a < 3; a++) gdir[a] += gc * sh[(i * nc + k) * 3 + ch] * dY[k][a];
             }
         }
         REAL dd = (dirv[0] * gdir[0] + dirv[1] * gdir[1]) + dirv[2] * gdir[2];

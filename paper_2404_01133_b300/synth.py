@@ -9,7 +9,7 @@ Scene format (all arrays C-contiguous numpy, FP32 unless stated):
 * ``mean_opac`` [N, 4]  world position x, y, z (metres, z up) and activated opacity o in (0, 1)
 * ``scale``     [N, 4]  linear (activated) scales sx, sy, sz and an unused fourth lane
 * ``quat``      [N, 4]  rotation quaternion (w, x, y, z), Hamilton convention
-* ``sh``        [(deg+1)^2 * 3, N]  planar SH coefficients, plane = coef * 3 + channel
+* ``sh``        [N, (deg+1)^2, 3]  SH coefficients, Gaussian-major, channel fastest
 * ``sh_degree`` int in 0..3
 * block table (optional): ``level_offset`` / ``level_count`` int64 [n_blocks, n_levels],
   ``block_cell`` FP32 [n_blocks, 4] = (x0, x1, y0, y1) of the block's ground cell.
@@ -86,12 +86,12 @@ def _attributes(rng, n, log_scale_mu, log_scale_sigma, sh_degree, hi_sigma=0.05)
     opac = 1.0 / (1.0 + np.exp(-rng.normal(0.0, 1.0, size=n)))
     base = rng.uniform(0.0, 1.0, size=(n, 3))
     n_coef = (sh_degree + 1) ** 2
-    sh = np.empty((n_coef * 3, n), dtype=np.float32)
-    sh[0:3] = ((base - 0.5) * SQRT_4PI).T.astype(np.float32)
+    sh = np.empty((n, n_coef, 3), dtype=np.float32)
+    sh[:, 0, :] = ((base - 0.5) * SQRT_4PI).astype(np.float32)
     if n_coef > 1:
-        # higher orders drawn plane by plane in FP32 to bound host memory at 20M+ Gaussians
-        for p in range(3, n_coef * 3):
-            sh[p] = rng.standard_normal(n, dtype=np.float32) * np.float32(hi_sigma)
+        # higher orders drawn coefficient by coefficient in FP32 to bound host memory at 20M+ Gaussians
+        for k in range(1, n_coef):
+            sh[:, k, :] = rng.standard_normal((n, 3), dtype=np.float32) * np.float32(hi_sigma)
     scale4 = np.zeros((n, 4), dtype=np.float32)
     scale4[:, :3] = scale
     return scale4, q.astype(np.float32), opac, sh
@@ -218,7 +218,7 @@ def build_blocks(scene, grid, fractions=(1.0, 0.5, 0.25), extent=None):
         "mean_opac": np.ascontiguousarray(mo[order]),
         "scale": np.ascontiguousarray(scene["scale"][order]),
         "quat": np.ascontiguousarray(scene["quat"][order]),
-        "sh": np.ascontiguousarray(scene["sh"][:, order]),
+        "sh": np.ascontiguousarray(scene["sh"][order]),
         "sh_degree": scene["sh_degree"],
         "level_offset": level_offset, "level_count": level_count, "block_cell": cells,
         "perm": order,
@@ -299,7 +299,7 @@ def training_blocks(n_blocks=32, views_per_block=8, seed=4, lo=200_000, hi=3_000
         "mean_opac": np.concatenate([p["mean_opac"] for p in parts]),
         "scale": np.concatenate([p["scale"] for p in parts]),
         "quat": np.concatenate([p["quat"] for p in parts]),
-        "sh": np.concatenate([p["sh"] for p in parts], axis=1),
+        "sh": np.concatenate([p["sh"] for p in parts], axis=0),
         "sh_degree": 3,
     }
     starts = np.concatenate([[0], np.cumsum(counts)[:-1]])

@@ -20,8 +20,8 @@ def fd_scene(seed, n=10, deg=3):
     sc[:, :3] = np.exp(r.normal(-2.3, 0.4, size=(n, 3)))
     q = r.normal(size=(n, 4))
     nc = (deg + 1) ** 2
-    sh = r.normal(0, 0.3, size=(nc * 3, n))
-    sh[0:3] = r.uniform(-1.5, 1.5, size=(3, n))
+    sh = r.normal(0, 0.3, size=(n, nc, 3))
+    sh[:, 0, :] = r.uniform(-1.5, 1.5, size=(n, 3))
     return {"mean_opac": mo, "scale": sc, "quat": q, "sh": sh, "sh_degree": deg}
 
 
@@ -76,8 +76,9 @@ def test_analytic_gradient_matches_central_differences(seed):
     for i in range(n):
         for name, a in PARAMS:
             samples.append((name, (i, a)))
-        for k in range(sc["sh"].shape[0]):
-            samples.append(("sh", (k, i)))
+        for k in range(sc["sh"].shape[1]):
+            for ch in range(3):
+                samples.append(("sh", (i, k, ch)))
     gmax = {k: max(np.abs(v).max(), 1e-30) for k, v in an.items()}
     for name, ix in samples:
         x0 = sc[name][ix]

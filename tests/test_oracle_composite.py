@@ -16,7 +16,7 @@ def test_single_isotropic_gaussian_closed_form():
     s, o = 0.04, 0.8
     c = np.array([0.9, 0.4, 0.1])
     f0 = (c - 0.5) * 2 * math.sqrt(math.pi)
-    sc = make_scene([[0, 0, 0]], [[s, s, s]], [[1, 0, 0, 0]], [o], sh=f0.reshape(3, 1))
+    sc = make_scene([[0, 0, 0]], [[s, s, s]], [[1, 0, 0, 0]], [o], sh=f0.reshape(1, 1, 3))
     out = oracle.render(sc, cam, real="f64")
     sig2 = (150.0 * s / 4.0) ** 2 + 0.3
     jj, ii = np.mgrid[0:H, 0:W].astype(np.float64)
@@ -34,7 +34,7 @@ def test_opaque_stack_stops_on_transmittance():
     W = H = 33
     cam = synth.small_scene_camera(W, H, f=100.0, dist=4.0)
     cols = np.array([[0.9, 0.2, 0.3], [0.1, 0.8, 0.5], [0.6, 0.6, 0.9]])
-    f0 = ((cols - 0.5) * 2 * math.sqrt(math.pi)).T
+    f0 = ((cols - 0.5) * 2 * math.sqrt(math.pi)).reshape(3, 1, 3)
     sc = make_scene([[0, 0, 0.0], [0, 0, 0.5], [0, 0, 1.0]], [[0.2] * 3] * 3, [[1, 0, 0, 0]] * 3, [1.0] * 3, sh=f0)
     out = oracle.render(sc, cam, real="f32")
     a = np.float32(0.99)
@@ -64,7 +64,7 @@ def test_input_order_invariance(rng):
         perm[slots] = np.sort(perm[slots])
     sp = dict(sc)
     sp["mean_opac"], sp["scale"], sp["quat"] = sc["mean_opac"][perm], sc["scale"][perm], sc["quat"][perm]
-    sp["sh"] = np.ascontiguousarray(sc["sh"][:, perm])
+    sp["sh"] = np.ascontiguousarray(sc["sh"][perm])
     b = oracle.render(sp, cams[0], real="f32")
     np.testing.assert_array_equal(a["image"], b["image"])
     np.testing.assert_array_equal(a["final_T"], b["final_T"])

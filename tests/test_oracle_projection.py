@@ -19,7 +19,7 @@ def make_scene(means, scales, quats, opac, sh=None, deg=0):
     sc = np.zeros((n, 4), np.float64)
     sc[:, :3] = scales
     if sh is None:
-        sh = np.zeros(((deg + 1) ** 2 * 3, n))
+        sh = np.zeros((n, (deg + 1) ** 2, 3))
     return {"mean_opac": mo, "scale": sc, "quat": np.asarray(quats, np.float64), "sh": np.asarray(sh, np.float64),
             "sh_degree": deg}
 
@@ -173,7 +173,7 @@ def test_degree0_colour_is_base_colour():
     sc, cams = synth.workload_small()
     pr = oracle.project(sc, cams[0], real="f64")
     vis = (pr["flags"] & 3) == 0
-    f0 = sc["sh"][0:3].T.astype(np.float64)
+    f0 = sc["sh"][:, 0, :].astype(np.float64)
     # the DC basis function is 1 / (2 sqrt(pi)); the generator stored (c - 0.5) * 2 sqrt(pi)
     np.testing.assert_allclose(pr["rgb"][vis], np.clip(f0[vis] / (2 * math.sqrt(math.pi)) + 0.5, 0, None),
                                rtol=1e-12, atol=1e-12)
