@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark of the CityGaussian rendering hot path on B300.
+
+Default workload: one training step on the 1,000,000-Gaussian SH-3 synthetic city viewed at
+1920x1080 from 150 m, pitched 45 degrees: block LoD selection (one block), projection, depth
+sort, tile duplication, tile sort, compositing, L1 loss against a seeded target and the
+full backward.  Prints ONE JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs one independent replica per GPU (launched with torch.distributed.run): each rank
+renders the same workload; only the timing is combined (barrier + max over ranks).
+`--impl reference` times the CPU oracle (plain C, single thread) on a bounded sample of the
+same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd / fwd+bwd Mpix/s at 1080p, 20M-Gaussian LoD FPS, batched vs plain"
+UNIT = "Mpix/s"
+WORKLOAD = "city-1M-SH3 1920x1080 fwd+bwd (L1), 16x16 tiles"
+L2_FLUSH_BYTES = 256 << 20
+FP32_OPS_PER_EVAL_PAIR = 12     # forward: offset, quadratic form, exp argument, alpha, skip test
+FP32_OPS_PER_BLEND = 7          # forward: transmittance update, stop test, colour accumulation
+FP32_OPS_PER_BWD_PAIR = 45      # backward: re-evaluation, T recovery, dalpha, 9 gradient terms
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# -----------------------------------------------------------------------------------------
+# our arm
+# -----------------------------------------------------------------------------------------
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2404_01133_b300 import build as libbuild
+    libbuild.build()
+    from paper_2404_01133_b300 import cgs, synth
+    from paper_2404_01133_b300 import torch_api as ta
+
+    dev = torch.device("cuda", local)
+    sc, cams = synth.workload_city_1m()
+    cam = cams[0]
+    W, H = cam["width"], cam["height"]
+    n = sc["mean_opac"].shape[0]
+    ds = ta.DeviceScene(sc, dev)
+    cfg = ta.make_config(tile=args.tile, batch=args.batch)
+    frame = ta.Frame(1, W, H, args.tile, 1, n, 8_000_000, dev)
+    d_cams = ta.cameras_device(cams, dev)
+    tgt_host = torch.from_numpy(synth.target_image(1, W, H))[None].pin_memory()
+    tgt = tgt_host.to(dev)
+    img, T, nc = frame.outputs()
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    dL = torch.empty_like(img)
+    grads = (torch.zeros_like(ds.mean_opac), torch.zeros_like(ds.scale), torch.zeros_like(ds.quat),
+             torch.zeros_like(ds.sh))
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev)
+    s_struct = ds.struct()
+
+    def step(fwd_only=False):
+        cgs.cgs_render_forward(s_struct, frame.struct, cfg, d_cams, None, None, img, T, nc, st)
+        if fwd_only:
+            return
+        for gbuf in grads:
+            gbuf.zero_()
+        loss.zero_()
+        cgs.cgs_l1_loss(img, tgt, img.numel(), loss, dL, st)
+        cgs.cgs_render_backward(s_struct, frame.struct, cfg, d_cams, dL, T, nc, *grads, st)
+
+    def timed(k, fwd_only=False, with_stages=False):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        if with_stages:
+            cgs.cgs_timing_enable(True)
+        launches0 = cgs.cgs_kernel_launches()
+        barrier(world)
+        torch.cuda.synchronize()
+        for i in range(k):
+            flush.fill_(i & 0xff)  # evict L2 between timed steps (outside the event pair)
+            ev[i][0].record(st)
+            step(fwd_only)
+            ev[i][1].record(st)
+        torch.cuda.synchronize()
+        barrier(world)
+        launches = cgs.cgs_kernel_launches() - launches0
+        stages = cgs.cgs_timing_read() if with_stages else None
+        if with_stages:
+            cgs.cgs_timing_enable(False)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return ms, launches, stages
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    status, counts = frame.status()
+    if status != cgs.CGS_OK:
+        raise RuntimeError(f"frame status: {cgs.cgs_status_string(status)}")
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, launches, stages = timed(args.steps, with_stages=True)
+    clk = clocks.stop()
+    ms_fwd, _, stages_fwd = timed(args.steps, fwd_only=True, with_stages=True)
+    status, counts = frame.status()
+    if status != cgs.CGS_OK:
+        raise RuntimeError(f"frame status: {cgs.cgs_status_string(status)}")
+
+    step_ms = max_over_ranks(sum(ms) / len(ms), world)
+    fwd_ms = max_over_ranks(sum(ms_fwd) / len(ms_fwd), world)
+    pix = W * H
+    value = world * pix / (step_ms * 1e-3) / 1e6
+    fwd_value = world * pix / (fwd_ms * 1e-3) / 1e6
+
+    # per-stage averages (ms per launch of the stage)
+    stage_ms = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in stages.items()}
+    n_sel, n_vis, k_ent, pairs_f, pairs_b = counts[0], counts[1], counts[2], counts[3], counts[4]
+    nc_coef = (sc["sh_degree"] + 1) ** 2
+    peaks, peak_src = load_peaks()
+    alu_peak = 148 * 128 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12  # FP32 lane-ops / s, in T/s
+    depth_passes, tile_passes = 4, 2
+    work = {
+        # algorithmic bytes per launch (HBM-bound stages)
+        "project": ("hbm", n_sel * (16 + 4 + 4) + n_vis * (32 + 12 * nc_coef + 48 + 8 + 8)),
+        "depth_sort": ("hbm", n_sel * 4 + n_vis * 12 + n_vis * 8 + depth_passes * n_vis * 24),
+        "emit": ("hbm", n_vis * (12 + 4 + 8) + k_ent * 8),
+        "tile_sort": ("hbm", k_ent * 4 + tile_passes * k_ent * 16 + k_ent * 4),
+        # algorithmic FP32 operations per launch (issue-bound stages)
+        "render": ("alu", pairs_f * FP32_OPS_PER_EVAL_PAIR + pairs_b * FP32_OPS_PER_BLEND),
+        "render_bwd": ("alu", pairs_b * FP32_OPS_PER_BWD_PAIR),
+        "project_bwd": ("hbm", n_vis * (16 * 3 + 12 * nc_coef + 48 + 4 * 4 * 3 + 12 * nc_coef)),
+    }
+    dom = max(work, key=lambda k: stage_ms.get(k, 0.0))
+    bound, amount = work[dom]
+    t = stage_ms[dom] * 1e-3
+    if bound == "hbm":
+        achieved = amount / t / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"]}
+    else:
+        achieved = amount / t / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFP32op/s",
+                "frac": achieved / alu_peak}
+    roof.update({"kernel": dom, "traffic": None, "peak_source": peak_src,
+                 "ms_per_launch": stage_ms[dom]})
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "gaussians": n, "visible": n_vis, "tile_entries": k_ent,
+                   "width": W, "height": H, "tile": args.tile, "batch": args.batch, "views_per_gpu": 1,
+                   "parallelism": f"replicas x{world}", "l2": "flushed between timed steps (256 MB write)"},
+        "fwd_mpix_s": fwd_value, "fwd_ms": fwd_ms, "fps_fwd_bwd": 1e3 / step_ms, "fps_fwd": 1e3 / fwd_ms,
+        "gaussians_per_s": world * n / (step_ms * 1e-3),
+        "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "stage_ms_fwd_only": {k: round(v[0] / v[1], 4) for k, v in stages_fwd.items() if v[1]},
+        "pairs": {"fwd_evaluated": pairs_f, "bwd_contributing": pairs_b},
+        "roofline": roof,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+
+    if not args.no_e2e:
+        out["e2e"] = run_e2e(args, ds, frame, sc, tgt_host, tgt, step, loss, st, world)
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(sc, cam, full=True)
+    return out
+
+
+def run_e2e(args, ds, frame, sc, tgt_host, tgt_dev, step, loss, st, world):
+    """Same step through the public API with HOST inputs: every step copies the scene and the
+    target from pinned host memory to the device and reads the loss back."""
+    import torch
+    host = {k: torch.from_numpy(np.ascontiguousarray(sc[k], np.float32)).pin_memory()
+            for k in ("mean_opac", "scale", "quat", "sh")}
+    dev_bufs = {"mean_opac": ds.mean_opac, "scale": ds.scale, "quat": ds.quat, "sh": ds.sh}
+    loss_host = torch.empty(1, dtype=torch.float32).pin_memory()
+    h2d = sum(t.numel() * 4 for t in host.values()) + tgt_host.numel() * 4
+    k = max(3, min(args.steps, 10))
+
+    def one():
+        for name, t in host.items():
+            dev_bufs[name].copy_(t, non_blocking=True)
+        tgt_dev.copy_(tgt_host, non_blocking=True)
+        step()
+        loss_host.copy_(loss, non_blocking=True)
+
+    for _ in range(2):
+        one()
+    torch.cuda.synchronize()
+    barrier(world)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(k):
+        one()
+    b.record(st)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(a.elapsed_time(b) / k, world)
+    W, H = frame.width, frame.height
+    return {"value": world * W * H / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}
+
+
+# -----------------------------------------------------------------------------------------
+# CPU oracle (baseline leg and the reference arm)
+# -----------------------------------------------------------------------------------------
+def band_mask(cam, tile, frac):
+    tx = (cam["width"] + tile - 1) // tile
+    ty = (cam["height"] + tile - 1) // tile
+    rows = max(1, int(round(ty * frac)))
+    r0 = (ty - rows) // 2
+    m = np.zeros((ty, tx), np.uint8)
+    m[r0:r0 + rows] = 1
+    pix = sum(min(tile, cam["height"] - r * tile) for r in range(r0, r0 + rows)) * cam["width"]
+    return m.reshape(-1), pix
+
+
+def oracle_step(sc, cam, tgt, mask):
+    import oracle
+    t0 = time.perf_counter()
+    pr = oracle.project(sc, cam)
+    srt = oracle.bin_and_sort(pr, cam)
+    o = oracle.composite(pr, srt, cam, tile_mask=mask)
+    o["proj"], o["sort"] = pr, srt
+    _, dL = oracle.l1(o["image"], tgt)
+    oracle.render_backward(sc, cam, dL, fwd=o, tile_mask=mask)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(sc, cam, full):
+    from paper_2404_01133_b300 import synth
+    tgt = synth.target_image(1, cam["width"], cam["height"])
+    if full:
+        mask, pix = None, cam["width"] * cam["height"]
+        sample = "one full 1920x1080 frame: projection, sort, compositing, L1, backward (oracle as is)"
+    else:
+        mask, pix = band_mask(cam, 16, 0.125)
+        sample = "central band of 1/8 of the tile rows; full projection and sort"
+    t = oracle_step(sc, cam, tgt, mask)
+    return {"value": pix / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+            "seconds": t}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    from paper_2404_01133_b300 import synth
+    import oracle
+    oracle.lib("f32")
+    sc, cams = synth.workload_city_1m()
+    cam = cams[0]
+    tgt = synth.target_image(1, cam["width"], cam["height"])
+    mask, pix = band_mask(cam, 16, 0.125)
+    for _ in range(args.warmup):
+        oracle_step(sc, cam, tgt, mask)
+    ts = [oracle_step(sc, cam, tgt, mask) for _ in range(args.steps)]
+    ms = 1e3 * sum(ts) / len(ts)
+    value = pix / (ms * 1e-3) / 1e6
+    sample = "central band of 1/8 of the tile rows per step (full projection and sort)"
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "gaussians": sc["mean_opac"].shape[0], "width": cam["width"],
+                       "height": cam["height"], "tile": 16, "parallelism": "cpu, 1 thread"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        out = run_reference(args, world, rank)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    world, rank, local = dist_setup()
+    out = run_ours(args, world, rank, local)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

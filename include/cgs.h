@@ -1,0 +1,202 @@
+/*
+ * cgs.h -- C ABI of libcgs.so, a B300 (sm_103a) implementation of the rendering hot path
+ * of CityGaussian (arXiv 2404.01133): block-wise level-of-detail selection over a
+ * block-partitioned Gaussian scene (Sec. 3.3.2), followed by 3D Gaussian Splatting tile
+ * rasterization (Eq. 1, Sec. 3.1) and its analytic backward pass.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers named d_* (and every pointer inside cgs_scene and cgs_frame) are DEVICE
+ *    pointers owned by the caller.  No entry point of this header allocates or frees
+ *    device memory or keeps a pointer after it returns.
+ *  - Every call only enqueues work on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and returns; only cgs_frame_status synchronizes.
+ *  - The return value is CGS_OK or the code of a failed host-side argument check or
+ *    launch.  Conditions found on the device (capacity overflow, a bounded inter-block
+ *    wait that gave up) are latched in the frame's device status word and reported by
+ *    cgs_frame_status.  No entry point aborts, traps or waits without bound.
+ *  - Floating-point inputs are FP32.  Gaussian attributes are ACTIVATED values: linear
+ *    scales, opacity in (0, 1), rotation quaternion (w, x, y, z) of any length
+ *    (normalised inside, Hamilton convention).
+ *  - Cameras use OpenCV axes (x right, y down, z forward), x_cam = R x_world + t; pixel
+ *    (i, j) has its centre at the integer coordinate (i, j).
+ */
+#ifndef CGS_H
+#define CGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CGS_OK 0
+#define CGS_ERR_INVALID_ARGUMENT 1
+#define CGS_ERR_WORKSPACE_TOO_SMALL 2
+#define CGS_ERR_CAPACITY 3     /* device: more selected Gaussians or tile entries than the frame holds */
+#define CGS_ERR_SPIN_TIMEOUT 4 /* device: a bounded inter-block wait gave up; outputs are invalid */
+#define CGS_ERR_CUDA 5         /* a CUDA launch or memset failed */
+#define CGS_ERR_UNSUPPORTED 6
+
+/* Pinhole camera of one view: intrinsics kappa and pose tau_i of Eq. 1 (Sec. 3.1). 96 bytes. */
+typedef struct cgs_camera {
+    float R[9];        /* world -> camera rotation, row major */
+    float t[3];        /* world -> camera translation */
+    float campos[3];   /* camera centre in world coordinates (= -R^T t) */
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float _pad[3];
+} cgs_camera;
+
+/* Block-partitioned Gaussian scene.  Per Gaussian (Sec. 3.1): position, opacity, scale and
+ * rotation (the covariance), SH features in R^{3x16} at degree 3.  Detail level l of block
+ * b (Sec. 3.3.1/3.3.2) is the index range [level_offset[b*L + l], + level_count[b*L + l]).
+ * Level 0 is the finest.  Segments of different blocks must not overlap and must ascend
+ * with b, because scene index order breaks depth ties.  A scene without blocks is one
+ * block with one level covering [0, n). */
+typedef struct cgs_scene {
+    const float* mean_opac;      /* [n][4] x, y, z, opacity */
+    const float* scale;          /* [n][4] sx, sy, sz, unused */
+    const float* quat;           /* [n][4] w, x, y, z */
+    const float* sh;             /* [n][(sh_degree+1)^2][3] SH coefficients, channel fastest */
+    int64_t n;                   /* Gaussians, < 2^31 */
+    int32_t sh_degree;           /* 0..3 */
+    int32_t n_blocks;            /* >= 1 */
+    int32_t n_levels;            /* >= 1 */
+    int32_t _pad;
+    const int64_t* level_offset; /* [n_blocks][n_levels] */
+    const int64_t* level_count;  /* [n_blocks][n_levels] */
+    const float* block_aabb;     /* [n_blocks][6] lo xyz, hi xyz: Eq. 7 bounds (cgs_block_bounds) */
+    const float* block_cell;     /* [n_blocks][4] x0, x1, y0, y1 ground cell of the block */
+} cgs_scene;
+
+/* Rendering parameters. */
+typedef struct cgs_config {
+    int32_t tile;        /* tile side in pixels: 16 or 8 */
+    int32_t batch;       /* Gaussians staged per round by the compositing kernels: 32..256, a
+                            multiple of 32 and at most tile*tile */
+    float near_z;        /* near plane on camera-space z (0.2) */
+    float bg[3];         /* background colour */
+    double lod_dist[2];  /* level thresholds d1 < d2 in scene units: level 0 if dmin < d1,
+                            1 if dmin < d2, else 2 */
+} cgs_config;
+
+/* A batch of n_views equally sized views rendered together, and the caller-owned device
+ * workspace holding its intermediate state (kept for the backward).  n_cap bounds the
+ * selected Gaussians summed over the views (< 2^31); k_cap bounds the (tile, Gaussian)
+ * entries summed over the views (< 2^30).  Size ws with cgs_frame_workspace_bytes. */
+typedef struct cgs_frame {
+    void* ws;
+    int64_t ws_bytes;
+    int32_t n_views, width, height, tile, n_blocks;
+    int32_t _pad;
+    int64_t n_cap;
+    int64_t k_cap;
+} cgs_frame;
+
+int32_t cgs_version(void);
+const char* cgs_status_string(int32_t code);
+
+/* Bytes of workspace a cgs_frame with these dimensions needs; 0 if they are invalid. */
+int64_t cgs_frame_workspace_bytes(int32_t n_views, int32_t width, int32_t height, int32_t tile,
+                                  int32_t n_blocks, int64_t n_cap, int64_t k_cap);
+
+/* Eq. 7 (Sec. 3.3.2), per block and axis over the means of the block's finest level:
+ *   MAD = median(|p - median(p)|),
+ *   lo = max(min p, median - n_mad MAD),  hi = min(max p, median + n_mad MAD),
+ * evaluated in FP64 (median of an even count = mean of the two middle values), stored in
+ * d_aabb [n_blocks][6] rounded outward to FP32.  Exact selection, deterministic.  d_ws
+ * holds cgs_block_bounds_workspace_bytes(scene->n) bytes. */
+int64_t cgs_block_bounds_workspace_bytes(int64_t n);
+int32_t cgs_block_bounds(const cgs_scene* scene, double n_mad, float* d_aabb, void* d_ws, int64_t ws_bytes,
+                         void* stream);
+
+/* Block-wise level selection and frustum culling (Sec. 3.3.2) in FP64 for n_views
+ * cameras: the corners of a block's box with camera-space z > near_z are projected; the
+ * block is visible if their screen bounding box overlaps the image (x in (-0.5, W-0.5),
+ * y in (-0.5, H-0.5)); the block whose ground cell holds the camera is always kept; the
+ * level follows the minimum distance from the 8 corners to the camera centre.  Writes
+ * d_levels [n_views][n_blocks]: -1 culled or empty, else the level (<= n_levels - 1). */
+int32_t cgs_lod_select(const cgs_scene* scene, const cgs_config* cfg, const cgs_camera* d_cams,
+                       int32_t n_views, int8_t* d_levels, void* stream);
+
+/* Forward render of the frame's views (Eq. 1, Sec. 3.1) over the selected Gaussians,
+ * fused by concatenation (Sec. 3.2.3, 3.3.2).  Per view v the rendered set is:
+ *   d_levels != NULL:     segments (b, d_levels[v*n_blocks + b]) with a level >= 0;
+ *   d_view_block != NULL: block d_view_block[v] at level 0 (per-block training views);
+ *   both NULL:            the cgs_lod_select choice for d_cams[v].
+ * d_cams holds n_views cameras of size frame->width x frame->height.  Writes d_image
+ * [n_views][3][H][W], d_final_T [n_views][H][W] and d_n_contrib [n_views][H][W] (one past
+ * the position, in the pixel's tile list, of its last blended Gaussian) and keeps the
+ * sorted per-tile lists in frame->ws for cgs_render_backward. */
+int32_t cgs_render_forward(const cgs_scene* scene, const cgs_frame* frame, const cgs_config* cfg,
+                           const cgs_camera* d_cams, const int32_t* d_view_block, const int8_t* d_levels,
+                           float* d_image, float* d_final_T, uint32_t* d_n_contrib, void* stream);
+
+/* Analytic backward of cgs_render_forward (differentiable rendering, Sec. 3.1) for the
+ * same scene, frame, config and cameras, replaying every pixel back to front from its
+ * final transmittance and n_contrib.  ADDS dL/d(attribute) into gradient buffers laid out
+ * like the scene: d_g_mean_opac [n][4] (x, y, z, opacity), d_g_scale [n][4], d_g_quat
+ * [n][4], d_g_sh [n][(deg+1)^2][3].  Discrete decisions (culls, clamps, skips, the stop)
+ * pass no gradient.  Accumulation order is not fixed: repeated runs may differ in the
+ * last bits. */
+int32_t cgs_render_backward(const cgs_scene* scene, const cgs_frame* frame, const cgs_config* cfg,
+                            const cgs_camera* d_cams, const float* d_dL_dimage, const float* d_final_T,
+                            const uint32_t* d_n_contrib, float* d_g_mean_opac, float* d_g_scale,
+                            float* d_g_quat, float* d_g_sh, void* stream);
+
+/* L1 photometric loss (the L1 term of the training loss, Sec. 3.2.3) over `count` values:
+ * ADDS mean|img - target| into *d_loss and writes d_grad = sign(img - target) / count
+ * (sign(0) = 0). */
+int32_t cgs_l1_loss(const float* d_img, const float* d_target, int64_t count, float* d_loss, float* d_grad,
+                    void* stream);
+
+/* Synchronizes `stream`, then copies the frame's device status word to *status and its
+ * counters to counts[0..5]: selected Gaussians, visible Gaussians, tile entries, forward
+ * evaluated pairs, backward evaluated pairs, bounded-wait give-ups.  Either output may be
+ * NULL.  Returns the status word (CGS_OK when nothing was latched). */
+int32_t cgs_frame_status(const cgs_frame* frame, int32_t* status, int64_t* counts, void* stream);
+
+/* Device address and capacity (elements) of an internal frame array, valid after
+ * cgs_render_forward; for parity tests and debugging.  which:
+ *   0 sorted tile keys    u32 [k_cap]  view * tiles_per_view + tile (row-major tile id)
+ *   1 sorted values       u32 [k_cap]  selected index (position in the concatenation)
+ *   2 tile ranges         u32 [n_views * tiles][2]  [start, end) into 0/1
+ *   3 scene index         u32 [n_cap]  selected index -> scene index
+ *   4 projected records   float [n_cap][12]  u, v, opacity, depth | A', B', C', radius |
+ *                                            r, g, b, view
+ *   5 tiles touched       u32 [n_cap]
+ *   6 selected per view   u32 [n_views + 1] exclusive prefix of the per-view counts
+ *   7 depth order         u32 [n_cap]  selected indices of visible Gaussians by (view, depth)
+ */
+int32_t cgs_frame_buffer(const cgs_frame* frame, int32_t which, void** d_ptr, int64_t* count);
+
+/* Stages of the hot path, for cgs_timing_read. */
+#define CGS_STAGE_SELECT 0       /* level selection and segment lists (Sec. 3.3.2) */
+#define CGS_STAGE_PROJECT 1      /* projection, SH colour, tile rect */
+#define CGS_STAGE_DEPTH_SORT 2   /* visible compaction and (view, depth) radix sort */
+#define CGS_STAGE_EMIT 3         /* duplication into (tile, Gaussian) entries */
+#define CGS_STAGE_TILE_SORT 4    /* stable radix sort by tile and per-tile ranges */
+#define CGS_STAGE_RENDER 5       /* front-to-back compositing (Eq. 1) */
+#define CGS_STAGE_RENDER_BWD 6   /* compositing backward */
+#define CGS_STAGE_PROJECT_BWD 7  /* projection and colour backward */
+#define CGS_STAGE_LOSS 8         /* L1 loss */
+#define CGS_N_STAGES 9
+
+/* Benchmark instrumentation.  While enabled (on != 0), every stage launched by
+ * cgs_render_forward, cgs_render_backward and cgs_l1_loss is bracketed by a pair of CUDA
+ * events recorded on the caller's stream (library-owned events, created on first use, at
+ * most 256 pairs per stage between reads).  cgs_timing_read synchronizes those events and
+ * returns, per stage, the summed milliseconds and the number of bracketed launches since the
+ * previous read.  Not for use during stream capture. */
+int32_t cgs_timing_enable(int32_t on);
+int32_t cgs_timing_read(double* ms /*[CGS_N_STAGES]*/, int64_t* count /*[CGS_N_STAGES]*/);
+
+/* Number of CUDA kernels this library has launched in the process so far (host counter). */
+int64_t cgs_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CGS_H */

@@ -73,7 +73,7 @@ def lib(real="f32"):
         L.orc_composite.restype = i64
         L.orc_composite.argtypes = [i64, vp, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         L.orc_composite_brute.argtypes = [i64, vp, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp]
-        L.orc_composite_backward.argtypes = [i64, vp, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
+        L.orc_composite_backward.argtypes = [i64, vp, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp]
         L.orc_project_backward.argtypes = [i64, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.orc_l1.argtypes = [i64, vp, vp, vp, vp]
         L.orc_block_bounds.argtypes = [i32, i32, vp, vp, vp, C.c_double, vp]
@@ -187,8 +187,9 @@ def composite_brute(pr, cam, cfg=None, real="f32"):
     return img, T
 
 
-def render_backward(scene, cam, dL_dimage, cfg=None, real="f32", idx=None, fwd=None):
-    """Analytic gradient of sum(dL_dimage * image) w.r.t. every Gaussian attribute."""
+def render_backward(scene, cam, dL_dimage, cfg=None, real="f32", idx=None, fwd=None, tile_mask=None):
+    """Analytic gradient of sum(dL_dimage * image) w.r.t. every Gaussian attribute
+    (restricted to the pixels of the tiles in ``tile_mask`` when given)."""
     cfg = cfg or make_config()
     L = lib(real)
     dt = _dtype(real)
@@ -202,8 +203,9 @@ def render_backward(scene, cam, dL_dimage, cfg=None, real="f32", idx=None, fwd=N
           "rgb": np.zeros((n, 3), dt)}
     gimg = np.ascontiguousarray(dL_dimage, dtype=dt)
     vals = srt["vals"] if srt["vals"].size else np.zeros(1, np.uint32)
+    tm = None if tile_mask is None else np.ascontiguousarray(tile_mask, dtype=np.uint8)
     L.orc_composite_backward(n, _p(pr["xy"]), _p(pr["conic"]), _p(mo), _p(pr["rgb"]), _p(vals), _p(srt["ranges"]),
-                             W, H, C.byref(cfg), _p(gimg), _p(g2["xy"]), _p(g2["conic"]), _p(g2["opac"]),
+                             W, H, C.byref(cfg), _p(tm), _p(gimg), _p(g2["xy"]), _p(g2["conic"]), _p(g2["opac"]),
                              _p(g2["rgb"]))
     g = {"mean": np.zeros((n, 3), dt), "scale": np.zeros((n, 3), dt), "quat": np.zeros((n, 4), dt),
          "opac": np.zeros(n, dt), "sh": np.zeros_like(sh)}

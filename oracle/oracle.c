@@ -448,7 +448,8 @@ void orc_composite_brute(int64_t n, const REAL* xy, const REAL* conic, const REA
 /* ------------------------------------------------------------------------------------- */
 void orc_composite_backward(int64_t n, const REAL* xy, const REAL* conic, const REAL* mean_opac, const REAL* rgb,
                             const uint32_t* vals, const int64_t* ranges, int32_t W, int32_t H, const orc_config* cfg,
-                            const REAL* dL_dimage, REAL* g_xy, REAL* g_conic, REAL* g_opac, REAL* g_rgb)
+                            const uint8_t* tile_mask, const REAL* dL_dimage, REAL* g_xy, REAL* g_conic,
+                            REAL* g_opac, REAL* g_rgb)
 {
     const int B = cfg->tile;
     const int tiles_x = (W + B - 1) / B, tiles_y = (H + B - 1) / B;
@@ -465,6 +466,7 @@ void orc_composite_backward(int64_t n, const REAL* xy, const REAL* conic, const 
     for (int ty = 0; ty < tiles_y; ty++)
         for (int tx = 0; tx < tiles_x; tx++) {
             int t = ty * tiles_x + tx;
+            if (tile_mask && !tile_mask[t]) continue;
             int64_t s = ranges[2 * t], e = ranges[2 * t + 1];
             for (int64_t p = s; p < e; p++) list[p - s] = vals[p];
             for (int j = ty * B; j < (ty + 1) * B && j < H; j++)

@@ -1,0 +1,204 @@
+"""ctypes binding of libcgs.so (include/cgs.h): the same entry points, same names.
+
+This module only marshals arguments: device pointers come from torch tensors
+(``tensor.data_ptr()``), streams from ``torch.cuda.current_stream().cuda_stream``.  Every
+step of the rendering path runs in the CUDA library; if the library is missing this module
+raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcgs.so")
+
+CGS_OK = 0
+CGS_ERR_INVALID_ARGUMENT = 1
+CGS_ERR_WORKSPACE_TOO_SMALL = 2
+CGS_ERR_CAPACITY = 3
+CGS_ERR_SPIN_TIMEOUT = 4
+CGS_ERR_CUDA = 5
+CGS_ERR_UNSUPPORTED = 6
+
+BUF_TILE_KEYS, BUF_TILE_VALS, BUF_RANGES, BUF_SCENE_INDEX, BUF_RECORDS, BUF_TILES_TOUCHED, BUF_VIEW_BASE, \
+    BUF_DEPTH_ORDER = range(8)
+
+
+class cgs_camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("campos", C.c_float * 3),
+                ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("width", C.c_int32), ("height", C.c_int32), ("_pad", C.c_float * 3)]
+
+
+class cgs_scene(C.Structure):
+    _fields_ = [("mean_opac", C.c_void_p), ("scale", C.c_void_p), ("quat", C.c_void_p), ("sh", C.c_void_p),
+                ("n", C.c_int64), ("sh_degree", C.c_int32), ("n_blocks", C.c_int32), ("n_levels", C.c_int32),
+                ("_pad", C.c_int32), ("level_offset", C.c_void_p), ("level_count", C.c_void_p),
+                ("block_aabb", C.c_void_p), ("block_cell", C.c_void_p)]
+
+
+class cgs_config(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("batch", C.c_int32), ("near_z", C.c_float), ("bg", C.c_float * 3),
+                ("lod_dist", C.c_double * 2)]
+
+
+class cgs_frame(C.Structure):
+    _fields_ = [("ws", C.c_void_p), ("ws_bytes", C.c_int64), ("n_views", C.c_int32), ("width", C.c_int32),
+                ("height", C.c_int32), ("tile", C.c_int32), ("n_blocks", C.c_int32), ("_pad", C.c_int32),
+                ("n_cap", C.c_int64), ("k_cap", C.c_int64)]
+
+
+assert C.sizeof(cgs_camera) == 96
+
+_lib = None
+
+
+def lib():
+    """Loads libcgs.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libcgs.so not found at {LIB_PATH}; build it with "
+                               "`python -m paper_2404_01133_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, P = C.c_void_p, C.c_int32, C.c_int64, C.POINTER
+        L.cgs_version.restype = i32
+        L.cgs_status_string.restype = C.c_char_p
+        L.cgs_status_string.argtypes = [i32]
+        L.cgs_frame_workspace_bytes.restype = i64
+        L.cgs_frame_workspace_bytes.argtypes = [i32, i32, i32, i32, i32, i64, i64]
+        L.cgs_block_bounds_workspace_bytes.restype = i64
+        L.cgs_block_bounds_workspace_bytes.argtypes = [i64]
+        L.cgs_block_bounds.restype = i32
+        L.cgs_block_bounds.argtypes = [P(cgs_scene), C.c_double, vp, vp, i64, vp]
+        L.cgs_lod_select.restype = i32
+        L.cgs_lod_select.argtypes = [P(cgs_scene), P(cgs_config), vp, i32, vp, vp]
+        L.cgs_render_forward.restype = i32
+        L.cgs_render_forward.argtypes = [P(cgs_scene), P(cgs_frame), P(cgs_config), vp, vp, vp, vp, vp, vp, vp]
+        L.cgs_render_backward.restype = i32
+        L.cgs_render_backward.argtypes = [P(cgs_scene), P(cgs_frame), P(cgs_config), vp, vp, vp, vp, vp, vp, vp,
+                                          vp, vp]
+        L.cgs_l1_loss.restype = i32
+        L.cgs_l1_loss.argtypes = [vp, vp, i64, vp, vp, vp]
+        L.cgs_frame_status.restype = i32
+        L.cgs_frame_status.argtypes = [P(cgs_frame), P(i32), P(i64), vp]
+        L.cgs_timing_enable.restype = i32
+        L.cgs_timing_enable.argtypes = [i32]
+        L.cgs_timing_read.restype = i32
+        L.cgs_timing_read.argtypes = [P(C.c_double), P(i64)]
+        L.cgs_kernel_launches.restype = i64
+        L.cgs_frame_buffer.restype = i32
+        L.cgs_frame_buffer.argtypes = [P(cgs_frame), i32, P(vp), P(i64)]
+        _lib = L
+    return _lib
+
+
+class CgsError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"{where}: {lib().cgs_status_string(code).decode()} (code {code})")
+        self.code = code
+
+
+def _check(code, where):
+    if code != CGS_OK:
+        raise CgsError(code, where)
+    return code
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+# ---------------------------------------------------------------------------------------
+# the C entry points, one for one
+# ---------------------------------------------------------------------------------------
+def cgs_version():
+    return lib().cgs_version()
+
+
+def cgs_status_string(code):
+    return lib().cgs_status_string(code).decode()
+
+
+def cgs_frame_workspace_bytes(n_views, width, height, tile, n_blocks, n_cap, k_cap):
+    return lib().cgs_frame_workspace_bytes(n_views, width, height, tile, n_blocks, n_cap, k_cap)
+
+
+def cgs_block_bounds_workspace_bytes(n):
+    return lib().cgs_block_bounds_workspace_bytes(n)
+
+
+def cgs_block_bounds(scene, n_mad, d_aabb, d_ws=None, ws_bytes=0, stream=None):
+    return _check(lib().cgs_block_bounds(C.byref(scene), float(n_mad), _ptr(d_aabb), _ptr(d_ws), ws_bytes,
+                                         _stream(stream)), "cgs_block_bounds")
+
+
+def cgs_lod_select(scene, cfg, d_cams, n_views, d_levels, stream=None):
+    return _check(lib().cgs_lod_select(C.byref(scene), C.byref(cfg), _ptr(d_cams), n_views, _ptr(d_levels),
+                                       _stream(stream)), "cgs_lod_select")
+
+
+def cgs_render_forward(scene, frame, cfg, d_cams, d_view_block, d_levels, d_image, d_final_T, d_n_contrib,
+                       stream=None):
+    return _check(lib().cgs_render_forward(C.byref(scene), C.byref(frame), C.byref(cfg), _ptr(d_cams),
+                                           _ptr(d_view_block), _ptr(d_levels), _ptr(d_image), _ptr(d_final_T),
+                                           _ptr(d_n_contrib), _stream(stream)), "cgs_render_forward")
+
+
+def cgs_render_backward(scene, frame, cfg, d_cams, d_dL_dimage, d_final_T, d_n_contrib, d_g_mean_opac, d_g_scale,
+                        d_g_quat, d_g_sh, stream=None):
+    return _check(lib().cgs_render_backward(C.byref(scene), C.byref(frame), C.byref(cfg), _ptr(d_cams),
+                                            _ptr(d_dL_dimage), _ptr(d_final_T), _ptr(d_n_contrib),
+                                            _ptr(d_g_mean_opac), _ptr(d_g_scale), _ptr(d_g_quat), _ptr(d_g_sh),
+                                            _stream(stream)), "cgs_render_backward")
+
+
+def cgs_l1_loss(d_img, d_target, count, d_loss, d_grad, stream=None):
+    return _check(lib().cgs_l1_loss(_ptr(d_img), _ptr(d_target), count, _ptr(d_loss), _ptr(d_grad),
+                                    _stream(stream)), "cgs_l1_loss")
+
+
+def cgs_frame_status(frame, stream=None):
+    """Returns (status code, [selected, visible, entries, fwd pairs, bwd pairs, give-ups])."""
+    st = C.c_int32(0)
+    counts = (C.c_int64 * 6)()
+    lib().cgs_frame_status(C.byref(frame), C.byref(st), counts, _stream(stream))
+    return st.value, list(counts)
+
+
+STAGES = ("select", "project", "depth_sort", "emit", "tile_sort", "render", "render_bwd", "project_bwd", "loss")
+
+
+def cgs_timing_enable(on):
+    return _check(lib().cgs_timing_enable(1 if on else 0), "cgs_timing_enable")
+
+
+def cgs_timing_read():
+    """Returns {stage: (milliseconds summed, launches)} since the previous read."""
+    ms = (C.c_double * len(STAGES))()
+    cnt = (C.c_int64 * len(STAGES))()
+    _check(lib().cgs_timing_read(ms, cnt), "cgs_timing_read")
+    return {s: (ms[i], cnt[i]) for i, s in enumerate(STAGES)}
+
+
+def cgs_kernel_launches():
+    return lib().cgs_kernel_launches()
+
+
+def cgs_frame_buffer(frame, which):
+    p = C.c_void_p(0)
+    n = C.c_int64(0)
+    _check(lib().cgs_frame_buffer(C.byref(frame), which, C.byref(p), C.byref(n)), "cgs_frame_buffer")
+    return p.value, n.value

@@ -1,0 +1,135 @@
+// Shared definitions of libcgs: frame workspace layout, device status, small helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cgs.h"
+
+namespace cgs {
+
+// ---------------------------------------------------------------------------------------
+// device status and counters (first bytes of every frame workspace; zeroed per forward)
+// ---------------------------------------------------------------------------------------
+enum : uint32_t { ST_CAPACITY = 1u << 0, ST_SPIN = 1u << 1, ST_UNSUPPORTED = 1u << 2 };
+
+// Dynamic tile counters of the single-pass (decoupled look-back) kernels.
+enum { CTR_DEPTH_PASS0 = 0, CTR_TILE_PASS0 = 8, CTR_SCAN_COMPACT = 16, CTR_SCAN_EMIT = 17, N_CTR = 24 };
+
+struct Header {
+    uint32_t status;
+    uint32_t n_sel;        // selected Gaussians summed over views, capped at n_cap
+    uint32_t n_vis;        // visible (tiles touched > 0)
+    uint32_t k_used;       // tile entries kept, min(k_total, k_cap)
+    unsigned long long n_sel_raw;
+    unsigned long long k_total;
+    unsigned long long pairs_fwd;
+    unsigned long long pairs_bwd;
+    uint32_t spin_giveups;
+    uint32_t _pad;
+    uint32_t ctr[N_CTR];
+};
+
+// Polls of a look-back flag before a kernel gives up and latches ST_SPIN.
+constexpr int SPIN_LIMIT = 1 << 22;
+
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_IPT = 12;                       // keys per thread per tile
+constexpr int SORT_TILE = SORT_THREADS * SORT_IPT; // 3072 keys per look-back tile
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_IPT = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_IPT;
+constexpr int MAX_DEPTH_PASSES = 6;                // (view bits <= 16) + 32 depth bits
+constexpr int MAX_TILE_PASSES = 4;                 // view * tile id < 2^32
+
+// Pointers into one frame workspace.  Built on the host by make_layout (api.cu).
+struct Layout {
+    Header* hdr;
+    // zeroed at every forward (one memset over [zero_begin, zero_end))
+    uint32_t* hist_depth;        // [MAX_DEPTH_PASSES][256]
+    uint32_t* hist_tile;         // [MAX_TILE_PASSES][256]
+    unsigned long long* scan_lb; // [2][scan tiles]
+    uint32_t* ranges;            // [V * T][2]
+    // not zeroed
+    uint32_t* view_base;         // [V + 1] exclusive prefix of per-view selected counts
+    uint32_t* view_cnt;          // [V] selected count per view
+    uint32_t* n_seg;             // [V]
+    uint32_t* seg_base;          // [V][NB + 1]
+    long long* seg_off;          // [V][NB]
+    int8_t* levels;              // [V][NB]
+    float4* rec;                 // [n_cap][3]
+    uint2* rect;                 // [n_cap] (x0 | y0 << 16, x1 | y1 << 16), tile units, end exclusive
+    uint32_t* tt;                // [n_cap] tiles touched
+    uint32_t* gidx;              // [n_cap] scene index
+    unsigned long long* pkey;    // [n_cap] view << 32 | depth bits
+    unsigned long long* dkey[2]; // [n_cap] depth sort ping-pong
+    uint32_t* dval[2];           // [n_cap]
+    uint32_t* tkey[2];           // [k_cap] tile sort ping-pong
+    uint32_t* tval[2];           // [k_cap]
+    uint32_t* lb[2];             // [max(sort tiles)][256] look-back, ping-pong between passes
+    float4* gs;                  // [n_cap][3] screen-space gradients (du dv dA dB | dC do dr dg | db - - -)
+    size_t zero_bytes;           // bytes to clear from hdr
+    long long n_cap, k_cap;
+    int V, W, H, B, tiles_x, tiles_y, T, NB;
+    int depth_passes, tile_passes;
+    int depth_sorted;            // which ping-pong buffer holds the final depth order
+    int tile_sorted;             // which ping-pong buffer holds the final tile order
+    long long sort_tiles_max;
+};
+
+// ---------------------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) { return *(const volatile uint32_t*)p; }
+__device__ __forceinline__ void st_volatile(uint32_t* p, uint32_t v) { *(volatile uint32_t*)p = v; }
+__device__ __forceinline__ unsigned long long ld_volatile64(const unsigned long long* p)
+{
+    return *(const volatile unsigned long long*)p;
+}
+__device__ __forceinline__ void st_volatile64(unsigned long long* p, unsigned long long v)
+{
+    *(volatile unsigned long long*)p = v;
+}
+
+__device__ __forceinline__ void latch(Header* h, uint32_t bits) { atomicOr(&h->status, bits); }
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Block-wide exclusive scan over blockDim.x (<= 1024, multiple of 32) values; returns the
+// exclusive prefix and writes the total to *total.  `warp_buf` holds >= 33 entries.
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T x, T* warp_buf, T* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_buf[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < nw ? warp_buf[lane] : T(0);
+        T wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < nw) warp_buf[lane] = wi - w;
+        if (lane == nw - 1) warp_buf[32] = wi;
+    }
+    __syncthreads();
+    T res = warp_buf[warp] + inc - x;
+    *total = warp_buf[32];
+    __syncthreads();
+    return res;
+}
+
+}  // namespace cgs

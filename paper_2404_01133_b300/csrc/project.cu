@@ -1,0 +1,78 @@
+// Forward projection of every selected Gaussian (stage b of the hot path): Eq. 1's proj,
+// SH colour, screen radius and tile rectangle.  Compiled with -fmad=false so the key path
+// is evaluated exactly in the order proj_math.cuh writes it.
+#include "proj_math.cuh"
+
+namespace cgs {
+
+// One thread per selected Gaussian j (flattened over views), grid-stride over the device
+// count written by the selection kernels.  Writes tiles touched and the scene index of every
+// selected Gaussian and, for the visible ones, the projected record, tile rect, (view, depth)
+// sort key and cleared screen-gradient accumulators for the backward.
+__global__ void __launch_bounds__(256) k_project(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams,
+                                                 float near_z)
+{
+    const uint32_t n = L.hdr->n_sel;
+    const int deg = S.sh_degree;
+    const int nc = (deg + 1) * (deg + 1);
+    const float4* __restrict__ mo4 = reinterpret_cast<const float4*>(S.mean_opac);
+    const float4* __restrict__ sc4 = reinterpret_cast<const float4*>(S.scale);
+    const float4* __restrict__ q4 = reinterpret_cast<const float4*>(S.quat);
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        int v;
+        long long g;
+        locate(L, j, &v, &g);
+        L.gidx[j] = (uint32_t)g;
+        const cgs_camera c = cams[v];
+        const float4 mo = __ldg(mo4 + g);
+        const float m[3] = {mo.x, mo.y, mo.z};
+        // near-plane test first, so culled Gaussians never read scale, rotation or SH
+        const float tz = ((c.R[6] * m[0] + c.R[7] * m[1]) + c.R[8] * m[2]) + c.t[2];
+        uint32_t tt = 0;
+        if (tz > near_z) {
+            const float4 s4 = __ldg(sc4 + g), qq = __ldg(q4 + g);
+            const float s[3] = {s4.x, s4.y, s4.z};
+            const float q[4] = {qq.x, qq.y, qq.z, qq.w};
+            Proj p;
+            if (project_one(m, s, q, c, near_z, p) == 0) {
+                const float r = ceilf(3.0f * sqrtf(p.lam1));
+                const float W1 = (float)(L.W - 1), H1 = (float)(L.H - 1);
+                float x0 = ceilf(p.u - r), x1 = floorf(p.u + r);
+                float y0 = ceilf(p.v - r), y1 = floorf(p.v + r);
+                if (x0 < 0.0f) x0 = 0.0f;
+                if (y0 < 0.0f) y0 = 0.0f;
+                if (x1 > W1) x1 = W1;
+                if (y1 > H1) y1 = H1;
+                if (x0 <= x1 && y0 <= y1) {
+                    const uint32_t tx0 = (uint32_t)x0 / L.B, tx1 = (uint32_t)x1 / L.B + 1;
+                    const uint32_t ty0 = (uint32_t)y0 / L.B, ty1 = (uint32_t)y1 / L.B + 1;
+                    tt = (tx1 - tx0) * (ty1 - ty0);
+                    L.rect[j] = make_uint2(tx0 | (ty0 << 16), tx1 | (ty1 << 16));
+                    float f[48], rgb[3], dir[3], len, Y[16];
+                    load_sh(S.sh, g, nc, f);
+                    sh_colour(m, c, f, deg, rgb, dir, &len, Y);
+                    L.rec[3 * (size_t)j] = make_float4(p.u, p.v, mo.w, p.tz);
+                    L.rec[3 * (size_t)j + 1] = make_float4(p.conic[0], p.conic[1], p.conic[2], r);
+                    L.rec[3 * (size_t)j + 2] = make_float4(rgb[0], rgb[1], rgb[2], __int_as_float(v));
+                    L.pkey[j] = ((unsigned long long)(uint32_t)v << 32) | __float_as_uint(p.tz);
+                    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    L.gs[3 * (size_t)j] = z4;
+                    L.gs[3 * (size_t)j + 1] = z4;
+                    L.gs[3 * (size_t)j + 2] = z4;
+                }
+            }
+        }
+        L.tt[j] = tt;
+    }
+}
+
+void launch_project(const Layout& L, const cgs_scene& S, const cgs_camera* cams, float near_z, int n_sm,
+                    cudaStream_t st)
+{
+    long long want = (L.n_cap + 255) / 256;
+    long long grid = want < (long long)n_sm * 8 ? want : (long long)n_sm * 8;
+    if (grid < 1) grid = 1;
+    k_project<<<(unsigned)grid, 256, 0, st>>>(L, S, cams, near_z);
+}
+
+}  // namespace cgs

@@ -1,0 +1,143 @@
+// Backward of the projection and colour (differentiable rendering, Sec. 3.1): chains the
+// per-Gaussian screen-space gradients (u, v, conic, opacity, rgb) accumulated by the
+// compositing backward to the scene attributes.  Discrete decisions pass no gradient: the
+// guard-band clamp zeroes the clamped coordinate's direct term, the colour clamp masks its
+// channel, and the quaternion gradient goes through the normalisation.
+#include "proj_math.cuh"
+
+namespace cgs {
+
+__global__ void __launch_bounds__(128) k_project_bwd(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams,
+                                                     float near_z, float* __restrict__ g_mo, float* __restrict__ g_sc,
+                                                     float* __restrict__ g_q, float* __restrict__ g_sh)
+{
+    const uint32_t n = L.hdr->n_sel;
+    const int deg = S.sh_degree;
+    const int nc = (deg + 1) * (deg + 1);
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        if (L.tt[j] == 0) continue;
+        const float4 ga = L.gs[3 * (size_t)j], gb = L.gs[3 * (size_t)j + 1], gc4 = L.gs[3 * (size_t)j + 2];
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        L.gs[3 * (size_t)j] = z4;
+        L.gs[3 * (size_t)j + 1] = z4;
+        L.gs[3 * (size_t)j + 2] = z4;
+        const float gu = ga.x, gv = ga.y, gA_ = ga.z, gB_ = ga.w, gC_ = gb.x, gop = gb.y;
+        const float grgb[3] = {gb.z, gb.w, gc4.x};
+        const int v = __float_as_int(L.rec[3 * (size_t)j + 2].w);
+        const long long g = L.gidx[j];
+        const cgs_camera c = cams[v];
+        const float4 mo = __ldg(reinterpret_cast<const float4*>(S.mean_opac) + g);
+        const float4 s4 = __ldg(reinterpret_cast<const float4*>(S.scale) + g);
+        const float4 q4 = __ldg(reinterpret_cast<const float4*>(S.quat) + g);
+        const float m[3] = {mo.x, mo.y, mo.z}, s[3] = {s4.x, s4.y, s4.z}, q[4] = {q4.x, q4.y, q4.z, q4.w};
+        Proj p;
+        if (project_one(m, s, q, c, near_z, p) != 0) continue;
+
+        // colour -> SH coefficients and the view direction
+        float f[48], rgb[3], dir[3], len, Y[16], dY[16][3];
+        load_sh(S.sh, g, nc, f);
+        const int cl = sh_colour(m, c, f, deg, rgb, dir, &len, Y);
+        sh_grad(dir[0], dir[1], dir[2], deg, dY);
+        float gdir[3] = {0.f, 0.f, 0.f};
+        float* gsh = g_sh + g * (long long)(nc * 3);
+        for (int ch = 0; ch < 3; ch++) {
+            if (cl & (1 << ch)) continue;
+            const float gcol = grgb[ch];
+            for (int k = 0; k < nc; k++) {
+                atomicAdd(gsh + k * 3 + ch, Y[k] * gcol);
+                const float fk = f[k * 3 + ch] * gcol;
+                gdir[0] += fk * dY[k][0];
+                gdir[1] += fk * dY[k][1];
+                gdir[2] += fk * dY[k][2];
+            }
+        }
+        const float dd = dir[0] * gdir[0] + dir[1] * gdir[1] + dir[2] * gdir[2];
+        float gm[3];
+        for (int a = 0; a < 3; a++) gm[a] = (gdir[a] - dir[a] * dd) / len;
+
+        // conic (C/D, -B/D, A/D) -> Sigma2D entries (A, B, C)
+        const float A = p.A, Bv = p.B, C = p.C, D = p.det, D2 = p.det * p.det, iD = 1.0f / p.det;
+        const float dA = gA_ * (-C * C / D2) + gB_ * (Bv * C / D2) + gC_ * (iD - A * C / D2);
+        const float dB = gA_ * (2.0f * Bv * C / D2) + gB_ * (-iD - 2.0f * Bv * Bv / D2) + gC_ * (2.0f * A * Bv / D2);
+        const float dC = gA_ * (iD - A * C / D2) + gB_ * (Bv * A / D2) + gC_ * (-A * A / D2);
+        (void)D;
+
+        // Sigma2D = T S T^T
+        const float* Tm = p.Tm;
+        const float* S3 = p.S3;
+        float gS[9];
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++)
+                gS[a * 3 + b] = dA * Tm[a] * Tm[b] + dB * Tm[a] * Tm[3 + b] + dC * Tm[3 + a] * Tm[3 + b];
+        float gT[6];
+        for (int a = 0; a < 3; a++) {
+            const float st0 = S3[a * 3] * Tm[0] + S3[a * 3 + 1] * Tm[1] + S3[a * 3 + 2] * Tm[2];
+            const float st1 = S3[a * 3] * Tm[3] + S3[a * 3 + 1] * Tm[4] + S3[a * 3 + 2] * Tm[5];
+            gT[a] = 2.0f * dA * st0 + dB * st1;
+            gT[3 + a] = 2.0f * dC * st1 + dB * st0;
+        }
+        const float* W = c.R;
+        float gJ00 = 0.f, gJ02 = 0.f, gJ11 = 0.f, gJ12 = 0.f;
+        for (int a = 0; a < 3; a++) {
+            gJ00 += gT[a] * W[a];
+            gJ02 += gT[a] * W[6 + a];
+            gJ11 += gT[3 + a] * W[3 + a];
+            gJ12 += gT[3 + a] * W[6 + a];
+        }
+        const float fx = c.fx, fy = c.fy, tx = p.tx, ty = p.ty, tz = p.tz;
+        const float tz2 = tz * tz, tz3 = tz2 * tz;
+        float gtx = 0.f, gty = 0.f, gtz = 0.f;
+        gtz += gJ00 * (-fx / tz2) + gJ11 * (-fy / tz2);
+        if (!p.clampx) { gtx += gJ02 * (-fx / tz2); gtz += gJ02 * (2.0f * fx * tx / tz3); }
+        else { const float lim = tx / tz > 0.f ? p.limx : -p.limx; gtz += gJ02 * (fx * lim / tz2); }
+        if (!p.clampy) { gty += gJ12 * (-fy / tz2); gtz += gJ12 * (2.0f * fy * ty / tz3); }
+        else { const float lim = ty / tz > 0.f ? p.limy : -p.limy; gtz += gJ12 * (fy * lim / tz2); }
+        gtx += gu * fx / tz;
+        gtz += gu * (-fx * tx / tz2);
+        gty += gv * fy / tz;
+        gtz += gv * (-fy * ty / tz2);
+        for (int a = 0; a < 3; a++) gm[a] += W[a] * gtx + W[3 + a] * gty + W[6 + a] * gtz;
+        float* gmo = g_mo + 4 * g;
+        atomicAdd(gmo + 0, gm[0]);
+        atomicAdd(gmo + 1, gm[1]);
+        atomicAdd(gmo + 2, gm[2]);
+        atomicAdd(gmo + 3, gop);
+
+        // Sigma3D = M M^T, M = Rq diag(s)
+        float gM[9];
+        for (int a = 0; a < 3; a++)
+            for (int k = 0; k < 3; k++) {
+                float acc = 0.f;
+                for (int b = 0; b < 3; b++) acc += (gS[a * 3 + b] + gS[b * 3 + a]) * p.M[b * 3 + k];
+                gM[a * 3 + k] = acc;
+            }
+        float gR[9];
+        float* gsc = g_sc + 4 * g;
+        for (int k = 0; k < 3; k++) {
+            float acc = 0.f;
+            for (int a = 0; a < 3; a++) acc += gM[a * 3 + k] * p.Rq[a * 3 + k];
+            atomicAdd(gsc + k, acc);
+            for (int a = 0; a < 3; a++) gR[a * 3 + k] = gM[a * 3 + k] * s[k];
+        }
+        const float w = p.qn[0], x = p.qn[1], y = p.qn[2], z = p.qn[3];
+        float gq[4];
+        gq[0] = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+        gq[1] = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] + z * gR[6] + w * gR[7] - 2.f * x * gR[8]);
+        gq[2] = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7] - 2.f * y * gR[8]);
+        gq[3] = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] + y * gR[5] + x * gR[6] + y * gR[7]);
+        const float qd = w * gq[0] + x * gq[1] + y * gq[2] + z * gq[3];
+        float* gqq = g_q + 4 * g;
+        for (int a = 0; a < 4; a++) atomicAdd(gqq + a, (gq[a] - p.qn[a] * qd) / p.qlen);
+    }
+}
+
+void launch_project_bwd(const Layout& L, const cgs_scene& S, const cgs_camera* cams, float near_z, float* g_mo,
+                        float* g_sc, float* g_q, float* g_sh, int n_sm, cudaStream_t st)
+{
+    long long want = (L.n_cap + 127) / 128;
+    long long grid = want < (long long)n_sm * 16 ? want : (long long)n_sm * 16;
+    if (grid < 1) grid = 1;
+    k_project_bwd<<<(unsigned)grid, 128, 0, st>>>(L, S, cams, near_z, g_mo, g_sc, g_q, g_sh);
+}
+
+}  // namespace cgs

@@ -1,0 +1,286 @@
+// Stage d of the hot path: per-tile front-to-back alpha compositing (Eq. 1, Sec. 3.1) and
+// its backward replay (differentiable rendering, Sec. 3.1), plus the L1 loss (Sec. 3.2.3).
+//
+// One CTA per (view, tile), one thread per pixel.  Each round stages `BATCH` projected
+// records of the tile's depth-sorted list in shared memory; a pixel blends with
+// alpha = min(0.99, o exp(power)), skips alpha < 1/255 and stops before the entry that
+// would take its transmittance below 1e-4.  The CTA leaves as soon as every pixel stopped
+// (__syncthreads_count).
+#include "common.cuh"
+
+namespace cgs {
+
+// power = -0.5 (A' dx^2 + C' dy^2) - B' dx dy and G = exp(power), with every rounding step
+// fixed by intrinsics so the forward and the backward kernels take identical decisions.
+__device__ __forceinline__ float pair_power(const float4& a, const float4& b, float fpx, float fpy, float* dx_out,
+                                            float* dy_out)
+{
+    const float dx = __fsub_rn(a.x, fpx), dy = __fsub_rn(a.y, fpy);
+    float q = __fmul_rn(__fmul_rn(b.x, dx), dx);
+    q = __fmaf_rn(__fmul_rn(b.z, dy), dy, q);
+    const float cr = __fmul_rn(__fmul_rn(b.y, dx), dy);
+    *dx_out = dx;
+    *dy_out = dy;
+    return __fmaf_rn(-0.5f, q, -cr);
+}
+
+template <int B, int BATCH>
+__global__ void __launch_bounds__(B * B) k_render_fwd(Layout L, const uint32_t* __restrict__ tval, float bg0, float bg1,
+                                                      float bg2, float* __restrict__ image, float* __restrict__ final_T,
+                                                      uint32_t* __restrict__ n_contrib)
+{
+    constexpr int NT = B * B;
+    __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
+    const int v = blockIdx.z;
+    const int tile = blockIdx.y * L.tiles_x + blockIdx.x;
+    const uint2 rg = reinterpret_cast<const uint2*>(L.ranges)[(size_t)v * L.T + tile];
+    const int px = blockIdx.x * B + (threadIdx.x % B), py = blockIdx.y * B + (threadIdx.x / B);
+    const bool inside = px < L.W && py < L.H;
+    const float fpx = (float)px, fpy = (float)py;
+    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
+    uint32_t last = 0, visited = 0;
+    bool done = !inside;
+    for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
+        if (__syncthreads_count(done) == NT) break;
+        const uint32_t idx = start + threadIdx.x;
+        if (threadIdx.x < BATCH && idx < rg.y) {
+            const size_t j = tval[idx];
+            s_a[threadIdx.x] = L.rec[3 * j];
+            s_b[threadIdx.x] = L.rec[3 * j + 1];
+            s_c[threadIdx.x] = L.rec[3 * j + 2];
+        }
+        __syncthreads();
+        const int nb = (int)min((uint32_t)BATCH, rg.y - start);
+        for (int k = 0; !done && k < nb; k++) {
+            visited++;
+            const float4 a = s_a[k], b = s_b[k];
+            float dx, dy;
+            const float power = pair_power(a, b, fpx, fpy, &dx, &dy);
+            if (power > 0.0f) continue;
+            const float alpha = fminf(0.99f, __fmul_rn(a.z, __expf(power)));
+            if (alpha < 1.0f / 255.0f) continue;
+            const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+            if (Tn < 1e-4f) { done = true; break; }
+            const float4 c = s_c[k];
+            const float w = alpha * T;
+            C0 += c.x * w;
+            C1 += c.y * w;
+            C2 += c.z * w;
+            T = Tn;
+            last = start - rg.x + (uint32_t)k + 1u;
+        }
+    }
+    if (inside) {
+        const size_t HW = (size_t)L.W * L.H, pix = (size_t)py * L.W + px;
+        image[(3 * (size_t)v + 0) * HW + pix] = C0 + T * bg0;
+        image[(3 * (size_t)v + 1) * HW + pix] = C1 + T * bg1;
+        image[(3 * (size_t)v + 2) * HW + pix] = C2 + T * bg2;
+        final_T[(size_t)v * HW + pix] = T;
+        n_contrib[(size_t)v * HW + pix] = last;
+    }
+    const uint32_t ws = __reduce_add_sync(0xffffffffu, visited);
+    if ((threadIdx.x & 31) == 0 && ws) atomicAdd(&L.hdr->pairs_fwd, (unsigned long long)ws);
+}
+
+// Backward: each pixel replays its blended entries from the last one (n_contrib) to the
+// first, recovering T before entry i as T_{i+1} / (1 - alpha_i) from the final
+// transmittance.  With S_i = sum_{m > i} alpha_m T_m c_m + T_end bg:
+//   dP/dc_i = alpha_i T_i,  dP/dalpha_i = T_i c_i - S_i / (1 - alpha_i),
+//   alpha = min(0.99, o G), G = exp(power): dalpha/do = G, dalpha/dpower = o G (not clamped).
+// Per entry, the nine screen-space gradients are summed over the warp, then over the CTA in
+// shared memory, then added once per (tile, Gaussian) to the global accumulator.
+template <int B, int BATCH>
+__global__ void __launch_bounds__(B * B) k_render_bwd(Layout L, const uint32_t* __restrict__ tval, float bg0, float bg1,
+                                                      float bg2, const float* __restrict__ dL_dimg,
+                                                      const float* __restrict__ final_T,
+                                                      const uint32_t* __restrict__ n_contrib)
+{
+    constexpr int NT = B * B;
+    __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
+    __shared__ uint32_t s_j[BATCH];
+    __shared__ float s_g[9][BATCH];
+    __shared__ uint32_t s_maxnc;
+    const int v = blockIdx.z;
+    const int tile = blockIdx.y * L.tiles_x + blockIdx.x;
+    const uint2 rg = reinterpret_cast<const uint2*>(L.ranges)[(size_t)v * L.T + tile];
+    const int px = blockIdx.x * B + (threadIdx.x % B), py = blockIdx.y * B + (threadIdx.x / B);
+    const bool inside = px < L.W && py < L.H;
+    const float fpx = (float)px, fpy = (float)py;
+    const size_t HW = (size_t)L.W * L.H, pix = (size_t)py * L.W + px;
+    float T = 1.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
+    uint32_t nc = 0;
+    if (inside) {
+        T = final_T[(size_t)v * HW + pix];
+        nc = n_contrib[(size_t)v * HW + pix];
+        g0 = dL_dimg[(3 * (size_t)v + 0) * HW + pix];
+        g1 = dL_dimg[(3 * (size_t)v + 1) * HW + pix];
+        g2 = dL_dimg[(3 * (size_t)v + 2) * HW + pix];
+    }
+    float S0 = T * bg0, S1 = T * bg1, S2 = T * bg2;
+    if (threadIdx.x == 0) s_maxnc = 0;
+    __syncthreads();
+    if (nc) atomicMax(&s_maxnc, nc);
+    __syncthreads();
+    const long long first = rg.x;
+    // n_contrib never exceeds the tile's list length; clamp so a mismatched buffer cannot
+    // move the replay outside this tile's entries
+    const long long end = (first + s_maxnc) < (long long)rg.y ? (first + s_maxnc) : (long long)rg.y;
+    uint32_t pairs = 0;
+    for (long long be = end; be > first; be -= BATCH) {
+        const long long bs = (be - BATCH) > first ? (be - BATCH) : first;
+        const int nb = (int)(be - bs);
+        __syncthreads();
+        if (threadIdx.x < nb) {
+            const uint32_t j = tval[bs + threadIdx.x];
+            s_j[threadIdx.x] = j;
+            s_a[threadIdx.x] = L.rec[3 * (size_t)j];
+            s_b[threadIdx.x] = L.rec[3 * (size_t)j + 1];
+            s_c[threadIdx.x] = L.rec[3 * (size_t)j + 2];
+        }
+        for (int i = threadIdx.x; i < 9 * BATCH; i += NT) (&s_g[0][0])[i] = 0.0f;
+        __syncthreads();
+        for (int k = nb - 1; k >= 0; k--) {
+            const uint32_t lp = (uint32_t)(bs + k - first);
+            bool contrib = lp < nc;
+            const float4 a = s_a[k], b = s_b[k];
+            float dx, dy;
+            float G = 0.0f, alpha = 0.0f;
+            if (contrib) {
+                const float power = pair_power(a, b, fpx, fpy, &dx, &dy);
+                if (power > 0.0f) contrib = false;
+                else {
+                    G = __expf(power);
+                    alpha = fminf(0.99f, __fmul_rn(a.z, G));
+                    if (alpha < 1.0f / 255.0f) contrib = false;
+                }
+            }
+            float gr[9];
+#pragma unroll
+            for (int c = 0; c < 9; c++) gr[c] = 0.0f;
+            if (contrib) {
+                pairs++;
+                const float oma = 1.0f - alpha;
+                T = T / oma;
+                const float4 c = s_c[k];
+                const float dal = g0 * (T * c.x - S0 / oma) + g1 * (T * c.y - S1 / oma) + g2 * (T * c.z - S2 / oma);
+                const float aT = alpha * T;
+                S0 += aT * c.x;
+                S1 += aT * c.y;
+                S2 += aT * c.z;
+                gr[6] = g0 * aT;
+                gr[7] = g1 * aT;
+                gr[8] = g2 * aT;
+                if (!(__fmul_rn(a.z, G) > 0.99f)) {
+                    gr[5] = dal * G;
+                    const float dp = dal * a.z * G;
+                    gr[2] = dp * (-0.5f * dx * dx);
+                    gr[3] = dp * (-(dx * dy));
+                    gr[4] = dp * (-0.5f * dy * dy);
+                    gr[0] = dp * (-(b.x * dx + b.y * dy));
+                    gr[1] = dp * (-(b.z * dy + b.y * dx));
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+#pragma unroll
+                for (int c = 0; c < 9; c++) {
+#pragma unroll
+                    for (int o = 16; o; o >>= 1) gr[c] += __shfl_xor_sync(0xffffffffu, gr[c], o);
+                }
+                if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+                    for (int c = 0; c < 9; c++) atomicAdd(&s_g[c][k], gr[c]);
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < nb) {
+            float* dst = reinterpret_cast<float*>(L.gs) + 12 * (size_t)s_j[threadIdx.x];
+#pragma unroll
+            for (int c = 0; c < 9; c++) {
+                const float x = s_g[c][threadIdx.x];
+                if (x != 0.0f) atomicAdd(dst + c, x);
+            }
+        }
+    }
+    const uint32_t ws = __reduce_add_sync(0xffffffffu, pairs);
+    if ((threadIdx.x & 31) == 0 && ws) atomicAdd(&L.hdr->pairs_bwd, (unsigned long long)ws);
+}
+
+template <int B, int BATCH>
+static void fwd_launch(const Layout& L, const uint32_t* tval, const cgs_config& c, float* img, float* T, uint32_t* nc,
+                       cudaStream_t st)
+{
+    dim3 grid(L.tiles_x, L.tiles_y, L.V);
+    k_render_fwd<B, BATCH><<<grid, B * B, 0, st>>>(L, tval, c.bg[0], c.bg[1], c.bg[2], img, T, nc);
+}
+template <int B, int BATCH>
+static void bwd_launch(const Layout& L, const uint32_t* tval, const cgs_config& c, const float* dimg, const float* T,
+                       const uint32_t* nc, cudaStream_t st)
+{
+    dim3 grid(L.tiles_x, L.tiles_y, L.V);
+    k_render_bwd<B, BATCH><<<grid, B * B, 0, st>>>(L, tval, c.bg[0], c.bg[1], c.bg[2], dimg, T, nc);
+}
+
+bool launch_render_fwd(const Layout& L, const cgs_config& c, float* img, float* T, uint32_t* nc, cudaStream_t st)
+{
+    const uint32_t* tv = L.tval[L.tile_sorted];
+    if (L.B == 16) {
+        switch (c.batch) {
+            case 32: fwd_launch<16, 32>(L, tv, c, img, T, nc, st); return true;
+            case 64: fwd_launch<16, 64>(L, tv, c, img, T, nc, st); return true;
+            case 128: fwd_launch<16, 128>(L, tv, c, img, T, nc, st); return true;
+            case 256: fwd_launch<16, 256>(L, tv, c, img, T, nc, st); return true;
+        }
+    } else if (L.B == 8) {
+        switch (c.batch) {
+            case 32: fwd_launch<8, 32>(L, tv, c, img, T, nc, st); return true;
+            case 64: fwd_launch<8, 64>(L, tv, c, img, T, nc, st); return true;
+        }
+    }
+    return false;
+}
+
+bool launch_render_bwd(const Layout& L, const cgs_config& c, const float* dimg, const float* T, const uint32_t* nc,
+                       cudaStream_t st)
+{
+    const uint32_t* tv = L.tval[L.tile_sorted];
+    if (L.B == 16) {
+        switch (c.batch) {
+            case 32: bwd_launch<16, 32>(L, tv, c, dimg, T, nc, st); return true;
+            case 64: bwd_launch<16, 64>(L, tv, c, dimg, T, nc, st); return true;
+            case 128: bwd_launch<16, 128>(L, tv, c, dimg, T, nc, st); return true;
+            case 256: bwd_launch<16, 256>(L, tv, c, dimg, T, nc, st); return true;
+        }
+    } else if (L.B == 8) {
+        switch (c.batch) {
+            case 32: bwd_launch<8, 32>(L, tv, c, dimg, T, nc, st); return true;
+            case 64: bwd_launch<8, 64>(L, tv, c, dimg, T, nc, st); return true;
+        }
+    }
+    return false;
+}
+
+// L1 loss: loss += mean |img - target|, grad = sign(img - target) / count.
+__global__ void k_l1(const float* __restrict__ img, const float* __restrict__ tgt, long long n, float* loss,
+                     float* __restrict__ grad)
+{
+    const float inv = 1.0f / (float)n;
+    float acc = 0.0f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float d = img[i] - tgt[i];
+        acc += fabsf(d);
+        grad[i] = d > 0.0f ? inv : (d < 0.0f ? -inv : 0.0f);
+    }
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc != 0.0f) atomicAdd(loss, acc * inv);
+}
+
+void launch_l1(const float* img, const float* tgt, long long n, float* loss, float* grad, int n_sm, cudaStream_t st)
+{
+    long long g = (n + 255) / 256;
+    if (g > (long long)n_sm * 8) g = (long long)n_sm * 8;
+    if (g < 1) g = 1;
+    k_l1<<<(unsigned)g, 256, 0, st>>>(img, tgt, n, loss, grad);
+}
+
+}  // namespace cgs

@@ -1,0 +1,262 @@
+// Block-wise level-of-detail selection (stage a of the hot path, Sec. 3.3.2) and the MAD
+// block bounds of Eq. 7.  FP64 throughout; compiled with -fmad=false so every expression is
+// evaluated in the order written.
+#include "common.cuh"
+
+namespace cgs {
+
+// Level of block b seen from camera c: -1 culled or empty, else 0..n_levels-1.
+// The box corners in front of the camera are projected; the block is visible if their
+// screen bounding box overlaps the image; the block whose ground cell holds the camera
+// centre is always kept; the level follows the minimum corner-to-camera distance.
+__device__ int lod_level(const cgs_scene& S, int b, const cgs_camera& c, double near_z, double d1, double d2)
+{
+    if (S.level_count[(long long)b * S.n_levels] <= 0) return -1;
+    const float* bb = S.block_aabb + 6 * (long long)b;
+    double R[9], t[3], cp[3];
+    for (int i = 0; i < 9; i++) R[i] = (double)c.R[i];
+    for (int i = 0; i < 3; i++) { t[i] = (double)c.t[i]; cp[i] = (double)c.campos[i]; }
+    const double fx = c.fx, fy = c.fy, cx = c.cx, cy = c.cy, Wd = c.width, Hd = c.height;
+    bool any_front = false;
+    double xmin = 0, xmax = 0, ymin = 0, ymax = 0, dmin = 0;
+    for (int k = 0; k < 8; k++) {
+        const double p0 = (double)bb[(k & 1) ? 3 : 0], p1 = (double)bb[(k & 2) ? 4 : 1], p2 = (double)bb[(k & 4) ? 5 : 2];
+        const double e0 = p0 - cp[0], e1 = p1 - cp[1], e2 = p2 - cp[2];
+        const double dist = sqrt((e0 * e0 + e1 * e1) + e2 * e2);
+        if (k == 0 || dist < dmin) dmin = dist;
+        const double tx = ((R[0] * p0 + R[1] * p1) + R[2] * p2) + t[0];
+        const double ty = ((R[3] * p0 + R[4] * p1) + R[5] * p2) + t[1];
+        const double tz = ((R[6] * p0 + R[7] * p1) + R[8] * p2) + t[2];
+        if (!(tz > near_z)) continue;
+        const double u = (fx * tx) / tz + cx, v = (fy * ty) / tz + cy;
+        if (!any_front) { xmin = xmax = u; ymin = ymax = v; any_front = true; }
+        else {
+            if (u < xmin) xmin = u;
+            if (u > xmax) xmax = u;
+            if (v < ymin) ymin = v;
+            if (v > ymax) ymax = v;
+        }
+    }
+    const bool visible = any_front && xmax > -0.5 && xmin < Wd - 0.5 && ymax > -0.5 && ymin < Hd - 0.5;
+    const float* ce = S.block_cell + 4 * (long long)b;
+    const bool inside = cp[0] >= (double)ce[0] && cp[0] < (double)ce[1] && cp[1] >= (double)ce[2] &&
+                        cp[1] < (double)ce[3];
+    if (!visible && !inside) return -1;
+    int lv = dmin < d1 ? 0 : (dmin < d2 ? 1 : 2);
+    if (lv > S.n_levels - 1) lv = S.n_levels - 1;
+    return lv;
+}
+
+__global__ void k_lod_levels(cgs_scene S, const cgs_camera* __restrict__ cams, int n_views, cgs_config cfg,
+                             int8_t* levels)
+{
+    const int v = blockIdx.x;
+    if (v >= n_views) return;
+    const cgs_camera c = cams[v];
+    for (int b = threadIdx.x; b < S.n_blocks; b += blockDim.x)
+        levels[(long long)v * S.n_blocks + b] =
+            (int8_t)lod_level(S, b, c, (double)cfg.near_z, cfg.lod_dist[0], cfg.lod_dist[1]);
+}
+
+// Per view: the level of every block (given, one training block, or LoD), then the ordered
+// list of selected segments (fusion by concatenation, Sec. 3.3.2) and its prefix counts.
+__global__ void k_select(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams, const int32_t* view_block,
+                         const int8_t* levels_in, cgs_config cfg)
+{
+    const int v = blockIdx.x;
+    const int NB = S.n_blocks, NL = S.n_levels;
+    int8_t* lev = L.levels + (long long)v * NB;
+    const cgs_camera c = cams[v];
+    for (int b = threadIdx.x; b < NB; b += blockDim.x) {
+        int l;
+        if (levels_in) {
+            l = levels_in[(long long)v * NB + b];
+            if (l >= NL) l = NL - 1;
+            if (l < 0) l = -1;
+        } else if (view_block) {
+            l = (b == view_block[v]) ? 0 : -1;
+        } else {
+            l = lod_level(S, b, c, (double)cfg.near_z, cfg.lod_dist[0], cfg.lod_dist[1]);
+        }
+        if (l >= 0 && S.level_count[(long long)b * NL + l] <= 0) l = -1;
+        lev[b] = (int8_t)l;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t* sb = L.seg_base + (long long)v * (NB + 1);
+        long long* so = L.seg_off + (long long)v * NB;
+        unsigned long long acc = 0;
+        int s = 0;
+        for (int b = 0; b < NB; b++) {
+            if (lev[b] < 0) continue;
+            so[s] = S.level_offset[(long long)b * NL + lev[b]];
+            sb[s] = (uint32_t)acc;
+            acc += (unsigned long long)S.level_count[(long long)b * NL + lev[b]];
+            s++;
+        }
+        sb[s] = (uint32_t)(acc < 0xffffffffull ? acc : 0xffffffffull);
+        L.n_seg[v] = (uint32_t)s;
+        L.view_cnt[v] = (uint32_t)(acc < 0xffffffffull ? acc : 0xffffffffull);
+    }
+}
+
+// Exclusive prefix of the per-view counts; total capped at the frame capacity.
+__global__ void k_select_finish(Layout L)
+{
+    __shared__ unsigned long long wb[33];
+    const int V = L.V;
+    const int per = (V + blockDim.x - 1) / blockDim.x;
+    const int v0 = threadIdx.x * per;
+    unsigned long long local = 0;
+    for (int v = v0; v < v0 + per && v < V; v++) local += L.view_cnt[v];
+    unsigned long long total;
+    unsigned long long run = block_exclusive_scan<unsigned long long>(local, wb, &total);
+    for (int v = v0; v < v0 + per && v < V; v++) {
+        L.view_base[v] = (uint32_t)(run < 0xffffffffull ? run : 0xffffffffull);
+        run += L.view_cnt[v];
+    }
+    if (threadIdx.x == 0) {
+        L.view_base[V] = (uint32_t)(total < 0xffffffffull ? total : 0xffffffffull);
+        L.hdr->n_sel_raw = total;
+        unsigned long long cap = (unsigned long long)L.n_cap;
+        L.hdr->n_sel = (uint32_t)(total < cap ? total : cap);
+        if (total > cap) latch(L.hdr, ST_CAPACITY);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Eq. 7 MAD bounds by exact radix selection.  One CTA per (block, axis).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t f2o(float f)
+{
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float o2f(uint32_t o)
+{
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+// Selects the keys of ranks r0 and r1 (0-based, ascending) among m keys produced by key(k).
+// KEY is uint32_t or unsigned long long; runs in all threads of the CTA.
+template <typename KEY, typename F>
+__device__ void radix_select2(long long m, F key, unsigned long long r0, unsigned long long r1, KEY* out0, KEY* out1)
+{
+    constexpr int KBITS = sizeof(KEY) * 8;
+    __shared__ uint32_t h0[256], h1[256];
+    __shared__ KEY s_pre[2], s_mask;
+    __shared__ unsigned long long s_rank[2];
+    if (threadIdx.x == 0) { s_pre[0] = s_pre[1] = 0; s_mask = 0; s_rank[0] = r0; s_rank[1] = r1; }
+    __syncthreads();
+    for (int shift = KBITS - 8; shift >= 0; shift -= 8) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) { h0[i] = 0; h1[i] = 0; }
+        __syncthreads();
+        const KEY mask = s_mask, p0 = s_pre[0], p1 = s_pre[1];
+        for (long long k = threadIdx.x; k < m; k += blockDim.x) {
+            const KEY x = key(k);
+            const uint32_t d = (uint32_t)(x >> shift) & 255u;
+            if ((x & mask) == p0) atomicAdd(&h0[d], 1u);
+            if ((x & mask) == p1) atomicAdd(&h1[d], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            uint32_t* h = threadIdx.x == 0 ? h0 : h1;
+            unsigned long long r = s_rank[threadIdx.x], cum = 0;
+            int d = 0;
+            for (; d < 255; d++) {
+                if (cum + h[d] > r) break;
+                cum += h[d];
+            }
+            s_rank[threadIdx.x] = r - cum;
+            s_pre[threadIdx.x] |= (KEY)d << shift;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_mask |= (KEY)255 << shift;
+        __syncthreads();
+    }
+    *out0 = s_pre[0];
+    *out1 = s_pre[1];
+    __syncthreads();
+}
+
+__device__ __forceinline__ float round_down_f(double x)
+{
+    float f = __double2float_rn(x);
+    if ((double)f > x) f = nextafterf(f, -INFINITY);
+    return f;
+}
+__device__ __forceinline__ float round_up_f(double x)
+{
+    float f = __double2float_rn(x);
+    if ((double)f < x) f = nextafterf(f, INFINITY);
+    return f;
+}
+
+__global__ void __launch_bounds__(256) k_block_bounds(cgs_scene S, double n_mad, float* aabb)
+{
+    const int b = blockIdx.x / 3, a = blockIdx.x % 3;
+    const long long off = S.level_offset[(long long)b * S.n_levels];
+    const long long m = S.level_count[(long long)b * S.n_levels];
+    if (m <= 0) {
+        if (threadIdx.x == 0) { aabb[6 * b + a] = 0.0f; aabb[6 * b + 3 + a] = 0.0f; }
+        return;
+    }
+    const float* base = S.mean_opac + 4 * off + a;
+    // min and max
+    __shared__ float s_mn[32], s_mx[32];
+    float mn = INFINITY, mx = -INFINITY;
+    for (long long k = threadIdx.x; k < m; k += blockDim.x) {
+        const float x = base[4 * k];
+        mn = fminf(mn, x);
+        mx = fmaxf(mx, x);
+    }
+    for (int o = 16; o; o >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) { s_mn[threadIdx.x >> 5] = mn; s_mx[threadIdx.x >> 5] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) { s_mn[0] = fminf(s_mn[0], s_mn[w]); s_mx[0] = fmaxf(s_mx[0], s_mx[w]); }
+    }
+    __syncthreads();
+    const double dmn = (double)s_mn[0], dmx = (double)s_mx[0];
+    // median: ranks (m-1)/2 and m/2 of the values
+    uint32_t o0, o1;
+    radix_select2<uint32_t>(m, [&](long long k) { return f2o(base[4 * k]); }, (unsigned long long)((m - 1) / 2),
+                            (unsigned long long)(m / 2), &o0, &o1);
+    const double med = ((double)o2f(o0) + (double)o2f(o1)) * 0.5;
+    // MAD: the same ranks of |p - median| (non-negative doubles order like their bits)
+    unsigned long long a0, a1;
+    radix_select2<unsigned long long>(
+        m, [&](long long k) { return (unsigned long long)__double_as_longlong(fabs((double)base[4 * k] - med)); },
+        (unsigned long long)((m - 1) / 2), (unsigned long long)(m / 2), &a0, &a1);
+    const double mad = (__longlong_as_double((long long)a0) + __longlong_as_double((long long)a1)) * 0.5;
+    if (threadIdx.x == 0) {
+        double lo = med - n_mad * mad, hi = med + n_mad * mad;
+        if (dmn > lo) lo = dmn;
+        if (dmx < hi) hi = dmx;
+        aabb[6 * b + a] = round_down_f(lo);
+        aabb[6 * b + 3 + a] = round_up_f(hi);
+    }
+}
+
+void launch_select(const Layout& L, const cgs_scene& S, const cgs_camera* cams, const int32_t* view_block,
+                   const int8_t* levels, const cgs_config& cfg, cudaStream_t st)
+{
+    k_select<<<L.V, 128, 0, st>>>(L, S, cams, view_block, levels, cfg);
+    k_select_finish<<<1, 1024, 0, st>>>(L);
+}
+
+void launch_lod_levels(const cgs_scene& S, const cgs_config& cfg, const cgs_camera* cams, int n_views,
+                       int8_t* levels, cudaStream_t st)
+{
+    k_lod_levels<<<n_views, 128, 0, st>>>(S, cams, n_views, cfg, levels);
+}
+
+void launch_block_bounds(const cgs_scene& S, double n_mad, float* aabb, cudaStream_t st)
+{
+    k_block_bounds<<<S.n_blocks * 3, 256, 0, st>>>(S, n_mad, aabb);
+}
+
+}  // namespace cgs

@@ -1,0 +1,195 @@
+"""GPU parity of the forward hot path against the CPU oracle, through the C ABI:
+projection records, tile keys / values / ranges (bit-exact), pixels (FP32 tolerance),
+LoD selection and MAD bounds (bit-exact), batched views, edge cases."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2404_01133_b300 import cgs, synth
+from paper_2404_01133_b300 import torch_api as ta
+from gpu_common import compare_image, frame_arrays, gpu_render
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    from paper_2404_01133_b300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def check_against_oracle(scene, cam, g, tile, idx=None, view=0):
+    cfg = oracle.make_config(tile=tile)
+    o = oracle.render(scene, cam, cfg, idx=idx)
+    pr, srt = o["proj"], o["sort"]
+    n_sel = pr["depth"].shape[0]
+    assert g["status"] == 0, cgs.cgs_status_string(g["status"])
+    fr = g["frame"]
+    vb = fr.buffer(cgs.BUF_VIEW_BASE, torch.int32, count=fr.n_views + 1).cpu().numpy().astype(np.int64)
+    a = frame_arrays(g, n_sel=int(vb[-1]))
+    j0, j1 = vb[view], vb[view + 1]
+    assert j1 - j0 == n_sel
+    if fr.n_views == 1:
+        assert g["counts"][1] == int((pr["tiles_touched"] > 0).sum())
+        assert g["counts"][2] == pr["n_entries"]
+    gidx = a["scene_index"][j0:j1].astype(np.int64)
+    exp_idx = np.arange(n_sel) if idx is None else np.asarray(idx)
+    np.testing.assert_array_equal(gidx, exp_idx)
+    np.testing.assert_array_equal(a["tiles_touched"][j0:j1], pr["tiles_touched"].astype(np.uint32))
+    vis = pr["tiles_touched"] > 0
+    rec = a["records"][j0:j1]
+    # key path and values: bit-exact with the FP32 oracle
+    np.testing.assert_array_equal(rec[vis, 0], pr["xy"][vis, 0])
+    np.testing.assert_array_equal(rec[vis, 1], pr["xy"][vis, 1])
+    np.testing.assert_array_equal(rec[vis, 3], pr["depth"][vis])
+    np.testing.assert_array_equal(rec[vis, 7], pr["radius"][vis].astype(np.float32))
+    np.testing.assert_array_equal(rec[vis, 4:7], pr["conic"][vis])
+    np.testing.assert_array_equal(rec[vis, 8:11], pr["rgb"][vis])
+    # sorted (tile, depth, index) entries and ranges: bit-exact
+    T = ((cam["width"] + tile - 1) // tile) * ((cam["height"] + tile - 1) // tile)
+    keys = a["keys"].astype(np.int64)
+    sel = (keys // T) == view
+    np.testing.assert_array_equal(keys[sel] - view * T, (srt["keys"] >> np.uint64(32)).astype(np.int64))
+    np.testing.assert_array_equal(a["vals"][sel].astype(np.int64) - j0, srt["vals"].astype(np.int64))
+    r = a["ranges"].astype(np.int64)[view * T:(view + 1) * T]
+    first = int(np.flatnonzero(sel)[0]) if sel.any() else 0
+    np.testing.assert_array_equal(np.where(r[:, 1:] > r[:, :1], r - first, 0), srt["ranges"])
+    namb = compare_image(g["image"][view], g["final_T"][view], g["n_contrib"][view], o)
+    return o, namb
+
+
+@pytest.mark.parametrize("tile,batch", [(16, 256), (16, 64), (16, 32), (8, 64), (8, 32)])
+def test_small_scene_parity(tile, batch):
+    sc, cams = synth.workload_small()
+    g = gpu_render(sc, cams, tile=tile, batch=batch)
+    o, namb = check_against_oracle(sc, cams[0], g, tile)
+    assert namb < 0.01 * 128 * 128
+    pairs_gpu = g["counts"][3]
+    assert abs(pairs_gpu - o["pairs"]) <= int(o["n_visited"][o["ambiguous"].astype(bool)].sum()) + 0
+
+
+def test_depth_tie_broken_by_index():
+    sc, cams = synth.workload_small()
+    o = oracle.project(sc, cams[0])
+    d = o["depth"][o["tiles_touched"] > 0]
+    assert len(np.unique(d)) < len(d), "the 2,000-Gaussian workload has an FP32 depth tie"
+    g = gpu_render(sc, cams, tile=16)
+    check_against_oracle(sc, cams[0], g, 16)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_ragged_image_and_sh_degrees(seed):
+    deg = seed % 4
+    sc = synth.single_block(synth.random_cube_scene(3000, seed=seed, sh_degree=deg, log_scale_mu=-2.5))
+    cam = synth.small_scene_camera(100, 75, f=90.0, dist=3.5)
+    for tile in (16, 8):
+        g = gpu_render(sc, [cam], tile=tile)
+        check_against_oracle(sc, cam, g, tile)
+
+
+def test_all_culled_view_gives_background():
+    sc, cams = synth.workload_small()
+    cam = synth.camera_from_rt(np.diag([-1.0, 1.0, -1.0]), [0.0, 0.0, -10.0], 150, 150, 63.5, 63.5, 128, 128)
+    g = gpu_render(sc, [cam], cfg_kw={"bg": (0.25, 0.5, 0.75)})
+    assert g["status"] == 0 and g["counts"][1] == 0 and g["counts"][2] == 0
+    img = g["image"][0].cpu().numpy()
+    for ch, v in enumerate((0.25, 0.5, 0.75)):
+        assert np.all(img[ch] == np.float32(v))
+    assert torch.all(g["final_T"] == 1.0) and torch.all(g["n_contrib"] == 0)
+
+
+def test_capacity_overflow_is_reported_not_faulted():
+    sc, cams = synth.workload_small()
+    g = gpu_render(sc, cams, k_cap=1000)
+    assert g["status"] == cgs.CGS_ERR_CAPACITY
+    assert g["counts"][2] > 1000
+    g = gpu_render(sc, cams, n_cap=500, k_cap=100000)
+    assert g["status"] == cgs.CGS_ERR_CAPACITY
+    assert g["counts"][0] == 2000
+
+
+def test_batched_views_equal_single_views():
+    sc, _ = synth.workload_small()
+    cams = [synth.look_at((x, 0.5, -4.0), (0, 0, 0), (0, -1, 0), 150, 150, 128, 128) for x in (-1.0, 0.0, 1.5)]
+    gb = gpu_render(sc, cams)
+    assert gb["status"] == 0
+    for v, cam in enumerate(cams):
+        gs = gpu_render(sc, [cam])
+        assert torch.equal(gb["image"][v], gs["image"][0])
+        assert torch.equal(gb["final_T"][v], gs["final_T"][0])
+        assert torch.equal(gb["n_contrib"][v], gs["n_contrib"][0])
+    # and each view of the batch matches the oracle
+    check_against_oracle(sc, cams[2], gb, 16, view=2)
+
+
+def lod_scene(n=60000, grid=4, seed=7):
+    return synth.build_blocks(synth.city_scene(n, 0.4, seed, sh_degree=1), grid)
+
+
+def test_block_bounds_bit_exact():
+    sc = lod_scene()
+    ds = ta.DeviceScene(sc)
+    got = ds.compute_block_bounds(4.0).cpu().numpy()
+    np.testing.assert_array_equal(got, oracle.block_bounds(sc, 4.0))
+    got2 = ds.compute_block_bounds(2.5).cpu().numpy()
+    np.testing.assert_array_equal(got2, oracle.block_bounds(sc, 2.5))
+
+
+def lod_cameras(side, n=12, seed=11):
+    rng = np.random.default_rng(seed)
+    cams = []
+    for k in range(n):
+        x, y = rng.uniform(-side / 2, side / 2, size=2)
+        z = math.exp(rng.uniform(math.log(20.0), math.log(1500.0)))
+        pitch = rng.uniform(0.3, math.pi / 2)
+        cams.append(synth.pitched_camera((x, y, z), rng.uniform(0, 2 * math.pi), pitch, 300.0, 300.0, 320, 240))
+    return cams
+
+
+@pytest.mark.parametrize("dist", [(200.0, 600.0), (200.0, 400.0)])
+def test_lod_selection_bit_exact(dist):
+    sc = lod_scene()
+    ds = ta.DeviceScene(sc)
+    ds.compute_block_bounds(4.0)
+    aabb = oracle.block_bounds(sc, 4.0)
+    cams = lod_cameras(sc["side"])
+    cfg = ta.make_config(lod_dist=dist)
+    lv = torch.empty((len(cams), ds.n_blocks), dtype=torch.int8, device="cuda")
+    cgs.cgs_lod_select(ds.struct(), cfg, ta.cameras_device(cams), len(cams), lv)
+    got = lv.cpu().numpy()
+    for v, cam in enumerate(cams):
+        np.testing.assert_array_equal(got[v], oracle.lod_select(sc, aabb, cam, dist=dist))
+    assert (got == -1).any() and (got >= 0).any()
+
+
+def test_lod_render_matches_oracle_on_concatenated_selection():
+    sc = lod_scene()
+    aabb = oracle.block_bounds(sc, 4.0)
+    cams = [synth.pitched_camera((30.0, -40.0, 120.0), 0.3, 0.6, 300.0, 300.0, 320, 240),
+            synth.pitched_camera((-150.0, 100.0, 400.0), 2.0, 1.2, 300.0, 300.0, 320, 240)]
+    g = gpu_render(sc, cams, n_mad=4.0)
+    assert g["status"] == 0
+    for v, cam in enumerate(cams):
+        lev = oracle.lod_select(sc, aabb, cam)
+        idx = oracle.concat(sc, lev)
+        assert 0 < len(idx) < sc["mean_opac"].shape[0]
+        gv = gpu_render(sc, [cam], n_mad=4.0)
+        check_against_oracle(sc, cam, gv, 16, idx=idx)
+        assert torch.equal(gv["image"][0], g["image"][v])
+
+
+def test_explicit_levels_and_view_block_modes():
+    sc = lod_scene()
+    cam = synth.pitched_camera((0.0, 0.0, 300.0), 0.0, 1.0, 300.0, 300.0, 320, 240)
+    nb = sc["level_offset"].shape[0]
+    lev = np.array([(b % 4) - 1 for b in range(nb)], np.int8)  # -1, 0, 1, 2 repeating
+    g = gpu_render(sc, [cam], levels=lev[None, :])
+    check_against_oracle(sc, cam, g, 16, idx=oracle.concat(sc, lev))
+    g = gpu_render(sc, [cam], view_block=[5])
+    lev = np.full(nb, -1, np.int8)
+    lev[5] = 0
+    check_against_oracle(sc, cam, g, 16, idx=oracle.concat(sc, lev))
