@@ -34,9 +34,14 @@ METRIC = "fwd / fwd+bwd Mpix/s at 1080p, 20M-Gaussian LoD FPS, batched vs plain"
 UNIT = "Mpix/s"
 WORKLOAD = "city-1M-SH3 1920x1080 fwd+bwd (L1), 16x16 tiles"
 L2_FLUSH_BYTES = 256 << 20
-FP32_OPS_PER_EVAL_PAIR = 12     # forward: offset, quadratic form, exp argument, alpha, skip test
-FP32_OPS_PER_BLEND = 7          # forward: transmittance update, stop test, colour accumulation
-FP32_OPS_PER_BWD_PAIR = 45      # backward: re-evaluation, T recovery, dalpha, 9 gradient terms
+# Algorithmic FP32 work of compositing, counted per CONTRIBUTING pair (a pair that passes the
+# alpha >= 1/255 test and is blended before the transmittance stop): evaluating the pair
+# (offset 2, quadratic form 5, exp argument 1, alpha 2, skip test 1) and blending it
+# (transmittance 2, stop test 1, weight 1, colour 3).  Pairs that fail the test are overhead.
+FP32_OPS_PER_FWD_PAIR = 19
+# backward per contributing pair: re-evaluation 11, T recovery 2, dalpha 9, S update 4,
+# colour gradient 4, opacity / power 3, conic 6, mean 6
+FP32_OPS_PER_BWD_PAIR = 45
 
 
 def parse_args():
@@ -210,6 +215,7 @@ def run_ours(args, world, rank, local):
     ms, launches, stages = timed(args.steps, with_stages=True)
     clk = clocks.stop()
     ms_fwd, _, stages_fwd = timed(args.steps, fwd_only=True, with_stages=True)
+    step()  # one full step so the frame's counters hold both the forward and the backward
     status, counts = frame.status()
     if status != cgs.CGS_OK:
         raise RuntimeError(f"frame status: {cgs.cgs_status_string(status)}")
@@ -229,12 +235,14 @@ def run_ours(args, world, rank, local):
     depth_passes, tile_passes = 4, 2
     work = {
         # algorithmic bytes per launch (HBM-bound stages)
-        "project": ("hbm", n_sel * (16 + 4 + 4) + n_vis * (32 + 12 * nc_coef + 48 + 8 + 8)),
-        "depth_sort": ("hbm", n_sel * 4 + n_vis * 12 + n_vis * 8 + depth_passes * n_vis * 24),
-        "emit": ("hbm", n_vis * (12 + 4 + 8) + k_ent * 8),
+        # mean+opacity read and tiles-touched write for every selected Gaussian; scale, rotation,
+        # SH read and record, rect, key write for the visible ones; compaction and colour pass
+        "project": ("hbm", n_sel * (16 + 4 + 4) + n_vis * (32 + 12 * nc_coef + 48 + 8 + 8 + 12)),
+        "depth_sort": ("hbm", n_vis * 8 + depth_passes * n_vis * 24),
+        "emit": ("hbm", n_vis * (4 + 4 + 8 + 8) + k_ent * 8),
         "tile_sort": ("hbm", k_ent * 4 + tile_passes * k_ent * 16 + k_ent * 4),
         # algorithmic FP32 operations per launch (issue-bound stages)
-        "render": ("alu", pairs_f * FP32_OPS_PER_EVAL_PAIR + pairs_b * FP32_OPS_PER_BLEND),
+        "render": ("alu", pairs_b * FP32_OPS_PER_FWD_PAIR),
         "render_bwd": ("alu", pairs_b * FP32_OPS_PER_BWD_PAIR),
         "project_bwd": ("hbm", n_vis * (16 * 3 + 12 * nc_coef + 48 + 4 * 4 * 3 + 12 * nc_coef)),
     }

@@ -164,11 +164,13 @@ int32_t cgs_frame_status(const cgs_frame* frame, int32_t* status, int64_t* count
  *   1 sorted values       u32 [k_cap]  selected index (position in the concatenation)
  *   2 tile ranges         u32 [n_views * tiles][2]  [start, end) into 0/1
  *   3 scene index         u32 [n_cap]  selected index -> scene index
- *   4 projected records   float [n_cap][12]  u, v, opacity, depth | A', B', C', radius |
- *                                            r, g, b, view
+ *   4 projected records   float [n_cap][12]  u, v, opacity, ext_x | A', B', C', ext_y |
+ *                                            r, g, b, view (ext: half-extent of alpha >= 1/255)
  *   5 tiles touched       u32 [n_cap]
  *   6 selected per view   u32 [n_views + 1] exclusive prefix of the per-view counts
  *   7 depth order         u32 [n_cap]  selected indices of visible Gaussians by (view, depth)
+ *   8 depth keys          u64 [n_cap]  view << 32 | FP32 depth bits (visible entries only)
+ *   9 tile rects          u32 [n_cap][2]  x0 | y0 << 16, x1 | y1 << 16 (end exclusive, visible only)
  */
 int32_t cgs_frame_buffer(const cgs_frame* frame, int32_t which, void** d_ptr, int64_t* count);
 

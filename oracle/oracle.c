@@ -550,12 +550,14 @@ void orc_project_backward(int64_t n, const REAL* mean_opac, const REAL* scale, c
         REAL gm[3];
         for (int a = 0; a < 3; a++) gm[a] = (gdir[a] - dirv[a] * dd) / len;
 
-        /* conic -> Sigma2D entries (A, B, C) */
-        REAL A = p.A, Bv = p.B, C = p.C, D = p.det, D2 = p.det * p.det;
+        /* conic (C/D, -B/D, A/D), D = AC - B^2 -> Sigma2D entries (A, B, C).  The partials are
+         * written over the common denominator D^2 (1/D - AC/D^2 = -B^2/D^2), which avoids the
+         * cancellation of the unsimplified form. */
+        REAL A = p.A, Bv = p.B, C = p.C, D2 = p.det * p.det;
         REAL ga_ = g_conic[3 * i], gb_ = g_conic[3 * i + 1], gc_ = g_conic[3 * i + 2];
-        REAL dA = ga_ * (-C * C / D2) + gb_ * (Bv * C / D2) + gc_ * ((REAL)1 / D - A * C / D2);
-        REAL dB = ga_ * (2 * Bv * C / D2) + gb_ * ((REAL)-1 / D - 2 * Bv * Bv / D2) + gc_ * (2 * A * Bv / D2);
-        REAL dC = ga_ * ((REAL)1 / D - A * C / D2) + gb_ * (Bv * A / D2) + gc_ * (-A * A / D2);
+        REAL dA = (-ga_ * C * C + gb_ * Bv * C - gc_ * Bv * Bv) / D2;
+        REAL dB = (2 * ga_ * Bv * C - gb_ * (A * C + Bv * Bv) + 2 * gc_ * A * Bv) / D2;
+        REAL dC = (-ga_ * Bv * Bv + gb_ * A * Bv - gc_ * A * A) / D2;
 
         /* Sigma2D = T S T^T:  dL/dS_ij and dL/dT */
         const REAL* Tm = p.Tm;

@@ -22,7 +22,7 @@ CGS_ERR_CUDA = 5
 CGS_ERR_UNSUPPORTED = 6
 
 BUF_TILE_KEYS, BUF_TILE_VALS, BUF_RANGES, BUF_SCENE_INDEX, BUF_RECORDS, BUF_TILES_TOUCHED, BUF_VIEW_BASE, \
-    BUF_DEPTH_ORDER = range(8)
+    BUF_DEPTH_ORDER, BUF_DEPTH_KEYS, BUF_RECTS = range(10)
 
 
 class cgs_camera(C.Structure):

@@ -13,7 +13,9 @@ void launch_lod_levels(const cgs_scene& S, const cgs_config& cfg, const cgs_came
 void launch_block_bounds(const cgs_scene& S, double n_mad, float* aabb, cudaStream_t st);
 void launch_project(const Layout& L, const cgs_scene& S, const cgs_camera* cams, float near_z, int n_sm,
                     cudaStream_t st);
-int launch_depth_stage(const Layout& L, int n_sm, cudaStream_t st);
+void launch_colour(const Layout& L, const cgs_scene& S, const cgs_camera* cams, int n_sm, cudaStream_t st);
+int launch_compact(const Layout& L, int n_sm, cudaStream_t st);
+int launch_depth_sort(const Layout& L, int n_sm, cudaStream_t st);
 int launch_emit_stage(const Layout& L, int n_sm, cudaStream_t st);
 int launch_tile_stage(const Layout& L, int n_sm, cudaStream_t st);
 bool launch_render_fwd(const Layout& L, const cgs_config& c, float* img, float* T, uint32_t* nc, cudaStream_t st);
@@ -128,6 +130,7 @@ static bool make_layout(const cgs_frame* f, Layout* L, size_t* bytes)
         l.dkey[i] = c.take<unsigned long long>(l.n_cap);
         l.dval[i] = c.take<uint32_t>(l.n_cap);
     }
+    l.offs = c.take<uint32_t>(l.n_cap);
     for (int i = 0; i < 2; i++) {
         l.tkey[i] = c.take<uint32_t>(l.k_cap);
         l.tval[i] = c.take<uint32_t>(l.k_cap);
@@ -262,10 +265,13 @@ int32_t cgs_render_forward(const cgs_scene* scene, const cgs_frame* frame, const
         StageScope s(CGS_STAGE_PROJECT, st);
         launch_project(L, *scene, d_cams, cfg->near_z, n_sm, st);
         counted(1);
+        counted(launch_compact(L, n_sm, st));
+        launch_colour(L, *scene, d_cams, n_sm, st);
+        counted(1);
     }
     {
         StageScope s(CGS_STAGE_DEPTH_SORT, st);
-        counted(launch_depth_stage(L, n_sm, st));
+        counted(launch_depth_sort(L, n_sm, st));
     }
     {
         StageScope s(CGS_STAGE_EMIT, st);
@@ -395,6 +401,8 @@ int32_t cgs_frame_buffer(const cgs_frame* frame, int32_t which, void** d_ptr, in
         case 5: p = L.tt; n = L.n_cap; break;
         case 6: p = L.view_base; n = L.V + 1; break;
         case 7: p = L.dval[L.depth_sorted]; n = L.n_cap; break;
+        case 8: p = L.pkey; n = L.n_cap; break;
+        case 9: p = L.rect; n = L.n_cap; break;
         default: return CGS_ERR_INVALID_ARGUMENT;
     }
     *d_ptr = p;

@@ -57,13 +57,14 @@ struct Layout {
     uint32_t* seg_base;          // [V][NB + 1]
     long long* seg_off;          // [V][NB]
     int8_t* levels;              // [V][NB]
-    float4* rec;                 // [n_cap][3]
+    float4* rec;                 // [n_cap][3] (u, v, o, ext_x) (A', B', C', ext_y) (r, g, b, view)
     uint2* rect;                 // [n_cap] (x0 | y0 << 16, x1 | y1 << 16), tile units, end exclusive
     uint32_t* tt;                // [n_cap] tiles touched
     uint32_t* gidx;              // [n_cap] scene index
     unsigned long long* pkey;    // [n_cap] view << 32 | depth bits
     unsigned long long* dkey[2]; // [n_cap] depth sort ping-pong
     uint32_t* dval[2];           // [n_cap]
+    uint32_t* offs;              // [n_cap] first entry of each depth-sorted visible Gaussian
     uint32_t* tkey[2];           // [k_cap] tile sort ping-pong
     uint32_t* tval[2];           // [k_cap]
     uint32_t* lb[2];             // [max(sort tiles)][256] look-back, ping-pong between passes

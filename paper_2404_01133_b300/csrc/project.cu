@@ -5,16 +5,31 @@
 
 namespace cgs {
 
+// Conservative half-extents (pixels) of the region where alpha = min(0.99, o exp(-q/2)) can
+// reach 1/255, i.e. q <= t = 2 ln(255 o).  Since q(d) >= dx^2 / Sigma_xx for a positive
+// definite Sigma, |dx| > sqrt(t Sigma_xx) implies alpha < 1/255 (likewise for y).  The
+// threshold and extents get relative and absolute slack far above FP32 rounding of q; for
+// strongly correlated 2D covariances (rho^2 > 0.99), where the rounding of q is not bounded
+// by that slack, the extent is infinite (never culled).  Opacity below 1/255 can never pass
+// the test: extent -1 (always culled).
+__device__ __forceinline__ void cull_extent(float o, float A, float B, float C, float* ex, float* ey)
+{
+    if (!(o * 255.0f > 1.0f)) { *ex = -1.0f; *ey = -1.0f; return; }
+    if (B * B > 0.99f * A * C) { *ex = INFINITY; *ey = INFINITY; return; }
+    const float t = 2.0f * logf(255.0f * o) * 1.002f + 0.002f;
+    *ex = sqrtf(t * A) * 1.001f + 0.01f;
+    *ey = sqrtf(t * C) * 1.001f + 0.01f;
+}
+
 // One thread per selected Gaussian j (flattened over views), grid-stride over the device
 // count written by the selection kernels.  Writes tiles touched and the scene index of every
-// selected Gaussian and, for the visible ones, the projected record, tile rect, (view, depth)
-// sort key and cleared screen-gradient accumulators for the backward.
+// selected Gaussian and, for the visible ones, the screen-space part of the projected record,
+// the tile rect, the (view, depth) sort key and cleared screen-gradient accumulators.  Colour
+// is evaluated later by k_colour over the compacted visible list.
 __global__ void __launch_bounds__(256) k_project(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams,
                                                  float near_z)
 {
     const uint32_t n = L.hdr->n_sel;
-    const int deg = S.sh_degree;
-    const int nc = (deg + 1) * (deg + 1);
     const float4* __restrict__ mo4 = reinterpret_cast<const float4*>(S.mean_opac);
     const float4* __restrict__ sc4 = reinterpret_cast<const float4*>(S.scale);
     const float4* __restrict__ q4 = reinterpret_cast<const float4*>(S.quat);
@@ -23,10 +38,10 @@ __global__ void __launch_bounds__(256) k_project(Layout L, cgs_scene S, const cg
         long long g;
         locate(L, j, &v, &g);
         L.gidx[j] = (uint32_t)g;
-        const cgs_camera c = cams[v];
+        const cgs_camera& c = cams[v];
         const float4 mo = __ldg(mo4 + g);
         const float m[3] = {mo.x, mo.y, mo.z};
-        // near-plane test first, so culled Gaussians never read scale, rotation or SH
+        // near-plane test first, so culled Gaussians never read scale or rotation
         const float tz = ((c.R[6] * m[0] + c.R[7] * m[1]) + c.R[8] * m[2]) + c.t[2];
         uint32_t tt = 0;
         if (tz > near_z) {
@@ -48,12 +63,10 @@ __global__ void __launch_bounds__(256) k_project(Layout L, cgs_scene S, const cg
                     const uint32_t ty0 = (uint32_t)y0 / L.B, ty1 = (uint32_t)y1 / L.B + 1;
                     tt = (tx1 - tx0) * (ty1 - ty0);
                     L.rect[j] = make_uint2(tx0 | (ty0 << 16), tx1 | (ty1 << 16));
-                    float f[48], rgb[3], dir[3], len, Y[16];
-                    load_sh(S.sh, g, nc, f);
-                    sh_colour(m, c, f, deg, rgb, dir, &len, Y);
-                    L.rec[3 * (size_t)j] = make_float4(p.u, p.v, mo.w, p.tz);
-                    L.rec[3 * (size_t)j + 1] = make_float4(p.conic[0], p.conic[1], p.conic[2], r);
-                    L.rec[3 * (size_t)j + 2] = make_float4(rgb[0], rgb[1], rgb[2], __int_as_float(v));
+                    float ex, ey;
+                    cull_extent(mo.w, p.A, p.B, p.C, &ex, &ey);
+                    L.rec[3 * (size_t)j] = make_float4(p.u, p.v, mo.w, ex);
+                    L.rec[3 * (size_t)j + 1] = make_float4(p.conic[0], p.conic[1], p.conic[2], ey);
                     L.pkey[j] = ((unsigned long long)(uint32_t)v << 32) | __float_as_uint(p.tz);
                     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
                     L.gs[3 * (size_t)j] = z4;
@@ -66,6 +79,26 @@ __global__ void __launch_bounds__(256) k_project(Layout L, cgs_scene S, const cg
     }
 }
 
+// View-dependent colour (SH, Sec. 3.1) of each visible Gaussian, over the compacted visible
+// list so every lane has work.  Writes the third record (r, g, b, view).
+__global__ void __launch_bounds__(256) k_colour(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams)
+{
+    const uint32_t n = L.hdr->n_vis;
+    const int deg = S.sh_degree;
+    const int nc = (deg + 1) * (deg + 1);
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const uint32_t j = L.dval[0][r];
+        const int v = (int)(L.pkey[j] >> 32);
+        const long long g = L.gidx[j];
+        const float4 mo = __ldg(reinterpret_cast<const float4*>(S.mean_opac) + g);
+        const float m[3] = {mo.x, mo.y, mo.z};
+        float f[48], rgb[3], dir[3], len, Y[16];
+        load_sh(S.sh, g, nc, f);
+        sh_colour(m, cams[v], f, deg, rgb, dir, &len, Y);
+        L.rec[3 * (size_t)j + 2] = make_float4(rgb[0], rgb[1], rgb[2], __int_as_float(v));
+    }
+}
+
 void launch_project(const Layout& L, const cgs_scene& S, const cgs_camera* cams, float near_z, int n_sm,
                     cudaStream_t st)
 {
@@ -73,6 +106,14 @@ void launch_project(const Layout& L, const cgs_scene& S, const cgs_camera* cams,
     long long grid = want < (long long)n_sm * 8 ? want : (long long)n_sm * 8;
     if (grid < 1) grid = 1;
     k_project<<<(unsigned)grid, 256, 0, st>>>(L, S, cams, near_z);
+}
+
+void launch_colour(const Layout& L, const cgs_scene& S, const cgs_camera* cams, int n_sm, cudaStream_t st)
+{
+    long long want = (L.n_cap + 255) / 256;
+    long long grid = want < (long long)n_sm * 8 ? want : (long long)n_sm * 8;
+    if (grid < 1) grid = 1;
+    k_colour<<<(unsigned)grid, 256, 0, st>>>(L, S, cams);
 }
 
 }  // namespace cgs

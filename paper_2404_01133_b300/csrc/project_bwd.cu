@@ -2,7 +2,9 @@
 // per-Gaussian screen-space gradients (u, v, conic, opacity, rgb) accumulated by the
 // compositing backward to the scene attributes.  Discrete decisions pass no gradient: the
 // guard-band clamp zeroes the clamped coordinate's direct term, the colour clamp masks its
-// channel, and the quaternion gradient goes through the normalisation.
+// channel, and the quaternion gradient goes through the normalisation.  Compiled with
+// -fmad=false like the forward projection, so the recomputed clamp decisions match it.
+// Gradients are added with 16-byte vector atomics (one per attribute row).
 #include "proj_math.cuh"
 
 namespace cgs {
@@ -11,11 +13,13 @@ __global__ void __launch_bounds__(128) k_project_bwd(Layout L, cgs_scene S, cons
                                                      float near_z, float* __restrict__ g_mo, float* __restrict__ g_sc,
                                                      float* __restrict__ g_q, float* __restrict__ g_sh)
 {
-    const uint32_t n = L.hdr->n_sel;
+    // over the (view, depth)-sorted visible Gaussians, so every lane has work
+    const uint32_t n = L.hdr->n_vis;
+    const uint32_t* __restrict__ vis = L.dval[L.depth_sorted];
     const int deg = S.sh_degree;
     const int nc = (deg + 1) * (deg + 1);
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        if (L.tt[j] == 0) continue;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const uint32_t j = vis[r];
         const float4 ga = L.gs[3 * (size_t)j], gb = L.gs[3 * (size_t)j + 1], gc4 = L.gs[3 * (size_t)j + 2];
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         L.gs[3 * (size_t)j] = z4;
@@ -39,28 +43,35 @@ __global__ void __launch_bounds__(128) k_project_bwd(Layout L, cgs_scene S, cons
         const int cl = sh_colour(m, c, f, deg, rgb, dir, &len, Y);
         sh_grad(dir[0], dir[1], dir[2], deg, dY);
         float gdir[3] = {0.f, 0.f, 0.f};
-        float* gsh = g_sh + g * (long long)(nc * 3);
-        for (int ch = 0; ch < 3; ch++) {
-            if (cl & (1 << ch)) continue;
-            const float gcol = grgb[ch];
-            for (int k = 0; k < nc; k++) {
-                atomicAdd(gsh + k * 3 + ch, Y[k] * gcol);
-                const float fk = f[k * 3 + ch] * gcol;
+        float gc[3];
+        for (int ch = 0; ch < 3; ch++) gc[ch] = (cl & (1 << ch)) ? 0.0f : grgb[ch];
+        float gf[48];
+        for (int k = 0; k < nc; k++)
+            for (int ch = 0; ch < 3; ch++) {
+                gf[k * 3 + ch] = Y[k] * gc[ch];
+                const float fk = f[k * 3 + ch] * gc[ch];
                 gdir[0] += fk * dY[k][0];
                 gdir[1] += fk * dY[k][1];
                 gdir[2] += fk * dY[k][2];
             }
+        float* gsh = g_sh + g * (long long)(nc * 3);
+        if ((nc * 3) % 4 == 0) {
+            float4* g4 = reinterpret_cast<float4*>(gsh);
+            for (int i = 0; i < nc * 3 / 4; i++)
+                atomicAdd(g4 + i, make_float4(gf[4 * i], gf[4 * i + 1], gf[4 * i + 2], gf[4 * i + 3]));
+        } else {
+            for (int i = 0; i < nc * 3; i++) atomicAdd(gsh + i, gf[i]);
         }
         const float dd = dir[0] * gdir[0] + dir[1] * gdir[1] + dir[2] * gdir[2];
         float gm[3];
         for (int a = 0; a < 3; a++) gm[a] = (gdir[a] - dir[a] * dd) / len;
 
-        // conic (C/D, -B/D, A/D) -> Sigma2D entries (A, B, C)
-        const float A = p.A, Bv = p.B, C = p.C, D = p.det, D2 = p.det * p.det, iD = 1.0f / p.det;
-        const float dA = gA_ * (-C * C / D2) + gB_ * (Bv * C / D2) + gC_ * (iD - A * C / D2);
-        const float dB = gA_ * (2.0f * Bv * C / D2) + gB_ * (-iD - 2.0f * Bv * Bv / D2) + gC_ * (2.0f * A * Bv / D2);
-        const float dC = gA_ * (iD - A * C / D2) + gB_ * (Bv * A / D2) + gC_ * (-A * A / D2);
-        (void)D;
+        // conic (C/D, -B/D, A/D), D = AC - B^2 -> Sigma2D entries (A, B, C), over the common
+        // denominator D^2 (1/D - AC/D^2 = -B^2/D^2 carries no cancellation this way)
+        const float A = p.A, Bv = p.B, C = p.C, D2 = p.det * p.det;
+        const float dA = (-gA_ * C * C + gB_ * Bv * C - gC_ * Bv * Bv) / D2;
+        const float dB = (2.0f * gA_ * Bv * C - gB_ * (A * C + Bv * Bv) + 2.0f * gC_ * A * Bv) / D2;
+        const float dC = (-gA_ * Bv * Bv + gB_ * A * Bv - gC_ * A * A) / D2;
 
         // Sigma2D = T S T^T
         const float* Tm = p.Tm;
@@ -97,11 +108,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(Layout L, cgs_scene S, cons
         gty += gv * fy / tz;
         gtz += gv * (-fy * ty / tz2);
         for (int a = 0; a < 3; a++) gm[a] += W[a] * gtx + W[3 + a] * gty + W[6 + a] * gtz;
-        float* gmo = g_mo + 4 * g;
-        atomicAdd(gmo + 0, gm[0]);
-        atomicAdd(gmo + 1, gm[1]);
-        atomicAdd(gmo + 2, gm[2]);
-        atomicAdd(gmo + 3, gop);
+        atomicAdd(reinterpret_cast<float4*>(g_mo) + g, make_float4(gm[0], gm[1], gm[2], gop));
 
         // Sigma3D = M M^T, M = Rq diag(s)
         float gM[9];
@@ -111,14 +118,14 @@ __global__ void __launch_bounds__(128) k_project_bwd(Layout L, cgs_scene S, cons
                 for (int b = 0; b < 3; b++) acc += (gS[a * 3 + b] + gS[b * 3 + a]) * p.M[b * 3 + k];
                 gM[a * 3 + k] = acc;
             }
-        float gR[9];
-        float* gsc = g_sc + 4 * g;
+        float gR[9], gsv[3];
         for (int k = 0; k < 3; k++) {
             float acc = 0.f;
             for (int a = 0; a < 3; a++) acc += gM[a * 3 + k] * p.Rq[a * 3 + k];
-            atomicAdd(gsc + k, acc);
+            gsv[k] = acc;
             for (int a = 0; a < 3; a++) gR[a * 3 + k] = gM[a * 3 + k] * s[k];
         }
+        atomicAdd(reinterpret_cast<float4*>(g_sc) + g, make_float4(gsv[0], gsv[1], gsv[2], 0.0f));
         const float w = p.qn[0], x = p.qn[1], y = p.qn[2], z = p.qn[3];
         float gq[4];
         gq[0] = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
@@ -126,8 +133,10 @@ __global__ void __launch_bounds__(128) k_project_bwd(Layout L, cgs_scene S, cons
         gq[2] = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7] - 2.f * y * gR[8]);
         gq[3] = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] + y * gR[5] + x * gR[6] + y * gR[7]);
         const float qd = w * gq[0] + x * gq[1] + y * gq[2] + z * gq[3];
-        float* gqq = g_q + 4 * g;
-        for (int a = 0; a < 4; a++) atomicAdd(gqq + a, (gq[a] - p.qn[a] * qd) / p.qlen);
+        const float il = 1.0f / p.qlen;
+        atomicAdd(reinterpret_cast<float4*>(g_q) + g,
+                  make_float4((gq[0] - p.qn[0] * qd) * il, (gq[1] - p.qn[1] * qd) * il, (gq[2] - p.qn[2] * qd) * il,
+                              (gq[3] - p.qn[3] * qd) * il));
     }
 }
 

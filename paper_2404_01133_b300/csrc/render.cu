@@ -24,6 +24,45 @@ __device__ __forceinline__ float pair_power(const float4& a, const float4& b, fl
     return __fmaf_rn(-0.5f, q, -cr);
 }
 
+// Warp sum of 16 values per lane by halving exchanges: at each step a lane keeps half of its
+// values and adds the partner's copy of that half.  On return lane l holds the warp total of
+// v[l >> 1] (16 shuffles instead of 16 x 5).
+__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], int lane)
+{
+#pragma unroll
+    for (int o = 16, n = 8; o >= 2; o >>= 1, n >>= 1) {
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < n; k++) {
+            const float send = hi ? v[k] : v[k + n];
+            const float keep = hi ? v[k + n] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// Pixel of thread `tid` in a B x B tile: warps cover 8 x 4 pixel blocks (B/8 blocks per row).
+template <int B>
+__device__ __forceinline__ void pixel_of(int tid, int* x, int* y, int* wx0, int* wy0)
+{
+    const int w = tid >> 5, lane = tid & 31;
+    *wx0 = (w % (B / 8)) * 8;
+    *wy0 = (w / (B / 8)) * 4;
+    *x = *wx0 + (lane & 7);
+    *y = *wy0 + (lane >> 3);
+}
+
+// Whole-warp skip: true if the Gaussian's 1/255 extent box (record .w lanes) misses the
+// warp's 8 x 4 pixel block [bx0, bx0 + 7] x [by0, by0 + 3].  Skipped pairs would all fail
+// the alpha >= 1/255 test, so skipping changes no result.
+__device__ __forceinline__ bool warp_culled(const float4& a, const float4& b, float bx0, float by0)
+{
+    const float dx = fmaxf(fmaxf(bx0 - a.x, a.x - (bx0 + 7.0f)), 0.0f);
+    const float dy = fmaxf(fmaxf(by0 - a.y, a.y - (by0 + 3.0f)), 0.0f);
+    return dx > a.w || dy > b.w;
+}
+
 template <int B, int BATCH>
 __global__ void __launch_bounds__(B * B) k_render_fwd(Layout L, const uint32_t* __restrict__ tval, float bg0, float bg1,
                                                       float bg2, float* __restrict__ image, float* __restrict__ final_T,
@@ -34,9 +73,12 @@ __global__ void __launch_bounds__(B * B) k_render_fwd(Layout L, const uint32_t* 
     const int v = blockIdx.z;
     const int tile = blockIdx.y * L.tiles_x + blockIdx.x;
     const uint2 rg = reinterpret_cast<const uint2*>(L.ranges)[(size_t)v * L.T + tile];
-    const int px = blockIdx.x * B + (threadIdx.x % B), py = blockIdx.y * B + (threadIdx.x / B);
+    int lx, ly, wx0, wy0;
+    pixel_of<B>(threadIdx.x, &lx, &ly, &wx0, &wy0);
+    const int px = blockIdx.x * B + lx, py = blockIdx.y * B + ly;
     const bool inside = px < L.W && py < L.H;
     const float fpx = (float)px, fpy = (float)py;
+    const float bx0 = (float)(blockIdx.x * B + wx0), by0 = (float)(blockIdx.y * B + wy0);
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
     uint32_t last = 0, visited = 0;
     bool done = !inside;
@@ -54,6 +96,7 @@ __global__ void __launch_bounds__(B * B) k_render_fwd(Layout L, const uint32_t* 
         for (int k = 0; !done && k < nb; k++) {
             visited++;
             const float4 a = s_a[k], b = s_b[k];
+            if (warp_culled(a, b, bx0, by0)) continue;
             float dx, dy;
             const float power = pair_power(a, b, fpx, fpy, &dx, &dy);
             if (power > 0.0f) continue;
@@ -98,14 +141,18 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(Layout L, const uint32_t* 
     constexpr int NT = B * B;
     __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
     __shared__ uint32_t s_j[BATCH];
-    __shared__ float s_g[9][BATCH];
+    __shared__ float s_g[BATCH][9];
     __shared__ uint32_t s_maxnc;
     const int v = blockIdx.z;
     const int tile = blockIdx.y * L.tiles_x + blockIdx.x;
     const uint2 rg = reinterpret_cast<const uint2*>(L.ranges)[(size_t)v * L.T + tile];
-    const int px = blockIdx.x * B + (threadIdx.x % B), py = blockIdx.y * B + (threadIdx.x / B);
+    int lx, ly, wx0, wy0;
+    pixel_of<B>(threadIdx.x, &lx, &ly, &wx0, &wy0);
+    const int px = blockIdx.x * B + lx, py = blockIdx.y * B + ly;
     const bool inside = px < L.W && py < L.H;
     const float fpx = (float)px, fpy = (float)py;
+    const float bx0 = (float)(blockIdx.x * B + wx0), by0 = (float)(blockIdx.y * B + wy0);
+    const int lane = threadIdx.x & 31;
     const size_t HW = (size_t)L.W * L.H, pix = (size_t)py * L.W + px;
     float T = 1.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
     uint32_t nc = 0;
@@ -125,6 +172,10 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(Layout L, const uint32_t* 
     // n_contrib never exceeds the tile's list length; clamp so a mismatched buffer cannot
     // move the replay outside this tile's entries
     const long long end = (first + s_maxnc) < (long long)rg.y ? (first + s_maxnc) : (long long)rg.y;
+    // last list position any pixel of this warp blends: entries past it are skipped whole
+    uint32_t wmax = nc;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
     uint32_t pairs = 0;
     for (long long be = end; be > first; be -= BATCH) {
         const long long bs = (be - BATCH) > first ? (be - BATCH) : first;
@@ -141,8 +192,10 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(Layout L, const uint32_t* 
         __syncthreads();
         for (int k = nb - 1; k >= 0; k--) {
             const uint32_t lp = (uint32_t)(bs + k - first);
-            bool contrib = lp < nc;
+            if (lp >= wmax) continue;  // warp-uniform
             const float4 a = s_a[k], b = s_b[k];
+            if (warp_culled(a, b, bx0, by0)) continue;  // warp-uniform
+            bool contrib = lp < nc;
             float dx, dy;
             float G = 0.0f, alpha = 0.0f;
             if (contrib) {
@@ -154,9 +207,9 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(Layout L, const uint32_t* 
                     if (alpha < 1.0f / 255.0f) contrib = false;
                 }
             }
-            float gr[9];
+            float gr[16];
 #pragma unroll
-            for (int c = 0; c < 9; c++) gr[c] = 0.0f;
+            for (int c = 0; c < 16; c++) gr[c] = 0.0f;
             if (contrib) {
                 pairs++;
                 const float oma = 1.0f - alpha;
@@ -181,15 +234,8 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(Layout L, const uint32_t* 
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-                for (int c = 0; c < 9; c++) {
-#pragma unroll
-                    for (int o = 16; o; o >>= 1) gr[c] += __shfl_xor_sync(0xffffffffu, gr[c], o);
-                }
-                if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-                    for (int c = 0; c < 9; c++) atomicAdd(&s_g[c][k], gr[c]);
-                }
+                const float tot = warp_transpose_sum16(gr, lane);
+                if ((lane & 1) == 0 && (lane >> 1) < 9) atomicAdd(&s_g[k][lane >> 1], tot);
             }
         }
         __syncthreads();
@@ -197,7 +243,7 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(Layout L, const uint32_t* 
             float* dst = reinterpret_cast<float*>(L.gs) + 12 * (size_t)s_j[threadIdx.x];
 #pragma unroll
             for (int c = 0; c < 9; c++) {
-                const float x = s_g[c][threadIdx.x];
+                const float x = s_g[threadIdx.x][c];
                 if (x != 0.0f) atomicAdd(dst + c, x);
             }
         }

@@ -198,18 +198,20 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(Op op, unsigned long long
         }
         unsigned long long tot;
         const unsigned long long ex = block_exclusive_scan<unsigned long long>(sum, s_buf, &tot);
-        if (tid == 0) {
+        if (tid < 32) {
+            // warp-parallel look-back: lane l inspects tile p - l; the window slides back by 32
+            // until a tile with an inclusive prefix is found
+            const int lane = tid;
+            if (lane == 0) st_volatile64(&lb[t], (t == 0 ? SF_INC : SF_AGG) | tot);
             unsigned long long excl = 0;
-            if (t == 0) {
-                st_volatile64(&lb[0], SF_INC | tot);
-            } else {
-                st_volatile64(&lb[t], SF_AGG | tot);
-                long long p = t - 1;
-                while (true) {
-                    unsigned long long w;
+            long long p = t - 1;
+            while (p >= 0) {
+                const long long q = p - lane;
+                unsigned long long w = SF_INC;  // before tile 0: an inclusive zero
+                if (q >= 0) {
                     int spins = 0;
                     while (true) {
-                        w = ld_volatile64(&lb[p]);
+                        w = ld_volatile64(&lb[q]);
                         if (w & SF_FLAGS) break;
                         if (++spins > SPIN_LIMIT) {
                             latch(hdr, ST_SPIN);
@@ -217,16 +219,23 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(Op op, unsigned long long
                             w = SF_INC;
                             break;
                         }
-                        __nanosleep(64);
+                        __nanosleep(32);
                     }
-                    excl += w & ~SF_FLAGS;
-                    if ((w & SF_FLAGS) == SF_INC || p == 0) break;
-                    --p;
                 }
-                st_volatile64(&lb[t], SF_INC | (excl + tot));
+                const uint32_t inc = __ballot_sync(0xffffffffu, (w & SF_FLAGS) == SF_INC);
+                const int stop = inc ? __ffs(inc) - 1 : 31;
+                unsigned long long val = lane <= stop ? (w & ~SF_FLAGS) : 0ull;
+#pragma unroll
+                for (int o = 16; o; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+                excl += val;
+                if (inc) break;
+                p -= 32;
             }
-            s_prefix = excl;
-            if (t == n_tiles - 1) op.finish(excl + tot);
+            if (lane == 0) {
+                if (t > 0) st_volatile64(&lb[t], SF_INC | (excl + tot));
+                s_prefix = excl;
+                if (t == n_tiles - 1) op.finish(excl + tot);
+            }
         }
         __syncthreads();
         unsigned long long run = s_prefix + ex;
@@ -254,30 +263,16 @@ struct CompactOp {
     __device__ void finish(unsigned long long total) const { L.hdr->n_vis = (uint32_t)total; }
 };
 
-// Walks the (view, depth)-sorted visible Gaussians and writes one entry per covered tile,
-// row-major inside the rect, at the scanned offset.
-struct EmitOp {
+// Exclusive offsets of the tile entries of the (view, depth)-sorted visible Gaussians.
+struct OffsetOp {
     Layout L;
-    const unsigned long long* dkey;
     const uint32_t* dval;
     __device__ long long count() const { return L.hdr->n_vis; }
     __device__ uint32_t load(long long r) const { return L.tt[dval[r]]; }
     __device__ void store(long long r, unsigned long long e, uint32_t x) const
     {
-        if (!x) return;
-        const uint32_t j = dval[r];
-        const uint32_t view = (uint32_t)(dkey[r] >> 32);
-        const uint2 rc = L.rect[j];
-        const uint32_t tx0 = rc.x & 0xffffu, ty0 = rc.x >> 16, tx1 = rc.y & 0xffffu, ty1 = rc.y >> 16;
-        const uint32_t base = view * (uint32_t)L.T;
-        unsigned long long pos = e;
-        const unsigned long long cap = (unsigned long long)L.k_cap;
-        for (uint32_t ty = ty0; ty < ty1; ty++)
-            for (uint32_t tx = tx0; tx < tx1; tx++, pos++)
-                if (pos < cap) {
-                    L.tkey[0][pos] = base + ty * (uint32_t)L.tiles_x + tx;
-                    L.tval[0][pos] = j;
-                }
+        (void)x;
+        L.offs[r] = (uint32_t)(e < 0xffffffffull ? e : 0xffffffffull);
     }
     __device__ void finish(unsigned long long total) const
     {
@@ -287,6 +282,31 @@ struct EmitOp {
         if (total > cap) latch(L.hdr, ST_CAPACITY);
     }
 };
+
+// Duplication, one thread per output entry k: the owning Gaussian is the last r with
+// offs[r] <= k (binary search), the tile is the (k - offs[r])-th of its rect in row-major
+// order.  Entries come out in (view, depth, index) order, tiles row-major inside a rect.
+__global__ void __launch_bounds__(256) k_emit(Layout L, const unsigned long long* __restrict__ dkey,
+                                              const uint32_t* __restrict__ dval)
+{
+    const long long n = L.hdr->k_used;
+    const uint32_t nv = L.hdr->n_vis;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        uint32_t lo = 0, hi = nv;  // offs[lo] <= k < offs[hi] (offs[nv] taken as +inf)
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if ((long long)L.offs[mid] <= k) lo = mid; else hi = mid;
+        }
+        const uint32_t j = dval[lo];
+        const uint32_t view = (uint32_t)(dkey[lo] >> 32);
+        const uint2 rc = L.rect[j];
+        const uint32_t tx0 = rc.x & 0xffffu, ty0 = rc.x >> 16, w = (rc.y & 0xffffu) - tx0;
+        const uint32_t local = (uint32_t)(k - (long long)L.offs[lo]);
+        const uint32_t ty = ty0 + local / w, tx = tx0 + local % w;
+        L.tkey[0][k] = view * (uint32_t)L.T + ty * (uint32_t)L.tiles_x + tx;
+        L.tval[0][k] = j;
+    }
+}
 
 // [start, end) of every (view, tile) key in the sorted entries; ranges were cleared.
 __global__ void k_ranges(const uint32_t* __restrict__ keys, const Header* hdr, uint32_t* ranges)
@@ -326,25 +346,33 @@ static long long grid_for(long long items, long long per_cta, int n_sm, int per_
     return g < 1 ? 1 : g;
 }
 
-// Visible compaction and the (view, depth) sort.  Returns the number of kernels launched.
-int launch_depth_stage(const Layout& L, int n_sm, cudaStream_t st)
+// Visible compaction in selected-index order.  Returns the number of kernels launched.
+int launch_compact(const Layout& L, int n_sm, cudaStream_t st)
 {
     CompactOp cop{L};
     k_scan<CompactOp><<<(unsigned)grid_for(L.n_cap, SCAN_TILE, n_sm, 8), SCAN_THREADS, 0, st>>>(
         cop, L.scan_lb, L.hdr->ctr + CTR_SCAN_COMPACT, L.hdr);
-    radix_sort<unsigned long long>(L.dkey, L.dval, &L.hdr->n_vis, L.n_cap, L.hist_depth, L.depth_passes, L.lb,
-                                   L.hdr->ctr + CTR_DEPTH_PASS0, L.hdr, n_sm, st);
-    return 2 + L.depth_passes;
+    return 1;
 }
 
-// Duplication into tile entries in depth order.
+// Stable (view, depth) radix sort of the compacted visible Gaussians.
+int launch_depth_sort(const Layout& L, int n_sm, cudaStream_t st)
+{
+    radix_sort<unsigned long long>(L.dkey, L.dval, &L.hdr->n_vis, L.n_cap, L.hist_depth, L.depth_passes, L.lb,
+                                   L.hdr->ctr + CTR_DEPTH_PASS0, L.hdr, n_sm, st);
+    return 1 + L.depth_passes;
+}
+
+// Offsets of every visible Gaussian's entries, then duplication into tile entries.
 int launch_emit_stage(const Layout& L, int n_sm, cudaStream_t st)
 {
     const long long scan_tiles = (L.n_cap + SCAN_TILE - 1) / SCAN_TILE;
-    EmitOp eop{L, L.dkey[L.depth_sorted], L.dval[L.depth_sorted]};
-    k_scan<EmitOp><<<(unsigned)grid_for(L.n_cap, SCAN_TILE, n_sm, 8), SCAN_THREADS, 0, st>>>(
-        eop, L.scan_lb + scan_tiles, L.hdr->ctr + CTR_SCAN_EMIT, L.hdr);
-    return 1;
+    OffsetOp oop{L, L.dval[L.depth_sorted]};
+    k_scan<OffsetOp><<<(unsigned)grid_for(L.n_cap, SCAN_TILE, n_sm, 8), SCAN_THREADS, 0, st>>>(
+        oop, L.scan_lb + scan_tiles, L.hdr->ctr + CTR_SCAN_EMIT, L.hdr);
+    k_emit<<<(unsigned)grid_for(L.k_cap, 256, n_sm, 16), 256, 0, st>>>(L, L.dkey[L.depth_sorted],
+                                                                       L.dval[L.depth_sorted]);
+    return 2;
 }
 
 // Stable sort by tile (keeps the depth order inside each tile) and the per-tile ranges.

@@ -45,6 +45,8 @@ def frame_arrays(g, n_sel=None, k=None):
         "records": fr.buffer(cgs.BUF_RECORDS, torch.float32, (12,), count=n_sel).cpu().numpy(),
         "keys": fr.buffer(cgs.BUF_TILE_KEYS, torch.int32, count=k).cpu().numpy().view(np.uint32),
         "vals": fr.buffer(cgs.BUF_TILE_VALS, torch.int32, count=k).cpu().numpy().view(np.uint32),
+        "depth_keys": fr.buffer(cgs.BUF_DEPTH_KEYS, torch.int64, count=n_sel).cpu().numpy().view(np.uint64),
+        "rects": fr.buffer(cgs.BUF_RECTS, torch.int32, (2,), count=n_sel).cpu().numpy().view(np.uint32),
     }
     V, T = fr.n_views, ((fr.width + fr.tile - 1) // fr.tile) * ((fr.height + fr.tile - 1) // fr.tile)
     out["ranges"] = fr.buffer(cgs.BUF_RANGES, torch.int32, (2,), count=V * T).cpu().numpy().view(np.uint32)

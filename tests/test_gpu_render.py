@@ -45,8 +45,15 @@ def check_against_oracle(scene, cam, g, tile, idx=None, view=0):
     # key path and values: bit-exact with the FP32 oracle
     np.testing.assert_array_equal(rec[vis, 0], pr["xy"][vis, 0])
     np.testing.assert_array_equal(rec[vis, 1], pr["xy"][vis, 1])
-    np.testing.assert_array_equal(rec[vis, 3], pr["depth"][vis])
-    np.testing.assert_array_equal(rec[vis, 7], pr["radius"][vis].astype(np.float32))
+    np.testing.assert_array_equal(rec[vis, 2], pr["arrays"][0][vis, 3])
+    dk = a["depth_keys"][j0:j1][vis]
+    np.testing.assert_array_equal(dk & np.uint64(0xFFFFFFFF), pr["depth"][vis].view(np.uint32).astype(np.uint64))
+    np.testing.assert_array_equal(dk >> np.uint64(32), np.full(int(vis.sum()), view, np.uint64))
+    rc = a["rects"][j0:j1][vis].astype(np.int64)
+    np.testing.assert_array_equal(rc[:, 0] & 0xFFFF, pr["rect"][vis, 0])
+    np.testing.assert_array_equal(rc[:, 0] >> 16, pr["rect"][vis, 1])
+    np.testing.assert_array_equal(rc[:, 1] & 0xFFFF, pr["rect"][vis, 2])
+    np.testing.assert_array_equal(rc[:, 1] >> 16, pr["rect"][vis, 3])
     np.testing.assert_array_equal(rec[vis, 4:7], pr["conic"][vis])
     np.testing.assert_array_equal(rec[vis, 8:11], pr["rgb"][vis])
     # sorted (tile, depth, index) entries and ranges: bit-exact
@@ -89,6 +96,22 @@ def test_ragged_image_and_sh_degrees(seed):
     for tile in (16, 8):
         g = gpu_render(sc, [cam], tile=tile)
         check_against_oracle(sc, cam, g, tile)
+
+
+@pytest.mark.parametrize("tile", [16, 8])
+def test_elongated_and_opaque_gaussians(tile):
+    """Needle-like covariances (one tiny axis), opacities near 1 and below 1/255: the warp
+    skip must never drop a pair the per-pixel test would blend."""
+    r = np.random.default_rng(31)
+    sc = synth.random_cube_scene(1500, seed=31, sh_degree=0, log_scale_mu=-2.5)
+    sc["scale"][:500, 0] = np.float32(1e-4)          # flat / needle Gaussians
+    sc["scale"][500:700, :2] = np.float32(2e-4)
+    sc["mean_opac"][:300, 3] = r.uniform(0.95, 0.9999, size=300).astype(np.float32)
+    sc["mean_opac"][1200:1300, 3] = r.uniform(0.0, 1.0 / 255.0, size=100).astype(np.float32)
+    sc = synth.single_block(sc)
+    cam = synth.small_scene_camera(120, 90, f=110.0, dist=3.2)
+    g = gpu_render(sc, [cam], tile=tile)
+    check_against_oracle(sc, cam, g, tile)
 
 
 def test_all_culled_view_gives_background():
