@@ -63,6 +63,25 @@ __device__ __forceinline__ bool warp_culled(const float4& a, const float4& b, fl
     return dx > a.w || dy > b.w;
 }
 
+// Bit w set: the Gaussian's 1/255 extent box meets warp w's 8 x 4 pixel block of the tile
+// whose top-left pixel is (tx0, ty0).
+template <int B>
+__device__ __forceinline__ uint32_t warp_mask(const float4& a, const float4& b, float tx0, float ty0)
+{
+    constexpr int NW = B * B / 32;
+    uint32_t m = 0;
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
+        const float bx0 = tx0 + (float)((w % (B / 8)) * 8), by0 = ty0 + (float)((w / (B / 8)) * 4);
+        if (!warp_culled(a, b, bx0, by0)) m |= 1u << w;
+    }
+    return m;
+}
+
+// Forward.  Staging a batch, each loading thread also records which warps its Gaussian can
+// reach; each warp then visits only those entries (ballot over 32-entry chunks), in list
+// order.  n_contrib and the evaluated-pair count keep the semantics of a walk over the full
+// list: entries up to and including the stopping one, or the whole list.
 template <int B, int BATCH>
 __global__ void __launch_bounds__(B * B) k_render_fwd(Layout L, const uint32_t* __restrict__ tval, float bg0, float bg1,
                                                       float bg2, float* __restrict__ image, float* __restrict__ final_T,
@@ -70,6 +89,7 @@ __global__ void __launch_bounds__(B * B) k_render_fwd(Layout L, const uint32_t* 
 {
     constexpr int NT = B * B;
     __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
+    __shared__ uint32_t s_m[BATCH];
     const int v = blockIdx.z;
     const int tile = blockIdx.y * L.tiles_x + blockIdx.x;
     const uint2 rg = reinterpret_cast<const uint2*>(L.ranges)[(size_t)v * L.T + tile];
@@ -78,39 +98,57 @@ __global__ void __launch_bounds__(B * B) k_render_fwd(Layout L, const uint32_t* 
     const int px = blockIdx.x * B + lx, py = blockIdx.y * B + ly;
     const bool inside = px < L.W && py < L.H;
     const float fpx = (float)px, fpy = (float)py;
-    const float bx0 = (float)(blockIdx.x * B + wx0), by0 = (float)(blockIdx.y * B + wy0);
+    const float tx0 = (float)(blockIdx.x * B), ty0 = (float)(blockIdx.y * B);
+    const int lane = threadIdx.x & 31;
+    const uint32_t wbit = 1u << (threadIdx.x >> 5);
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-    uint32_t last = 0, visited = 0;
+    uint32_t last = 0;
+    uint32_t stop_at = 0xffffffffu;  // list position of the stopping entry
     bool done = !inside;
     for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
         if (__syncthreads_count(done) == NT) break;
         const uint32_t idx = start + threadIdx.x;
-        if (threadIdx.x < BATCH && idx < rg.y) {
-            const size_t j = tval[idx];
-            s_a[threadIdx.x] = L.rec[3 * j];
-            s_b[threadIdx.x] = L.rec[3 * j + 1];
-            s_c[threadIdx.x] = L.rec[3 * j + 2];
+        if (threadIdx.x < BATCH) {
+            uint32_t m = 0;
+            if (idx < rg.y) {
+                const size_t j = tval[idx];
+                const float4 a = L.rec[3 * j], b = L.rec[3 * j + 1];
+                s_a[threadIdx.x] = a;
+                s_b[threadIdx.x] = b;
+                s_c[threadIdx.x] = L.rec[3 * j + 2];
+                m = warp_mask<B>(a, b, tx0, ty0);
+            }
+            s_m[threadIdx.x] = m;
         }
         __syncthreads();
         const int nb = (int)min((uint32_t)BATCH, rg.y - start);
-        for (int k = 0; !done && k < nb; k++) {
-            visited++;
-            const float4 a = s_a[k], b = s_b[k];
-            if (warp_culled(a, b, bx0, by0)) continue;
-            float dx, dy;
-            const float power = pair_power(a, b, fpx, fpy, &dx, &dy);
-            if (power > 0.0f) continue;
-            const float alpha = fminf(0.99f, __fmul_rn(a.z, __expf(power)));
-            if (alpha < 1.0f / 255.0f) continue;
-            const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
-            if (Tn < 1e-4f) { done = true; break; }
-            const float4 c = s_c[k];
-            const float w = alpha * T;
-            C0 += c.x * w;
-            C1 += c.y * w;
-            C2 += c.z * w;
-            T = Tn;
-            last = start - rg.x + (uint32_t)k + 1u;
+        for (int c0 = 0; c0 < nb; c0 += 32) {
+            if (__all_sync(0xffffffffu, done)) break;
+            uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < nb && (s_m[c0 + lane] & wbit));
+            while (bits) {
+                const int k = c0 + __ffs(bits) - 1;
+                bits &= bits - 1;
+                if (done) continue;
+                const float4 a = s_a[k], b = s_b[k];
+                float dx, dy;
+                const float power = pair_power(a, b, fpx, fpy, &dx, &dy);
+                if (power > 0.0f) continue;
+                const float alpha = fminf(0.99f, __fmul_rn(a.z, __expf(power)));
+                if (alpha < 1.0f / 255.0f) continue;
+                const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+                if (Tn < 1e-4f) {
+                    done = true;
+                    stop_at = start - rg.x + (uint32_t)k;
+                    continue;
+                }
+                const float4 c = s_c[k];
+                const float w = alpha * T;
+                C0 += c.x * w;
+                C1 += c.y * w;
+                C2 += c.z * w;
+                T = Tn;
+                last = start - rg.x + (uint32_t)k + 1u;
+            }
         }
     }
     if (inside) {
@@ -121,8 +159,10 @@ __global__ void __launch_bounds__(B * B) k_render_fwd(Layout L, const uint32_t* 
         final_T[(size_t)v * HW + pix] = T;
         n_contrib[(size_t)v * HW + pix] = last;
     }
+    const uint32_t len = rg.y - rg.x;
+    const uint32_t visited = inside ? (stop_at != 0xffffffffu ? stop_at + 1u : len) : 0u;
     const uint32_t ws = __reduce_add_sync(0xffffffffu, visited);
-    if ((threadIdx.x & 31) == 0 && ws) atomicAdd(&L.hdr->pairs_fwd, (unsigned long long)ws);
+    if (lane == 0 && ws) atomicAdd(&L.hdr->pairs_fwd, (unsigned long long)ws);
 }
 
 // Backward: each pixel replays its blended entries from the last one (n_contrib) to the
@@ -130,8 +170,10 @@ __global__ void __launch_bounds__(B * B) k_render_fwd(Layout L, const uint32_t* 
 // transmittance.  With S_i = sum_{m > i} alpha_m T_m c_m + T_end bg:
 //   dP/dc_i = alpha_i T_i,  dP/dalpha_i = T_i c_i - S_i / (1 - alpha_i),
 //   alpha = min(0.99, o G), G = exp(power): dalpha/do = G, dalpha/dpower = o G (not clamped).
-// Per entry, the nine screen-space gradients are summed over the warp, then over the CTA in
-// shared memory, then added once per (tile, Gaussian) to the global accumulator.
+// A warp visits only the entries its pixels can reach (staged warp masks) and that lie
+// before its last blended position.  Per entry, the nine screen-space gradients are summed
+// over the warp, then over the CTA in shared memory, then added once per (tile, Gaussian)
+// to the global accumulator.
 template <int B, int BATCH>
 __global__ void __launch_bounds__(B * B) k_render_bwd(Layout L, const uint32_t* __restrict__ tval, float bg0, float bg1,
                                                       float bg2, const float* __restrict__ dL_dimg,
@@ -140,7 +182,7 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(Layout L, const uint32_t* 
 {
     constexpr int NT = B * B;
     __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
-    __shared__ uint32_t s_j[BATCH];
+    __shared__ uint32_t s_j[BATCH], s_m[BATCH];
     __shared__ float s_g[BATCH][9];
     __shared__ uint32_t s_maxnc;
     const int v = blockIdx.z;
@@ -151,8 +193,9 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(Layout L, const uint32_t* 
     const int px = blockIdx.x * B + lx, py = blockIdx.y * B + ly;
     const bool inside = px < L.W && py < L.H;
     const float fpx = (float)px, fpy = (float)py;
-    const float bx0 = (float)(blockIdx.x * B + wx0), by0 = (float)(blockIdx.y * B + wy0);
+    const float tx0 = (float)(blockIdx.x * B), ty0 = (float)(blockIdx.y * B);
     const int lane = threadIdx.x & 31;
+    const uint32_t wbit = 1u << (threadIdx.x >> 5);
     const size_t HW = (size_t)L.W * L.H, pix = (size_t)py * L.W + px;
     float T = 1.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
     uint32_t nc = 0;
@@ -172,8 +215,7 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(Layout L, const uint32_t* 
     // n_contrib never exceeds the tile's list length; clamp so a mismatched buffer cannot
     // move the replay outside this tile's entries
     const long long end = (first + s_maxnc) < (long long)rg.y ? (first + s_maxnc) : (long long)rg.y;
-    // last list position any pixel of this warp blends: entries past it are skipped whole
-    uint32_t wmax = nc;
+    uint32_t wmax = nc;  // entries at or past the warp's last blended position are skipped
 #pragma unroll
     for (int o = 16; o; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
     uint32_t pairs = 0;
@@ -181,61 +223,72 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(Layout L, const uint32_t* 
         const long long bs = (be - BATCH) > first ? (be - BATCH) : first;
         const int nb = (int)(be - bs);
         __syncthreads();
-        if (threadIdx.x < nb) {
-            const uint32_t j = tval[bs + threadIdx.x];
-            s_j[threadIdx.x] = j;
-            s_a[threadIdx.x] = L.rec[3 * (size_t)j];
-            s_b[threadIdx.x] = L.rec[3 * (size_t)j + 1];
-            s_c[threadIdx.x] = L.rec[3 * (size_t)j + 2];
+        if (threadIdx.x < BATCH) {
+            uint32_t m = 0;
+            if (threadIdx.x < nb) {
+                const uint32_t j = tval[bs + threadIdx.x];
+                const float4 a = L.rec[3 * (size_t)j], b = L.rec[3 * (size_t)j + 1];
+                s_j[threadIdx.x] = j;
+                s_a[threadIdx.x] = a;
+                s_b[threadIdx.x] = b;
+                s_c[threadIdx.x] = L.rec[3 * (size_t)j + 2];
+                m = warp_mask<B>(a, b, tx0, ty0);
+            }
+            s_m[threadIdx.x] = m;
         }
         for (int i = threadIdx.x; i < 9 * BATCH; i += NT) (&s_g[0][0])[i] = 0.0f;
         __syncthreads();
-        for (int k = nb - 1; k >= 0; k--) {
-            const uint32_t lp = (uint32_t)(bs + k - first);
-            if (lp >= wmax) continue;  // warp-uniform
-            const float4 a = s_a[k], b = s_b[k];
-            if (warp_culled(a, b, bx0, by0)) continue;  // warp-uniform
-            bool contrib = lp < nc;
-            float dx, dy;
-            float G = 0.0f, alpha = 0.0f;
-            if (contrib) {
-                const float power = pair_power(a, b, fpx, fpy, &dx, &dy);
-                if (power > 0.0f) contrib = false;
-                else {
-                    G = __expf(power);
-                    alpha = fminf(0.99f, __fmul_rn(a.z, G));
-                    if (alpha < 1.0f / 255.0f) contrib = false;
+        const int kmax = (int)min((long long)nb, (long long)wmax - (bs - first));  // entries k < kmax
+        for (int c0 = ((kmax - 1) & ~31); kmax > 0 && c0 >= 0; c0 -= 32) {
+            uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < kmax && (s_m[c0 + lane] & wbit));
+            while (bits) {
+                const int hb = 31 - __clz(bits);
+                bits &= ~(1u << hb);
+                const int k = c0 + hb;
+                const uint32_t lp = (uint32_t)(bs + k - first);
+                const float4 a = s_a[k], b = s_b[k];
+                bool contrib = lp < nc;
+                float dx, dy;
+                float G = 0.0f, alpha = 0.0f;
+                if (contrib) {
+                    const float power = pair_power(a, b, fpx, fpy, &dx, &dy);
+                    if (power > 0.0f) contrib = false;
+                    else {
+                        G = __expf(power);
+                        alpha = fminf(0.99f, __fmul_rn(a.z, G));
+                        if (alpha < 1.0f / 255.0f) contrib = false;
+                    }
                 }
-            }
-            float gr[16];
+                float gr[16];
 #pragma unroll
-            for (int c = 0; c < 16; c++) gr[c] = 0.0f;
-            if (contrib) {
-                pairs++;
-                const float oma = 1.0f - alpha;
-                T = T / oma;
-                const float4 c = s_c[k];
-                const float dal = g0 * (T * c.x - S0 / oma) + g1 * (T * c.y - S1 / oma) + g2 * (T * c.z - S2 / oma);
-                const float aT = alpha * T;
-                S0 += aT * c.x;
-                S1 += aT * c.y;
-                S2 += aT * c.z;
-                gr[6] = g0 * aT;
-                gr[7] = g1 * aT;
-                gr[8] = g2 * aT;
-                if (!(__fmul_rn(a.z, G) > 0.99f)) {
-                    gr[5] = dal * G;
-                    const float dp = dal * a.z * G;
-                    gr[2] = dp * (-0.5f * dx * dx);
-                    gr[3] = dp * (-(dx * dy));
-                    gr[4] = dp * (-0.5f * dy * dy);
-                    gr[0] = dp * (-(b.x * dx + b.y * dy));
-                    gr[1] = dp * (-(b.z * dy + b.y * dx));
+                for (int c = 0; c < 16; c++) gr[c] = 0.0f;
+                if (contrib) {
+                    pairs++;
+                    const float oma = 1.0f - alpha;
+                    T = T / oma;
+                    const float4 c = s_c[k];
+                    const float dal = g0 * (T * c.x - S0 / oma) + g1 * (T * c.y - S1 / oma) + g2 * (T * c.z - S2 / oma);
+                    const float aT = alpha * T;
+                    S0 += aT * c.x;
+                    S1 += aT * c.y;
+                    S2 += aT * c.z;
+                    gr[6] = g0 * aT;
+                    gr[7] = g1 * aT;
+                    gr[8] = g2 * aT;
+                    if (!(__fmul_rn(a.z, G) > 0.99f)) {
+                        gr[5] = dal * G;
+                        const float dp = dal * a.z * G;
+                        gr[2] = dp * (-0.5f * dx * dx);
+                        gr[3] = dp * (-(dx * dy));
+                        gr[4] = dp * (-0.5f * dy * dy);
+                        gr[0] = dp * (-(b.x * dx + b.y * dy));
+                        gr[1] = dp * (-(b.z * dy + b.y * dx));
+                    }
                 }
-            }
-            if (__any_sync(0xffffffffu, contrib)) {
-                const float tot = warp_transpose_sum16(gr, lane);
-                if ((lane & 1) == 0 && (lane >> 1) < 9) atomicAdd(&s_g[k][lane >> 1], tot);
+                if (__any_sync(0xffffffffu, contrib)) {
+                    const float tot = warp_transpose_sum16(gr, lane);
+                    if ((lane & 1) == 0 && (lane >> 1) < 9) atomicAdd(&s_g[k][lane >> 1], tot);
+                }
             }
         }
         __syncthreads();

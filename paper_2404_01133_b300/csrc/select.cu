@@ -6,42 +6,53 @@
 namespace cgs {
 
 // Level of block b seen from camera c: -1 culled or empty, else 0..n_levels-1.
-// The box corners in front of the camera are projected; the block is visible if their
-// screen bounding box overlaps the image; the block whose ground cell holds the camera
-// centre is always kept; the level follows the minimum corner-to-camera distance.
-__device__ int lod_level(const cgs_scene& S, int b, const cgs_camera& c, double near_z, double d1, double d2)
+// Called by an aligned group of 8 lanes, lane `k` of the group handling box corner k; every
+// lane of the warp must call it (inactive groups pass b < 0).  The corners of the box in
+// front of the camera are projected; the block is visible if their screen bounding box
+// overlaps the image; the block whose ground cell holds the camera centre is always kept;
+// the level follows the minimum corner-to-camera distance.  sqrt is monotone and correctly
+// rounded, so the minimum distance is sqrt of the minimum squared distance, bit for bit.
+__device__ int lod_level8(const cgs_scene& S, int b, const cgs_camera& c, double near_z, double d1, double d2)
 {
-    if (S.level_count[(long long)b * S.n_levels] <= 0) return -1;
-    const float* bb = S.block_aabb + 6 * (long long)b;
-    double R[9], t[3], cp[3];
-    for (int i = 0; i < 9; i++) R[i] = (double)c.R[i];
-    for (int i = 0; i < 3; i++) { t[i] = (double)c.t[i]; cp[i] = (double)c.campos[i]; }
-    const double fx = c.fx, fy = c.fy, cx = c.cx, cy = c.cy, Wd = c.width, Hd = c.height;
-    bool any_front = false;
-    double xmin = 0, xmax = 0, ymin = 0, ymax = 0, dmin = 0;
-    for (int k = 0; k < 8; k++) {
+    const int k = threadIdx.x & 7;
+    const bool active = b >= 0 && b < S.n_blocks && S.level_count[(long long)(b < 0 ? 0 : b) * S.n_levels] > 0;
+    double e2 = INFINITY, xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY;
+    int front = 0;
+    const double cp0 = (double)c.campos[0], cp1 = (double)c.campos[1], cp2 = (double)c.campos[2];
+    if (active) {
+        const float* bb = S.block_aabb + 6 * (long long)b;
         const double p0 = (double)bb[(k & 1) ? 3 : 0], p1 = (double)bb[(k & 2) ? 4 : 1], p2 = (double)bb[(k & 4) ? 5 : 2];
-        const double e0 = p0 - cp[0], e1 = p1 - cp[1], e2 = p2 - cp[2];
-        const double dist = sqrt((e0 * e0 + e1 * e1) + e2 * e2);
-        if (k == 0 || dist < dmin) dmin = dist;
+        const double e0 = p0 - cp0, ee1 = p1 - cp1, ee2 = p2 - cp2;
+        e2 = (e0 * e0 + ee1 * ee1) + ee2 * ee2;
+        double R[9], t[3];
+        for (int i = 0; i < 9; i++) R[i] = (double)c.R[i];
+        for (int i = 0; i < 3; i++) t[i] = (double)c.t[i];
         const double tx = ((R[0] * p0 + R[1] * p1) + R[2] * p2) + t[0];
         const double ty = ((R[3] * p0 + R[4] * p1) + R[5] * p2) + t[1];
         const double tz = ((R[6] * p0 + R[7] * p1) + R[8] * p2) + t[2];
-        if (!(tz > near_z)) continue;
-        const double u = (fx * tx) / tz + cx, v = (fy * ty) / tz + cy;
-        if (!any_front) { xmin = xmax = u; ymin = ymax = v; any_front = true; }
-        else {
-            if (u < xmin) xmin = u;
-            if (u > xmax) xmax = u;
-            if (v < ymin) ymin = v;
-            if (v > ymax) ymax = v;
+        if (tz > near_z) {
+            front = 1;
+            const double u = ((double)c.fx * tx) / tz + (double)c.cx, v = ((double)c.fy * ty) / tz + (double)c.cy;
+            xmin = xmax = u;
+            ymin = ymax = v;
         }
     }
-    const bool visible = any_front && xmax > -0.5 && xmin < Wd - 0.5 && ymax > -0.5 && ymin < Hd - 0.5;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        e2 = fmin(e2, __shfl_xor_sync(0xffffffffu, e2, o, 8));
+        xmin = fmin(xmin, __shfl_xor_sync(0xffffffffu, xmin, o, 8));
+        xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o, 8));
+        ymin = fmin(ymin, __shfl_xor_sync(0xffffffffu, ymin, o, 8));
+        ymax = fmax(ymax, __shfl_xor_sync(0xffffffffu, ymax, o, 8));
+        front |= __shfl_xor_sync(0xffffffffu, front, o, 8);
+    }
+    if (!active) return -1;
+    const double Wd = c.width, Hd = c.height;
+    const bool visible = front && xmax > -0.5 && xmin < Wd - 0.5 && ymax > -0.5 && ymin < Hd - 0.5;
     const float* ce = S.block_cell + 4 * (long long)b;
-    const bool inside = cp[0] >= (double)ce[0] && cp[0] < (double)ce[1] && cp[1] >= (double)ce[2] &&
-                        cp[1] < (double)ce[3];
+    const bool inside = cp0 >= (double)ce[0] && cp0 < (double)ce[1] && cp1 >= (double)ce[2] && cp1 < (double)ce[3];
     if (!visible && !inside) return -1;
+    const double dmin = sqrt(e2);
     int lv = dmin < d1 ? 0 : (dmin < d2 ? 1 : 2);
     if (lv > S.n_levels - 1) lv = S.n_levels - 1;
     return lv;
@@ -53,9 +64,12 @@ __global__ void k_lod_levels(cgs_scene S, const cgs_camera* __restrict__ cams, i
     const int v = blockIdx.x;
     if (v >= n_views) return;
     const cgs_camera c = cams[v];
-    for (int b = threadIdx.x; b < S.n_blocks; b += blockDim.x)
-        levels[(long long)v * S.n_blocks + b] =
-            (int8_t)lod_level(S, b, c, (double)cfg.near_z, cfg.lod_dist[0], cfg.lod_dist[1]);
+    const int groups = blockDim.x >> 3;
+    for (int b0 = 0; b0 < S.n_blocks; b0 += groups) {
+        const int b = b0 + (threadIdx.x >> 3);
+        const int l = lod_level8(S, b < S.n_blocks ? b : -1, c, (double)cfg.near_z, cfg.lod_dist[0], cfg.lod_dist[1]);
+        if (b < S.n_blocks && (threadIdx.x & 7) == 0) levels[(long long)v * S.n_blocks + b] = (int8_t)l;
+    }
 }
 
 // Per view: the level of every block (given, one training block, or LoD), then the ordered
@@ -67,19 +81,29 @@ __global__ void k_select(Layout L, cgs_scene S, const cgs_camera* __restrict__ c
     const int NB = S.n_blocks, NL = S.n_levels;
     int8_t* lev = L.levels + (long long)v * NB;
     const cgs_camera c = cams[v];
-    for (int b = threadIdx.x; b < NB; b += blockDim.x) {
-        int l;
-        if (levels_in) {
-            l = levels_in[(long long)v * NB + b];
-            if (l >= NL) l = NL - 1;
-            if (l < 0) l = -1;
-        } else if (view_block) {
-            l = (b == view_block[v]) ? 0 : -1;
-        } else {
-            l = lod_level(S, b, c, (double)cfg.near_z, cfg.lod_dist[0], cfg.lod_dist[1]);
+    if (levels_in || view_block) {
+        for (int b = threadIdx.x; b < NB; b += blockDim.x) {
+            int l;
+            if (levels_in) {
+                l = levels_in[(long long)v * NB + b];
+                if (l >= NL) l = NL - 1;
+                if (l < 0) l = -1;
+            } else {
+                l = (b == view_block[v]) ? 0 : -1;
+            }
+            if (l >= 0 && S.level_count[(long long)b * NL + l] <= 0) l = -1;
+            lev[b] = (int8_t)l;
         }
-        if (l >= 0 && S.level_count[(long long)b * NL + l] <= 0) l = -1;
-        lev[b] = (int8_t)l;
+    } else {
+        const int groups = blockDim.x >> 3;
+        for (int b0 = 0; b0 < NB; b0 += groups) {
+            const int b = b0 + (threadIdx.x >> 3);
+            int l = lod_level8(S, b < NB ? b : -1, c, (double)cfg.near_z, cfg.lod_dist[0], cfg.lod_dist[1]);
+            if (b < NB && (threadIdx.x & 7) == 0) {
+                if (l >= 0 && S.level_count[(long long)b * NL + l] <= 0) l = -1;
+                lev[b] = (int8_t)l;
+            }
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -244,14 +268,14 @@ __global__ void __launch_bounds__(256) k_block_bounds(cgs_scene S, double n_mad,
 void launch_select(const Layout& L, const cgs_scene& S, const cgs_camera* cams, const int32_t* view_block,
                    const int8_t* levels, const cgs_config& cfg, cudaStream_t st)
 {
-    k_select<<<L.V, 128, 0, st>>>(L, S, cams, view_block, levels, cfg);
+    k_select<<<L.V, 256, 0, st>>>(L, S, cams, view_block, levels, cfg);
     k_select_finish<<<1, 1024, 0, st>>>(L);
 }
 
 void launch_lod_levels(const cgs_scene& S, const cgs_config& cfg, const cgs_camera* cams, int n_views,
                        int8_t* levels, cudaStream_t st)
 {
-    k_lod_levels<<<n_views, 128, 0, st>>>(S, cams, n_views, cfg, levels);
+    k_lod_levels<<<n_views, 256, 0, st>>>(S, cams, n_views, cfg, levels);
 }
 
 void launch_block_bounds(const cgs_scene& S, double n_mad, float* aabb, cudaStream_t st)

