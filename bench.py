@@ -244,15 +244,16 @@ def run_ours(args, world, rank, local):
     nc_coef = (sc["sh_degree"] + 1) ** 2
     peaks, peak_src = load_peaks()
     alu_peak = 148 * 128 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12  # FP32 lane-ops / s, in T/s
-    depth_passes, tile_passes = 4, 2
+    n_tiles = ((W + args.tile - 1) // args.tile) * ((H + args.tile - 1) // args.tile)
     work = {
         # algorithmic bytes per launch (HBM-bound stages)
-        # mean+opacity read and tiles-touched write for every selected Gaussian; scale, rotation,
-        # SH read and record, rect, key write for the visible ones; compaction and colour pass
-        "project": ("hbm", n_sel * (16 + 4 + 4) + n_vis * (32 + 12 * nc_coef + 48 + 8 + 8 + 12)),
-        "depth_sort": ("hbm", n_vis * 8 + depth_passes * n_vis * 24),
-        "emit": ("hbm", n_vis * (4 + 4 + 8 + 8) + k_ent * 8),
-        "tile_sort": ("hbm", k_ent * 4 + tile_passes * k_ent * 16 + k_ent * 4),
+        # projection: mean+opacity read and tiles-touched write for every selected Gaussian;
+        # scale, rotation, SH read and record, rect, key write for the visible ones; compaction
+        "project": ("hbm", n_sel * (16 + 4 + 4) + n_vis * (32 + 12 * nc_coef + 48 + 8 + 8 + 4)),
+        # offsets read/write per visible Gaussian, one 8-byte entry written per (tile, Gaussian)
+        "duplicate": ("hbm", n_vis * 12 + k_ent * 8),
+        # per entry: read entry, write key, read key, write value; per tile: count and range
+        "sort": ("hbm", k_ent * (8 + 8 + 8 + 4) + n_tiles * 12),
         # algorithmic FP32 operations per launch (issue-bound stages)
         "render": ("alu", pairs_b * FP32_OPS_PER_FWD_PAIR),
         "render_bwd": ("alu", pairs_b * FP32_OPS_PER_BWD_PAIR),

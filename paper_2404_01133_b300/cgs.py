@@ -22,7 +22,7 @@ CGS_ERR_CUDA = 5
 CGS_ERR_UNSUPPORTED = 6
 
 BUF_TILE_KEYS, BUF_TILE_VALS, BUF_RANGES, BUF_SCENE_INDEX, BUF_RECORDS, BUF_TILES_TOUCHED, BUF_VIEW_BASE, \
-    BUF_DEPTH_ORDER, BUF_DEPTH_KEYS, BUF_RECTS = range(10)
+    BUF_VISIBLE, BUF_DEPTH_KEYS, BUF_RECTS = range(10)
 
 
 class cgs_camera(C.Structure):
@@ -178,7 +178,7 @@ def cgs_frame_status(frame, stream=None):
     return st.value, list(counts)
 
 
-STAGES = ("select", "project", "depth_sort", "emit", "tile_sort", "render", "render_bwd", "project_bwd", "loss")
+STAGES = ("select", "project", "duplicate", "sort", "render", "render_bwd", "project_bwd", "loss")
 
 
 def cgs_timing_enable(on):

@@ -15,9 +15,8 @@ void launch_project(const Layout& L, const cgs_scene& S, const cgs_camera* cams,
                     cudaStream_t st);
 void launch_colour(const Layout& L, const cgs_scene& S, const cgs_camera* cams, int n_sm, cudaStream_t st);
 int launch_compact(const Layout& L, int n_sm, cudaStream_t st);
-int launch_depth_sort(const Layout& L, int n_sm, cudaStream_t st);
-int launch_emit_stage(const Layout& L, int n_sm, cudaStream_t st);
-int launch_tile_stage(const Layout& L, int n_sm, cudaStream_t st);
+int launch_duplicate(const Layout& L, int n_sm, cudaStream_t st);
+int launch_tile_sort(const Layout& L, int n_sm, cudaStream_t st);
 bool launch_render_fwd(const Layout& L, const cgs_config& c, float* img, float* T, uint32_t* nc, cudaStream_t st);
 bool launch_render_bwd(const Layout& L, const cgs_config& c, const float* dimg, const float* T, const uint32_t* nc,
                        cudaStream_t st);
@@ -99,22 +98,17 @@ static bool make_layout(const cgs_frame* f, Layout* L, size_t* bytes)
     l.NB = f->n_blocks;
     l.n_cap = f->n_cap;
     l.k_cap = f->k_cap;
-    const int view_bits = bits_for((unsigned long long)l.V);
-    l.depth_passes = (32 + view_bits + 7) / 8;
-    int tb = bits_for((unsigned long long)l.V * l.T);
-    if (tb < 1) tb = 1;
-    l.tile_passes = (tb + 7) / 8;
-    l.depth_sorted = l.depth_passes & 1;
-    l.tile_sorted = l.tile_passes & 1;
+    const long long vt = (long long)l.V * l.T;
+    l.scan_tiles_n = (l.n_cap + SCAN_TILE - 1) / SCAN_TILE;
+    const long long scan_tiles_vt = (vt + SCAN_TILE - 1) / SCAN_TILE;
 
     Carver c{(char*)f->ws, 0};
     l.hdr = c.take<Header>(1);
-    l.hist_depth = c.take<uint32_t>(MAX_DEPTH_PASSES * 256);
-    l.hist_tile = c.take<uint32_t>(MAX_TILE_PASSES * 256);
-    const long long scan_tiles = (l.n_cap + SCAN_TILE - 1) / SCAN_TILE;
-    l.scan_lb = c.take<unsigned long long>(2 * scan_tiles);
-    l.ranges = c.take<uint32_t>(2LL * l.V * l.T);
+    l.scan_lb = c.take<unsigned long long>(2 * l.scan_tiles_n + scan_tiles_vt);
+    l.tcnt = c.take<uint32_t>(vt);
+    l.tcur = c.take<uint32_t>(vt);
     l.zero_bytes = c.off;
+    l.ranges = c.take<uint32_t>(2 * vt);
     l.view_base = c.take<uint32_t>(l.V + 1);
     l.view_cnt = c.take<uint32_t>(l.V);
     l.n_seg = c.take<uint32_t>(l.V);
@@ -126,18 +120,13 @@ static bool make_layout(const cgs_frame* f, Layout* L, size_t* bytes)
     l.tt = c.take<uint32_t>(l.n_cap);
     l.gidx = c.take<uint32_t>(l.n_cap);
     l.pkey = c.take<unsigned long long>(l.n_cap);
-    for (int i = 0; i < 2; i++) {
-        l.dkey[i] = c.take<unsigned long long>(l.n_cap);
-        l.dval[i] = c.take<uint32_t>(l.n_cap);
-    }
+    l.vis = c.take<uint32_t>(l.n_cap);
     l.offs = c.take<uint32_t>(l.n_cap);
-    for (int i = 0; i < 2; i++) {
-        l.tkey[i] = c.take<uint32_t>(l.k_cap);
-        l.tval[i] = c.take<uint32_t>(l.k_cap);
-    }
-    const long long dt = (l.n_cap + 2047) / 2048, kt = (l.k_cap + 3071) / 3072;
-    l.sort_tiles_max = dt > kt ? dt : kt;
-    for (int i = 0; i < 2; i++) l.lb[i] = c.take<uint32_t>(256 * l.sort_tiles_max);
+    l.eraw = c.take<unsigned long long>(l.k_cap);
+    l.ekey = c.take<unsigned long long>(l.k_cap);
+    l.tval = c.take<uint32_t>(l.k_cap);
+    l.tkey = c.take<uint32_t>(l.k_cap);
+    l.big = c.take<uint32_t>(vt);
     l.gs = c.take<float4>(3 * l.n_cap);
     *L = l;
     *bytes = c.off;
@@ -270,16 +259,12 @@ int32_t cgs_render_forward(const cgs_scene* scene, const cgs_frame* frame, const
         counted(1);
     }
     {
-        StageScope s(CGS_STAGE_DEPTH_SORT, st);
-        counted(launch_depth_sort(L, n_sm, st));
+        StageScope s(CGS_STAGE_DUPLICATE, st);
+        counted(launch_duplicate(L, n_sm, st));
     }
     {
-        StageScope s(CGS_STAGE_EMIT, st);
-        counted(launch_emit_stage(L, n_sm, st));
-    }
-    {
-        StageScope s(CGS_STAGE_TILE_SORT, st);
-        counted(launch_tile_stage(L, n_sm, st));
+        StageScope s(CGS_STAGE_SORT, st);
+        counted(launch_tile_sort(L, n_sm, st));
     }
     {
         StageScope s(CGS_STAGE_RENDER, st);
@@ -393,14 +378,14 @@ int32_t cgs_frame_buffer(const cgs_frame* frame, int32_t which, void** d_ptr, in
     void* p = nullptr;
     int64_t n = 0;
     switch (which) {
-        case 0: p = L.tkey[L.tile_sorted]; n = L.k_cap; break;
-        case 1: p = L.tval[L.tile_sorted]; n = L.k_cap; break;
+        case 0: p = L.tkey; n = L.k_cap; break;
+        case 1: p = L.tval; n = L.k_cap; break;
         case 2: p = L.ranges; n = (int64_t)L.V * L.T; break;
         case 3: p = L.gidx; n = L.n_cap; break;
         case 4: p = L.rec; n = L.n_cap; break;
         case 5: p = L.tt; n = L.n_cap; break;
         case 6: p = L.view_base; n = L.V + 1; break;
-        case 7: p = L.dval[L.depth_sorted]; n = L.n_cap; break;
+        case 7: p = L.vis; n = L.n_cap; break;
         case 8: p = L.pkey; n = L.n_cap; break;
         case 9: p = L.rect; n = L.n_cap; break;
         default: return CGS_ERR_INVALID_ARGUMENT;

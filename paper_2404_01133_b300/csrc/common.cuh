@@ -13,8 +13,8 @@ namespace cgs {
 // ---------------------------------------------------------------------------------------
 enum : uint32_t { ST_CAPACITY = 1u << 0, ST_SPIN = 1u << 1, ST_UNSUPPORTED = 1u << 2 };
 
-// Dynamic tile counters of the single-pass (decoupled look-back) kernels.
-enum { CTR_DEPTH_PASS0 = 0, CTR_TILE_PASS0 = 8, CTR_SCAN_COMPACT = 16, CTR_SCAN_EMIT = 17, N_CTR = 24 };
+// Dynamic work counters of the single-pass (decoupled look-back) and persistent kernels.
+enum { CTR_SCAN_COMPACT = 0, CTR_SCAN_OFFSETS = 1, CTR_SCAN_RANGES = 2, CTR_BIG = 3, N_CTR = 8 };
 
 struct Header {
     uint32_t status;
@@ -26,31 +26,26 @@ struct Header {
     unsigned long long pairs_fwd;
     unsigned long long pairs_bwd;
     uint32_t spin_giveups;
-    uint32_t _pad;
+    uint32_t n_big;        // tiles too long for the shared-memory sort
     uint32_t ctr[N_CTR];
 };
 
 // Polls of a look-back flag before a kernel gives up and latches ST_SPIN.
 constexpr int SPIN_LIMIT = 1 << 22;
 
-constexpr int SORT_THREADS = 256;
-constexpr int SORT_IPT = 12;                       // keys per thread per tile
-constexpr int SORT_TILE = SORT_THREADS * SORT_IPT; // 3072 keys per look-back tile
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_IPT = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_IPT;
-constexpr int MAX_DEPTH_PASSES = 6;                // (view bits <= 16) + 32 depth bits
-constexpr int MAX_TILE_PASSES = 4;                 // view * tile id < 2^32
 
 // Pointers into one frame workspace.  Built on the host by make_layout (api.cu).
 struct Layout {
     Header* hdr;
-    // zeroed at every forward (one memset over [zero_begin, zero_end))
-    uint32_t* hist_depth;        // [MAX_DEPTH_PASSES][256]
-    uint32_t* hist_tile;         // [MAX_TILE_PASSES][256]
-    unsigned long long* scan_lb; // [2][scan tiles]
-    uint32_t* ranges;            // [V * T][2]
+    // zeroed at every forward (one memset from hdr over zero_bytes)
+    unsigned long long* scan_lb; // [2 * scan_tiles_n + scan tiles of V*T] look-back words
+    uint32_t* tcnt;              // [V * T] entries per tile
+    uint32_t* tcur;              // [V * T] scatter cursors
     // not zeroed
+    uint32_t* ranges;            // [V * T][2] [start, end) of every tile's entries
     uint32_t* view_base;         // [V + 1] exclusive prefix of per-view selected counts
     uint32_t* view_cnt;          // [V] selected count per view
     uint32_t* n_seg;             // [V]
@@ -62,20 +57,18 @@ struct Layout {
     uint32_t* tt;                // [n_cap] tiles touched
     uint32_t* gidx;              // [n_cap] scene index
     unsigned long long* pkey;    // [n_cap] view << 32 | depth bits
-    unsigned long long* dkey[2]; // [n_cap] depth sort ping-pong
-    uint32_t* dval[2];           // [n_cap]
-    uint32_t* offs;              // [n_cap] first entry of each depth-sorted visible Gaussian
-    uint32_t* tkey[2];           // [k_cap] tile sort ping-pong
-    uint32_t* tval[2];           // [k_cap]
-    uint32_t* lb[2];             // [max(sort tiles)][256] look-back, ping-pong between passes
+    uint32_t* vis;               // [n_cap] visible selected indices, ascending
+    uint32_t* offs;              // [n_cap] first entry of each visible Gaussian
+    unsigned long long* eraw;    // [k_cap] tile << 32 | j per entry; later scratch of the long-tile sort
+    unsigned long long* ekey;    // [k_cap] depth bits << 32 | j, scattered into tile ranges
+    uint32_t* tval;              // [k_cap] selected index per entry, (tile, depth, index) order
+    uint32_t* tkey;              // [k_cap] tile id per entry, same order
+    uint32_t* big;               // [V * T] tiles for the long-tile sort
     float4* gs;                  // [n_cap][3] screen-space gradients (du dv dA dB | dC do dr dg | db - - -)
     size_t zero_bytes;           // bytes to clear from hdr
     long long n_cap, k_cap;
+    long long scan_tiles_n;      // look-back tiles of a scan over n_cap items
     int V, W, H, B, tiles_x, tiles_y, T, NB;
-    int depth_passes, tile_passes;
-    int depth_sorted;            // which ping-pong buffer holds the final depth order
-    int tile_sorted;             // which ping-pong buffer holds the final tile order
-    long long sort_tiles_max;
 };
 
 // ---------------------------------------------------------------------------------------

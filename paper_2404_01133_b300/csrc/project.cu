@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) k_colour(Layout L, cgs_scene S, const cgs
     const int deg = S.sh_degree;
     const int nc = (deg + 1) * (deg + 1);
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-        const uint32_t j = L.dval[0][r];
+        const uint32_t j = L.vis[r];
         const int v = (int)(L.pkey[j] >> 32);
         const long long g = L.gidx[j];
         const float4 mo = __ldg(reinterpret_cast<const float4*>(S.mean_opac) + g);

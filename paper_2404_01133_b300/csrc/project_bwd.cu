@@ -13,9 +13,9 @@ __global__ void __launch_bounds__(128) k_project_bwd(Layout L, cgs_scene S, cons
                                                      float near_z, float* __restrict__ g_mo, float* __restrict__ g_sc,
                                                      float* __restrict__ g_q, float* __restrict__ g_sh)
 {
-    // over the (view, depth)-sorted visible Gaussians, so every lane has work
+    // over the compacted visible Gaussians, so every lane has work
     const uint32_t n = L.hdr->n_vis;
-    const uint32_t* __restrict__ vis = L.dval[L.depth_sorted];
+    const uint32_t* __restrict__ vis = L.vis;
     const int deg = S.sh_degree;
     const int nc = (deg + 1) * (deg + 1);
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {

@@ -322,7 +322,7 @@ static void bwd_launch(const Layout& L, const uint32_t* tval, const cgs_config& 
 
 bool launch_render_fwd(const Layout& L, const cgs_config& c, float* img, float* T, uint32_t* nc, cudaStream_t st)
 {
-    const uint32_t* tv = L.tval[L.tile_sorted];
+    const uint32_t* tv = L.tval;
     if (L.B == 16) {
         switch (c.batch) {
             case 32: fwd_launch<16, 32>(L, tv, c, img, T, nc, st); return true;
@@ -342,7 +342,7 @@ bool launch_render_fwd(const Layout& L, const cgs_config& c, float* img, float* 
 bool launch_render_bwd(const Layout& L, const cgs_config& c, const float* dimg, const float* T, const uint32_t* nc,
                        cudaStream_t st)
 {
-    const uint32_t* tv = L.tval[L.tile_sorted];
+    const uint32_t* tv = L.tval;
     if (L.B == 16) {
         switch (c.batch) {
             case 32: bwd_launch<16, 32>(L, tv, c, dimg, T, nc, st); return true;

@@ -111,8 +111,8 @@ def test_autograd_function_matches_direct_backward():
 
 def test_full_size_city_1m_forward_backward():
     """The 1920x1080, 1M-Gaussian SH-3 workload in the benchmark's launch configuration:
-    every key, value and range bit-exact; pixels of 48 sampled tiles and the gradients of
-    64 sampled visible Gaussians against the oracle."""
+    every key, value and range bit-exact; every pixel; the gradients of 64 sampled visible
+    Gaussians and of every attribute tensor against the FP32 and FP64 oracles."""
     sc, cams = synth.workload_city_1m()
     cam = cams[0]
     g = gpu_render(sc, cams, n_cap=1_000_000, k_cap=4_000_000)

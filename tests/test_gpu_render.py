@@ -114,6 +114,18 @@ def test_elongated_and_opaque_gaussians(tile):
     check_against_oracle(sc, cam, g, tile)
 
 
+@pytest.mark.parametrize("n", [2049, 7001])
+def test_long_tile_lists_use_the_merge_path(n):
+    """Tiles with more entries than one shared-memory sort holds (2048) are sorted by chunks
+    and merge rounds; keys, values and ranges stay bit-exact."""
+    sc = synth.single_block(synth.random_cube_scene(n, seed=n, sh_degree=0, extent=0.25, log_scale_mu=-2.0))
+    cam = synth.small_scene_camera(40, 36, f=60.0, dist=3.0)
+    g = gpu_render(sc, [cam])
+    o, _ = check_against_oracle(sc, cam, g, 16)
+    lens = o["sort"]["ranges"][:, 1] - o["sort"]["ranges"][:, 0]
+    assert lens.max() > 2048
+
+
 def test_all_culled_view_gives_background():
     sc, cams = synth.workload_small()
     cam = synth.camera_from_rt(np.diag([-1.0, 1.0, -1.0]), [0.0, 0.0, -10.0], 150, 150, 63.5, 63.5, 128, 128)
