@@ -24,13 +24,13 @@ __device__ __forceinline__ float pair_power(const float4& a, const float4& b, fl
     return __fmaf_rn(-0.5f, q, -cr);
 }
 
-// Warp sum of 16 values per lane by halving exchanges: at each step a lane keeps half of its
+// Warp sum of 32 values per lane by halving exchanges: at each step a lane keeps half of its
 // values and adds the partner's copy of that half.  On return lane l holds the warp total of
-// v[l >> 1] (16 shuffles instead of 16 x 5).
-__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], int lane)
+// v[l] (31 shuffles for 32 sums).
+__device__ __forceinline__ float warp_transpose_sum32(float (&v)[32], int lane)
 {
 #pragma unroll
-    for (int o = 16, n = 8; o >= 2; o >>= 1, n >>= 1) {
+    for (int o = 16, n = 16; o >= 1; o >>= 1, n >>= 1) {
         const bool hi = (lane & o) != 0;
 #pragma unroll
         for (int k = 0; k < n; k++) {
@@ -39,148 +39,209 @@ __device__ __forceinline__ float warp_transpose_sum16(float (&v)[16], int lane)
             v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
         }
     }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+    return v[0];
 }
 
-// Pixel of thread `tid` in a B x B tile: warps cover 8 x 4 pixel blocks (B/8 blocks per row).
+// Threads of a B x B tile: B*B/2, two pixels each.  Warp w covers the 8 x 8 block at
+// ((w % (B/8)) * 8, (w / (B/8)) * 8); lane l takes pixels (l & 7, l >> 3) and (l & 7, (l >> 3) + 4).
 template <int B>
-__device__ __forceinline__ void pixel_of(int tid, int* x, int* y, int* wx0, int* wy0)
+__device__ __forceinline__ void pixels_of(int tid, int* x, int* y0, int* wx0, int* wy0)
 {
     const int w = tid >> 5, lane = tid & 31;
     *wx0 = (w % (B / 8)) * 8;
-    *wy0 = (w / (B / 8)) * 4;
+    *wy0 = (w / (B / 8)) * 8;
     *x = *wx0 + (lane & 7);
-    *y = *wy0 + (lane >> 3);
+    *y0 = *wy0 + (lane >> 3);
 }
 
 // Whole-warp skip: true if the Gaussian's 1/255 extent box (record .w lanes) misses the
-// warp's 8 x 4 pixel block [bx0, bx0 + 7] x [by0, by0 + 3].  Skipped pairs would all fail
+// warp's 8 x 8 pixel block [bx0, bx0 + 7] x [by0, by0 + 7].  Skipped pairs would all fail
 // the alpha >= 1/255 test, so skipping changes no result.
 __device__ __forceinline__ bool warp_culled(const float4& a, const float4& b, float bx0, float by0)
 {
     const float dx = fmaxf(fmaxf(bx0 - a.x, a.x - (bx0 + 7.0f)), 0.0f);
-    const float dy = fmaxf(fmaxf(by0 - a.y, a.y - (by0 + 3.0f)), 0.0f);
+    const float dy = fmaxf(fmaxf(by0 - a.y, a.y - (by0 + 7.0f)), 0.0f);
     return dx > a.w || dy > b.w;
 }
 
-// Bit w set: the Gaussian's 1/255 extent box meets warp w's 8 x 4 pixel block of the tile
-// whose top-left pixel is (tx0, ty0).
+// Bit w set: the Gaussian's extent box meets warp w's pixel block of the tile whose top-left
+// pixel is (tx0, ty0).
 template <int B>
 __device__ __forceinline__ uint32_t warp_mask(const float4& a, const float4& b, float tx0, float ty0)
 {
-    constexpr int NW = B * B / 32;
+    constexpr int NW = B * B / 64;
     uint32_t m = 0;
 #pragma unroll
     for (int w = 0; w < NW; w++) {
-        const float bx0 = tx0 + (float)((w % (B / 8)) * 8), by0 = ty0 + (float)((w / (B / 8)) * 4);
+        const float bx0 = tx0 + (float)((w % (B / 8)) * 8), by0 = ty0 + (float)((w / (B / 8)) * 8);
         if (!warp_culled(a, b, bx0, by0)) m |= 1u << w;
     }
     return m;
 }
+
+// Forward blend of one entry into one pixel (Eq. 1 with the 3DGS thresholds).
+struct FwdPixel {
+    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
+    uint32_t last = 0, stop_at = 0xffffffffu;
+    bool done = false;
+    __device__ __forceinline__ void blend(const float4& a, const float4& b, const float4& c, float fpx, float fpy,
+                                          uint32_t pos)
+    {
+        if (done) return;
+        float dx, dy;
+        const float power = pair_power(a, b, fpx, fpy, &dx, &dy);
+        if (power > 0.0f) return;
+        const float alpha = fminf(0.99f, __fmul_rn(a.z, __expf(power)));
+        if (alpha < 1.0f / 255.0f) return;
+        const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+        if (Tn < 1e-4f) {
+            done = true;
+            stop_at = pos;
+            return;
+        }
+        const float w = alpha * T;
+        C0 += c.x * w;
+        C1 += c.y * w;
+        C2 += c.z * w;
+        T = Tn;
+        last = pos + 1u;
+    }
+};
 
 // Forward.  Staging a batch, each loading thread also records which warps its Gaussian can
 // reach; each warp then visits only those entries (ballot over 32-entry chunks), in list
 // order.  n_contrib and the evaluated-pair count keep the semantics of a walk over the full
 // list: entries up to and including the stopping one, or the whole list.
 template <int B, int BATCH>
-__global__ void __launch_bounds__(B * B) k_render_fwd(Layout L, const uint32_t* __restrict__ tval, float bg0, float bg1,
-                                                      float bg2, float* __restrict__ image, float* __restrict__ final_T,
-                                                      uint32_t* __restrict__ n_contrib)
+__global__ void __launch_bounds__(B * B / 2) k_render_fwd(Layout L, const uint32_t* __restrict__ tval, float bg0,
+                                                          float bg1, float bg2, float* __restrict__ image,
+                                                          float* __restrict__ final_T, uint32_t* __restrict__ n_contrib)
 {
-    constexpr int NT = B * B;
+    constexpr int NT = B * B / 2;
     __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
     __shared__ uint32_t s_m[BATCH];
     const int v = blockIdx.z;
     const int tile = blockIdx.y * L.tiles_x + blockIdx.x;
     const uint2 rg = reinterpret_cast<const uint2*>(L.ranges)[(size_t)v * L.T + tile];
     int lx, ly, wx0, wy0;
-    pixel_of<B>(threadIdx.x, &lx, &ly, &wx0, &wy0);
-    const int px = blockIdx.x * B + lx, py = blockIdx.y * B + ly;
-    const bool inside = px < L.W && py < L.H;
-    const float fpx = (float)px, fpy = (float)py;
+    pixels_of<B>(threadIdx.x, &lx, &ly, &wx0, &wy0);
+    const int px = blockIdx.x * B + lx, py0 = blockIdx.y * B + ly, py1 = py0 + 4;
+    const bool in0 = px < L.W && py0 < L.H, in1 = px < L.W && py1 < L.H;
+    const float fpx = (float)px, fpy0 = (float)py0, fpy1 = (float)py1;
     const float tx0 = (float)(blockIdx.x * B), ty0 = (float)(blockIdx.y * B);
     const int lane = threadIdx.x & 31;
     const uint32_t wbit = 1u << (threadIdx.x >> 5);
-    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-    uint32_t last = 0;
-    uint32_t stop_at = 0xffffffffu;  // list position of the stopping entry
-    bool done = !inside;
+    FwdPixel p0, p1;
+    p0.done = !in0;
+    p1.done = !in1;
     for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
-        if (__syncthreads_count(done) == NT) break;
-        const uint32_t idx = start + threadIdx.x;
-        if (threadIdx.x < BATCH) {
+        if (__syncthreads_count(p0.done && p1.done) == NT) break;
+        for (int i = threadIdx.x; i < BATCH; i += NT) {
             uint32_t m = 0;
-            if (idx < rg.y) {
-                const size_t j = tval[idx];
+            if (start + i < rg.y) {
+                const size_t j = tval[start + i];
                 const float4 a = L.rec[3 * j], b = L.rec[3 * j + 1];
-                s_a[threadIdx.x] = a;
-                s_b[threadIdx.x] = b;
-                s_c[threadIdx.x] = L.rec[3 * j + 2];
+                s_a[i] = a;
+                s_b[i] = b;
+                s_c[i] = L.rec[3 * j + 2];
                 m = warp_mask<B>(a, b, tx0, ty0);
             }
-            s_m[threadIdx.x] = m;
+            s_m[i] = m;
         }
         __syncthreads();
         const int nb = (int)min((uint32_t)BATCH, rg.y - start);
         for (int c0 = 0; c0 < nb; c0 += 32) {
-            if (__all_sync(0xffffffffu, done)) break;
+            if (__all_sync(0xffffffffu, p0.done && p1.done)) break;
             uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < nb && (s_m[c0 + lane] & wbit));
             while (bits) {
                 const int k = c0 + __ffs(bits) - 1;
                 bits &= bits - 1;
-                if (done) continue;
-                const float4 a = s_a[k], b = s_b[k];
-                float dx, dy;
-                const float power = pair_power(a, b, fpx, fpy, &dx, &dy);
-                if (power > 0.0f) continue;
-                const float alpha = fminf(0.99f, __fmul_rn(a.z, __expf(power)));
-                if (alpha < 1.0f / 255.0f) continue;
-                const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
-                if (Tn < 1e-4f) {
-                    done = true;
-                    stop_at = start - rg.x + (uint32_t)k;
-                    continue;
-                }
-                const float4 c = s_c[k];
-                const float w = alpha * T;
-                C0 += c.x * w;
-                C1 += c.y * w;
-                C2 += c.z * w;
-                T = Tn;
-                last = start - rg.x + (uint32_t)k + 1u;
+                const float4 a = s_a[k], b = s_b[k], c = s_c[k];
+                const uint32_t pos = start - rg.x + (uint32_t)k;
+                p0.blend(a, b, c, fpx, fpy0, pos);
+                p1.blend(a, b, c, fpx, fpy1, pos);
             }
         }
     }
-    if (inside) {
-        const size_t HW = (size_t)L.W * L.H, pix = (size_t)py * L.W + px;
-        image[(3 * (size_t)v + 0) * HW + pix] = C0 + T * bg0;
-        image[(3 * (size_t)v + 1) * HW + pix] = C1 + T * bg1;
-        image[(3 * (size_t)v + 2) * HW + pix] = C2 + T * bg2;
-        final_T[(size_t)v * HW + pix] = T;
-        n_contrib[(size_t)v * HW + pix] = last;
+    const size_t HW = (size_t)L.W * L.H;
+    if (in0) {
+        const size_t pix = (size_t)py0 * L.W + px;
+        image[(3 * (size_t)v + 0) * HW + pix] = p0.C0 + p0.T * bg0;
+        image[(3 * (size_t)v + 1) * HW + pix] = p0.C1 + p0.T * bg1;
+        image[(3 * (size_t)v + 2) * HW + pix] = p0.C2 + p0.T * bg2;
+        final_T[(size_t)v * HW + pix] = p0.T;
+        n_contrib[(size_t)v * HW + pix] = p0.last;
+    }
+    if (in1) {
+        const size_t pix = (size_t)py1 * L.W + px;
+        image[(3 * (size_t)v + 0) * HW + pix] = p1.C0 + p1.T * bg0;
+        image[(3 * (size_t)v + 1) * HW + pix] = p1.C1 + p1.T * bg1;
+        image[(3 * (size_t)v + 2) * HW + pix] = p1.C2 + p1.T * bg2;
+        final_T[(size_t)v * HW + pix] = p1.T;
+        n_contrib[(size_t)v * HW + pix] = p1.last;
     }
     const uint32_t len = rg.y - rg.x;
-    const uint32_t visited = inside ? (stop_at != 0xffffffffu ? stop_at + 1u : len) : 0u;
+    const uint32_t visited = (in0 ? (p0.stop_at != 0xffffffffu ? p0.stop_at + 1u : len) : 0u) +
+                             (in1 ? (p1.stop_at != 0xffffffffu ? p1.stop_at + 1u : len) : 0u);
     const uint32_t ws = __reduce_add_sync(0xffffffffu, visited);
     if (lane == 0 && ws) atomicAdd(&L.hdr->pairs_fwd, (unsigned long long)ws);
 }
 
-// Backward: each pixel replays its blended entries from the last one (n_contrib) to the
-// first, recovering T before entry i as T_{i+1} / (1 - alpha_i) from the final
-// transmittance.  With S_i = sum_{m > i} alpha_m T_m c_m + T_end bg:
+// Backward replay of one pixel.  The pixel visits its blended entries from the last one
+// (n_contrib) to the first, recovering T before entry i as T_{i+1} / (1 - alpha_i) from the
+// final transmittance.  With S_i = sum_{m > i} alpha_m T_m c_m + T_end bg:
 //   dP/dc_i = alpha_i T_i,  dP/dalpha_i = T_i c_i - S_i / (1 - alpha_i),
 //   alpha = min(0.99, o G), G = exp(power): dalpha/do = G, dalpha/dpower = o G (not clamped).
-// A warp visits only the entries its pixels can reach (staged warp masks) and that lie
-// before its last blended position.  Per entry, the nine screen-space gradients are summed
-// over the warp, then over the CTA in shared memory, then added once per (tile, Gaussian)
-// to the global accumulator.
+// Adds the nine screen-space gradients of the entry (du, dv, dA', dB', dC', do, dr, dg, db)
+// into g[0..8]; returns whether the entry contributed.
+struct BwdPixel {
+    float T = 1.0f, S0 = 0.0f, S1 = 0.0f, S2 = 0.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
+    uint32_t nc = 0;
+    __device__ __forceinline__ bool replay(const float4& a, const float4& b, const float4& c, float fpx, float fpy,
+                                           uint32_t lp, float* g)
+    {
+        if (lp >= nc) return false;
+        float dx, dy;
+        const float power = pair_power(a, b, fpx, fpy, &dx, &dy);
+        if (power > 0.0f) return false;
+        const float G = __expf(power);
+        const float alpha = fminf(0.99f, __fmul_rn(a.z, G));
+        if (alpha < 1.0f / 255.0f) return false;
+        const float oma = 1.0f - alpha;
+        T = T / oma;
+        const float dal = g0 * (T * c.x - S0 / oma) + g1 * (T * c.y - S1 / oma) + g2 * (T * c.z - S2 / oma);
+        const float aT = alpha * T;
+        S0 += aT * c.x;
+        S1 += aT * c.y;
+        S2 += aT * c.z;
+        g[6] += g0 * aT;
+        g[7] += g1 * aT;
+        g[8] += g2 * aT;
+        if (!(__fmul_rn(a.z, G) > 0.99f)) {
+            g[5] += dal * G;
+            const float dp = dal * a.z * G;
+            g[2] += dp * (-0.5f * dx * dx);
+            g[3] += dp * (-(dx * dy));
+            g[4] += dp * (-0.5f * dy * dy);
+            g[0] += dp * (-(b.x * dx + b.y * dy));
+            g[1] += dp * (-(b.z * dy + b.y * dx));
+        }
+        return true;
+    }
+};
+
+// Backward.  A warp visits the entries its pixels can reach (staged warp masks) that lie
+// before its last blended position, three at a time: the 27 gradient sums of the three
+// entries over the warp's 64 pixels come out of one transpose reduction (lane l holds sum
+// l), are added in shared memory per entry, and once per (tile, Gaussian) to the global
+// accumulator.
 template <int B, int BATCH>
-__global__ void __launch_bounds__(B * B) k_render_bwd(Layout L, const uint32_t* __restrict__ tval, float bg0, float bg1,
-                                                      float bg2, const float* __restrict__ dL_dimg,
-                                                      const float* __restrict__ final_T,
-                                                      const uint32_t* __restrict__ n_contrib)
+__global__ void __launch_bounds__(B * B / 2) k_render_bwd(Layout L, const uint32_t* __restrict__ tval, float bg0,
+                                                          float bg1, float bg2, const float* __restrict__ dL_dimg,
+                                                          const float* __restrict__ final_T,
+                                                          const uint32_t* __restrict__ n_contrib)
 {
-    constexpr int NT = B * B;
+    constexpr int NT = B * B / 2;
     __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
     __shared__ uint32_t s_j[BATCH], s_m[BATCH];
     __shared__ float s_g[BATCH][9];
@@ -189,33 +250,43 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(Layout L, const uint32_t* 
     const int tile = blockIdx.y * L.tiles_x + blockIdx.x;
     const uint2 rg = reinterpret_cast<const uint2*>(L.ranges)[(size_t)v * L.T + tile];
     int lx, ly, wx0, wy0;
-    pixel_of<B>(threadIdx.x, &lx, &ly, &wx0, &wy0);
-    const int px = blockIdx.x * B + lx, py = blockIdx.y * B + ly;
-    const bool inside = px < L.W && py < L.H;
-    const float fpx = (float)px, fpy = (float)py;
+    pixels_of<B>(threadIdx.x, &lx, &ly, &wx0, &wy0);
+    const int px = blockIdx.x * B + lx, py0 = blockIdx.y * B + ly, py1 = py0 + 4;
+    const bool in0 = px < L.W && py0 < L.H, in1 = px < L.W && py1 < L.H;
+    const float fpx = (float)px, fpy0 = (float)py0, fpy1 = (float)py1;
     const float tx0 = (float)(blockIdx.x * B), ty0 = (float)(blockIdx.y * B);
     const int lane = threadIdx.x & 31;
     const uint32_t wbit = 1u << (threadIdx.x >> 5);
-    const size_t HW = (size_t)L.W * L.H, pix = (size_t)py * L.W + px;
-    float T = 1.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
-    uint32_t nc = 0;
-    if (inside) {
-        T = final_T[(size_t)v * HW + pix];
-        nc = n_contrib[(size_t)v * HW + pix];
-        g0 = dL_dimg[(3 * (size_t)v + 0) * HW + pix];
-        g1 = dL_dimg[(3 * (size_t)v + 1) * HW + pix];
-        g2 = dL_dimg[(3 * (size_t)v + 2) * HW + pix];
+    const size_t HW = (size_t)L.W * L.H;
+    BwdPixel q0, q1;
+    if (in0) {
+        const size_t pix = (size_t)py0 * L.W + px;
+        q0.T = final_T[(size_t)v * HW + pix];
+        q0.nc = n_contrib[(size_t)v * HW + pix];
+        q0.g0 = dL_dimg[(3 * (size_t)v + 0) * HW + pix];
+        q0.g1 = dL_dimg[(3 * (size_t)v + 1) * HW + pix];
+        q0.g2 = dL_dimg[(3 * (size_t)v + 2) * HW + pix];
     }
-    float S0 = T * bg0, S1 = T * bg1, S2 = T * bg2;
+    if (in1) {
+        const size_t pix = (size_t)py1 * L.W + px;
+        q1.T = final_T[(size_t)v * HW + pix];
+        q1.nc = n_contrib[(size_t)v * HW + pix];
+        q1.g0 = dL_dimg[(3 * (size_t)v + 0) * HW + pix];
+        q1.g1 = dL_dimg[(3 * (size_t)v + 1) * HW + pix];
+        q1.g2 = dL_dimg[(3 * (size_t)v + 2) * HW + pix];
+    }
+    q0.S0 = q0.T * bg0; q0.S1 = q0.T * bg1; q0.S2 = q0.T * bg2;
+    q1.S0 = q1.T * bg0; q1.S1 = q1.T * bg1; q1.S2 = q1.T * bg2;
     if (threadIdx.x == 0) s_maxnc = 0;
     __syncthreads();
-    if (nc) atomicMax(&s_maxnc, nc);
+    const uint32_t mnc = max(q0.nc, q1.nc);
+    if (mnc) atomicMax(&s_maxnc, mnc);
     __syncthreads();
     const long long first = rg.x;
     // n_contrib never exceeds the tile's list length; clamp so a mismatched buffer cannot
     // move the replay outside this tile's entries
     const long long end = (first + s_maxnc) < (long long)rg.y ? (first + s_maxnc) : (long long)rg.y;
-    uint32_t wmax = nc;  // entries at or past the warp's last blended position are skipped
+    uint32_t wmax = mnc;  // entries at or past the warp's last blended position are skipped
 #pragma unroll
     for (int o = 16; o; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
     uint32_t pairs = 0;
@@ -223,18 +294,18 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(Layout L, const uint32_t* 
         const long long bs = (be - BATCH) > first ? (be - BATCH) : first;
         const int nb = (int)(be - bs);
         __syncthreads();
-        if (threadIdx.x < BATCH) {
+        for (int i = threadIdx.x; i < BATCH; i += NT) {
             uint32_t m = 0;
-            if (threadIdx.x < nb) {
-                const uint32_t j = tval[bs + threadIdx.x];
+            if (i < nb) {
+                const uint32_t j = tval[bs + i];
                 const float4 a = L.rec[3 * (size_t)j], b = L.rec[3 * (size_t)j + 1];
-                s_j[threadIdx.x] = j;
-                s_a[threadIdx.x] = a;
-                s_b[threadIdx.x] = b;
-                s_c[threadIdx.x] = L.rec[3 * (size_t)j + 2];
+                s_j[i] = j;
+                s_a[i] = a;
+                s_b[i] = b;
+                s_c[i] = L.rec[3 * (size_t)j + 2];
                 m = warp_mask<B>(a, b, tx0, ty0);
             }
-            s_m[threadIdx.x] = m;
+            s_m[i] = m;
         }
         for (int i = threadIdx.x; i < 9 * BATCH; i += NT) (&s_g[0][0])[i] = 0.0f;
         __syncthreads();
@@ -242,67 +313,55 @@ __global__ void __launch_bounds__(B * B) k_render_bwd(Layout L, const uint32_t* 
         for (int c0 = ((kmax - 1) & ~31); kmax > 0 && c0 >= 0; c0 -= 32) {
             uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < kmax && (s_m[c0 + lane] & wbit));
             while (bits) {
-                const int hb = 31 - __clz(bits);
-                bits &= ~(1u << hb);
-                const int k = c0 + hb;
-                const uint32_t lp = (uint32_t)(bs + k - first);
-                const float4 a = s_a[k], b = s_b[k];
-                bool contrib = lp < nc;
-                float dx, dy;
-                float G = 0.0f, alpha = 0.0f;
-                if (contrib) {
-                    const float power = pair_power(a, b, fpx, fpy, &dx, &dy);
-                    if (power > 0.0f) contrib = false;
-                    else {
-                        G = __expf(power);
-                        alpha = fminf(0.99f, __fmul_rn(a.z, G));
-                        if (alpha < 1.0f / 255.0f) contrib = false;
-                    }
-                }
-                float gr[16];
+                // up to three entries, in descending list order
+                int ks[3];
 #pragma unroll
-                for (int c = 0; c < 16; c++) gr[c] = 0.0f;
-                if (contrib) {
-                    pairs++;
-                    const float oma = 1.0f - alpha;
-                    T = T / oma;
-                    const float4 c = s_c[k];
-                    const float dal = g0 * (T * c.x - S0 / oma) + g1 * (T * c.y - S1 / oma) + g2 * (T * c.z - S2 / oma);
-                    const float aT = alpha * T;
-                    S0 += aT * c.x;
-                    S1 += aT * c.y;
-                    S2 += aT * c.z;
-                    gr[6] = g0 * aT;
-                    gr[7] = g1 * aT;
-                    gr[8] = g2 * aT;
-                    if (!(__fmul_rn(a.z, G) > 0.99f)) {
-                        gr[5] = dal * G;
-                        const float dp = dal * a.z * G;
-                        gr[2] = dp * (-0.5f * dx * dx);
-                        gr[3] = dp * (-(dx * dy));
-                        gr[4] = dp * (-0.5f * dy * dy);
-                        gr[0] = dp * (-(b.x * dx + b.y * dy));
-                        gr[1] = dp * (-(b.z * dy + b.y * dx));
+                for (int e = 0; e < 3; e++) {
+                    if (bits) {
+                        const int hb = 31 - __clz(bits);
+                        bits &= ~(1u << hb);
+                        ks[e] = c0 + hb;
+                    } else {
+                        ks[e] = -1;
                     }
                 }
-                if (__any_sync(0xffffffffu, contrib)) {
-                    const float tot = warp_transpose_sum16(gr, lane);
-                    if ((lane & 1) == 0 && (lane >> 1) < 9) atomicAdd(&s_g[k][lane >> 1], tot);
+                float acc[32];
+#pragma unroll
+                for (int i = 0; i < 32; i++) acc[i] = 0.0f;
+                bool any = false;
+#pragma unroll
+                for (int e = 0; e < 3; e++) {
+                    if (ks[e] < 0) continue;
+                    const int k = ks[e];
+                    const float4 a = s_a[k], b = s_b[k], c = s_c[k];
+                    const uint32_t lp = (uint32_t)(bs + k - first);
+                    const bool c0_ = q0.replay(a, b, c, fpx, fpy0, lp, acc + 9 * e);
+                    const bool c1_ = q1.replay(a, b, c, fpx, fpy1, lp, acc + 9 * e);
+                    pairs += (uint32_t)c0_ + (uint32_t)c1_;
+                    any = any || c0_ || c1_;
+                }
+                if (__any_sync(0xffffffffu, any)) {
+                    const float tot = warp_transpose_sum32(acc, lane);
+                    if (lane < 27) {
+                        const int e = lane / 9, comp = lane - 9 * e;
+                        const int k = e == 0 ? ks[0] : (e == 1 ? ks[1] : ks[2]);
+                        if (k >= 0 && tot != 0.0f) atomicAdd(&s_g[k][comp], tot);
+                    }
                 }
             }
         }
         __syncthreads();
-        if (threadIdx.x < nb) {
-            float* dst = reinterpret_cast<float*>(L.gs) + 12 * (size_t)s_j[threadIdx.x];
+        for (int i = threadIdx.x; i < nb; i += NT) {
+            float* dst = reinterpret_cast<float*>(L.gs) + 12 * (size_t)s_j[i];
 #pragma unroll
             for (int c = 0; c < 9; c++) {
-                const float x = s_g[threadIdx.x][c];
+                const float x = s_g[i][c];
                 if (x != 0.0f) atomicAdd(dst + c, x);
             }
         }
     }
     const uint32_t ws = __reduce_add_sync(0xffffffffu, pairs);
-    if ((threadIdx.x & 31) == 0 && ws) atomicAdd(&L.hdr->pairs_bwd, (unsigned long long)ws);
+    if (lane == 0 && ws) atomicAdd(&L.hdr->pairs_bwd, (unsigned long long)ws);
 }
 
 template <int B, int BATCH>
@@ -310,14 +369,14 @@ static void fwd_launch(const Layout& L, const uint32_t* tval, const cgs_config& 
                        cudaStream_t st)
 {
     dim3 grid(L.tiles_x, L.tiles_y, L.V);
-    k_render_fwd<B, BATCH><<<grid, B * B, 0, st>>>(L, tval, c.bg[0], c.bg[1], c.bg[2], img, T, nc);
+    k_render_fwd<B, BATCH><<<grid, B * B / 2, 0, st>>>(L, tval, c.bg[0], c.bg[1], c.bg[2], img, T, nc);
 }
 template <int B, int BATCH>
 static void bwd_launch(const Layout& L, const uint32_t* tval, const cgs_config& c, const float* dimg, const float* T,
                        const uint32_t* nc, cudaStream_t st)
 {
     dim3 grid(L.tiles_x, L.tiles_y, L.V);
-    k_render_bwd<B, BATCH><<<grid, B * B, 0, st>>>(L, tval, c.bg[0], c.bg[1], c.bg[2], dimg, T, nc);
+    k_render_bwd<B, BATCH><<<grid, B * B / 2, 0, st>>>(L, tval, c.bg[0], c.bg[1], c.bg[2], dimg, T, nc);
 }
 
 bool launch_render_fwd(const Layout& L, const cgs_config& c, float* img, float* T, uint32_t* nc, cudaStream_t st)
@@ -359,10 +418,12 @@ bool launch_render_bwd(const Layout& L, const cgs_config& c, const float* dimg, 
     return false;
 }
 
-// L1 loss: loss += mean |img - target|, grad = sign(img - target) / count.
-__global__ void k_l1(const float* __restrict__ img, const float* __restrict__ tgt, long long n, float* loss,
-                     float* __restrict__ grad)
+// L1 loss: loss += mean |img - target|, grad = sign(img - target) / count.  The partial
+// sums are reduced per CTA, so the loss takes one atomic per CTA.
+__global__ void __launch_bounds__(256) k_l1(const float* __restrict__ img, const float* __restrict__ tgt, long long n,
+                                            float* loss, float* __restrict__ grad)
 {
+    __shared__ float s_w[8];
     const float inv = 1.0f / (float)n;
     float acc = 0.0f;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -371,7 +432,13 @@ __global__ void k_l1(const float* __restrict__ img, const float* __restrict__ tg
         grad[i] = d > 0.0f ? inv : (d < 0.0f ? -inv : 0.0f);
     }
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0 && acc != 0.0f) atomicAdd(loss, acc * inv);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_w[w];
+        if (t != 0.0f) atomicAdd(loss, t * inv);
+    }
 }
 
 void launch_l1(const float* img, const float* tgt, long long n, float* loss, float* grad, int n_sm, cudaStream_t st)
