@@ -116,6 +116,7 @@ static bool make_layout(const cgs_frame* f, Layout* L, size_t* bytes)
     l.seg_off = c.take<long long>((long long)l.V * l.NB);
     l.levels = c.take<int8_t>((long long)l.V * l.NB);
     l.rec = c.take<float4>(3 * l.n_cap);
+    l.tq = c.take<float>(l.n_cap);
     l.rect = c.take<uint2>(l.n_cap);
     l.tt = c.take<uint32_t>(l.n_cap);
     l.gidx = c.take<uint32_t>(l.n_cap);
@@ -128,6 +129,10 @@ static bool make_layout(const cgs_frame* f, Layout* L, size_t* bytes)
     l.tkey = c.take<uint32_t>(l.k_cap);
     l.big = c.take<uint32_t>(vt);
     l.gs = c.take<float4>(3 * l.n_cap);
+    // per tile t and warp w: NW words per 32 entries of the tile plus one, at NW * (start_t / 32 + t)
+    const int nw = (l.B * l.B) / 64;
+    l.cbits_words = (long long)nw * (l.k_cap / 32 + vt + 1);
+    l.cbits = c.take<uint32_t>(l.cbits_words);
     *L = l;
     *bytes = c.off;
     return true;

@@ -52,7 +52,8 @@ struct Layout {
     uint32_t* seg_base;          // [V][NB + 1]
     long long* seg_off;          // [V][NB]
     int8_t* levels;              // [V][NB]
-    float4* rec;                 // [n_cap][3] (u, v, o, ext_x) (A', B', C', ext_y) (r, g, b, view)
+    float4* rec;                 // [n_cap][3] (u, v, o, ext_x) (A', B', C', ext_y) (r, g, b, t)
+    float* tq;                   // [n_cap] culling threshold t on the quadratic form
     uint2* rect;                 // [n_cap] (x0 | y0 << 16, x1 | y1 << 16), tile units, end exclusive
     uint32_t* tt;                // [n_cap] tiles touched
     uint32_t* gidx;              // [n_cap] scene index
@@ -65,6 +66,8 @@ struct Layout {
     uint32_t* tkey;              // [k_cap] tile id per entry, same order
     uint32_t* big;               // [V * T] tiles for the long-tile sort
     float4* gs;                  // [n_cap][3] screen-space gradients (du dv dA dB | dC do dr dg | db - - -)
+    uint32_t* cbits;             // per (tile, warp): bit p set when entry p blends into any of the warp's pixels
+    long long cbits_words;
     size_t zero_bytes;           // bytes to clear from hdr
     long long n_cap, k_cap;
     long long scan_tiles_n;      // look-back tiles of a scan over n_cap items

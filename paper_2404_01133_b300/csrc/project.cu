@@ -12,13 +12,16 @@ namespace cgs {
 // strongly correlated 2D covariances (rho^2 > 0.99), where the rounding of q is not bounded
 // by that slack, the extent is infinite (never culled).  Opacity below 1/255 can never pass
 // the test: extent -1 (always culled).
-__device__ __forceinline__ void cull_extent(float o, float A, float B, float C, float* ex, float* ey)
+// *tq receives the slackened threshold t itself (for the exact ellipse test of the
+// compositing kernels), or +inf when no culling is safe.
+__device__ __forceinline__ void cull_extent(float o, float A, float B, float C, float* ex, float* ey, float* tq)
 {
-    if (!(o * 255.0f > 1.0f)) { *ex = -1.0f; *ey = -1.0f; return; }
-    if (B * B > 0.99f * A * C) { *ex = INFINITY; *ey = INFINITY; return; }
+    if (!(o * 255.0f > 1.0f)) { *ex = -1.0f; *ey = -1.0f; *tq = -1.0f; return; }
+    if (B * B > 0.99f * A * C) { *ex = INFINITY; *ey = INFINITY; *tq = INFINITY; return; }
     const float t = 2.0f * logf(255.0f * o) * 1.002f + 0.002f;
     *ex = sqrtf(t * A) * 1.001f + 0.01f;
     *ey = sqrtf(t * C) * 1.001f + 0.01f;
+    *tq = t;
 }
 
 // One thread per selected Gaussian j (flattened over views), grid-stride over the device
@@ -63,8 +66,9 @@ __global__ void __launch_bounds__(256) k_project(Layout L, cgs_scene S, const cg
                     const uint32_t ty0 = (uint32_t)y0 / L.B, ty1 = (uint32_t)y1 / L.B + 1;
                     tt = (tx1 - tx0) * (ty1 - ty0);
                     L.rect[j] = make_uint2(tx0 | (ty0 << 16), tx1 | (ty1 << 16));
-                    float ex, ey;
-                    cull_extent(mo.w, p.A, p.B, p.C, &ex, &ey);
+                    float ex, ey, tq;
+                    cull_extent(mo.w, p.A, p.B, p.C, &ex, &ey, &tq);
+                    L.tq[j] = tq;
                     L.rec[3 * (size_t)j] = make_float4(p.u, p.v, mo.w, ex);
                     L.rec[3 * (size_t)j + 1] = make_float4(p.conic[0], p.conic[1], p.conic[2], ey);
                     L.pkey[j] = ((unsigned long long)(uint32_t)v << 32) | __float_as_uint(p.tz);
@@ -80,7 +84,8 @@ __global__ void __launch_bounds__(256) k_project(Layout L, cgs_scene S, const cg
 }
 
 // View-dependent colour (SH, Sec. 3.1) of each visible Gaussian, over the compacted visible
-// list so every lane has work.  Writes the third record (r, g, b, view).
+// list so every lane has work.  Writes the third record (r, g, b, t), t the culling
+// threshold on the quadratic form (see cull_extent).
 __global__ void __launch_bounds__(256) k_colour(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams)
 {
     const uint32_t n = L.hdr->n_vis;
@@ -95,7 +100,7 @@ __global__ void __launch_bounds__(256) k_colour(Layout L, cgs_scene S, const cgs
         float f[48], rgb[3], dir[3], len, Y[16];
         load_sh(S.sh, g, nc, f);
         sh_colour(m, cams[v], f, deg, rgb, dir, &len, Y);
-        L.rec[3 * (size_t)j + 2] = make_float4(rgb[0], rgb[1], rgb[2], __int_as_float(v));
+        L.rec[3 * (size_t)j + 2] = make_float4(rgb[0], rgb[1], rgb[2], L.tq[j]);
     }
 }
 

@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(Layout L, cgs_scene S, cons
         L.gs[3 * (size_t)j + 2] = z4;
         const float gu = ga.x, gv = ga.y, gA_ = ga.z, gB_ = ga.w, gC_ = gb.x, gop = gb.y;
         const float grgb[3] = {gb.z, gb.w, gc4.x};
-        const int v = __float_as_int(L.rec[3 * (size_t)j + 2].w);
+        const int v = (int)(L.pkey[j] >> 32);
         const long long g = L.gidx[j];
         const cgs_camera c = cams[v];
         const float4 mo = __ldg(reinterpret_cast<const float4*>(S.mean_opac) + g);

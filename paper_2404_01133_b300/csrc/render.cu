@@ -64,17 +64,42 @@ __device__ __forceinline__ bool warp_culled(const float4& a, const float4& b, fl
     return dx > a.w || dy > b.w;
 }
 
-// Bit w set: the Gaussian's extent box meets warp w's pixel block of the tile whose top-left
-// pixel is (tx0, ty0).
+// Minimum over the pixel-centre box [x0, x0 + 7] x [y0, y0 + 7] of the quadratic form
+// q(d) = A' dx^2 + 2 B' dx dy + C' dy^2, d = p - (u, v), or 0 if the centre lies inside.
+// For a convex q with its minimum outside the box, the box minimum lies on an edge; along an
+// edge q is a parabola minimised at the clamped stationary point.
+__device__ __forceinline__ float box_min_q(const float4& a, const float4& b, float x0, float y0)
+{
+    const float dx0 = x0 - a.x, dx1 = x0 + 7.0f - a.x, dy0 = y0 - a.y, dy1 = y0 + 7.0f - a.y;
+    if (dx0 <= 0.0f && dx1 >= 0.0f && dy0 <= 0.0f && dy1 >= 0.0f) return 0.0f;
+    const float qa = b.x, qb = b.y, qc = b.z;
+    float m = INFINITY;
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+        const float dx = e ? dx1 : dx0;
+        const float dy = fminf(fmaxf(-qb * dx / qc, dy0), dy1);
+        m = fminf(m, qa * dx * dx + 2.0f * qb * dx * dy + qc * dy * dy);
+        const float ey = e ? dy1 : dy0;
+        const float ex = fminf(fmaxf(-qb * ey / qa, dx0), dx1);
+        m = fminf(m, qa * ex * ex + 2.0f * qb * ex * ey + qc * ey * ey);
+    }
+    return m;
+}
+
+// Bit w set: the Gaussian can pass the 1/255 test at some pixel of warp w's block of the
+// tile whose top-left pixel is (tx0, ty0): its extent box meets the block and the block's
+// minimum of q is within the slackened threshold t (record c.w; +inf disables the test).
 template <int B>
-__device__ __forceinline__ uint32_t warp_mask(const float4& a, const float4& b, float tx0, float ty0)
+__device__ __forceinline__ uint32_t warp_mask(const float4& a, const float4& b, float t, float tx0, float ty0)
 {
     constexpr int NW = B * B / 64;
     uint32_t m = 0;
 #pragma unroll
     for (int w = 0; w < NW; w++) {
         const float bx0 = tx0 + (float)((w % (B / 8)) * 8), by0 = ty0 + (float)((w / (B / 8)) * 8);
-        if (!warp_culled(a, b, bx0, by0)) m |= 1u << w;
+        if (warp_culled(a, b, bx0, by0)) continue;
+        if (t < INFINITY && box_min_q(a, b, bx0, by0) > t) continue;
+        m |= 1u << w;
     }
     return m;
 }
@@ -84,20 +109,20 @@ struct FwdPixel {
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
     uint32_t last = 0, stop_at = 0xffffffffu;
     bool done = false;
-    __device__ __forceinline__ void blend(const float4& a, const float4& b, const float4& c, float fpx, float fpy,
+    __device__ __forceinline__ bool blend(const float4& a, const float4& b, const float4& c, float fpx, float fpy,
                                           uint32_t pos)
     {
-        if (done) return;
+        if (done) return false;
         float dx, dy;
         const float power = pair_power(a, b, fpx, fpy, &dx, &dy);
-        if (power > 0.0f) return;
+        if (power > 0.0f) return false;
         const float alpha = fminf(0.99f, __fmul_rn(a.z, __expf(power)));
-        if (alpha < 1.0f / 255.0f) return;
+        if (alpha < 1.0f / 255.0f) return false;
         const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
         if (Tn < 1e-4f) {
             done = true;
             stop_at = pos;
-            return;
+            return false;
         }
         const float w = alpha * T;
         C0 += c.x * w;
@@ -105,6 +130,7 @@ struct FwdPixel {
         C2 += c.z * w;
         T = Tn;
         last = pos + 1u;
+        return true;
     }
 };
 
@@ -131,6 +157,10 @@ __global__ void __launch_bounds__(B * B / 2) k_render_fwd(Layout L, const uint32
     const float tx0 = (float)(blockIdx.x * B), ty0 = (float)(blockIdx.y * B);
     const int lane = threadIdx.x & 31;
     const uint32_t wbit = 1u << (threadIdx.x >> 5);
+    // this warp's contribution words: NW * (start / 32 + tile index) + warp * (len / 32 + 1)
+    constexpr int NW = B * B / 64;
+    const size_t tg = (size_t)v * L.T + tile;
+    uint32_t* cbits = L.cbits + (size_t)NW * (rg.x / 32 + tg) + (size_t)(threadIdx.x >> 5) * ((rg.y - rg.x) / 32 + 1);
     FwdPixel p0, p1;
     p0.done = !in0;
     p1.done = !in1;
@@ -140,11 +170,11 @@ __global__ void __launch_bounds__(B * B / 2) k_render_fwd(Layout L, const uint32
             uint32_t m = 0;
             if (start + i < rg.y) {
                 const size_t j = tval[start + i];
-                const float4 a = L.rec[3 * j], b = L.rec[3 * j + 1];
+                const float4 a = L.rec[3 * j], b = L.rec[3 * j + 1], c = L.rec[3 * j + 2];
                 s_a[i] = a;
                 s_b[i] = b;
-                s_c[i] = L.rec[3 * j + 2];
-                m = warp_mask<B>(a, b, tx0, ty0);
+                s_c[i] = c;
+                m = warp_mask<B>(a, b, c.w, tx0, ty0);
             }
             s_m[i] = m;
         }
@@ -153,14 +183,18 @@ __global__ void __launch_bounds__(B * B / 2) k_render_fwd(Layout L, const uint32
         for (int c0 = 0; c0 < nb; c0 += 32) {
             if (__all_sync(0xffffffffu, p0.done && p1.done)) break;
             uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < nb && (s_m[c0 + lane] & wbit));
+            uint32_t word = 0;
             while (bits) {
-                const int k = c0 + __ffs(bits) - 1;
+                const int kk = __ffs(bits) - 1;
                 bits &= bits - 1;
+                const int k = c0 + kk;
                 const float4 a = s_a[k], b = s_b[k], c = s_c[k];
                 const uint32_t pos = start - rg.x + (uint32_t)k;
-                p0.blend(a, b, c, fpx, fpy0, pos);
-                p1.blend(a, b, c, fpx, fpy1, pos);
+                const bool b0 = p0.blend(a, b, c, fpx, fpy0, pos);
+                const bool b1 = p1.blend(a, b, c, fpx, fpy1, pos);
+                if (__any_sync(0xffffffffu, b0 || b1)) word |= 1u << kk;
             }
+            if (lane == 0) cbits[(start - rg.x + c0) >> 5] = word;
         }
     }
     const size_t HW = (size_t)L.W * L.H;
@@ -230,11 +264,11 @@ struct BwdPixel {
     }
 };
 
-// Backward.  A warp visits the entries its pixels can reach (staged warp masks) that lie
-// before its last blended position, three at a time: the 27 gradient sums of the three
-// entries over the warp's 64 pixels come out of one transpose reduction (lane l holds sum
-// l), are added in shared memory per entry, and once per (tile, Gaussian) to the global
-// accumulator.
+// Backward.  A warp visits exactly the entries that blended into at least one of its pixels
+// in the forward (the forward's contribution bits), three at a time: the 27 gradient sums
+// of the three entries over the warp's 64 pixels come out of one transpose reduction (lane l
+// holds sum l), are added in shared memory per entry, and once per (tile, Gaussian) to the
+// global accumulator.
 template <int B, int BATCH>
 __global__ void __launch_bounds__(B * B / 2) k_render_bwd(Layout L, const uint32_t* __restrict__ tval, float bg0,
                                                           float bg1, float bg2, const float* __restrict__ dL_dimg,
@@ -242,8 +276,9 @@ __global__ void __launch_bounds__(B * B / 2) k_render_bwd(Layout L, const uint32
                                                           const uint32_t* __restrict__ n_contrib)
 {
     constexpr int NT = B * B / 2;
+    constexpr int NW = B * B / 64;
     __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
-    __shared__ uint32_t s_j[BATCH], s_m[BATCH];
+    __shared__ uint32_t s_j[BATCH];
     __shared__ float s_g[BATCH][9];
     __shared__ uint32_t s_maxnc;
     const int v = blockIdx.z;
@@ -254,9 +289,10 @@ __global__ void __launch_bounds__(B * B / 2) k_render_bwd(Layout L, const uint32
     const int px = blockIdx.x * B + lx, py0 = blockIdx.y * B + ly, py1 = py0 + 4;
     const bool in0 = px < L.W && py0 < L.H, in1 = px < L.W && py1 < L.H;
     const float fpx = (float)px, fpy0 = (float)py0, fpy1 = (float)py1;
-    const float tx0 = (float)(blockIdx.x * B), ty0 = (float)(blockIdx.y * B);
     const int lane = threadIdx.x & 31;
-    const uint32_t wbit = 1u << (threadIdx.x >> 5);
+    const size_t tg = (size_t)v * L.T + tile;
+    const uint32_t* cbits =
+        L.cbits + (size_t)NW * (rg.x / 32 + tg) + (size_t)(threadIdx.x >> 5) * ((rg.y - rg.x) / 32 + 1);
     const size_t HW = (size_t)L.W * L.H;
     BwdPixel q0, q1;
     if (in0) {
@@ -286,7 +322,8 @@ __global__ void __launch_bounds__(B * B / 2) k_render_bwd(Layout L, const uint32
     // n_contrib never exceeds the tile's list length; clamp so a mismatched buffer cannot
     // move the replay outside this tile's entries
     const long long end = (first + s_maxnc) < (long long)rg.y ? (first + s_maxnc) : (long long)rg.y;
-    uint32_t wmax = mnc;  // entries at or past the warp's last blended position are skipped
+    // the forward wrote this warp's contribution words up to its last blended position
+    uint32_t wmax = mnc;
 #pragma unroll
     for (int o = 16; o; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
     uint32_t pairs = 0;
@@ -294,24 +331,20 @@ __global__ void __launch_bounds__(B * B / 2) k_render_bwd(Layout L, const uint32
         const long long bs = (be - BATCH) > first ? (be - BATCH) : first;
         const int nb = (int)(be - bs);
         __syncthreads();
-        for (int i = threadIdx.x; i < BATCH; i += NT) {
-            uint32_t m = 0;
-            if (i < nb) {
-                const uint32_t j = tval[bs + i];
-                const float4 a = L.rec[3 * (size_t)j], b = L.rec[3 * (size_t)j + 1];
-                s_j[i] = j;
-                s_a[i] = a;
-                s_b[i] = b;
-                s_c[i] = L.rec[3 * (size_t)j + 2];
-                m = warp_mask<B>(a, b, tx0, ty0);
-            }
-            s_m[i] = m;
+        for (int i = threadIdx.x; i < nb; i += NT) {
+            const uint32_t j = tval[bs + i];
+            s_j[i] = j;
+            s_a[i] = L.rec[3 * (size_t)j];
+            s_b[i] = L.rec[3 * (size_t)j + 1];
+            s_c[i] = L.rec[3 * (size_t)j + 2];
         }
         for (int i = threadIdx.x; i < 9 * BATCH; i += NT) (&s_g[0][0])[i] = 0.0f;
         __syncthreads();
         const int kmax = (int)min((long long)nb, (long long)wmax - (bs - first));  // entries k < kmax
         for (int c0 = ((kmax - 1) & ~31); kmax > 0 && c0 >= 0; c0 -= 32) {
-            uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < kmax && (s_m[c0 + lane] & wbit));
+            const int avail = kmax - c0;
+            uint32_t bits = cbits[(uint32_t)(bs - first + c0) >> 5];
+            if (avail < 32) bits &= (1u << avail) - 1u;
             while (bits) {
                 // up to three entries, in descending list order
                 int ks[3];
@@ -328,25 +361,20 @@ __global__ void __launch_bounds__(B * B / 2) k_render_bwd(Layout L, const uint32
                 float acc[32];
 #pragma unroll
                 for (int i = 0; i < 32; i++) acc[i] = 0.0f;
-                bool any = false;
 #pragma unroll
                 for (int e = 0; e < 3; e++) {
                     if (ks[e] < 0) continue;
                     const int k = ks[e];
                     const float4 a = s_a[k], b = s_b[k], c = s_c[k];
                     const uint32_t lp = (uint32_t)(bs + k - first);
-                    const bool c0_ = q0.replay(a, b, c, fpx, fpy0, lp, acc + 9 * e);
-                    const bool c1_ = q1.replay(a, b, c, fpx, fpy1, lp, acc + 9 * e);
-                    pairs += (uint32_t)c0_ + (uint32_t)c1_;
-                    any = any || c0_ || c1_;
+                    pairs += (uint32_t)q0.replay(a, b, c, fpx, fpy0, lp, acc + 9 * e);
+                    pairs += (uint32_t)q1.replay(a, b, c, fpx, fpy1, lp, acc + 9 * e);
                 }
-                if (__any_sync(0xffffffffu, any)) {
-                    const float tot = warp_transpose_sum32(acc, lane);
-                    if (lane < 27) {
-                        const int e = lane / 9, comp = lane - 9 * e;
-                        const int k = e == 0 ? ks[0] : (e == 1 ? ks[1] : ks[2]);
-                        if (k >= 0 && tot != 0.0f) atomicAdd(&s_g[k][comp], tot);
-                    }
+                const float tot = warp_transpose_sum32(acc, lane);
+                if (lane < 27) {
+                    const int e = lane / 9, comp = lane - 9 * e;
+                    const int k = e == 0 ? ks[0] : (e == 1 ? ks[1] : ks[2]);
+                    if (k >= 0 && tot != 0.0f) atomicAdd(&s_g[k][comp], tot);
                 }
             }
         }
