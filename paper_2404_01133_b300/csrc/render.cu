@@ -327,8 +327,11 @@ __global__ void __launch_bounds__(B * B / 2) k_render_bwd(Layout L, const uint32
 #pragma unroll
     for (int o = 16; o; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
     uint32_t pairs = 0;
-    for (long long be = end; be > first; be -= BATCH) {
-        const long long bs = (be - BATCH) > first ? (be - BATCH) : first;
+    // batches at list positions that are multiples of BATCH (as in the forward), last first,
+    // so contribution words line up with 32-entry chunks
+    for (long long bi = (end - first - 1) / BATCH; end > first && bi >= 0; bi--) {
+        const long long bs = first + bi * BATCH;
+        const long long be = (bs + BATCH) < end ? (bs + BATCH) : end;
         const int nb = (int)(be - bs);
         __syncthreads();
         for (int i = threadIdx.x; i < nb; i += NT) {
