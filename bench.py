@@ -285,7 +285,8 @@ def run_ours(args, world, rank, local):
         "gaussians_per_s": world * n / (step_ms * 1e-3),
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "stage_ms_fwd_only": {k: round(v[0] / v[1], 4) for k, v in stages_fwd.items() if v[1]},
-        "pairs": {"fwd_evaluated": pairs_f, "bwd_contributing": pairs_b},
+        "pairs": {"fwd_evaluated": pairs_f, "bwd_contributing": pairs_b, "fwd_warp_steps": counts[6],
+                  "fwd_useful_warp_steps": counts[7]},
         "roofline": roof,
         "gpu_launches": launches,
         "clocks": clk,

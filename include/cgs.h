@@ -153,9 +153,11 @@ int32_t cgs_l1_loss(const float* d_img, const float* d_target, int64_t count, fl
                     void* stream);
 
 /* Synchronizes `stream`, then copies the frame's device status word to *status and its
- * counters to counts[0..5]: selected Gaussians, visible Gaussians, tile entries, forward
- * evaluated pairs, backward evaluated pairs, bounded-wait give-ups.  Either output may be
- * NULL.  Returns the status word (CGS_OK when nothing was latched). */
+ * counters to counts[0..7]: selected Gaussians, visible Gaussians, tile entries, forward
+ * evaluated pairs (entries walked per pixel up to its stop), backward contributing pairs,
+ * bounded-wait give-ups, forward (warp, entry) steps visited after culling, and steps in
+ * which the entry blended into a pixel of the warp.  Either output may be NULL.  Returns
+ * the status word (CGS_OK when nothing was latched). */
 int32_t cgs_frame_status(const cgs_frame* frame, int32_t* status, int64_t* counts, void* stream);
 
 /* Device address and capacity (elements) of an internal frame array, valid after

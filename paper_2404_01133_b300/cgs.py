@@ -171,9 +171,10 @@ def cgs_l1_loss(d_img, d_target, count, d_loss, d_grad, stream=None):
 
 
 def cgs_frame_status(frame, stream=None):
-    """Returns (status code, [selected, visible, entries, fwd pairs, bwd pairs, give-ups])."""
+    """Returns (status code, [selected, visible, entries, fwd pairs, bwd pairs, give-ups,
+    fwd warp steps, useful fwd warp steps])."""
     st = C.c_int32(0)
-    counts = (C.c_int64 * 6)()
+    counts = (C.c_int64 * 8)()
     lib().cgs_frame_status(C.byref(frame), C.byref(st), counts, _stream(stream))
     return st.value, list(counts)
 

@@ -70,13 +70,6 @@ struct Carver {
     }
 };
 
-static int bits_for(unsigned long long x)  // bits needed to represent values 0..x-1
-{
-    int b = 0;
-    while (b < 64 && (1ull << b) < x) b++;
-    return b;
-}
-
 // Fills L from the frame dimensions; returns false if they are invalid.
 static bool make_layout(const cgs_frame* f, Layout* L, size_t* bytes)
 {
@@ -338,6 +331,8 @@ int32_t cgs_frame_status(const cgs_frame* frame, int32_t* status, int64_t* count
         counts[3] = (int64_t)h.pairs_fwd;
         counts[4] = (int64_t)h.pairs_bwd;
         counts[5] = (int64_t)h.spin_giveups;
+        counts[6] = (int64_t)h.steps_fwd;
+        counts[7] = (int64_t)h.steps_useful;
     }
     return code;
 }

@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(B * B / 2) k_render_fwd(Layout L, const uint32
     constexpr int NW = B * B / 64;
     const size_t tg = (size_t)v * L.T + tile;
     uint32_t* cbits = L.cbits + (size_t)NW * (rg.x / 32 + tg) + (size_t)(threadIdx.x >> 5) * ((rg.y - rg.x) / 32 + 1);
+    uint32_t steps = 0, useful = 0;  // warp steps visited / with a blend (lane 0 counts)
     FwdPixel p0, p1;
     p0.done = !in0;
     p1.done = !in1;
@@ -183,6 +184,7 @@ __global__ void __launch_bounds__(B * B / 2) k_render_fwd(Layout L, const uint32
         for (int c0 = 0; c0 < nb; c0 += 32) {
             if (__all_sync(0xffffffffu, p0.done && p1.done)) break;
             uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < nb && (s_m[c0 + lane] & wbit));
+            const uint32_t s_bits = bits;
             uint32_t word = 0;
             while (bits) {
                 const int kk = __ffs(bits) - 1;
@@ -194,7 +196,11 @@ __global__ void __launch_bounds__(B * B / 2) k_render_fwd(Layout L, const uint32
                 const bool b1 = p1.blend(a, b, c, fpx, fpy1, pos);
                 if (__any_sync(0xffffffffu, b0 || b1)) word |= 1u << kk;
             }
-            if (lane == 0) cbits[(start - rg.x + c0) >> 5] = word;
+            if (lane == 0) {
+                cbits[(start - rg.x + c0) >> 5] = word;
+                steps += (uint32_t)__popc(s_bits);
+                useful += (uint32_t)__popc(word);
+            }
         }
     }
     const size_t HW = (size_t)L.W * L.H;
@@ -218,57 +224,65 @@ __global__ void __launch_bounds__(B * B / 2) k_render_fwd(Layout L, const uint32
     const uint32_t visited = (in0 ? (p0.stop_at != 0xffffffffu ? p0.stop_at + 1u : len) : 0u) +
                              (in1 ? (p1.stop_at != 0xffffffffu ? p1.stop_at + 1u : len) : 0u);
     const uint32_t ws = __reduce_add_sync(0xffffffffu, visited);
-    if (lane == 0 && ws) atomicAdd(&L.hdr->pairs_fwd, (unsigned long long)ws);
+    if (lane == 0) {
+        if (ws) atomicAdd(&L.hdr->pairs_fwd, (unsigned long long)ws);
+        if (steps) atomicAdd(&L.hdr->steps_fwd, (unsigned long long)steps);
+        if (useful) atomicAdd(&L.hdr->steps_useful, (unsigned long long)useful);
+    }
 }
 
 // Backward replay of one pixel.  The pixel visits its blended entries from the last one
 // (n_contrib) to the first, recovering T before entry i as T_{i+1} / (1 - alpha_i) from the
-// final transmittance.  With S_i = sum_{m > i} alpha_m T_m c_m + T_end bg:
-//   dP/dc_i = alpha_i T_i,  dP/dalpha_i = T_i c_i - S_i / (1 - alpha_i),
+// final transmittance.  With g = dL/dP (per channel) and S_i = sum_{m > i} alpha_m T_m c_m
+// + T_end bg, only the scalar gS = g . S_i is needed:
+//   dL/dc_i = g alpha_i T_i,  dL/dalpha_i = T_i (g . c_i) - gS / (1 - alpha_i),
 //   alpha = min(0.99, o G), G = exp(power): dalpha/do = G, dalpha/dpower = o G (not clamped).
-// Adds the nine screen-space gradients of the entry (du, dv, dA', dB', dC', do, dr, dg, db)
-// into g[0..8]; returns whether the entry contributed.
+// With dp = dL/dpower, the accumulated values are
+//   m[0..4] = sum dp dx, sum dp dy, sum dp dx^2, sum dp dx dy, sum dp dy^2,
+//   m[5] = dL/do, m[6..8] = dL/d(r, g, b),
+// from which the per-Gaussian factors of the conic give dL/d(u, v, A', B', C') (flush).
 struct BwdPixel {
-    float T = 1.0f, S0 = 0.0f, S1 = 0.0f, S2 = 0.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
+    float T = 1.0f, gS = 0.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
     uint32_t nc = 0;
     __device__ __forceinline__ bool replay(const float4& a, const float4& b, const float4& c, float fpx, float fpy,
-                                           uint32_t lp, float* g)
+                                           uint32_t lp, float* m)
     {
         if (lp >= nc) return false;
         float dx, dy;
         const float power = pair_power(a, b, fpx, fpy, &dx, &dy);
         if (power > 0.0f) return false;
         const float G = __expf(power);
-        const float alpha = fminf(0.99f, __fmul_rn(a.z, G));
+        const float og = __fmul_rn(a.z, G);
+        const float alpha = fminf(0.99f, og);
         if (alpha < 1.0f / 255.0f) return false;
-        const float oma = 1.0f - alpha;
-        T = T / oma;
-        const float dal = g0 * (T * c.x - S0 / oma) + g1 * (T * c.y - S1 / oma) + g2 * (T * c.z - S2 / oma);
+        const float inv = __frcp_rn(1.0f - alpha);
+        T = T * inv;
+        const float gc = g0 * c.x + g1 * c.y + g2 * c.z;
+        const float dal = gc * T - gS * inv;
         const float aT = alpha * T;
-        S0 += aT * c.x;
-        S1 += aT * c.y;
-        S2 += aT * c.z;
-        g[6] += g0 * aT;
-        g[7] += g1 * aT;
-        g[8] += g2 * aT;
-        if (!(__fmul_rn(a.z, G) > 0.99f)) {
-            g[5] += dal * G;
-            const float dp = dal * a.z * G;
-            g[2] += dp * (-0.5f * dx * dx);
-            g[3] += dp * (-(dx * dy));
-            g[4] += dp * (-0.5f * dy * dy);
-            g[0] += dp * (-(b.x * dx + b.y * dy));
-            g[1] += dp * (-(b.z * dy + b.y * dx));
+        gS += aT * gc;
+        m[6] += g0 * aT;
+        m[7] += g1 * aT;
+        m[8] += g2 * aT;
+        if (!(og > 0.99f)) {
+            m[5] += dal * G;
+            const float dp = dal * og;
+            const float px = dp * dx, py = dp * dy;
+            m[0] += px;
+            m[1] += py;
+            m[2] += px * dx;
+            m[3] += px * dy;
+            m[4] += py * dy;
         }
         return true;
     }
 };
 
 // Backward.  A warp visits exactly the entries that blended into at least one of its pixels
-// in the forward (the forward's contribution bits), three at a time: the 27 gradient sums
-// of the three entries over the warp's 64 pixels come out of one transpose reduction (lane l
-// holds sum l), are added in shared memory per entry, and once per (tile, Gaussian) to the
-// global accumulator.
+// in the forward (the forward's contribution bits), three at a time: the 27 sums of the
+// three entries over the warp's 64 pixels come out of one transpose reduction (lane l holds
+// sum l), are added in shared memory per entry, turned into dL/d(u, v, conic, o, rgb) with
+// the entry's conic, and added once per (tile, Gaussian) to the global accumulator.
 template <int B, int BATCH>
 __global__ void __launch_bounds__(B * B / 2) k_render_bwd(Layout L, const uint32_t* __restrict__ tval, float bg0,
                                                           float bg1, float bg2, const float* __restrict__ dL_dimg,
@@ -311,8 +325,8 @@ __global__ void __launch_bounds__(B * B / 2) k_render_bwd(Layout L, const uint32
         q1.g1 = dL_dimg[(3 * (size_t)v + 1) * HW + pix];
         q1.g2 = dL_dimg[(3 * (size_t)v + 2) * HW + pix];
     }
-    q0.S0 = q0.T * bg0; q0.S1 = q0.T * bg1; q0.S2 = q0.T * bg2;
-    q1.S0 = q1.T * bg0; q1.S1 = q1.T * bg1; q1.S2 = q1.T * bg2;
+    q0.gS = q0.T * (q0.g0 * bg0 + q0.g1 * bg1 + q0.g2 * bg2);
+    q1.gS = q1.T * (q1.g0 * bg0 + q1.g1 * bg1 + q1.g2 * bg2);
     if (threadIdx.x == 0) s_maxnc = 0;
     __syncthreads();
     const uint32_t mnc = max(q0.nc, q1.nc);
@@ -384,11 +398,19 @@ __global__ void __launch_bounds__(B * B / 2) k_render_bwd(Layout L, const uint32
         __syncthreads();
         for (int i = threadIdx.x; i < nb; i += NT) {
             float* dst = reinterpret_cast<float*>(L.gs) + 12 * (size_t)s_j[i];
+            const float4 cn = s_b[i];  // conic A', B', C'
+            const float mx = s_g[i][0], my = s_g[i][1];
+            float gsc[9];
+            gsc[0] = -(cn.x * mx + cn.y * my);  // dL/du
+            gsc[1] = -(cn.z * my + cn.y * mx);  // dL/dv
+            gsc[2] = -0.5f * s_g[i][2];         // dL/dA'
+            gsc[3] = -s_g[i][3];                // dL/dB'
+            gsc[4] = -0.5f * s_g[i][4];         // dL/dC'
 #pragma unroll
-            for (int c = 0; c < 9; c++) {
-                const float x = s_g[i][c];
-                if (x != 0.0f) atomicAdd(dst + c, x);
-            }
+            for (int c = 5; c < 9; c++) gsc[c] = s_g[i][c];
+#pragma unroll
+            for (int c = 0; c < 9; c++)
+                if (gsc[c] != 0.0f) atomicAdd(dst + c, gsc[c]);
         }
     }
     const uint32_t ws = __reduce_add_sync(0xffffffffu, pairs);
