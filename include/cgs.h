@@ -38,6 +38,7 @@ extern "C" {
 #define CGS_ERR_SPIN_TIMEOUT 4 /* device: a bounded inter-block wait gave up; outputs are invalid */
 #define CGS_ERR_CUDA 5         /* a CUDA launch or memset failed */
 #define CGS_ERR_UNSUPPORTED 6
+#define CGS_ERR_TOO_LARGE 7    /* request exceeds the fixed limits of cgs_render_forward_static */
 
 /* Pinhole camera of one view: intrinsics kappa and pose tau_i of Eq. 1 (Sec. 3.1). 96 bytes. */
 typedef struct cgs_camera {
@@ -159,6 +160,34 @@ int32_t cgs_l1_loss(const float* d_img, const float* d_target, int64_t count, fl
  * which the entry blended into a pixel of the warp.  Either output may be NULL.  Returns
  * the status word (CGS_OK when nothing was latched). */
 int32_t cgs_frame_status(const cgs_frame* frame, int32_t* status, int64_t* counts, void* stream);
+
+/* Forward render of ONE view with no caller workspace and no allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc or hold a
+ * workspace -- an application that owns all device memory and forbids allocation inside its
+ * frame loop, or a plugin handed only its input and output buffers.  Same inputs, outputs
+ * and results as cgs_render_forward for a one-view frame; the intermediate state lives in a
+ * fixed device array of CGS_STATIC_WORKSPACE_BYTES inside the library, which every GPU that
+ * loads the library keeps until the process exits.
+ *  - Limits: width * height <= CGS_STATIC_MAX_PIXELS, scene->n <= CGS_STATIC_MAX_GAUSSIANS,
+ *    scene->n_blocks <= CGS_STATIC_MAX_BLOCKS; larger requests return CGS_ERR_TOO_LARGE
+ *    before any device work.  More than CGS_STATIC_MAX_ENTRIES (tile, Gaussian) entries sets
+ *    CGS_ERR_CAPACITY in the device status.
+ *  - d_status (device int32, may be NULL) receives the device status of this call as a CGS_*
+ *    code, written on `stream` after the render.
+ *  - The first call on a device looks up the array's device address on that device (with the
+ *    device current); make that first call before any stream capture.
+ *  - Every call uses the same array and clears what must start at zero; calls that overlap
+ *    on the GPU (other streams, other host threads) race and must be serialized by the
+ *    caller.  d_image etc. stay valid after later calls; the array's contents do not. */
+#define CGS_STATIC_MAX_PIXELS (256 * 256)
+#define CGS_STATIC_MAX_GAUSSIANS 32768
+#define CGS_STATIC_MAX_ENTRIES 262144
+#define CGS_STATIC_MAX_BLOCKS 64
+#define CGS_STATIC_WORKSPACE_BYTES (12 << 20)
+int32_t cgs_render_forward_static(const cgs_scene* scene, const cgs_config* cfg, const cgs_camera* d_cam,
+                                  int32_t width, int32_t height, const int32_t* d_view_block,
+                                  const int8_t* d_levels, float* d_image, float* d_final_T,
+                                  uint32_t* d_n_contrib, int32_t* d_status, void* stream);
 
 /* Device address and capacity (elements) of an internal frame array, valid after
  * cgs_render_forward; for parity tests and debugging.  which:

@@ -20,6 +20,7 @@ CGS_ERR_CAPACITY = 3
 CGS_ERR_SPIN_TIMEOUT = 4
 CGS_ERR_CUDA = 5
 CGS_ERR_UNSUPPORTED = 6
+CGS_ERR_TOO_LARGE = 7
 
 BUF_TILE_KEYS, BUF_TILE_VALS, BUF_RANGES, BUF_SCENE_INDEX, BUF_RECORDS, BUF_TILES_TOUCHED, BUF_VIEW_BASE, \
     BUF_VISIBLE, BUF_DEPTH_KEYS, BUF_RECTS = range(10)
@@ -88,6 +89,8 @@ def lib():
         L.cgs_timing_read.restype = i32
         L.cgs_timing_read.argtypes = [P(C.c_double), P(i64)]
         L.cgs_kernel_launches.restype = i64
+        L.cgs_render_forward_static.restype = i32
+        L.cgs_render_forward_static.argtypes = [P(cgs_scene), P(cgs_config), vp, i32, i32, vp, vp, vp, vp, vp, vp, vp]
         L.cgs_frame_buffer.restype = i32
         L.cgs_frame_buffer.argtypes = [P(cgs_frame), i32, P(vp), P(i64)]
         _lib = L
@@ -155,6 +158,14 @@ def cgs_render_forward(scene, frame, cfg, d_cams, d_view_block, d_levels, d_imag
     return _check(lib().cgs_render_forward(C.byref(scene), C.byref(frame), C.byref(cfg), _ptr(d_cams),
                                            _ptr(d_view_block), _ptr(d_levels), _ptr(d_image), _ptr(d_final_T),
                                            _ptr(d_n_contrib), _stream(stream)), "cgs_render_forward")
+
+
+def cgs_render_forward_static(scene, cfg, d_cam, width, height, d_view_block, d_levels, d_image, d_final_T,
+                              d_n_contrib, d_status=None, stream=None):
+    """Returns the host status code (no exception), so callers can see CGS_ERR_TOO_LARGE."""
+    return lib().cgs_render_forward_static(C.byref(scene), C.byref(cfg), _ptr(d_cam), width, height,
+                                           _ptr(d_view_block), _ptr(d_levels), _ptr(d_image), _ptr(d_final_T),
+                                           _ptr(d_n_contrib), _ptr(d_status), _stream(stream))
 
 
 def cgs_render_backward(scene, frame, cfg, d_cams, d_dL_dimage, d_final_T, d_n_contrib, d_g_mean_opac, d_g_scale,

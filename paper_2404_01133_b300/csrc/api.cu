@@ -178,6 +178,7 @@ const char* cgs_status_string(int32_t code)
         case CGS_ERR_SPIN_TIMEOUT: return "a bounded inter-block wait gave up";
         case CGS_ERR_CUDA: return "CUDA error";
         case CGS_ERR_UNSUPPORTED: return "unsupported configuration";
+        case CGS_ERR_TOO_LARGE: return "request exceeds the limits of the static-workspace entry point";
     }
     return "unknown status";
 }
