@@ -79,22 +79,33 @@ def pitched_camera(pos, yaw, pitch_down, fx, fy, width, height):
 # ----------------------------------------------------------------------------------------
 # attribute draws
 # ----------------------------------------------------------------------------------------
-def _attributes(rng, n, log_scale_mu, log_scale_sigma, sh_degree, hi_sigma=0.05):
+def _attributes(rng, n, log_scale_mu, log_scale_sigma):
+    """Scales, rotations, opacities and base colours of n Gaussians."""
     scale = np.exp(rng.normal(log_scale_mu, log_scale_sigma, size=(n, 3)))
     q = rng.normal(0.0, 1.0, size=(n, 4))
     q /= np.linalg.norm(q, axis=1, keepdims=True)
     opac = 1.0 / (1.0 + np.exp(-rng.normal(0.0, 1.0, size=n)))
     base = rng.uniform(0.0, 1.0, size=(n, 3))
+    scale4 = np.zeros((n, 4), dtype=np.float32)
+    scale4[:, :3] = scale
+    return scale4, q.astype(np.float32), opac, base
+
+
+def sh_from_base(rng, base, sh_degree, hi_sigma=0.05, chunk=1 << 22):
+    """SH coefficients [n, (deg+1)^2, 3]: DC from the base colours, higher orders N(0, hi_sigma)
+    in FP32, drawn in chunks by torch's CPU generator (multithreaded) seeded from ``rng``."""
+    import torch
+    n = base.shape[0]
     n_coef = (sh_degree + 1) ** 2
     sh = np.empty((n, n_coef, 3), dtype=np.float32)
     sh[:, 0, :] = ((base - 0.5) * SQRT_4PI).astype(np.float32)
     if n_coef > 1:
-        # higher orders drawn coefficient by coefficient in FP32 to bound host memory at 20M+ Gaussians
-        for k in range(1, n_coef):
-            sh[:, k, :] = rng.standard_normal((n, 3), dtype=np.float32) * np.float32(hi_sigma)
-    scale4 = np.zeros((n, 4), dtype=np.float32)
-    scale4[:, :3] = scale
-    return scale4, q.astype(np.float32), opac, sh
+        gen = torch.Generator().manual_seed(int(rng.integers(0, 2**62)))
+        for c0 in range(0, n, chunk):
+            c1 = min(n, c0 + chunk)
+            block = torch.randn((c1 - c0, n_coef - 1, 3), generator=gen, dtype=torch.float32)
+            sh[c0:c1, 1:, :] = block.numpy() * np.float32(hi_sigma)
+    return sh
 
 
 def _pack(mean, opac, scale4, quat, sh, sh_degree):
@@ -103,15 +114,15 @@ def _pack(mean, opac, scale4, quat, sh, sh_degree):
     mo[:, :3] = mean
     mo[:, 3] = opac
     return {"mean_opac": mo, "scale": np.ascontiguousarray(scale4), "quat": np.ascontiguousarray(quat),
-            "sh": np.ascontiguousarray(sh), "sh_degree": int(sh_degree)}
+            "sh": None if sh is None else np.ascontiguousarray(sh), "sh_degree": int(sh_degree)}
 
 
 def random_cube_scene(n, seed=0, sh_degree=0, extent=1.0, log_scale_mu=-3.0, log_scale_sigma=0.5):
     """Means uniform in [-extent, extent]^3 (the 2,000-Gaussian 128x128 workload with defaults)."""
     rng = np.random.default_rng(seed)
     mean = rng.uniform(-extent, extent, size=(n, 3))
-    scale4, quat, opac, sh = _attributes(rng, n, log_scale_mu, log_scale_sigma, sh_degree)
-    return _pack(mean, opac, scale4, quat, sh, sh_degree)
+    scale4, quat, opac, base = _attributes(rng, n, log_scale_mu, log_scale_sigma)
+    return _pack(mean, opac, scale4, quat, sh_from_base(rng, base, sh_degree), sh_degree)
 
 
 def small_scene_camera(width=128, height=128, f=150.0, dist=4.0):
@@ -156,13 +167,20 @@ def city_points(rng, n, side, lot=50.0, p_build=0.5, foot=(10.0, 40.0), height=(
     return pts
 
 
-def city_scene(n, area_km2, seed, sh_degree=3, origin=(0.0, 0.0)):
-    """Seeded aerial-city scene: n Gaussians over a square of area ``area_km2``."""
+def city_scene(n, area_km2, seed, sh_degree=3, origin=(0.0, 0.0), defer_sh=False):
+    """Seeded aerial-city scene: n Gaussians over a square of area ``area_km2``.
+
+    With defer_sh the SH coefficients are not drawn (``sh`` is None); the base colours are
+    kept in ``base_colour`` so a later reordering can draw them in the final order."""
     rng = np.random.default_rng(seed)
     side = math.sqrt(area_km2) * 1000.0
     mean = city_points(rng, n, side, origin=origin)
-    scale4, quat, opac, sh = _attributes(rng, n, -1.0, 0.7, sh_degree)
+    scale4, quat, opac, base = _attributes(rng, n, -1.0, 0.7)
+    sh = None if defer_sh else sh_from_base(rng, base, sh_degree)
     sc = _pack(mean, opac, scale4, quat, sh, sh_degree)
+    if defer_sh:
+        sc["base_colour"] = base.astype(np.float32)
+        sc["sh_seed"] = seed
     sc["side"] = side
     sc["origin"] = origin
     return sc
@@ -203,7 +221,9 @@ def build_blocks(scene, grid, fractions=(1.0, 0.5, 0.25), extent=None):
     blk = by * grid + bx
     sc = scene["scale"].astype(np.float64)
     score = mo[:, 3].astype(np.float64) * sc[:, 0] * sc[:, 1] * sc[:, 2]
-    order = np.lexsort((np.arange(n), -score, blk))
+    # by block, then by descending score, ties to the lower index (two stable sorts)
+    order = np.argsort(-score, kind="stable")
+    order = order[np.argsort(blk[order], kind="stable")]
     nb = grid * grid
     counts = np.bincount(blk, minlength=nb)
     starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
@@ -214,11 +234,16 @@ def build_blocks(scene, grid, fractions=(1.0, 0.5, 0.25), extent=None):
     for b in range(nb):
         i, j = b % grid, b // grid
         cells[b] = (x0 + i * cw, x0 + (i + 1) * cw, y0 + j * ch, y0 + (j + 1) * ch)
+    if scene["sh"] is not None:
+        sh = np.ascontiguousarray(scene["sh"][order])
+    else:
+        sh = sh_from_base(np.random.default_rng([scene["sh_seed"], 1]), scene["base_colour"][order],
+                          scene["sh_degree"])
     out = {
         "mean_opac": np.ascontiguousarray(mo[order]),
         "scale": np.ascontiguousarray(scene["scale"][order]),
         "quat": np.ascontiguousarray(scene["quat"][order]),
-        "sh": np.ascontiguousarray(scene["sh"][order]),
+        "sh": sh,
         "sh_degree": scene["sh_degree"],
         "level_offset": level_offset, "level_count": level_count, "block_cell": cells,
         "perm": order,
@@ -254,7 +279,7 @@ def target_image(seed, width, height):
 def workload_city_lod(n=20_000_000, grid=8, seed=3, heights=(50.0, 200.0, 500.0, 1000.0, 2000.0),
                       width=1920, height=1080):
     """Block-LoD city (6 km^2, grid x grid blocks, 3 nested levels) and top-down cameras."""
-    sc = build_blocks(city_scene(n, 6.0, seed, sh_degree=3), grid)
+    sc = build_blocks(city_scene(n, 6.0, seed, sh_degree=3, defer_sh=True), grid)
     cams = [pitched_camera((0.0, 0.0, z), 0.0, math.pi / 2.0, 1200.0, 1200.0, width, height)
             for z in heights]
     return sc, cams

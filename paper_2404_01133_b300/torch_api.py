@@ -179,3 +179,105 @@ def l1_loss(img, target, stream=None):
     grad = torch.empty_like(img)
     _c.cgs_l1_loss(img, target, img.numel(), loss, grad, stream)
     return loss, grad
+
+
+# ---------------------------------------------------------------------------------------
+# capacity calibration, CUDA graphs, autotuning
+# ---------------------------------------------------------------------------------------
+def frame_counts(dscene, cams, width, height, tile=16, view_block=None, levels=None, device="cuda",
+                 n_cap=None, k_cap=None):
+    """Selected Gaussians and tile entries of each view, rendered one view at a time.
+
+    Used to size batched frames: returns two lists (selected, entries) per view."""
+    n_cap = n_cap or max(1, dscene.n)
+    k_cap = k_cap or min((1 << 30) - 1, 64 * n_cap)
+    fr = Frame(1, width, height, tile, dscene.n_blocks, n_cap, k_cap, device)
+    cfg = make_config(tile=tile)
+    sel, ent = [], []
+    out = fr.outputs()
+    for v in range(len(cams)):
+        d_cam = cameras_device([cams[v]], device)
+        vb = None if view_block is None else view_block[v:v + 1]
+        lv = None if levels is None else levels[v:v + 1]
+        render_forward(dscene, fr, cfg, d_cam, vb, lv, out=out)
+        st, c = fr.status()
+        if st not in (_c.CGS_OK, _c.CGS_ERR_CAPACITY):
+            raise _c.CgsError(st, "frame_counts")
+        sel.append(int(c[0]))
+        ent.append(int(c[2]))
+    return sel, ent
+
+
+def waves(sel, ent, n_cap_max=(1 << 31) - 1, k_cap_max=(1 << 30) - 1, slack=1.05):
+    """Splits views into consecutive groups whose summed counts fit the frame capacities."""
+    groups, cur, s_sum, e_sum = [], [], 0, 0
+    for v, (s, e) in enumerate(zip(sel, ent)):
+        s2, e2 = int(s * slack) + 1024, int(e * slack) + 4096
+        if cur and (s_sum + s2 > n_cap_max or e_sum + e2 > k_cap_max):
+            groups.append((cur, s_sum, e_sum))
+            cur, s_sum, e_sum = [], 0, 0
+        cur.append(v)
+        s_sum += s2
+        e_sum += e2
+    if cur:
+        groups.append((cur, s_sum, e_sum))
+    return groups
+
+
+def capture(fn, warmup=2, stream=None):
+    """Runs fn() `warmup` times, then captures one call into a CUDA graph and returns it."""
+    s = stream or torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(warmup):
+            fn()
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        fn()
+    return g
+
+
+def autotune(run_step, candidates, reps=5, cache_path=None, key=None):
+    """Times run_step(tile, batch) for every (tile, batch) candidate with CUDA events (median of
+    `reps` after one warm-up) and returns (best, {candidate: ms}).  With cache_path and key,
+    the choice is read from / written to a JSON cache keyed by GPU name and workload."""
+    import json
+    import os
+    gpu = torch.cuda.get_device_name()
+    full_key = f"{gpu}|{key}" if key else None
+    if cache_path and full_key and os.path.exists(cache_path):
+        try:
+            cache = json.load(open(cache_path))
+            if full_key in cache:
+                t, b = cache[full_key]["choice"]
+                return (t, b), cache[full_key]["ms"]
+        except (ValueError, KeyError, TypeError):
+            pass
+    times = {}
+    for tile, batch in candidates:
+        run_step(tile, batch)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            run_step(tile, batch)
+            b_.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b_))
+        times[(tile, batch)] = sorted(ms)[len(ms) // 2]
+    best = min(times, key=times.get)
+    if cache_path and full_key:
+        cache = {}
+        if os.path.exists(cache_path):
+            try:
+                cache = json.load(open(cache_path))
+            except ValueError:
+                cache = {}
+        cache[full_key] = {"choice": list(best), "ms": {f"{t}x{b}": v for (t, b), v in times.items()}}
+        json.dump(cache, open(cache_path, "w"), indent=1)
+    return best, {f"{t}x{b}": v for (t, b), v in times.items()}
+
+
+TUNE_CANDIDATES = [(16, 256), (16, 128), (16, 64), (8, 64), (8, 32)]
