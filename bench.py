@@ -44,6 +44,12 @@ FP32_OPS_PER_FWD_PAIR = 19
 FP32_OPS_PER_BWD_PAIR = 45
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the current kernels on this
+# workload (profiles/k_render_city1m.md).  A kernel absent here reports traffic null; an entry
+# must be removed when its kernel changes.
+NCU_TRAFFIC_BYTES = {"render": 14.700800e6 + 0.808192e6, "render_bwd": 65.559552e6 + 2.001152e6}
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -341,8 +347,8 @@ def run_ours(args, world, rank, local):
         achieved = amount / t / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFP32op/s",
                 "frac": achieved / alu_peak}
-    roof.update({"kernel": dom, "traffic": None, "peak_source": peak_src,
-                 "ms_per_launch": stage_ms[dom]})
+    roof.update({"kernel": dom, "traffic": NCU_TRAFFIC_BYTES.get(dom) if args.tile == 16 else None,
+                 "peak_source": peak_src, "ms_per_launch": stage_ms[dom]})
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
