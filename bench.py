@@ -34,14 +34,16 @@ METRIC = "fwd / fwd+bwd Mpix/s at 1080p, 20M-Gaussian LoD FPS, batched vs plain"
 UNIT = "Mpix/s"
 WORKLOAD = "city-1M-SH3 1920x1080 fwd+bwd (L1), 16x16 tiles"
 L2_FLUSH_BYTES = 256 << 20
-# Algorithmic FP32 work of compositing, counted per CONTRIBUTING pair (a pair that passes the
-# alpha >= 1/255 test and is blended before the transmittance stop): evaluating the pair
-# (offset 2, quadratic form 5, exp argument 1, alpha 2, skip test 1) and blending it
-# (transmittance 2, stop test 1, weight 1, colour 3).  Pairs that fail the test are overhead.
-FP32_OPS_PER_FWD_PAIR = 19
-# backward per contributing pair: re-evaluation 11, T recovery 2, dalpha 9, S update 4,
-# colour gradient 4, opacity / power 3, conic 6, mean 6
-FP32_OPS_PER_BWD_PAIR = 45
+# Algorithmic work per unit.  Compositing: the unit is the EVALUATED pair, an
+# entry of a pixel's tile list visited up to and including the pixel's stop (as the plain
+# per-pixel loop of Eq. 1 visits them); ~17 FP32-pipe instructions per pair forward and ~45
+# backward, plus one SFU exp each.  The kernels skip, per warp, entries that cannot pass the
+# 1/255 test, so they execute fewer than this; the stricter count over CONTRIBUTING pairs
+# (19 / 45 operations per blended pair) is reported beside it.
+FP32_OPS_PER_EVAL_PAIR_FWD = 17
+FP32_OPS_PER_EVAL_PAIR_BWD = 45
+FP32_OPS_PER_CONTRIB_PAIR_FWD = 19
+FP32_OPS_PER_CONTRIB_PAIR_BWD = 45
 
 
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels on this
@@ -86,13 +88,20 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """Maximum of a per-rank scalar over all ranks (timing only; no data-path collective)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_mpix_s(world, pixels_per_rank_step, max_ms):
+    """Whole-job throughput of replicas: the pixels all ranks rendered / the slowest rank's time."""
+    return world * pixels_per_rank_step / (max_ms * 1e-3) / 1e6
 
 
 def load_peaks():
@@ -312,8 +321,8 @@ def run_ours(args, world, rank, local):
     step_ms = max_over_ranks(sum(ms) / len(ms), world)
     fwd_ms = max_over_ranks(sum(ms_fwd) / len(ms_fwd), world)
     pix = W * H
-    value = world * pix / (step_ms * 1e-3) / 1e6
-    fwd_value = world * pix / (fwd_ms * 1e-3) / 1e6
+    value = whole_job_mpix_s(world, pix, step_ms)
+    fwd_value = whole_job_mpix_s(world, pix, fwd_ms)
 
     # per-stage averages (ms per launch of the stage)
     stage_ms = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in stages.items()}
@@ -332,10 +341,17 @@ def run_ours(args, world, rank, local):
         # per entry: read entry, write key, read key, write value; per tile: count and range
         "sort": ("hbm", k_ent * (8 + 8 + 8 + 4) + n_tiles * 12),
         # algorithmic FP32 operations per launch (issue-bound stages)
-        "render": ("alu", pairs_b * FP32_OPS_PER_FWD_PAIR),
-        "render_bwd": ("alu", pairs_b * FP32_OPS_PER_BWD_PAIR),
+        "render": ("alu", pairs_f * FP32_OPS_PER_EVAL_PAIR_FWD),
+        "render_bwd": ("alu", pairs_f * FP32_OPS_PER_EVAL_PAIR_BWD),
         "project_bwd": ("hbm", n_vis * (16 * 3 + 12 * nc_coef + 48 + 4 * 4 * 3 + 12 * nc_coef)),
+        # L1: image and target read, gradient written
+        "loss": ("hbm", W * H * 3 * 12),
     }
+    # overall fraction: time every stage would take at its binding peak / step time
+    ideal_ms = sum((amt / (peaks["hbm_gbs"] * 1e9) if b == "hbm" else amt / (alu_peak * 1e12)) * 1e3
+                   for b, amt in work.values())
+    strict = {"render": pairs_b * FP32_OPS_PER_CONTRIB_PAIR_FWD / (stage_ms["render"] * 1e-3) / 1e12 / alu_peak,
+              "render_bwd": pairs_b * FP32_OPS_PER_CONTRIB_PAIR_BWD / (stage_ms["render_bwd"] * 1e-3) / 1e12 / alu_peak}
     dom = max(work, key=lambda k: stage_ms.get(k, 0.0))
     bound, amount = work[dom]
     t = stage_ms[dom] * 1e-3
@@ -365,6 +381,11 @@ def run_ours(args, world, rank, local):
         "pairs": {"fwd_evaluated": pairs_f, "bwd_contributing": pairs_b, "fwd_warp_steps": counts[6],
                   "fwd_useful_warp_steps": counts[7]},
         "roofline": roof,
+        "roofline_overall": {"ideal_ms": ideal_ms, "frac": ideal_ms / step_ms,
+                             "definition": "sum over stages of algorithmic work / binding peak, over the step time"},
+        "roofline_stage_frac": {k: ((amt / (peaks["hbm_gbs"] * 1e9) if b == "hbm" else amt / (alu_peak * 1e12)) * 1e3
+                                    / stage_ms[k]) for k, (b, amt) in work.items() if stage_ms.get(k)},
+        "roofline_contributing_pairs_frac": strict,
         "gpu_launches": launches,
         "kernels_per_step": per_step_launches,
         "timing": "CUDA graph replay of the whole step" if graph is not None else "eager launches",
