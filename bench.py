@@ -594,19 +594,20 @@ def run_lod20m(args, world):
     ds = ta.DeviceScene(sc)
     ds.compute_block_bounds(4.0)
     cfg = ta.make_config(tile=16, batch=256, lod_dist=(200.0, 600.0))
+    cfg_pt = ta.make_config(tile=16, batch=256, lod_dist=(200.0, 600.0), lod_mode=cgs.CGS_LOD_POINT)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     nb = ds.n_blocks
     rows = []
     for cam in cams:
         d_cam = ta.cameras_device([cam])
         row = {"height_m": float(cam["campos"][2])}
-        variants = [("lod", None)] + [(f"level{l}", torch.full((1, nb), l, dtype=torch.int8, device="cuda"))
-                                      for l in range(3)]
-        for name, lv in variants:
-            sel, ent = ta.frame_counts(ds, [cam], 1920, 1080, levels=lv)
+        variants = [("lod", None, cfg), ("pointwise", None, cfg_pt)] + \
+            [(f"level{l}", torch.full((1, nb), l, dtype=torch.int8, device="cuda"), cfg) for l in range(3)]
+        for name, lv, c_ in variants:
+            sel, ent = ta.frame_counts(ds, [cam], 1920, 1080, levels=lv, cfg=c_)
             fr = ta.Frame(1, 1920, 1080, 16, nb, max(1, int(sel[0] * 1.02) + 1024),
                           min((1 << 30) - 1, int(ent[0] * 1.05) + 65536))
-            ms = _graph_ms(_fwd_runner(ds, fr, cfg, d_cam, None, lv), args.steps, flush, world)
+            ms = _graph_ms(_fwd_runner(ds, fr, c_, d_cam, None, lv), args.steps, flush, world)
             st, c = fr.status()
             t = max_over_ranks(sum(ms) / len(ms), world)
             row[name] = {"fps": 1e3 / t, "ms": t, "selected": c[0], "visible": c[1], "entries": c[2],
@@ -614,13 +615,13 @@ def run_lod20m(args, world):
             del fr
         rows.append(row)
     mean = lambda k: float(np.mean([r[k]["fps"] for r in rows]))
-    return {"metric": "20M-Gaussian LoD FPS at 1080p (block LoD vs fixed levels)", "value": mean("lod"),
+    return {"metric": "20M-Gaussian LoD FPS at 1080p (block LoD vs point-wise LoD vs fixed levels)", "value": mean("lod"),
             "unit": "FPS", "n_gpus": world, "steps": args.steps, "higher_is_better": True, "dtype": "f32",
             "data": "synthetic", "config": {"workload": "city-20M-SH3 6 km^2, 8x8 blocks, levels 100/50/25%, "
                                                         "top-down 1920x1080, f=1200, 16x16 tiles",
                                             "lod_dist_m": [200, 600], "generation_s": t_gen},
-            "mean_fps": {"lod": mean("lod"), "no_lod_level0": mean("level0"), "only_level1": mean("level1"),
-                         "only_level2": mean("level2")},
+            "mean_fps": {"lod": mean("lod"), "pointwise_lod": mean("pointwise"), "no_lod_level0": mean("level0"),
+                         "only_level1": mean("level1"), "only_level2": mean("level2")},
             "per_height": rows}
 
 

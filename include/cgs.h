@@ -81,7 +81,20 @@ typedef struct cgs_config {
     float bg[3];         /* background colour */
     double lod_dist[2];  /* level thresholds d1 < d2 in scene units: level 0 if dmin < d1,
                             1 if dmin < d2, else 2 */
+    int32_t lod_mode;    /* when the renderer selects levels itself (no d_levels, no
+                            d_view_block): CGS_LOD_BLOCK or CGS_LOD_POINT */
+    int32_t _pad2;
 } cgs_config;
+
+/* Level selection modes.
+ * CGS_LOD_BLOCK: the paper's block-wise selection (Sec. 3.3.2, cgs_lod_select).
+ * CGS_LOD_POINT: the point-wise baseline the paper compares against (Sec. 3.3.2, Table 4):
+ *   every non-empty block takes part without block culling; a Gaussian of block b at rank r
+ *   in the block's finest level (levels are nested prefixes) is rendered iff
+ *   r < level_count[b][l], l = 0 if dist < d1, 1 if dist < d2, else 2 (clamped), with
+ *   dist = sqrt((dx*dx + dy*dy) + dz*dz) in FP32 from the camera centre to its mean. */
+#define CGS_LOD_BLOCK 0
+#define CGS_LOD_POINT 1
 
 /* A batch of n_views equally sized views rendered together, and the caller-owned device
  * workspace holding its intermediate state (kept for the backward).  n_cap bounds the

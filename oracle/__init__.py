@@ -81,6 +81,8 @@ def lib(real="f32"):
         L.orc_concat.restype = i64
         L.orc_concat.argtypes = [i32, i32, vp, vp, vp, vp]
         L.orc_sh_basis.argtypes = [i64, vp, i32, vp, vp]
+        L.orc_pointwise_select.restype = i64
+        L.orc_pointwise_select.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp]
         L.orc_real_bytes.restype = i32
         _LIBS[real] = L
     return _LIBS[real]
@@ -259,6 +261,19 @@ def concat(scene, level):
     total = int(sum(lc[b, lev[b]] for b in range(nb) if lev[b] >= 0))
     out = np.zeros(max(total, 1), np.int64)
     m = lib("f64").orc_concat(nb, nl, _p(lo), _p(lc), _p(lev), _p(out))
+    return out[:m]
+
+
+def pointwise_select(scene, cam, dist=(200.0, 600.0)):
+    """Global indices kept by the point-wise level baseline (see oracle.c)."""
+    lo = np.ascontiguousarray(scene["level_offset"], np.int64)
+    lc = np.ascontiguousarray(scene["level_count"], np.int64)
+    nb, nl = lo.shape
+    mo = np.ascontiguousarray(scene["mean_opac"], np.float32)
+    out = np.zeros(max(int(lc[:, 0].sum()), 1), np.int64)
+    c = make_camera(cam)
+    d = np.asarray(dist, np.float64)
+    m = lib("f64").orc_pointwise_select(nb, nl, _p(lo), _p(lc), _p(mo), C.byref(c), _p(d), _p(out))
     return out[:m]
 
 

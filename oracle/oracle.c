@@ -751,4 +751,31 @@ int64_t orc_concat(int32_t n_blocks, int32_t n_levels, const int64_t* level_offs
     return m;
 }
 
+/* Point-wise level selection, the baseline Sec. 3.3.2 compares against (Table 4): each
+ * Gaussian takes the level of its own distance to the camera centre (FP32,
+ * dist = sqrt((dx*dx + dy*dy) + dz*dz), level 0 if dist < d1, 1 if < d2, else 2, clamped)
+ * and is kept iff its rank in its block's finest level is below that level's count (levels
+ * are nested prefixes).  No block culling.  Writes global indices in block order. */
+int64_t orc_pointwise_select(int32_t n_blocks, int32_t n_levels, const int64_t* level_offset,
+                             const int64_t* level_count, const float* mean_opac, const orc_camera* cam,
+                             const double* dist, int64_t* out_idx)
+{
+    const float d1 = (float)dist[0], d2 = (float)dist[1];
+    int64_t m = 0;
+    for (int32_t b = 0; b < n_blocks; b++) {
+        int64_t off = level_offset[(int64_t)b * n_levels], cnt = level_count[(int64_t)b * n_levels];
+        for (int64_t r = 0; r < cnt; r++) {
+            int64_t g = off + r;
+            float e0 = mean_opac[4 * g] - cam->campos[0];
+            float e1 = mean_opac[4 * g + 1] - cam->campos[1];
+            float e2 = mean_opac[4 * g + 2] - cam->campos[2];
+            float d = sqrtf((e0 * e0 + e1 * e1) + e2 * e2);
+            int lv = d < d1 ? 0 : (d < d2 ? 1 : 2);
+            if (lv > n_levels - 1) lv = n_levels - 1;
+            if (r < level_count[(int64_t)b * n_levels + lv]) out_idx[m++] = g;
+        }
+    }
+    return m;
+}
+
 int32_t orc_real_bytes(void) { return (int32_t)sizeof(REAL); }

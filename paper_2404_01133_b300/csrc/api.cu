@@ -107,6 +107,7 @@ static bool make_layout(const cgs_frame* f, Layout* L, size_t* bytes)
     l.n_seg = c.take<uint32_t>(l.V);
     l.seg_base = c.take<uint32_t>((long long)l.V * (l.NB + 1));
     l.seg_off = c.take<long long>((long long)l.V * l.NB);
+    l.seg_blk = c.take<int32_t>((long long)l.V * l.NB);
     l.levels = c.take<int8_t>((long long)l.V * l.NB);
     l.rec = c.take<float4>(3 * l.n_cap);
     l.tq = c.take<float>(l.n_cap);
@@ -241,6 +242,11 @@ int32_t cgs_render_forward(const cgs_scene* scene, const cgs_frame* frame, const
         !d_image || !d_final_T || !d_n_contrib)
         return CGS_ERR_INVALID_ARGUMENT;
     if (!d_levels && !d_view_block && (!scene->block_aabb || !scene->block_cell)) return CGS_ERR_INVALID_ARGUMENT;
+    if (cfg->lod_mode != CGS_LOD_BLOCK && cfg->lod_mode != CGS_LOD_POINT) return CGS_ERR_INVALID_ARGUMENT;
+    // the point-wise test applies only when the renderer chooses levels itself
+    L.lod_mode = (d_levels || d_view_block) ? CGS_LOD_BLOCK : cfg->lod_mode;
+    L.lod_d1 = (float)cfg->lod_dist[0];
+    L.lod_d2 = (float)cfg->lod_dist[1];
     cudaStream_t st = (cudaStream_t)stream;
     const int n_sm = sm_count();
     if (cudaMemsetAsync(frame->ws, 0, L.zero_bytes, st) != cudaSuccess) return CGS_ERR_CUDA;

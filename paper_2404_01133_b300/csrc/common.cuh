@@ -53,6 +53,9 @@ struct Layout {
     uint32_t* n_seg;             // [V]
     uint32_t* seg_base;          // [V][NB + 1]
     long long* seg_off;          // [V][NB]
+    int32_t* seg_blk;            // [V][NB] block of each selected segment
+    int lod_mode;                // CGS_LOD_BLOCK or CGS_LOD_POINT (point mode: per-Gaussian level test)
+    float lod_d1, lod_d2;        // FP32 thresholds of the point mode
     int8_t* levels;              // [V][NB]
     float4* rec;                 // [n_cap][3] (u, v, o, ext_x) (A', B', C', ext_y) (r, g, b, t)
     float* tq;                   // [n_cap] culling threshold t on the quadratic form

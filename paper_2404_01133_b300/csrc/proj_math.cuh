@@ -241,4 +241,18 @@ __device__ __forceinline__ void locate(const Layout& L, uint32_t j, int* view_ou
     *g_out = L.seg_off[(size_t)v * L.NB + s0] + (long long)(i - sb[s0]);
 }
 
+// Block of the selected index j and its rank inside the block's segment (segment of `view`).
+__device__ __forceinline__ void locate_block(const Layout& L, uint32_t j, int v, int* blk, uint32_t* rank)
+{
+    const uint32_t i = j - L.view_base[v];
+    const uint32_t* sb = L.seg_base + (size_t)v * (L.NB + 1);
+    int s0 = 0, s1 = (int)L.n_seg[v];
+    while (s1 - s0 > 1) {
+        int mid = (s0 + s1) >> 1;
+        if (sb[mid] <= i) s0 = mid; else s1 = mid;
+    }
+    *blk = L.seg_blk[(size_t)v * L.NB + s0];
+    *rank = i - sb[s0];
+}
+
 }  // namespace cgs

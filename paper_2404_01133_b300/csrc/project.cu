@@ -47,7 +47,20 @@ __global__ void __launch_bounds__(256) k_project(Layout L, cgs_scene S, const cg
         // near-plane test first, so culled Gaussians never read scale or rotation
         const float tz = ((c.R[6] * m[0] + c.R[7] * m[1]) + c.R[8] * m[2]) + c.t[2];
         uint32_t tt = 0;
-        if (tz > near_z) {
+        bool keep = tz > near_z;
+        if (keep && L.lod_mode == CGS_LOD_POINT) {
+            // point-wise baseline: the level of this Gaussian's own distance; kept iff its rank
+            // in the block lies inside that level's (nested) prefix
+            const float d0 = m[0] - c.campos[0], d1 = m[1] - c.campos[1], d2 = m[2] - c.campos[2];
+            const float dist = sqrtf((d0 * d0 + d1 * d1) + d2 * d2);
+            int lv = dist < L.lod_d1 ? 0 : (dist < L.lod_d2 ? 1 : 2);
+            if (lv > S.n_levels - 1) lv = S.n_levels - 1;
+            int blk;
+            uint32_t rank;
+            locate_block(L, j, v, &blk, &rank);
+            keep = (long long)rank < S.level_count[(long long)blk * S.n_levels + lv];
+        }
+        if (keep) {
             const float4 s4 = __ldg(sc4 + g), qq = __ldg(q4 + g);
             const float s[3] = {s4.x, s4.y, s4.z};
             const float q[4] = {qq.x, qq.y, qq.z, qq.w};

@@ -94,6 +94,10 @@ __global__ void k_select(Layout L, cgs_scene S, const cgs_camera* __restrict__ c
             if (l >= 0 && S.level_count[(long long)b * NL + l] <= 0) l = -1;
             lev[b] = (int8_t)l;
         }
+    } else if (L.lod_mode == CGS_LOD_POINT) {
+        // point-wise baseline: every non-empty block at its finest level; k_project applies the
+        // per-Gaussian distance test
+        for (int b = threadIdx.x; b < NB; b += blockDim.x) lev[b] = S.level_count[(long long)b * NL] > 0 ? 0 : -1;
     } else {
         const int groups = blockDim.x >> 3;
         for (int b0 = 0; b0 < NB; b0 += groups) {
@@ -114,6 +118,7 @@ __global__ void k_select(Layout L, cgs_scene S, const cgs_camera* __restrict__ c
         for (int b = 0; b < NB; b++) {
             if (lev[b] < 0) continue;
             so[s] = S.level_offset[(long long)b * NL + lev[b]];
+            L.seg_blk[(long long)v * NB + s] = b;
             sb[s] = (uint32_t)acc;
             acc += (unsigned long long)S.level_count[(long long)b * NL + lev[b]];
             s++;

@@ -35,8 +35,9 @@ def cameras_device(cams, device="cuda"):
     return cameras_host(cams).to(device, non_blocking=False)
 
 
-def make_config(tile=16, batch=None, near_z=0.2, bg=(0.0, 0.0, 0.0), lod_dist=(200.0, 600.0)):
+def make_config(tile=16, batch=None, near_z=0.2, bg=(0.0, 0.0, 0.0), lod_dist=(200.0, 600.0), lod_mode=0):
     c = _c.cgs_config()
+    c.lod_mode = lod_mode
     c.tile = tile
     c.batch = batch if batch is not None else (256 if tile == 16 else 64)
     c.near_z = near_z
@@ -185,14 +186,14 @@ def l1_loss(img, target, stream=None):
 # capacity calibration, CUDA graphs, autotuning
 # ---------------------------------------------------------------------------------------
 def frame_counts(dscene, cams, width, height, tile=16, view_block=None, levels=None, device="cuda",
-                 n_cap=None, k_cap=None):
+                 n_cap=None, k_cap=None, cfg=None):
     """Selected Gaussians and tile entries of each view, rendered one view at a time.
 
     Used to size batched frames: returns two lists (selected, entries) per view."""
     n_cap = n_cap or max(1, dscene.n)
     k_cap = k_cap or min((1 << 30) - 1, 64 * n_cap)
     fr = Frame(1, width, height, tile, dscene.n_blocks, n_cap, k_cap, device)
-    cfg = make_config(tile=tile)
+    cfg = cfg or make_config(tile=tile)
     sel, ent = [], []
     out = fr.outputs()
     for v in range(len(cams)):

@@ -217,6 +217,23 @@ def test_lod_render_matches_oracle_on_concatenated_selection():
         assert torch.equal(gv["image"][0], g["image"][v])
 
 
+@pytest.mark.parametrize("dist", [(200.0, 600.0), (100.0, 250.0)])
+def test_pointwise_lod_baseline_matches_oracle(dist):
+    """The point-wise level baseline: per-Gaussian distance levels, no block culling."""
+    sc = lod_scene()
+    cam = synth.pitched_camera((30.0, -40.0, 120.0), 0.3, 0.6, 300.0, 300.0, 320, 240)
+    g = gpu_render(sc, [cam], cfg_kw={"lod_mode": cgs.CGS_LOD_POINT, "lod_dist": dist})
+    assert g["status"] == 0
+    idx = oracle.pointwise_select(sc, cam, dist=dist)
+    o = oracle.render(sc, cam, idx=idx)
+    a = frame_arrays(g, n_sel=g["counts"][0])
+    np.testing.assert_array_equal(a["keys"].astype(np.int64), (o["sort"]["keys"] >> np.uint64(32)).astype(np.int64))
+    np.testing.assert_array_equal(a["scene_index"][a["vals"]].astype(np.int64), idx[o["sort"]["vals"]])
+    np.testing.assert_array_equal(a["ranges"].astype(np.int64), o["sort"]["ranges"])
+    compare_image(g["image"][0], g["final_T"][0], g["n_contrib"][0], o)
+    assert g["counts"][1] == int((o["proj"]["tiles_touched"] > 0).sum())
+
+
 def test_explicit_levels_and_view_block_modes():
     sc = lod_scene()
     cam = synth.pitched_camera((0.0, 0.0, 300.0), 0.0, 1.0, 300.0, 300.0, 320, 240)

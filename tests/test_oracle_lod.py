@@ -107,3 +107,16 @@ def test_levels_are_nested_prefixes_ranked_by_opacity_volume():
         s = sc["scale"][seg].astype(np.float64)
         score = sc["mean_opac"][seg, 3].astype(np.float64) * s[:, 0] * s[:, 1] * s[:, 2]
         assert (np.diff(score) <= 0).all()
+
+
+def test_pointwise_selection_by_hand():
+    # one block of 8 Gaussians on the x axis, levels 8 / 4 / 2 (nested prefixes); camera at the origin
+    mo = np.zeros((8, 4), np.float32)
+    mo[:, 0] = [10, 250, 700, 150, 500, 900, 30, 650]
+    mo[:, 3] = 0.5
+    sc = {"mean_opac": mo, "level_offset": np.zeros((1, 3), np.int64), "level_count": np.array([[8, 4, 2]], np.int64)}
+    cam = synth.camera_from_rt(np.eye(3), [0.0, 0.0, 0.0], 100, 100, 49.5, 49.5, 100, 100)
+    # ranks 0..7 at distances 10, 250, 700, 150, 500, 900, 30, 650 -> levels 0,1,2,0,1,2,0,2
+    # kept iff rank < count[level]: r0 (0<8), r1 (1<4), r2 (2<2 no), r3 (3<8), r4 (4<4 no),
+    # r5 (5<2 no), r6 (6<8), r7 (7<2 no)
+    assert list(oracle.pointwise_select(sc, cam, dist=(200.0, 600.0))) == [0, 1, 3, 6]
