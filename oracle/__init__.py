@@ -10,7 +10,8 @@ finite-difference pins).  In both, the key path that decides integers (culls, ra
 tile rect, depth bits) is FP32.
 
 Paper passages: Eq. 1 and Sec. 3.1 (projection, SH colour, depth-sorted alpha blending,
-differentiable rendering); Eq. 7 and Sec. 3.3.2 (MAD block bounds, block frustum test,
+differentiable rendering); Sec. 3.2.2, Eqs. 2 and 4 (normalisation, contraction, block grid,
+pose in block); Eq. 7 and Sec. 3.3.2 (MAD block bounds, block frustum test,
 camera block, distance-based level, concatenation).
 """
 from __future__ import annotations
@@ -83,6 +84,10 @@ def lib(real="f32"):
         L.orc_sh_basis.argtypes = [i64, vp, i32, vp, vp]
         L.orc_pointwise_select.restype = i64
         L.orc_pointwise_select.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp]
+        L.orc_contract.argtypes = [i64, vp, i64, vp, vp, vp]
+        L.orc_partition_assign.restype = i64
+        L.orc_partition_assign.argtypes = [i64, vp, i64, vp, vp, vp, vp, vp]
+        L.orc_partition_order.argtypes = [i64, vp, i32, vp, vp]
         L.orc_real_bytes.restype = i32
         _LIBS[real] = L
     return _LIBS[real]
@@ -284,3 +289,47 @@ def sh_basis(dirs, deg=3, real="f64", with_grad=False):
     dout = np.zeros((d.shape[0], 16, 3), dt) if with_grad else None
     lib(real).orc_sh_basis(d.shape[0], _p(d), deg, _p(out), _p(dout))
     return (out, dout) if with_grad else out
+
+
+# ---- block partition (Sec. 3.2.2, Eqs. 2 and 4) -------------------------------------------
+
+def _pos_rows(pos):
+    a = np.ascontiguousarray(pos, dtype=np.float32)
+    return a, a.shape[1]
+
+
+def contract(pos, pmin, pmax):
+    """Eq. 2 applied to the normalised positions (rows of pos, xyz first), FP32."""
+    a, stride = _pos_rows(pos)
+    out = np.zeros((a.shape[0], 3), np.float32)
+    pl, ph = np.asarray(pmin, np.float32), np.asarray(pmax, np.float32)
+    lib().orc_contract(a.shape[0], _p(a), stride, _p(pl), _p(ph), _p(out))
+    return out
+
+
+def partition_assign(pos, pmin, pmax, grid):
+    """Block of every point over the uniform grid of the contracted cube, and the per-block
+    counts; block -1 for a point whose contraction is not finite."""
+    a, stride = _pos_rows(pos)
+    g = np.asarray(grid, np.int32)
+    nb = int(np.prod(g))
+    block = np.zeros(a.shape[0], np.int32)
+    count = np.zeros(nb, np.int64)
+    pl, ph = np.asarray(pmin, np.float32), np.asarray(pmax, np.float32)
+    dropped = lib().orc_partition_assign(a.shape[0], _p(a), stride, _p(pl), _p(ph), _p(g), _p(block), _p(count))
+    return {"block": block, "count": count, "dropped": int(dropped)}
+
+
+def partition_order(block, n_blocks):
+    """Stable grouping by block: permutation (grouped position -> scene index) and offsets."""
+    b = np.ascontiguousarray(block, np.int32)
+    perm = np.zeros(max(1, b.shape[0]), np.int64)
+    offset = np.zeros(n_blocks + 1, np.int64)
+    lib().orc_partition_order(b.shape[0], _p(b), n_blocks, _p(perm), _p(offset))
+    return perm[:offset[-1]], offset
+
+
+def pose_blocks(campos, pmin, pmax, grid):
+    """Eq. 4 (B2): the block that contains each camera centre after normalisation and
+    contraction."""
+    return partition_assign(np.asarray(campos, np.float32).reshape(-1, 3), pmin, pmax, grid)["block"]

@@ -17,11 +17,11 @@ def lib_path(real):
 
 def build(force=False, extra=()):
     src = os.path.join(HERE, "oracle.c")
-    inc = os.path.join(HERE, "oracle_project.inc")
+    deps = [src] + [os.path.join(HERE, f) for f in ("oracle_project.inc", "oracle_partition.inc")]
     for real, ctype in (("f32", "float"), ("f64", "double")):
         out = lib_path(real)
         if (not force and os.path.exists(out)
-                and os.path.getmtime(out) >= max(os.path.getmtime(src), os.path.getmtime(inc))):
+                and os.path.getmtime(out) >= max(os.path.getmtime(d) for d in deps)):
             continue
         cmd = ["gcc", *FLAGS, *extra, f"-DREAL={ctype}", "-o", out + ".tmp", src, "-lm"]
         subprocess.check_call(cmd)

@@ -13,6 +13,9 @@
  *     entries with alpha < 1/255 are skipped, a pixel stops before the entry that would
  *     take its transmittance below 1e-4, ties in depth go to the lower index.
  *   - Differentiable rendering (Sec. 3.1): the analytic gradient of the above.
+ *   - Sec. 3.2.2 and Eqs. 2 and 4: foreground normalisation, contraction, the uniform block
+ *     grid over the contracted cube, stable grouping by block, the block of a camera pose
+ *     (oracle_partition.inc).
  *   - Eq. 7 (Sec. 3.3.2): MAD block bounds; block frustum test by projecting the corners
  *     in front of the camera; the camera's own block is always kept; the level of a
  *     block comes from the minimum corner distance; fusion by concatenation.
@@ -777,5 +780,7 @@ int64_t orc_pointwise_select(int32_t n_blocks, int32_t n_levels, const int64_t* 
     }
     return m;
 }
+
+#include "oracle_partition.inc"
 
 int32_t orc_real_bytes(void) { return (int32_t)sizeof(REAL); }

@@ -186,6 +186,35 @@ def city_scene(n, area_km2, seed, sh_degree=3, origin=(0.0, 0.0), defer_sh=False
     return sc
 
 
+def unbounded_city(n, seed, area_km2=6.0, bg_frac=0.1, sh_degree=3, defer_sh=False):
+    """An unbounded scene for the block partition: the aerial city of ``city_scene`` with a
+    fraction ``bg_frac`` of its Gaussians moved to a far background (directions uniform on
+    the upper hemisphere, distances log-uniform from 1 to 30 km), as an optimised global
+    prior of a real capture has.  Returns the scene and its foreground box (the city square,
+    z from -10 m to 100 m)."""
+    sc = city_scene(n, area_km2, seed, sh_degree=sh_degree, defer_sh=defer_sh)
+    rng = np.random.default_rng(seed + 1000)
+    nb = int(round(bg_frac * n))
+    idx = np.sort(rng.choice(n, size=nb, replace=False))
+    d = rng.normal(size=(nb, 3))
+    d[:, 2] = np.abs(d[:, 2])
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    r = np.exp(rng.uniform(math.log(1000.0), math.log(30000.0), size=(nb, 1)))
+    sc["mean_opac"][idx, :3] = (d * r).astype(np.float32)
+    h = sc["side"] / 2.0
+    box = (np.array([-h, -h, -10.0], np.float32), np.array([h, h, 100.0], np.float32))
+    return sc, box
+
+
+def aerial_poses(side, n_poses, seed, alt=(150.0, 400.0)):
+    """Camera centres of an aerial capture: uniform over a square of side ``side`` (1.2 times
+    the city) at altitudes in ``alt``."""
+    rng = np.random.default_rng(seed)
+    xy = rng.uniform(-0.6 * side, 0.6 * side, size=(n_poses, 2))
+    z = rng.uniform(alt[0], alt[1], size=(n_poses, 1))
+    return np.concatenate([xy, z], axis=1).astype(np.float32)
+
+
 # ----------------------------------------------------------------------------------------
 # blocks and detail levels
 # ----------------------------------------------------------------------------------------
