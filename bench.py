@@ -63,6 +63,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-fp16-compare", action="store_true")
     ap.add_argument("--workload", default="city1m", choices=["city1m", "lod20m", "lodqueue", "train32"])
     ap.add_argument("--batched-views", type=int, default=8)
     return ap.parse_args()
@@ -395,6 +396,9 @@ def run_ours(args, world, rank, local):
     if args.batched_views > 1:
         out["batched_vs_plain"] = run_batched_compare(args, ds, sc, cfg, st, flush, world, synth, ta, cgs)
 
+    if not args.no_fp16_compare:
+        out["fp16_attributes"] = run_fp16_compare(args, sc, cfg, d_cams, tgt, ds, st, flush, world, ta, cgs)
+
     if not args.no_e2e:
         out["e2e"] = run_e2e(args, ds, frame, sc, tgt_host, tgt, step, loss, zero_accumulators, st, world)
     if rank == 0 and not args.no_cpu_baseline:
@@ -454,6 +458,56 @@ def run_batched_compare(args, ds, sc, cfg, st, flush, world, synth, ta, cgs):
             "batched_mpix_s": world * V * W * H / (tb * 1e-3) / 1e6, "batched_ms": tb,
             "sequential_mpix_s": world * V * W * H / (ts * 1e-3) / 1e6, "sequential_ms": ts,
             "speedup": ts / tb, "both": "fwd+L1+bwd, CUDA graph replay"}
+
+
+def run_fp16_compare(args, sc, cfg, d_cams, tgt, ds32, st, flush, world, ta, cgs):
+    """The same 1080p fwd+L1+bwd step with scale, rotation and SH stored as FP16 (position and
+    opacity FP32) against the FP32 scene: attribute bytes, step time and the projection and
+    projection-backward stage times (library events, eager run)."""
+    import torch
+    ds16 = ta.DeviceScene(sc, ds32.device, fp16=True)
+    W, H = 1920, 1080
+    res = {}
+    for name, ds in (("fp32", ds32), ("fp16", ds16)):
+        frame = ta.Frame(1, W, H, cfg.tile, 1, ds.n, 8_000_000, ds.device)
+        img, T, nc = frame.outputs()
+        dL = torch.empty_like(img)
+        loss = torch.zeros(1, device=ds.device)
+        f32 = torch.float32
+        grads = (torch.zeros_like(ds.mean_opac), torch.zeros(ds.scale.shape, dtype=f32, device=ds.device),
+                 torch.zeros(ds.quat.shape, dtype=f32, device=ds.device),
+                 torch.zeros(ds.sh.shape, dtype=f32, device=ds.device))
+        s_struct = ds.struct()
+
+        def one():
+            cur = torch.cuda.current_stream().cuda_stream
+            cgs.cgs_render_forward(s_struct, frame.struct, cfg, d_cams, None, None, img, T, nc, cur)
+            cgs.cgs_l1_loss(img, tgt, img.numel(), loss, dL, cur)
+            cgs.cgs_render_backward(s_struct, frame.struct, cfg, d_cams, dL, T, nc, *grads, cur)
+
+        for _ in range(2):
+            one()
+        torch.cuda.synchronize()
+        cgs.cgs_timing_enable(True)
+        for _ in range(5):
+            flush.fill_(1)
+            one()
+        torch.cuda.synchronize()
+        stg = cgs.cgs_timing_read()
+        cgs.cgs_timing_enable(False)
+        g = ta.capture(one, warmup=1)
+        k = max(3, args.steps // 2)
+        ms, _ = timed_fn(g.replay, k, st, flush, world)
+        status, _ = frame.status()
+        attr_bytes = sum(t.numel() * t.element_size() for t in (ds.mean_opac, ds.scale, ds.quat, ds.sh))
+        res[name] = {"ms_per_step": max_over_ranks(sum(ms) / len(ms), world), "attribute_bytes": attr_bytes,
+                     "project_ms": stg["project"][0] / max(1, stg["project"][1]),
+                     "project_bwd_ms": stg["project_bwd"][0] / max(1, stg["project_bwd"][1]),
+                     "status": cgs.cgs_status_string(status)}
+    res["step_speedup"] = res["fp32"]["ms_per_step"] / res["fp16"]["ms_per_step"]
+    res["project_speedup"] = res["fp32"]["project_ms"] / res["fp16"]["project_ms"]
+    res["fp16_mpix_s"] = world * W * H / (res["fp16"]["ms_per_step"] * 1e-3) / 1e6
+    return res
 
 
 def run_e2e(args, ds, frame, sc, tgt_host, tgt_dev, step, loss, zero_accumulators, st, world):

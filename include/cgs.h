@@ -51,6 +51,11 @@ typedef struct cgs_camera {
 } cgs_camera;
 
 /* Block-partitioned Gaussian scene.  Per Gaussian (Sec. 3.1): position, opacity, scale and
+ * rotation (the covariance), SH features.  With attr_fp16 the non-position attributes are
+ * stored in half precision (the transfer variant noted, commented out, after Sec. 3.3.2:
+ * position FP32, the other properties FP16; opacity stays with the position here).
+ * Original summary follows.
+ * Per Gaussian (Sec. 3.1): position, opacity, scale and
  * rotation (the covariance), SH features in R^{3x16} at degree 3.  Detail level l of block
  * b (Sec. 3.3.1/3.3.2) is the index range [level_offset[b*L + l], + level_count[b*L + l]).
  * Level 0 is the finest.  Segments of different blocks must not overlap and must ascend
@@ -65,7 +70,10 @@ typedef struct cgs_scene {
     int32_t sh_degree;           /* 0..3 */
     int32_t n_blocks;            /* >= 1 */
     int32_t n_levels;            /* >= 1 */
-    int32_t _pad;
+    int32_t attr_fp16;           /* 0: scale, quat, sh are FP32 as above; 1: they are IEEE half
+                                    (binary16) with the same shapes ([n][4], [n][4],
+                                    [n][(deg+1)^2][3]); mean_opac stays FP32.  Gradients are FP32
+                                    in the FP32 layout either way. */
     const int64_t* level_offset; /* [n_blocks][n_levels] */
     const int64_t* level_count;  /* [n_blocks][n_levels] */
     const float* block_aabb;     /* [n_blocks][6] lo xyz, hi xyz: Eq. 7 bounds (cgs_block_bounds) */

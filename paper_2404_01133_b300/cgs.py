@@ -35,7 +35,7 @@ class cgs_camera(C.Structure):
 class cgs_scene(C.Structure):
     _fields_ = [("mean_opac", C.c_void_p), ("scale", C.c_void_p), ("quat", C.c_void_p), ("sh", C.c_void_p),
                 ("n", C.c_int64), ("sh_degree", C.c_int32), ("n_blocks", C.c_int32), ("n_levels", C.c_int32),
-                ("_pad", C.c_int32), ("level_offset", C.c_void_p), ("level_count", C.c_void_p),
+                ("attr_fp16", C.c_int32), ("level_offset", C.c_void_p), ("level_count", C.c_void_p),
                 ("block_aabb", C.c_void_p), ("block_cell", C.c_void_p)]
 
 

@@ -149,6 +149,7 @@ static int sm_count()
 static bool scene_ok(const cgs_scene* s)
 {
     return s && s->n >= 0 && s->n < (1ll << 31) && s->sh_degree >= 0 && s->sh_degree <= 3 && s->n_blocks >= 1 &&
+           (s->attr_fp16 == 0 || s->attr_fp16 == 1) &&
            s->n_levels >= 1 && s->mean_opac && s->scale && s->quat && s->sh && s->level_offset && s->level_count;
 }
 

@@ -7,6 +7,8 @@
 // FP32 implementation that evaluates the same expressions in the same order.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 
 namespace cgs {
@@ -172,6 +174,45 @@ __device__ __forceinline__ void sh_grad(float x, float y, float z, int deg, floa
     dY[13][2] = -SH_K7 * (8.0f * xz);
     dY[14][0] = SH_K9 * (2.0f * xz);          dY[14][1] = SH_K9 * (-2.0f * yz); dY[14][2] = SH_K9 * (xx - yy);
     dY[15][0] = -SH_K5 * (3.0f * xx - 3.0f * yy); dY[15][1] = -SH_K5 * (-6.0f * xy);
+}
+
+__device__ __forceinline__ float h2f(unsigned short b) { return __half2float(__ushort_as_half(b)); }
+
+// Scale and rotation of Gaussian g, FP32 or FP16 storage (exact conversion to FP32).
+__device__ __forceinline__ void load_scale_quat(const cgs_scene& S, long long g, float s[3], float q[4])
+{
+    if (S.attr_fp16) {
+        const uint2 a = __ldg(reinterpret_cast<const uint2*>(S.scale) + g);
+        const uint2 b = __ldg(reinterpret_cast<const uint2*>(S.quat) + g);
+        s[0] = h2f(a.x & 0xffffu); s[1] = h2f(a.x >> 16); s[2] = h2f(a.y & 0xffffu);
+        q[0] = h2f(b.x & 0xffffu); q[1] = h2f(b.x >> 16); q[2] = h2f(b.y & 0xffffu); q[3] = h2f(b.y >> 16);
+    } else {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(S.scale) + g);
+        const float4 b = __ldg(reinterpret_cast<const float4*>(S.quat) + g);
+        s[0] = a.x; s[1] = a.y; s[2] = a.z;
+        q[0] = b.x; q[1] = b.y; q[2] = b.z; q[3] = b.w;
+    }
+}
+
+// Loads the nc*3 SH coefficients of Gaussian g from FP16 storage.
+__device__ __forceinline__ void load_sh_half(const void* __restrict__ shv, long long g, int nc, float f[48])
+{
+    const unsigned short* src = reinterpret_cast<const unsigned short*>(shv) + g * (long long)(nc * 3);
+    if (nc == 16) {
+        const uint4* s4 = reinterpret_cast<const uint4*>(src);
+#pragma unroll
+        for (int i = 0; i < 6; i++) {
+            const uint4 v = __ldg(s4 + i);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                f[8 * i + 2 * k] = h2f(w[k] & 0xffffu);
+                f[8 * i + 2 * k + 1] = h2f(w[k] >> 16);
+            }
+        }
+    } else {
+        for (int i = 0; i < nc * 3; i++) f[i] = h2f(__ldg(src + i));
+    }
 }
 
 // Loads the nc*3 SH coefficients of Gaussian g (contiguous, channel fastest).

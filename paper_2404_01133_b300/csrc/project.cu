@@ -34,8 +34,6 @@ __global__ void __launch_bounds__(256) k_project(Layout L, cgs_scene S, const cg
 {
     const uint32_t n = L.hdr->n_sel;
     const float4* __restrict__ mo4 = reinterpret_cast<const float4*>(S.mean_opac);
-    const float4* __restrict__ sc4 = reinterpret_cast<const float4*>(S.scale);
-    const float4* __restrict__ q4 = reinterpret_cast<const float4*>(S.quat);
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         int v;
         long long g;
@@ -61,9 +59,8 @@ __global__ void __launch_bounds__(256) k_project(Layout L, cgs_scene S, const cg
             keep = (long long)rank < S.level_count[(long long)blk * S.n_levels + lv];
         }
         if (keep) {
-            const float4 s4 = __ldg(sc4 + g), qq = __ldg(q4 + g);
-            const float s[3] = {s4.x, s4.y, s4.z};
-            const float q[4] = {qq.x, qq.y, qq.z, qq.w};
+            float s[3], q[4];
+            load_scale_quat(S, g, s, q);
             Proj p;
             if (project_one(m, s, q, c, near_z, p) == 0) {
                 const float r = ceilf(3.0f * sqrtf(p.lam1));
@@ -111,7 +108,8 @@ __global__ void __launch_bounds__(256) k_colour(Layout L, cgs_scene S, const cgs
         const float4 mo = __ldg(reinterpret_cast<const float4*>(S.mean_opac) + g);
         const float m[3] = {mo.x, mo.y, mo.z};
         float f[48], rgb[3], dir[3], len, Y[16];
-        load_sh(S.sh, g, nc, f);
+        if (S.attr_fp16) load_sh_half(S.sh, g, nc, f);
+        else load_sh(S.sh, g, nc, f);
         sh_colour(m, cams[v], f, deg, rgb, dir, &len, Y);
         L.rec[3 * (size_t)j + 2] = make_float4(rgb[0], rgb[1], rgb[2], L.tq[j]);
     }

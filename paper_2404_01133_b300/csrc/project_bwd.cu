@@ -31,15 +31,16 @@ __global__ void __launch_bounds__(128) k_project_bwd(Layout L, cgs_scene S, cons
         const long long g = L.gidx[j];
         const cgs_camera c = cams[v];
         const float4 mo = __ldg(reinterpret_cast<const float4*>(S.mean_opac) + g);
-        const float4 s4 = __ldg(reinterpret_cast<const float4*>(S.scale) + g);
-        const float4 q4 = __ldg(reinterpret_cast<const float4*>(S.quat) + g);
-        const float m[3] = {mo.x, mo.y, mo.z}, s[3] = {s4.x, s4.y, s4.z}, q[4] = {q4.x, q4.y, q4.z, q4.w};
+        const float m[3] = {mo.x, mo.y, mo.z};
+        float s[3], q[4];
+        load_scale_quat(S, g, s, q);
         Proj p;
         if (project_one(m, s, q, c, near_z, p) != 0) continue;
 
         // colour -> SH coefficients and the view direction
         float f[48], rgb[3], dir[3], len, Y[16], dY[16][3];
-        load_sh(S.sh, g, nc, f);
+        if (S.attr_fp16) load_sh_half(S.sh, g, nc, f);
+        else load_sh(S.sh, g, nc, f);
         const int cl = sh_colour(m, c, f, deg, rgb, dir, &len, Y);
         sh_grad(dir[0], dir[1], dir[2], deg, dY);
         float gdir[3] = {0.f, 0.f, 0.f};

@@ -49,11 +49,15 @@ def make_config(tile=16, batch=None, near_z=0.2, bg=(0.0, 0.0, 0.0), lod_dist=(2
 class DeviceScene:
     """A synth-format scene uploaded to the device, with its cgs_scene descriptor."""
 
-    def __init__(self, scene, device="cuda", attrs=None):
+    def __init__(self, scene, device="cuda", attrs=None, fp16=False):
         dev = torch.device(device)
+        self.attr_fp16 = 1 if fp16 else 0
         if attrs is None:
             attrs = {k: torch.from_numpy(np.ascontiguousarray(scene[k], np.float32)).to(dev)
                      for k in ("mean_opac", "scale", "quat", "sh")}
+            if fp16:
+                for k in ("scale", "quat", "sh"):
+                    attrs[k] = attrs[k].to(torch.float16).contiguous()
         self.mean_opac, self.scale, self.quat, self.sh = (attrs["mean_opac"], attrs["scale"], attrs["quat"],
                                                           attrs["sh"])
         self.sh_degree = int(scene["sh_degree"])
@@ -78,6 +82,7 @@ class DeviceScene:
         s.sh_degree = self.sh_degree
         s.n_blocks = self.n_blocks
         s.n_levels = self.n_levels
+        s.attr_fp16 = self.attr_fp16
         s.level_offset = self.level_offset.data_ptr()
         s.level_count = self.level_count.data_ptr()
         s.block_aabb = self.block_aabb.data_ptr()
@@ -137,9 +142,9 @@ def render_forward(dscene, frame, cfg, d_cams, view_block=None, levels=None, out
 
 def render_backward(dscene, frame, cfg, d_cams, dL_dimage, final_T, n_contrib, grads=None, attrs=None, stream=None):
     if grads is None:
-        dev = dscene.device
-        grads = (torch.zeros_like(dscene.mean_opac), torch.zeros_like(dscene.scale),
-                 torch.zeros_like(dscene.quat), torch.zeros_like(dscene.sh))
+        f32 = torch.float32
+        grads = (torch.zeros_like(dscene.mean_opac), torch.zeros_like(dscene.scale, dtype=f32),
+                 torch.zeros_like(dscene.quat, dtype=f32), torch.zeros_like(dscene.sh, dtype=f32))
     g_mo, g_sc, g_q, g_sh = grads
     _c.cgs_render_backward(dscene.struct(attrs), frame.struct, cfg, d_cams, dL_dimage.contiguous(), final_T,
                            n_contrib, g_mo, g_sc, g_q, g_sh, stream)

@@ -15,9 +15,18 @@ PIX_ATOL = 1e-4
 AMB_ATOL = 0.03
 
 
+def fp16_rounded(scene):
+    """The scene with scale, rotation and SH rounded to IEEE half and widened back to FP32:
+    the values the FP16 attribute storage variant computes with."""
+    out = dict(scene)
+    for k in ("scale", "quat", "sh"):
+        out[k] = np.asarray(scene[k], np.float32).astype(np.float16).astype(np.float32)
+    return out
+
+
 def gpu_render(scene, cams, tile=16, batch=None, n_cap=None, k_cap=None, view_block=None, levels=None,
-               n_mad=None, cfg_kw=None):
-    ds = ta.DeviceScene(scene)
+               n_mad=None, cfg_kw=None, fp16=False):
+    ds = ta.DeviceScene(scene, fp16=fp16)
     if n_mad is not None:
         ds.compute_block_bounds(n_mad)
     cfg = ta.make_config(tile=tile, batch=batch, **(cfg_kw or {}))
@@ -51,6 +60,13 @@ def frame_arrays(g, n_sel=None, k=None):
     V, T = fr.n_views, ((fr.width + fr.tile - 1) // fr.tile) * ((fr.height + fr.tile - 1) // fr.tile)
     out["ranges"] = fr.buffer(cgs.BUF_RANGES, torch.int32, (2,), count=V * T).cpu().numpy().view(np.uint32)
     return out
+
+
+def canonical_ranges(r, first=0):
+    """Per-tile [start, end) with empty tiles written as [0, 0] (the oracle's form; the GPU
+    leaves an empty tile at [e, e], the running offset, which is equally empty)."""
+    r = np.asarray(r, np.int64)
+    return np.where(r[:, 1:] > r[:, :1], r - first, 0)
 
 
 def compare_image(gimg, gT, gnc, o):
