@@ -10,7 +10,8 @@ finite-difference pins).  In both, the key path that decides integers (culls, ra
 tile rect, depth bits) is FP32.
 
 Paper passages: Eq. 1 and Sec. 3.1 (projection, SH colour, depth-sorted alpha blending,
-differentiable rendering); Sec. 3.2.2, Eqs. 2 and 4 (normalisation, contraction, block grid,
+differentiable rendering); Sec. 3.3.1 (nested detail levels from a significance ranking);
+Sec. 3.2.2, Eqs. 2 and 4 (normalisation, contraction, block grid,
 pose in block); Eq. 7 and Sec. 3.3.2 (MAD block bounds, block frustum test,
 camera block, distance-based level, concatenation).
 """
@@ -88,6 +89,8 @@ def lib(real="f32"):
         L.orc_partition_assign.restype = i64
         L.orc_partition_assign.argtypes = [i64, vp, i64, vp, vp, vp, vp, vp]
         L.orc_partition_order.argtypes = [i64, vp, i32, vp, vp]
+        L.orc_hit_counts.argtypes = [i64, vp, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp]
+        L.orc_generate_levels.argtypes = [i32, vp, vp, vp, vp, vp, i32, vp, vp, vp]
         L.orc_real_bytes.restype = i32
         _LIBS[real] = L
     return _LIBS[real]
@@ -333,3 +336,45 @@ def pose_blocks(campos, pmin, pmax, grid):
     """Eq. 4 (B2): the block that contains each camera centre after normalisation and
     contraction."""
     return partition_assign(np.asarray(campos, np.float32).reshape(-1, 3), pmin, pmax, grid)["block"]
+
+
+# ---- detail levels (Sec. 3.3.1) ----------------------------------------------------------
+
+def hit_counts(scene, cams, cfg=None, idx=None):
+    """Pixels blending each scene Gaussian, summed over the views: (hits, amb_hits) as int64
+    arrays over the scene (idx selects the rendered subset, as in render)."""
+    cfg = cfg or make_config()
+    L = lib("f32")
+    n_scene = scene["mean_opac"].shape[0]
+    hits = np.zeros(n_scene, np.int64)
+    amb = np.zeros(n_scene, np.int64)
+    for cam in cams:
+        pr = project(scene, cam, cfg, idx=idx)
+        srt = bin_and_sort(pr, cam, cfg)
+        n = pr["depth"].shape[0]
+        h = np.zeros(n, np.int64)
+        a = np.zeros(n, np.int64)
+        vals = srt["vals"] if srt["vals"].size else np.zeros(1, np.uint32)
+        L.orc_hit_counts(n, _p(pr["xy"]), _p(pr["conic"]), _p(pr["arrays"][0]), _p(pr["rgb"]), _p(vals),
+                         _p(srt["ranges"]), cam["width"], cam["height"], C.byref(cfg), _p(h), _p(a))
+        rows = np.arange(n_scene) if idx is None else np.asarray(idx)
+        np.add.at(hits, rows, h)
+        np.add.at(amb, rows, a)
+    return hits, amb
+
+
+def generate_levels(scene, rates, hits=None):
+    """Nested levels of a block-grouped scene (one level per block in level_offset /
+    level_count on input): the ranked permutation and level_count [n_blocks][len(rates)]."""
+    off = np.ascontiguousarray(scene["level_offset"][:, 0], np.int64)
+    cnt = np.ascontiguousarray(scene["level_count"][:, 0], np.int64)
+    nb = off.shape[0]
+    mo = np.ascontiguousarray(scene["mean_opac"], np.float32)
+    sc = np.ascontiguousarray(scene["scale"], np.float32)
+    n = mo.shape[0]
+    perm = np.arange(n, dtype=np.int64)
+    r = np.ascontiguousarray(rates, np.float64)
+    lc = np.zeros((nb, len(r)), np.int64)
+    h = None if hits is None else np.ascontiguousarray(hits, np.int64)
+    lib("f32").orc_generate_levels(nb, _p(off), _p(cnt), _p(mo), _p(sc), _p(h), len(r), _p(r), _p(perm), _p(lc))
+    return perm, lc
