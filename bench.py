@@ -64,7 +64,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-fp16-compare", action="store_true")
-    ap.add_argument("--workload", default="city1m", choices=["city1m", "lod20m", "lodqueue", "train32"])
+    ap.add_argument("--workload", default="city1m", choices=["city1m", "lod20m", "lodqueue", "train32", "partition", "levels"])
     ap.add_argument("--batched-views", type=int, default=8)
     return ap.parse_args()
 
@@ -248,6 +248,13 @@ def run_ours(args, world, rank, local):
         # applies the optimizer -- one memset, outside the timed step
         grad_flat.zero_()
 
+    def step_with(tgt_buf, cam_buf):
+        # the same step reading the target image and the camera from the given device buffers
+        cur = torch.cuda.current_stream().cuda_stream
+        cgs.cgs_render_forward(s_struct, frame.struct, cfg, cam_buf, None, None, img, T, nc, cur)
+        cgs.cgs_l1_loss(img, tgt_buf, img.numel(), loss, dL, cur)
+        cgs.cgs_render_backward(s_struct, frame.struct, cfg, cam_buf, dL, T, nc, *grads, cur)
+
     def step(fwd_only=False):
         # the current stream at call time (the capture stream while a CUDA graph is recorded)
         cur = torch.cuda.current_stream().cuda_stream
@@ -400,7 +407,9 @@ def run_ours(args, world, rank, local):
         out["fp16_attributes"] = run_fp16_compare(args, sc, cfg, d_cams, tgt, ds, st, flush, world, ta, cgs)
 
     if not args.no_e2e:
-        out["e2e"] = run_e2e(args, ds, frame, sc, tgt_host, tgt, step, loss, zero_accumulators, st, world)
+        out["e2e"] = run_e2e(args, frame, cams, tgt_host, step_with, loss, zero_accumulators, st, world)
+        out["e2e_scene_upload"] = run_e2e_scene_upload(args, ds, frame, sc, tgt_host, tgt, step, loss,
+                                                       zero_accumulators, st, world)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, cam, full=True)
     return out
@@ -510,10 +519,64 @@ def run_fp16_compare(args, sc, cfg, d_cams, tgt, ds32, st, flush, world, ta, cgs
     return res
 
 
-def run_e2e(args, ds, frame, sc, tgt_host, tgt_dev, step, loss, zero_accumulators, st, world):
-    """Same step through the public API with HOST inputs: every step copies the scene and the
+def run_e2e(args, frame, cams, tgt_host, step_with, loss, zero_accumulators, st, world):
+    """The training step end to end through the public API with its per-step inputs on the
+    HOST: every step copies its camera and its target image from pinned host memory, runs
+    forward + L1 + backward, and reads the loss back; the Gaussian parameters (the model) stay
+    resident, as weights do in training.  Copies run on a second stream into two alternating
+    buffers, so step i+1's copy overlaps step i's kernels; every copy is inside the timed
+    region."""
+    import torch
+    from paper_2404_01133_b300 import torch_api as ta
+    cam_host = ta.cameras_host(cams[:1])
+    bufs = [(torch.empty(tgt_host.shape, dtype=tgt_host.dtype, device="cuda"),
+             torch.empty(cam_host.shape, dtype=cam_host.dtype, device="cuda")) for _ in range(2)]
+    cs = torch.cuda.Stream()
+    ready = [torch.cuda.Event() for _ in range(2)]
+    free = [torch.cuda.Event() for _ in range(2)]
+    k = max(3, min(args.steps, 20))
+    loss_host = torch.empty(k, dtype=torch.float32).pin_memory()
+    h2d = tgt_host.numel() * tgt_host.element_size() + cam_host.numel()
+
+    def copy_in(i):
+        b = i % 2
+        cs.wait_event(free[b])      # the buffer's previous step has finished with it
+        with torch.cuda.stream(cs):
+            bufs[b][0].copy_(tgt_host, non_blocking=True)
+            bufs[b][1].copy_(cam_host, non_blocking=True)
+        ready[b].record(cs)
+
+    def run(k_):
+        copy_in(0)
+        for i in range(k_):
+            if i + 1 < k_:
+                copy_in(i + 1)
+            b = i % 2
+            st.wait_event(ready[b])
+            zero_accumulators()
+            step_with(bufs[b][0], bufs[b][1])
+            free[b].record(st)
+            loss_host[i:i + 1].copy_(loss, non_blocking=True)
+
+    run(2)
+    torch.cuda.synchronize()
+    barrier(world)
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    run(k)
+    e.record(st)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(a.elapsed_time(e) / k, world)
+    W, H = frame.width, frame.height
+    return {"value": world * W * H / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4,
+            "inputs": "per step: camera + target image (pinned host, copy stream overlapped); model resident"}
+
+
+def run_e2e_scene_upload(args, ds, frame, sc, tgt_host, tgt_dev, step, loss, zero_accumulators, st, world):
+    """The step with the whole scene re-uploaded as well: every step copies the scene and the
     target from pinned host memory to the device, clears the accumulators, runs the step and
-    reads the loss back; all of it inside the timed region."""
+    reads the loss back; all of it inside the timed region (bound by the host link)."""
     import torch
     host = {k: torch.from_numpy(np.ascontiguousarray(sc[k], np.float32)).pin_memory()
             for k in ("mean_opac", "scale", "quat", "sh")}
@@ -679,6 +742,195 @@ def run_lod20m(args, world):
             "per_height": rows}
 
 
+def run_partition(args, world):
+    """Block partition of the 20M-Gaussian SH-3 unbounded city (Sec. 3.2.2): block of every
+    Gaussian after normalisation and contraction (Eq. 2), stable grouping by block, and the
+    gather of position, scale, rotation and SH rows into block segments; plus the block of
+    every pose of an aerial capture (Eq. 4)."""
+    import torch
+    from paper_2404_01133_b300 import build as libbuild, cgs, synth
+    from paper_2404_01133_b300 import torch_api as ta
+    libbuild.build()
+    t0 = time.time()
+    sc, box = synth.unbounded_city(20_000_000, seed=3)
+    t_gen = time.time() - t0
+    grid = (8, 8, 1)
+    nb = 64
+    dev = torch.device("cuda")
+    src = {k: torch.from_numpy(np.ascontiguousarray(sc[k], np.float32)).to(dev) for k in ("mean_opac", "scale", "quat", "sh")}
+    n = src["mean_opac"].shape[0]
+    dst = {k: torch.empty_like(v) for k, v in src.items()}
+    ws_bytes = cgs.cgs_partition_workspace_bytes(n, grid)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    block = torch.empty(n, dtype=torch.int32, device=dev)
+    offset = torch.empty(nb + 1, dtype=torch.int64, device=dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    rank = torch.empty(n, dtype=torch.int32, device=dev)
+    row_bytes = {k: v[0].numel() * 4 for k, v in src.items()}
+    poses = torch.from_numpy(synth.aerial_poses(sc["side"], 5000, seed=9)).to(dev)
+    pose_block = torch.empty(5000, dtype=torch.int32, device=dev)
+    st = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def assign_group():
+        cgs.cgs_partition(src["mean_opac"], n, 4, box[0], box[1], grid, block, offset, perm, rank, ws, ws_bytes, st)
+
+    assign_group()
+    torch.cuda.synchronize()
+    n_grouped = int(offset[-1].item())  # rows the permutation defines (all, unless positions are non-finite)
+
+    def gather():
+        for k in src:
+            cgs.cgs_gather_rows(src[k], dst[k], row_bytes[k], perm, n_grouped, st)
+
+    def scatter():
+        # the same move through the inverse permutation: sequential reads
+        for k in src:
+            cgs.cgs_scatter_rows(src[k], dst[k], row_bytes[k], rank, n, st)
+
+    def step():
+        assign_group()
+        scatter()
+        cgs.cgs_pose_blocks(poses, 5000, 3, box[0], box[1], grid, pose_block, st)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if cgs.cgs_partition_status(ws) != cgs.CGS_OK:
+        raise RuntimeError("partition status")
+    off = offset.cpu().numpy()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms, launches = timed_fn(step, args.steps, st, flush, world)
+    clk = clocks.stop()
+    ms_a, _ = timed_fn(assign_group, args.steps, st, flush, world)
+    ms_g, _ = timed_fn(gather, args.steps, st, flush, world)
+    ms_s, _ = timed_fn(scatter, args.steps, st, flush, world)
+    t = max_over_ranks(sum(ms) / len(ms), world)
+    ta_ = max_over_ranks(sum(ms_a) / len(ms_a), world)
+    tg = max_over_ranks(sum(ms_g) / len(ms_g), world)
+    ts = max_over_ranks(sum(ms_s) / len(ms_s), world)
+    peaks, peak_src = load_peaks()
+    # algorithmic bytes: the row move reads and writes every row once and reads the
+    # permutation once per array; assign+group reads the 16-byte position row, writes the
+    # block, reads it back and writes the permutation and its inverse
+    g_bytes = n_grouped * sum(2 * b + 4 for b in row_bytes.values())
+    a_bytes = n * (16 + 4 + 4 + 4 + 4)
+    achieved = g_bytes / (ts * 1e-3) / 1e9
+    return {"metric": "Gaussians partitioned per second (contract + grid + stable grouping + gather), 20M SH3",
+            "value": world * n / (t * 1e-3), "unit": "Gaussians/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak", "dtype": "f32",
+            "data": "synthetic", "gpu_launches": launches, "clocks": clk,
+            "config": {"workload": "unbounded city 20M SH3 (10% far background), 8x8x1 blocks over the contracted "
+                                   "cube, 5000 aerial poses", "gaussians": n, "grid": list(grid),
+                       "l2": "flushed between timed steps (256 MB write)", "generation_s": t_gen},
+            "stage_ms": {"assign_group": ta_, "scatter": ts, "gather_alternative": tg},
+            "block_sizes": {"min": int(np.diff(off).min()), "max": int(np.diff(off).max()),
+                            "grouped": int(off[-1])},
+            "roofline": {"bound": "hbm", "kernel": "k_scatter_rows", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                         "peak_source": peak_src},
+            "roofline_assign_group": {"achieved": a_bytes / (ta_ * 1e-3) / 1e9,
+                                      "frac": a_bytes / (ta_ * 1e-3) / 1e9 / peaks["hbm_gbs"]}}
+
+
+def run_levels(args, world):
+    """Detail-level generation on the device for the 20M-Gaussian SH-3 unbounded city
+    (Sec. 3.3.1): partition into 8x8 blocks and group, count per-Gaussian pixel hits over 8
+    aerial 1080p views (one batched forward), rank every block by hit-weighted opacity x
+    volume, and gather the attributes into the nested-level order (100/50/25%)."""
+    import torch
+    from paper_2404_01133_b300 import build as libbuild, cgs, synth
+    from paper_2404_01133_b300 import torch_api as ta
+    libbuild.build()
+    t0 = time.time()
+    sc, box = synth.unbounded_city(20_000_000, seed=3)
+    t_gen = time.time() - t0
+    grid, nb = (8, 8, 1), 64
+    dev = torch.device("cuda")
+    keys = ("mean_opac", "scale", "quat", "sh")
+    src = {k: torch.from_numpy(np.ascontiguousarray(sc[k], np.float32)).to(dev) for k in keys}
+    n = src["mean_opac"].shape[0]
+    row_bytes = {k: v[0].numel() * 4 for k, v in src.items()}
+    block, off, perm, _ = ta.partition(src["mean_opac"], box[0], box[1], grid)
+    grouped = {k: ta.gather_rows(src[k], perm) for k in keys}
+    del src
+    off_h = off.cpu().numpy()
+    gsc = {"sh_degree": sc["sh_degree"], "level_offset": off_h[:nb, None], "level_count": np.diff(off_h)[:, None],
+           "block_cell": np.zeros((nb, 4), np.float32)}
+    ds = ta.DeviceScene(gsc, dev, attrs=grouped)
+    side = sc["side"]
+    cams = [synth.pitched_camera((0.35 * side * math.cos(a), 0.35 * side * math.sin(a), 300.0), a + math.pi / 2,
+                                 math.radians(45.0), 1200.0, 1200.0, 1920, 1080)
+            for a in np.linspace(0.0, 2 * math.pi, 8, endpoint=False)]
+    V = len(cams)
+    lv = torch.zeros((V, nb), dtype=torch.int8, device=dev)
+    sel, ent = ta.frame_counts(ds, cams, 1920, 1080, levels=lv)
+    frame = ta.Frame(V, 1920, 1080, 16, nb, int(sum(sel) * 1.02) + 1024, min((1 << 30) - 1, int(sum(ent) * 1.05) + 65536))
+    d_cams = ta.cameras_device(cams)
+    cfg = ta.make_config(tile=16, batch=256)
+    img, T, nc = frame.outputs()
+    hits = torch.zeros(n, dtype=torch.int32, device=dev)
+    rates = [1.0, 0.5, 0.25]
+    lws_bytes = cgs.cgs_levels_workspace_bytes(n, nb)
+    lws = torch.empty(lws_bytes, dtype=torch.uint8, device=dev)
+    lperm = torch.empty(n, dtype=torch.int32, device=dev)
+    lc = torch.empty((nb, 3), dtype=torch.int64, device=dev)
+    final = {k: torch.empty_like(v) for k, v in grouped.items()}
+    st = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def count_hits():
+        hits.zero_()
+        cgs.cgs_render_forward_hits(ds.struct(), frame.struct, cfg, d_cams, None, lv, img, T, nc, hits, st)
+
+    def rank():
+        cgs.cgs_generate_levels(grouped["mean_opac"], grouped["scale"], 0, n, off, nb, hits, rates, lperm, lc, lws,
+                                lws_bytes, st)
+
+    def gather():
+        for k in keys:
+            cgs.cgs_gather_rows(grouped[k], final[k], row_bytes[k], lperm, n, st)
+
+    for _ in range(args.warmup):
+        count_hits(); rank(); gather()
+    torch.cuda.synchronize()
+    status, counts = frame.status()
+    if status != cgs.CGS_OK or cgs.cgs_levels_status(lws) != cgs.CGS_OK:
+        raise RuntimeError("levels workload status")
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms_h, l1 = timed_fn(count_hits, args.steps, st, flush, world)
+    ms_r, l2 = timed_fn(rank, args.steps, st, flush, world)
+    ms_g, l3 = timed_fn(gather, args.steps, st, flush, world)
+    clk = clocks.stop()
+    th, tr, tg = (max_over_ranks(sum(m) / len(m), world) for m in (ms_h, ms_r, ms_g))
+    peaks, peak_src = load_peaks()
+    passes = 4 + 1
+    # per radix pass: histogram reads the keys (8 B), scatter reads key + row (12 B) and writes
+    # them (12 B); the key pass reads opacity, scale and hits (4 + 16 + 4 B) and writes 12 B
+    r_bytes = n * (passes * 32 + 36)
+    g_bytes = n * sum(2 * b + 4 for b in row_bytes.values())
+    lc_h = lc.cpu().numpy()
+    hh = hits.cpu().numpy()
+    return {"metric": "Gaussians ranked into nested detail levels per second (hit-weighted significance, 20M SH3)",
+            "value": world * n / ((tr + tg) * 1e-3), "unit": "Gaussians/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": th + tr + tg, "higher_is_better": True, "scaling": "weak",
+            "dtype": "f32", "data": "synthetic", "gpu_launches": l1 + l2 + l3, "clocks": clk,
+            "config": {"workload": "unbounded city 20M SH3, 8x8x1 contracted blocks, hits over 8 aerial 1080p views "
+                                   "(300 m, 45 deg), levels 100/50/25%", "gaussians": n, "views": V,
+                       "l2": "flushed between timed calls (256 MB write)", "generation_s": t_gen},
+            "stage_ms": {"hit_count_render_8_views": th, "rank": tr, "gather": tg},
+            "hit_stats": {"gaussians_hit": int((hh > 0).sum()), "total_hits": int(hh.astype(np.int64).sum()),
+                          "entries": counts[2], "fwd_pairs": counts[3]},
+            "level_sizes": lc_h.sum(axis=0).tolist(),
+            "roofline": {"bound": "hbm", "kernel": "rank (radix passes)", "achieved": r_bytes / (tr * 1e-3) / 1e9,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": r_bytes / (tr * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                         "traffic": None, "peak_source": peak_src},
+            "roofline_gather": {"achieved": g_bytes / (tg * 1e-3) / 1e9,
+                                "frac": g_bytes / (tg * 1e-3) / 1e9 / peaks["hbm_gbs"]}}
+
+
 def run_lodqueue(args, world):
     """64 seeded top-down poses over the 20M-Gaussian LoD city: batched frames (views grouped
     to fit the frame capacity, one CUDA graph) against 64 sequential one-view renders."""
@@ -822,6 +1074,10 @@ def main():
         out = run_lodqueue(args, world)
     elif args.workload == "train32":
         out = run_train32(args, world)
+    elif args.workload == "partition":
+        out = run_partition(args, world)
+    elif args.workload == "levels":
+        out = run_levels(args, world)
     else:
         out = run_ours(args, world, rank, local)
     if rank == 0:

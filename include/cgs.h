@@ -249,6 +249,105 @@ int32_t cgs_timing_read(double* ms /*[CGS_N_STAGES]*/, int64_t* count /*[CGS_N_S
 /* Number of CUDA kernels this library has launched in the process so far (host counter). */
 int64_t cgs_kernel_launches(void);
 
+/* cgs_render_forward that also counts, for every scene Gaussian, the pixels (over all views of
+ * the frame) whose compositing blends it: d_hits[scene index] += that count.  d_hits is a
+ * device array of scene->n uint32 owned by the caller and only added to (clear it to start a
+ * count; accumulate over frames to count over many views).  The image, T and n_contrib
+ * outputs are those of cgs_render_forward.  The counts are the hit term of the significance
+ * ranking that builds the detail levels (Sec. 3.3.1, cgs_generate_levels). */
+int32_t cgs_render_forward_hits(const cgs_scene* scene, const cgs_frame* frame, const cgs_config* cfg,
+                                const cgs_camera* d_cams, const int32_t* d_view_block, const int8_t* d_levels,
+                                float* d_image, float* d_final_T, uint32_t* d_n_contrib, uint32_t* d_hits,
+                                void* stream);
+
+/* ---- Detail levels (Sec. 3.3.1) ---------------------------------------------------------
+ * Input: a block-grouped scene of n rows, block b = rows [d_block_offset[b],
+ * d_block_offset[b + 1]) (offsets non-decreasing, offset[0] = 0, offset[n_blocks] = n: what
+ * cgs_partition writes).  Inside every block the rows are ranked by descending significance
+ *     s = o * ((s_x * s_y) * s_z)                   (d_hits == NULL: opacity x volume)
+ *     s = (float)h * (o * ((s_x * s_y) * s_z))      (d_hits: pixel hit counts per row, from
+ *                                                    cgs_render_forward_hits)
+ * in FP32, this order; NaN ranks as -inf, -0 as +0; equal scores by increasing row.  Level l
+ * of a block of K rows keeps the first floor(K * rates[l]) rows (FP64 product, rates in
+ * [0, 1]), so the levels are nested prefixes of one order (the paper prunes with a
+ * compressor at several rates; level 0 is the finest here).
+ * Outputs: d_perm[n], position offset[b] + r = row of rank r in block b (gather the
+ * attributes with cgs_gather_rows), and d_level_count[n_blocks][n_levels]; the new scene's
+ * level_offset[b][l] is offset[b] for every l.  d_scale is [n][4] FP32, or [n][4] FP16 with
+ * attr_fp16 = 1.  n_blocks <= CGS_PARTITION_MAX_BLOCKS, n_levels <= CGS_MAX_LEVELS.
+ * Asynchronous; cgs_levels_status reads the device status. */
+#define CGS_MAX_LEVELS 16
+int64_t cgs_levels_workspace_bytes(int64_t n, int32_t n_blocks);
+int32_t cgs_generate_levels(const float* d_mean_opac, const void* d_scale, int32_t attr_fp16, int64_t n,
+                            const int64_t* d_block_offset, int32_t n_blocks, const uint32_t* d_hits,
+                            const double* rates, int32_t n_levels, int32_t* d_perm, int64_t* d_level_count,
+                            void* d_ws, int64_t ws_bytes, void* stream);
+/* Synchronises the stream; CGS_OK or CGS_ERR_SPIN_TIMEOUT for the last call on d_ws. */
+int32_t cgs_levels_status(const void* d_ws, void* stream);
+
+/* ---- Block partition of a scene (Sec. 3.2.2, Eqs. 2 and 4) --------------------------------
+ * Positions are rows of `stride` floats with x, y, z first (stride 4 reads the mean_opac rows
+ * of a scene directly; stride 3 reads plain xyz).  pmin, pmax (3 floats each) and grid
+ * (3 int32) are HOST pointers; every other pointer is device memory owned by the caller.
+ *
+ *   normalisation  h = 2 (p - pmin) / (pmax - pmin) - 1, per axis (the foreground box
+ *                  [pmin, pmax] maps to [-1, 1]^3); pmax > pmin, finite, on every axis
+ *   contraction    Eq. 2: h if ||h||_inf <= 1, else (2 - 1/||h||_inf) h / ||h||_inf, a point
+ *                  of the open cube (-2, 2)^3
+ *   grid           the contracted cube split evenly into grid[0] x grid[1] x grid[2] blocks
+ *                  (1..CGS_PARTITION_MAX_CELLS cells per axis, at most
+ *                  CGS_PARTITION_MAX_BLOCKS blocks): along an axis of g cells the inner bounds
+ *                  are b_i = 4 i / g - 2 and a coordinate c is in cell i when b_i <= c < b_{i+1}
+ *                  (the outer cells are open to -inf and +inf); block = ix + grid[0] (iy +
+ *                  grid[1] iz); -1 when the contracted point is not finite
+ * Every value that decides a block is FP32, one rounding per operation, in the order above.
+ * Invalid arguments return CGS_ERR_INVALID_ARGUMENT before any device work. */
+#define CGS_PARTITION_MAX_CELLS 64
+#define CGS_PARTITION_MAX_BLOCKS 1024
+
+/* Contracted positions d_out[n][3] (Eq. 2 after the normalisation).  Asynchronous. */
+int32_t cgs_contract(const float* d_pos, int64_t n, int64_t stride, const float* pmin, const float* pmax,
+                     float* d_out, void* stream);
+
+/* Eq. 4 (B2): d_block[i] = block of camera centre i, the same mapping as a Gaussian's. */
+int32_t cgs_pose_blocks(const float* d_pos, int64_t n, int64_t stride, const float* pmin, const float* pmax,
+                        const int32_t* grid, int32_t* d_block, void* stream);
+
+/* Bytes of device workspace cgs_partition needs for n points and this grid; -1 if invalid. */
+int64_t cgs_partition_workspace_bytes(int64_t n, const int32_t* grid);
+
+/* The partition of n < 2^31 Gaussians: d_block[n] (block per Gaussian, -1 for none),
+ * d_block_offset[n_blocks + 1] (first grouped position of every block; the last entry is the
+ * number of grouped Gaussians, n minus those with no block) and, if d_perm is not NULL,
+ * d_perm[offset[n_blocks]]: the scene index of every grouped position, block 0's Gaussians
+ * first, each block in increasing scene index (a stable grouping, Sec. 3.2.2's G_Kj), and,
+ * if d_rank is not NULL, d_rank[n]: the grouped position of every scene index (-1 for none),
+ * the inverse permutation.
+ * d_ws holds at least cgs_partition_workspace_bytes(n, grid) bytes, 256-byte aligned, not
+ * shared with a concurrent call.  Asynchronous; read the device status with
+ * cgs_partition_status.  Returns CGS_ERR_WORKSPACE_TOO_SMALL for a short workspace. */
+int32_t cgs_partition(const float* d_pos, int64_t n, int64_t stride, const float* pmin, const float* pmax,
+                      const int32_t* grid, int32_t* d_block, int64_t* d_block_offset, int32_t* d_perm,
+                      int32_t* d_rank, void* d_ws, int64_t ws_bytes, void* stream);
+
+/* Synchronises the stream and returns CGS_OK or CGS_ERR_SPIN_TIMEOUT (a bounded wait of the
+ * offsets scan gave up; outputs invalid) for the last cgs_partition on d_ws. */
+int32_t cgs_partition_status(const void* d_ws, void* stream);
+
+/* Row gather: dst row r = src row d_perm[r], for n_rows rows of row_bytes bytes (a multiple
+ * of 4).  Moves any per-Gaussian attribute array (FP32 or FP16) into the grouped order, so
+ * that each block's Gaussians form one contiguous segment.  src and dst must not overlap;
+ * every d_perm value must be a valid row of src.  Asynchronous. */
+int32_t cgs_gather_rows(const void* d_src, void* d_dst, int64_t row_bytes, const int32_t* d_perm, int64_t n_rows,
+                        void* stream);
+
+/* Row scatter, the inverse move: dst row d_rank[r] = src row r for n_rows rows (rows with a
+ * negative rank are skipped).  With the d_rank of cgs_partition it produces the grouped order
+ * while reading src sequentially (the faster of the two for rows of 16 bytes).  Every
+ * non-negative rank must be a valid row of dst and distinct.  Asynchronous. */
+int32_t cgs_scatter_rows(const void* d_src, void* d_dst, int64_t row_bytes, const int32_t* d_rank, int64_t n_rows,
+                         void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -341,8 +341,9 @@ def pose_blocks(campos, pmin, pmax, grid):
 # ---- detail levels (Sec. 3.3.1) ----------------------------------------------------------
 
 def hit_counts(scene, cams, cfg=None, idx=None):
-    """Pixels blending each scene Gaussian, summed over the views: (hits, amb_hits) as int64
-    arrays over the scene (idx selects the rendered subset, as in render)."""
+    """Pixels blending each scene Gaussian, summed over the views: (hits, unsure) as int64
+    arrays over the scene, unsure counting the pixels where that Gaussian's own decision lies
+    within a rounding margin of its threshold (idx selects the rendered subset, as in render)."""
     cfg = cfg or make_config()
     L = lib("f32")
     n_scene = scene["mean_opac"].shape[0]

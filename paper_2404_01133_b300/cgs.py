@@ -97,6 +97,29 @@ def lib():
         L.cgs_render_forward_static.argtypes = [P(cgs_scene), P(cgs_config), vp, i32, i32, vp, vp, vp, vp, vp, vp, vp]
         L.cgs_frame_buffer.restype = i32
         L.cgs_frame_buffer.argtypes = [P(cgs_frame), i32, P(vp), P(i64)]
+        L.cgs_render_forward_hits.restype = i32
+        L.cgs_render_forward_hits.argtypes = [P(cgs_scene), P(cgs_frame), P(cgs_config), vp, vp, vp, vp, vp, vp, vp,
+                                              vp]
+        L.cgs_levels_workspace_bytes.restype = i64
+        L.cgs_levels_workspace_bytes.argtypes = [i64, i32]
+        L.cgs_generate_levels.restype = i32
+        L.cgs_generate_levels.argtypes = [vp, vp, i32, i64, vp, i32, vp, vp, i32, vp, vp, vp, i64, vp]
+        L.cgs_levels_status.restype = i32
+        L.cgs_levels_status.argtypes = [vp, vp]
+        L.cgs_contract.restype = i32
+        L.cgs_contract.argtypes = [vp, i64, i64, vp, vp, vp, vp]
+        L.cgs_pose_blocks.restype = i32
+        L.cgs_pose_blocks.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp]
+        L.cgs_partition_workspace_bytes.restype = i64
+        L.cgs_partition_workspace_bytes.argtypes = [i64, vp]
+        L.cgs_partition.restype = i32
+        L.cgs_partition.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp, i64, vp]
+        L.cgs_scatter_rows.restype = i32
+        L.cgs_scatter_rows.argtypes = [vp, vp, i64, vp, i64, vp]
+        L.cgs_partition_status.restype = i32
+        L.cgs_partition_status.argtypes = [vp, vp]
+        L.cgs_gather_rows.restype = i32
+        L.cgs_gather_rows.argtypes = [vp, vp, i64, vp, i64, vp]
         _lib = L
     return _lib
 
@@ -218,3 +241,84 @@ def cgs_frame_buffer(frame, which):
     n = C.c_int64(0)
     _check(lib().cgs_frame_buffer(C.byref(frame), which, C.byref(p), C.byref(n)), "cgs_frame_buffer")
     return p.value, n.value
+
+
+# ---------------------------------------------------------------------------------------
+# block partition (Sec. 3.2.2, Eqs. 2 and 4); pmin, pmax, grid are host sequences
+# ---------------------------------------------------------------------------------------
+CGS_PARTITION_MAX_CELLS = 64
+CGS_PARTITION_MAX_BLOCKS = 1024
+
+
+def _host_f3(v):
+    return (C.c_float * 3)(*[float(x) for x in v])
+
+
+def _host_i3(v):
+    return (C.c_int32 * 3)(*[int(x) for x in v])
+
+
+def cgs_contract(d_pos, n, stride, pmin, pmax, d_out, stream=None):
+    return _check(lib().cgs_contract(_ptr(d_pos), n, stride, _host_f3(pmin), _host_f3(pmax), _ptr(d_out),
+                                     _stream(stream)), "cgs_contract")
+
+
+def cgs_pose_blocks(d_pos, n, stride, pmin, pmax, grid, d_block, stream=None):
+    return _check(lib().cgs_pose_blocks(_ptr(d_pos), n, stride, _host_f3(pmin), _host_f3(pmax), _host_i3(grid),
+                                        _ptr(d_block), _stream(stream)), "cgs_pose_blocks")
+
+
+def cgs_partition_workspace_bytes(n, grid):
+    return lib().cgs_partition_workspace_bytes(n, _host_i3(grid))
+
+
+def cgs_partition(d_pos, n, stride, pmin, pmax, grid, d_block, d_block_offset, d_perm, d_rank, d_ws, ws_bytes,
+                  stream=None):
+    return _check(lib().cgs_partition(_ptr(d_pos), n, stride, _host_f3(pmin), _host_f3(pmax), _host_i3(grid),
+                                      _ptr(d_block), _ptr(d_block_offset), _ptr(d_perm), _ptr(d_rank), _ptr(d_ws),
+                                      ws_bytes, _stream(stream)), "cgs_partition")
+
+
+def cgs_scatter_rows(d_src, d_dst, row_bytes, d_rank, n_rows, stream=None):
+    return _check(lib().cgs_scatter_rows(_ptr(d_src), _ptr(d_dst), row_bytes, _ptr(d_rank), n_rows,
+                                         _stream(stream)), "cgs_scatter_rows")
+
+
+def cgs_partition_status(d_ws, stream=None):
+    return lib().cgs_partition_status(_ptr(d_ws), _stream(stream))
+
+
+def cgs_gather_rows(d_src, d_dst, row_bytes, d_perm, n_rows, stream=None):
+    return _check(lib().cgs_gather_rows(_ptr(d_src), _ptr(d_dst), row_bytes, _ptr(d_perm), n_rows,
+                                        _stream(stream)), "cgs_gather_rows")
+
+
+# ---------------------------------------------------------------------------------------
+# detail levels (Sec. 3.3.1)
+# ---------------------------------------------------------------------------------------
+CGS_MAX_LEVELS = 16
+
+
+def cgs_render_forward_hits(scene, frame, cfg, d_cams, d_view_block, d_levels, d_image, d_final_T, d_n_contrib,
+                            d_hits, stream=None):
+    return _check(lib().cgs_render_forward_hits(C.byref(scene), C.byref(frame), C.byref(cfg), _ptr(d_cams),
+                                                _ptr(d_view_block), _ptr(d_levels), _ptr(d_image), _ptr(d_final_T),
+                                                _ptr(d_n_contrib), _ptr(d_hits), _stream(stream)),
+                  "cgs_render_forward_hits")
+
+
+def cgs_levels_workspace_bytes(n, n_blocks):
+    return lib().cgs_levels_workspace_bytes(n, n_blocks)
+
+
+def cgs_generate_levels(d_mean_opac, d_scale, attr_fp16, n, d_block_offset, n_blocks, d_hits, rates, d_perm,
+                        d_level_count, d_ws, ws_bytes, stream=None):
+    r = (C.c_double * len(rates))(*[float(x) for x in rates])
+    return _check(lib().cgs_generate_levels(_ptr(d_mean_opac), _ptr(d_scale), attr_fp16, n, _ptr(d_block_offset),
+                                            n_blocks, _ptr(d_hits), r, len(rates), _ptr(d_perm),
+                                            _ptr(d_level_count), _ptr(d_ws), ws_bytes, _stream(stream)),
+                  "cgs_generate_levels")
+
+
+def cgs_levels_status(d_ws, stream=None):
+    return lib().cgs_levels_status(_ptr(d_ws), _stream(stream))

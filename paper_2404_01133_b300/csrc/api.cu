@@ -127,6 +127,7 @@ static bool make_layout(const cgs_frame* f, Layout* L, size_t* bytes)
     const int nw = (l.B * l.B) / 64;
     l.cbits_words = (long long)nw * (l.k_cap / 32 + vt + 1);
     l.cbits = c.take<uint32_t>(l.cbits_words);
+    l.hits = nullptr;
     *L = l;
     *bytes = c.off;
     return true;
@@ -161,6 +162,10 @@ static bool config_ok(const cgs_config* c, int tile)
     if (b != 32 && b != 64 && b != 128 && b != 256) return false;
     return b <= tile * tile;
 }
+
+// shared with the entry points of the other files (partition.cu)
+void count_launches(int n) { counted(n); }
+int device_sm_count() { return sm_count(); }
 
 }  // namespace cgs
 
@@ -231,13 +236,14 @@ int32_t cgs_lod_select(const cgs_scene* scene, const cgs_config* cfg, const cgs_
     return cudaGetLastError() == cudaSuccess ? CGS_OK : CGS_ERR_CUDA;
 }
 
-int32_t cgs_render_forward(const cgs_scene* scene, const cgs_frame* frame, const cgs_config* cfg,
-                           const cgs_camera* d_cams, const int32_t* d_view_block, const int8_t* d_levels,
-                           float* d_image, float* d_final_T, uint32_t* d_n_contrib, void* stream)
+static int32_t render_forward(const cgs_scene* scene, const cgs_frame* frame, const cgs_config* cfg,
+                              const cgs_camera* d_cams, const int32_t* d_view_block, const int8_t* d_levels,
+                              float* d_image, float* d_final_T, uint32_t* d_n_contrib, uint32_t* d_hits, void* stream)
 {
     Layout L;
     size_t bytes = 0;
     if (!make_layout(frame, &L, &bytes) || !frame->ws) return CGS_ERR_INVALID_ARGUMENT;
+    L.hits = d_hits;
     if ((size_t)frame->ws_bytes < bytes) return CGS_ERR_WORKSPACE_TOO_SMALL;
     if (!scene_ok(scene) || scene->n_blocks != frame->n_blocks || !config_ok(cfg, frame->tile) || !d_cams ||
         !d_image || !d_final_T || !d_n_contrib)
@@ -278,6 +284,24 @@ int32_t cgs_render_forward(const cgs_scene* scene, const cgs_frame* frame, const
         counted(1);
     }
     return cudaGetLastError() == cudaSuccess ? CGS_OK : CGS_ERR_CUDA;
+}
+
+int32_t cgs_render_forward(const cgs_scene* scene, const cgs_frame* frame, const cgs_config* cfg,
+                           const cgs_camera* d_cams, const int32_t* d_view_block, const int8_t* d_levels,
+                           float* d_image, float* d_final_T, uint32_t* d_n_contrib, void* stream)
+{
+    return render_forward(scene, frame, cfg, d_cams, d_view_block, d_levels, d_image, d_final_T, d_n_contrib,
+                          nullptr, stream);
+}
+
+int32_t cgs_render_forward_hits(const cgs_scene* scene, const cgs_frame* frame, const cgs_config* cfg,
+                                const cgs_camera* d_cams, const int32_t* d_view_block, const int8_t* d_levels,
+                                float* d_image, float* d_final_T, uint32_t* d_n_contrib, uint32_t* d_hits,
+                                void* stream)
+{
+    if (!d_hits) return CGS_ERR_INVALID_ARGUMENT;
+    return render_forward(scene, frame, cfg, d_cams, d_view_block, d_levels, d_image, d_final_T, d_n_contrib,
+                          d_hits, stream);
 }
 
 int32_t cgs_render_backward(const cgs_scene* scene, const cgs_frame* frame, const cgs_config* cfg,

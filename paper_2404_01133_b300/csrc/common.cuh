@@ -71,6 +71,7 @@ struct Layout {
     uint32_t* tkey;              // [k_cap] tile id per entry, same order
     uint32_t* big;               // [V * T] tiles for the long-tile sort
     float4* gs;                  // [n_cap][3] screen-space gradients (du dv dA dB | dC do dr dg | db - - -)
+    uint32_t* hits;              // optional [scene n]: pixels blending each scene Gaussian (added to)
     uint32_t* cbits;             // per (tile, warp): bit p set when entry p blends into any of the warp's pixels
     long long cbits_words;
     size_t zero_bytes;           // bytes to clear from hdr
@@ -133,5 +134,10 @@ __device__ __forceinline__ T block_exclusive_scan(T x, T* warp_buf, T* total)
     __syncthreads();
     return res;
 }
+
+// host helpers defined in api.cu: the library-wide launch counter and the SM count of the
+// current device
+void count_launches(int n);
+int device_sm_count();
 
 }  // namespace cgs

@@ -138,7 +138,10 @@ struct FwdPixel {
 // reach; each warp then visits only those entries (ballot over 32-entry chunks), in list
 // order.  n_contrib and the evaluated-pair count keep the semantics of a walk over the full
 // list: entries up to and including the stopping one, or the whole list.
-template <int B, int BATCH>
+//
+// With HITS, every blend is also counted per scene Gaussian: one atomic add per (warp, entry)
+// of the number of the warp's pixels that blended it (L.hits, indexed by scene index).
+template <int B, int BATCH, bool HITS>
 __global__ void __launch_bounds__(B * B / 2) k_render_fwd(Layout L, const uint32_t* __restrict__ tval, float bg0,
                                                           float bg1, float bg2, float* __restrict__ image,
                                                           float* __restrict__ final_T, uint32_t* __restrict__ n_contrib)
@@ -146,6 +149,7 @@ __global__ void __launch_bounds__(B * B / 2) k_render_fwd(Layout L, const uint32
     constexpr int NT = B * B / 2;
     __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
     __shared__ uint32_t s_m[BATCH];
+    __shared__ uint32_t s_g[HITS ? BATCH : 1];
     const int v = blockIdx.z;
     const int tile = blockIdx.y * L.tiles_x + blockIdx.x;
     const uint2 rg = reinterpret_cast<const uint2*>(L.ranges)[(size_t)v * L.T + tile];
@@ -176,6 +180,7 @@ __global__ void __launch_bounds__(B * B / 2) k_render_fwd(Layout L, const uint32
                 s_b[i] = b;
                 s_c[i] = c;
                 m = warp_mask<B>(a, b, c.w, tx0, ty0);
+                if (HITS) s_g[i] = L.gidx[j];
             }
             s_m[i] = m;
         }
@@ -195,6 +200,10 @@ __global__ void __launch_bounds__(B * B / 2) k_render_fwd(Layout L, const uint32
                 const bool b0 = p0.blend(a, b, c, fpx, fpy0, pos);
                 const bool b1 = p1.blend(a, b, c, fpx, fpy1, pos);
                 if (__any_sync(0xffffffffu, b0 || b1)) word |= 1u << kk;
+                if (HITS) {
+                    const int cnt = __popc(__ballot_sync(0xffffffffu, b0)) + __popc(__ballot_sync(0xffffffffu, b1));
+                    if (lane == 0 && cnt) atomicAdd(&L.hits[s_g[k]], (uint32_t)cnt);
+                }
             }
             if (lane == 0) {
                 cbits[(start - rg.x + c0) >> 5] = word;
@@ -422,7 +431,10 @@ static void fwd_launch(const Layout& L, const uint32_t* tval, const cgs_config& 
                        cudaStream_t st)
 {
     dim3 grid(L.tiles_x, L.tiles_y, L.V);
-    k_render_fwd<B, BATCH><<<grid, B * B / 2, 0, st>>>(L, tval, c.bg[0], c.bg[1], c.bg[2], img, T, nc);
+    if (L.hits)
+        k_render_fwd<B, BATCH, true><<<grid, B * B / 2, 0, st>>>(L, tval, c.bg[0], c.bg[1], c.bg[2], img, T, nc);
+    else
+        k_render_fwd<B, BATCH, false><<<grid, B * B / 2, 0, st>>>(L, tval, c.bg[0], c.bg[1], c.bg[2], img, T, nc);
 }
 template <int B, int BATCH>
 static void bwd_launch(const Layout& L, const uint32_t* tval, const cgs_config& c, const float* dimg, const float* T,

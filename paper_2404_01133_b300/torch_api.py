@@ -287,3 +287,75 @@ def autotune(run_step, candidates, reps=5, cache_path=None, key=None):
 
 
 TUNE_CANDIDATES = [(16, 256), (16, 128), (16, 64), (8, 64), (8, 32)]
+
+
+def partition(pos, pmin, pmax, grid, perm=True, rank=False, stream=None):
+    """Block partition of the positions (rows of a float32 device tensor, xyz first): block
+    per row, block offsets and (optionally) the stable grouped order.  Returns
+    (block int32 [n], offset int64 [n_blocks + 1], perm int32 [offset[-1]] or None, workspace),
+    plus rank int32 [n] (the inverse permutation, -1 for no block) when ``rank``; with perm the
+    call synchronises to read the number of grouped points."""
+    n, stride = pos.shape[0], pos.shape[1]
+    assert pos.dtype == torch.float32 and pos.is_contiguous()
+    nb = int(np.prod(grid))
+    ws_bytes = _c.cgs_partition_workspace_bytes(n, grid)
+    if ws_bytes < 0:
+        raise ValueError("invalid partition grid")
+    dev = pos.device
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    block = torch.empty(max(1, n), dtype=torch.int32, device=dev)
+    offset = torch.empty(nb + 1, dtype=torch.int64, device=dev)
+    p = torch.empty(max(1, n), dtype=torch.int32, device=dev) if perm else None
+    r = torch.empty(max(1, n), dtype=torch.int32, device=dev) if rank else None
+    _c.cgs_partition(pos, n, stride, pmin, pmax, grid, block, offset, p, r, ws, ws_bytes, stream)
+    if p is not None:
+        # only the first offset[n_blocks] entries are written (points with no block are left out)
+        p = p[:int(offset[-1].item())]
+    if rank:
+        return block[:n], offset, p, ws, r[:n]
+    return block[:n], offset, p, ws
+
+
+def gather_rows(src, perm, out=None, stream=None):
+    """Rows of src (any dtype, contiguous) in the order perm (int32 device tensor)."""
+    n = perm.shape[0]
+    out = out if out is not None else torch.empty((n,) + tuple(src.shape[1:]), dtype=src.dtype, device=src.device)
+    row_bytes = src[0].numel() * src.element_size() if src.shape[0] else 4
+    _c.cgs_gather_rows(src, out, row_bytes, perm, n, stream)
+    return out
+
+
+def render_forward_hits(dscene, frame, cfg, d_cams, hits, view_block=None, levels=None, out=None, stream=None):
+    """Forward render that also adds each scene Gaussian's blended-pixel count to ``hits``
+    (uint32 stored in an int32 device tensor of scene length)."""
+    img, T, nc = out if out is not None else frame.outputs()
+    _c.cgs_render_forward_hits(dscene.struct(), frame.struct, cfg, d_cams, view_block, levels, img, T, nc, hits,
+                               stream)
+    return img, T, nc
+
+
+def generate_levels(dscene, block_offset, rates, hits=None, stream=None):
+    """Ranked permutation (int32 [n]) and level counts (int64 [n_blocks][len(rates)]) of the
+    block-grouped device scene (block b = rows [block_offset[b], block_offset[b + 1]))."""
+    n = dscene.n
+    nb = block_offset.shape[0] - 1
+    ws_bytes = _c.cgs_levels_workspace_bytes(n, nb)
+    if ws_bytes < 0:
+        raise ValueError("invalid level generation size")
+    dev = dscene.device
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    perm = torch.empty(max(1, n), dtype=torch.int32, device=dev)
+    lc = torch.empty((nb, len(rates)), dtype=torch.int64, device=dev)
+    _c.cgs_generate_levels(dscene.mean_opac, dscene.scale, dscene.attr_fp16, n, block_offset, nb, hits, rates, perm,
+                           lc, ws, ws_bytes, stream)
+    if _c.cgs_levels_status(ws, stream) != _c.CGS_OK:
+        raise RuntimeError("cgs_generate_levels: a bounded wait gave up")
+    return perm[:n], lc
+
+
+def scatter_rows(src, rank, n_out, out=None, stream=None):
+    """Rows of src moved to rows rank[r] of a new [n_out, ...] tensor (rank < 0 skipped)."""
+    out = out if out is not None else torch.empty((n_out,) + tuple(src.shape[1:]), dtype=src.dtype, device=src.device)
+    row_bytes = src[0].numel() * src.element_size() if src.shape[0] else 4
+    _c.cgs_scatter_rows(src, out, row_bytes, rank, src.shape[0], stream)
+    return out

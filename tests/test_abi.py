@@ -65,3 +65,35 @@ def test_oracle_is_not_imported_by_the_product_path():
                 text = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in text and "from oracle" not in text, fn
                 assert "liboracle" not in text, fn
+
+
+def test_partition_host_checks_need_no_device(libcgs):
+    from paper_2404_01133_b300 import cgs
+    libcgs = cgs.lib()  # with argument types set
+    # invalid grids and boxes are rejected before any device work
+    assert cgs.cgs_partition_workspace_bytes(1000, (8, 8, 1)) > 0
+    assert cgs.cgs_partition_workspace_bytes(1000, (0, 8, 1)) == -1
+    assert cgs.cgs_partition_workspace_bytes(1000, (65, 1, 1)) == -1
+    assert cgs.cgs_partition_workspace_bytes(1000, (32, 32, 2)) == -1        # 2048 blocks > 1024
+    assert cgs.cgs_partition_workspace_bytes(-1, (8, 8, 1)) == -1
+    f3 = lambda v: (C.c_float * 3)(*v)
+    i3 = lambda v: (C.c_int32 * 3)(*v)
+    bad_box = libcgs.cgs_partition(1, 10, 4, f3((0, 0, 0)), f3((1, 0, 1)), i3((2, 2, 1)), 1, 1, None, None, 1,
+                                   1 << 20, None)
+    assert bad_box == cgs.CGS_ERR_INVALID_ARGUMENT                           # pmax == pmin on y
+    assert libcgs.cgs_partition(1, 10, 2, f3((0, 0, 0)), f3((1, 1, 1)), i3((2, 2, 1)), 1, 1, None, None, 1,
+                                1 << 20, None) == cgs.CGS_ERR_INVALID_ARGUMENT   # stride < 3
+    assert libcgs.cgs_partition(1, 10, 4, f3((0, 0, 0)), f3((1, 1, 1)), i3((2, 2, 1)), 1, 1, None, None, 1, 16,
+                                None) == cgs.CGS_ERR_WORKSPACE_TOO_SMALL
+    assert libcgs.cgs_scatter_rows(1, 2, 6, 3, 10, None) == cgs.CGS_ERR_INVALID_ARGUMENT
+    assert libcgs.cgs_levels_workspace_bytes(100, 0) == -1 and libcgs.cgs_levels_workspace_bytes(100, 1025) == -1
+    r2 = (C.c_double * 2)(1.0, 1.5)                                               # a rate above 1
+    assert libcgs.cgs_generate_levels(1, 1, 0, 10, 1, 2, None, r2, 2, 1, 1, 1, 1 << 30, None) == \
+        cgs.CGS_ERR_INVALID_ARGUMENT
+    assert libcgs.cgs_render_forward_hits(C.byref(cgs.cgs_scene()), C.byref(cgs.cgs_frame()),
+                                          C.byref(cgs.cgs_config()), None, None, None, None, None, None, None,
+                                          None) == cgs.CGS_ERR_INVALID_ARGUMENT
+    assert libcgs.cgs_gather_rows(1, 2, 6, 3, 10, None) == cgs.CGS_ERR_INVALID_ARGUMENT   # row bytes % 4
+    assert libcgs.cgs_gather_rows(None, None, 16, None, 0, None) == cgs.CGS_OK             # nothing to move
+    assert libcgs.cgs_pose_blocks(1, 4, 3, f3((0, 0, 0)), f3((1, 1, 1)), i3((1, 1, 0)), 1, None) == \
+        cgs.CGS_ERR_INVALID_ARGUMENT
