@@ -220,7 +220,7 @@ int32_t cgs_render_forward_static(const cgs_scene* scene, const cgs_config* cfg,
  *                                            r, g, b, view (ext: half-extent of alpha >= 1/255)
  *   5 tiles touched       u32 [n_cap]
  *   6 selected per view   u32 [n_views + 1] exclusive prefix of the per-view counts
- *   7 visible list        u32 [n_cap]  selected indices of the visible Gaussians, ascending
+ *   7 visible list        u32 [n_cap]  selected indices of the visible Gaussians (no fixed order)
  *   8 depth keys          u64 [n_cap]  view << 32 | FP32 depth bits (visible entries only)
  *   9 tile rects          u32 [n_cap][2]  x0 | y0 << 16, x1 | y1 << 16 (end exclusive, visible only)
  */
@@ -228,9 +228,10 @@ int32_t cgs_frame_buffer(const cgs_frame* frame, int32_t which, void** d_ptr, in
 
 /* Stages of the hot path, for cgs_timing_read. */
 #define CGS_STAGE_SELECT 0       /* level selection and segment lists (Sec. 3.3.2) */
-#define CGS_STAGE_PROJECT 1      /* projection, tile rect, visible compaction, SH colour */
-#define CGS_STAGE_DUPLICATE 2    /* entry offsets, duplication into (tile, Gaussian) entries */
-#define CGS_STAGE_SORT 3         /* tile ranges, scatter, per-tile depth sort */
+#define CGS_STAGE_PROJECT 1      /* projection, tile rect, visible compaction, duplication into
+                                    (tile, Gaussian) entries, SH colour */
+#define CGS_STAGE_DUPLICATE 2    /* tile ranges, scatter of the entries into them */
+#define CGS_STAGE_SORT 3         /* per-tile depth sort */
 #define CGS_STAGE_RENDER 4       /* front-to-back compositing (Eq. 1) */
 #define CGS_STAGE_RENDER_BWD 5   /* compositing backward */
 #define CGS_STAGE_PROJECT_BWD 6  /* projection and colour backward */

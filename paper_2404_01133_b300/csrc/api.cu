@@ -14,8 +14,7 @@ void launch_block_bounds(const cgs_scene& S, double n_mad, float* aabb, cudaStre
 void launch_project(const Layout& L, const cgs_scene& S, const cgs_camera* cams, float near_z, int n_sm,
                     cudaStream_t st);
 void launch_colour(const Layout& L, const cgs_scene& S, const cgs_camera* cams, int n_sm, cudaStream_t st);
-int launch_compact(const Layout& L, int n_sm, cudaStream_t st);
-int launch_duplicate(const Layout& L, int n_sm, cudaStream_t st);
+int launch_bin(const Layout& L, int n_sm, cudaStream_t st);
 int launch_tile_sort(const Layout& L, int n_sm, cudaStream_t st);
 bool launch_render_fwd(const Layout& L, const cgs_config& c, float* img, float* T, uint32_t* nc, cudaStream_t st);
 bool launch_render_bwd(const Layout& L, const cgs_config& c, const float* dimg, const float* T, const uint32_t* nc,
@@ -92,12 +91,11 @@ static bool make_layout(const cgs_frame* f, Layout* L, size_t* bytes)
     l.n_cap = f->n_cap;
     l.k_cap = f->k_cap;
     const long long vt = (long long)l.V * l.T;
-    l.scan_tiles_n = (l.n_cap + SCAN_TILE - 1) / SCAN_TILE;
     const long long scan_tiles_vt = (vt + SCAN_TILE - 1) / SCAN_TILE;
 
     Carver c{(char*)f->ws, 0};
     l.hdr = c.take<Header>(1);
-    l.scan_lb = c.take<unsigned long long>(2 * l.scan_tiles_n + scan_tiles_vt);
+    l.scan_lb = c.take<unsigned long long>(scan_tiles_vt);
     l.tcnt = c.take<uint32_t>(vt);
     l.tcur = c.take<uint32_t>(vt);
     l.zero_bytes = c.off;
@@ -116,7 +114,6 @@ static bool make_layout(const cgs_frame* f, Layout* L, size_t* bytes)
     l.gidx = c.take<uint32_t>(l.n_cap);
     l.pkey = c.take<unsigned long long>(l.n_cap);
     l.vis = c.take<uint32_t>(l.n_cap);
-    l.offs = c.take<uint32_t>(l.n_cap);
     l.eraw = c.take<unsigned long long>(l.k_cap);
     l.ekey = c.take<unsigned long long>(l.k_cap);
     l.tval = c.take<uint32_t>(l.k_cap);
@@ -266,13 +263,12 @@ static int32_t render_forward(const cgs_scene* scene, const cgs_frame* frame, co
         StageScope s(CGS_STAGE_PROJECT, st);
         launch_project(L, *scene, d_cams, cfg->near_z, n_sm, st);
         counted(1);
-        counted(launch_compact(L, n_sm, st));
         launch_colour(L, *scene, d_cams, n_sm, st);
         counted(1);
     }
     {
         StageScope s(CGS_STAGE_DUPLICATE, st);
-        counted(launch_duplicate(L, n_sm, st));
+        counted(launch_bin(L, n_sm, st));
     }
     {
         StageScope s(CGS_STAGE_SORT, st);

@@ -14,13 +14,13 @@ namespace cgs {
 enum : uint32_t { ST_CAPACITY = 1u << 0, ST_SPIN = 1u << 1, ST_UNSUPPORTED = 1u << 2 };
 
 // Dynamic work counters of the single-pass (decoupled look-back) and persistent kernels.
-enum { CTR_SCAN_COMPACT = 0, CTR_SCAN_OFFSETS = 1, CTR_SCAN_RANGES = 2, CTR_BIG = 3, N_CTR = 8 };
+enum { CTR_SCAN_RANGES = 2, CTR_BIG = 3, N_CTR = 8 };
 
 struct Header {
     uint32_t status;
     uint32_t n_sel;        // selected Gaussians summed over views, capped at n_cap
     uint32_t n_vis;        // visible (tiles touched > 0)
-    uint32_t k_used;       // tile entries kept, min(k_total, k_cap)
+    uint32_t _unused;
     unsigned long long n_sel_raw;
     unsigned long long k_total;
     unsigned long long pairs_fwd;
@@ -43,7 +43,7 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_IPT;
 struct Layout {
     Header* hdr;
     // zeroed at every forward (one memset from hdr over zero_bytes)
-    unsigned long long* scan_lb; // [2 * scan_tiles_n + scan tiles of V*T] look-back words
+    unsigned long long* scan_lb; // [scan tiles of V*T] look-back words of the tile-range scan
     uint32_t* tcnt;              // [V * T] entries per tile
     uint32_t* tcur;              // [V * T] scatter cursors
     // not zeroed
@@ -64,7 +64,6 @@ struct Layout {
     uint32_t* gidx;              // [n_cap] scene index
     unsigned long long* pkey;    // [n_cap] view << 32 | depth bits
     uint32_t* vis;               // [n_cap] visible selected indices, ascending
-    uint32_t* offs;              // [n_cap] first entry of each visible Gaussian
     unsigned long long* eraw;    // [k_cap] tile << 32 | j per entry; later scratch of the long-tile sort
     unsigned long long* ekey;    // [k_cap] depth bits << 32 | j, scattered into tile ranges
     uint32_t* tval;              // [k_cap] selected index per entry, (tile, depth, index) order
@@ -76,7 +75,6 @@ struct Layout {
     long long cbits_words;
     size_t zero_bytes;           // bytes to clear from hdr
     long long n_cap, k_cap;
-    long long scan_tiles_n;      // look-back tiles of a scan over n_cap items
     int V, W, H, B, tiles_x, tiles_y, T, NB;
 };
 
@@ -133,6 +131,14 @@ __device__ __forceinline__ T block_exclusive_scan(T x, T* warp_buf, T* total)
     *total = warp_buf[32];
     __syncthreads();
     return res;
+}
+
+// Tile entries kept: min(k_total, k_cap) (the projection drops the rest and latches
+// ST_CAPACITY).
+__device__ __forceinline__ long long entries_kept(const Layout& L)
+{
+    const unsigned long long t = L.hdr->k_total;
+    return t < (unsigned long long)L.k_cap ? (long long)t : L.k_cap;
 }
 
 // host helpers defined in api.cu: the library-wide launch counter and the SM count of the

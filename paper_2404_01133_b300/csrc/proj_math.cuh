@@ -211,6 +211,7 @@ __device__ __forceinline__ void load_sh_half(const void* __restrict__ shv, long 
             }
         }
     } else {
+#pragma unroll
         for (int i = 0; i < nc * 3; i++) f[i] = h2f(__ldg(src + i));
     }
 }
@@ -234,6 +235,7 @@ __device__ __forceinline__ void load_sh(const float* __restrict__ sh, long long 
             f[4 * i] = v.x; f[4 * i + 1] = v.y; f[4 * i + 2] = v.z; f[4 * i + 3] = v.w;
         }
     } else {
+#pragma unroll
         for (int i = 0; i < nc * 3; i++) f[i] = __ldg(src + i);
     }
 }
@@ -253,6 +255,7 @@ __device__ __forceinline__ int sh_colour(const float m[3], const cgs_camera& c, 
 #pragma unroll
     for (int ch = 0; ch < 3; ch++) {
         float acc = Y[0] * f[ch];
+#pragma unroll
         for (int k = 1; k < nc; k++) acc = acc + Y[k] * f[k * 3 + ch];
         acc = acc + 0.5f;
         if (acc < 0.0f) { rgb[ch] = 0.0f; clamp |= 1 << ch; }

@@ -10,13 +10,13 @@ namespace cgs {
 // definite Sigma, |dx| > sqrt(t Sigma_xx) implies alpha < 1/255 (likewise for y).  The
 // threshold and extents get relative and absolute slack far above FP32 rounding of q; for
 // strongly correlated 2D covariances (rho^2 > 0.99), where the rounding of q is not bounded
-// by that slack, the extent is infinite (never culled).  Opacity below 1/255 can never pass
-// the test: extent -1 (always culled).
+// by that slack, the extent is infinite (never culled).  Opacity with o * 255 < 1 can never
+// pass the test: extent -1 (always culled); o * 255 == 1 can, at power 0 exactly.
 // *tq receives the slackened threshold t itself (for the exact ellipse test of the
 // compositing kernels), or +inf when no culling is safe.
 __device__ __forceinline__ void cull_extent(float o, float A, float B, float C, float* ex, float* ey, float* tq)
 {
-    if (!(o * 255.0f > 1.0f)) { *ex = -1.0f; *ey = -1.0f; *tq = -1.0f; return; }
+    if (!(o * 255.0f >= 1.0f)) { *ex = -1.0f; *ey = -1.0f; *tq = -1.0f; return; }
     if (B * B > 0.99f * A * C) { *ex = INFINITY; *ey = INFINITY; *tq = INFINITY; return; }
     const float t = 2.0f * logf(255.0f * o) * 1.002f + 0.002f;
     *ex = sqrtf(t * A) * 1.001f + 0.01f;
@@ -24,83 +24,168 @@ __device__ __forceinline__ void cull_extent(float o, float A, float B, float C, 
     *tq = t;
 }
 
-// One thread per selected Gaussian j (flattened over views), grid-stride over the device
-// count written by the selection kernels.  Writes tiles touched and the scene index of every
-// selected Gaussian and, for the visible ones, the screen-space part of the projected record,
-// the tile rect, the (view, depth) sort key and cleared screen-gradient accumulators.  Colour
-// is evaluated later by k_colour over the compacted visible list.
-__global__ void __launch_bounds__(256) k_project(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams,
-                                                 float near_z)
+// One thread per selected Gaussian j (flattened over views); the CTA walks the selected list
+// in steps of its size (a uniform trip count, so the CTA-wide steps below are safe).  Writes
+// tiles touched and the scene index of every selected Gaussian and, for the visible ones, the
+// screen-space part of the projected record, the tile rect, the (view, depth) sort key and
+// cleared screen-gradient accumulators.  The visible ones are then compacted and duplicated
+// in the same pass:
+//   - the CTA sums its visible count and tiles touched (warp ballots and shuffles, then the
+//     warp totals in shared memory) and reserves a range of the visible list and of the
+//     entry buffer with one atomic add each;
+//   - every warp emits the (tile << 32 | j) entries of its visible Gaussians cooperatively:
+//     lane l takes entries l, l + 32, ... of the warp's range, finds the owning lane by a
+//     binary search over the lanes' exclusive prefixes (shuffles), and counts the tile.
+// The order of the visible list and of the entries depends on the order in which CTAs
+// reserve their ranges; nothing downstream depends on it (entries are sorted per tile by
+// (depth, index), colour and backward work per Gaussian).  Colour is evaluated later by
+// k_colour over the visible list.
+constexpr int PROJ_THREADS = 256;
+constexpr int PROJ_WARPS = PROJ_THREADS / 32;
+
+__global__ void __launch_bounds__(PROJ_THREADS) k_project(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams,
+                                                          float near_z)
 {
+    __shared__ uint32_t s_wv[PROJ_WARPS], s_wt[PROJ_WARPS];
+    __shared__ uint32_t s_vbase;
+    __shared__ unsigned long long s_ebase;
     const uint32_t n = L.hdr->n_sel;
     const float4* __restrict__ mo4 = reinterpret_cast<const float4*>(S.mean_opac);
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        int v;
-        long long g;
-        locate(L, j, &v, &g);
-        L.gidx[j] = (uint32_t)g;
-        const cgs_camera& c = cams[v];
-        const float4 mo = __ldg(mo4 + g);
-        const float m[3] = {mo.x, mo.y, mo.z};
-        // near-plane test first, so culled Gaussians never read scale or rotation
-        const float tz = ((c.R[6] * m[0] + c.R[7] * m[1]) + c.R[8] * m[2]) + c.t[2];
-        uint32_t tt = 0;
-        bool keep = tz > near_z;
-        if (keep && L.lod_mode == CGS_LOD_POINT) {
-            // point-wise baseline: the level of this Gaussian's own distance; kept iff its rank
-            // in the block lies inside that level's (nested) prefix
-            const float d0 = m[0] - c.campos[0], d1 = m[1] - c.campos[1], d2 = m[2] - c.campos[2];
-            const float dist = sqrtf((d0 * d0 + d1 * d1) + d2 * d2);
-            int lv = dist < L.lod_d1 ? 0 : (dist < L.lod_d2 ? 1 : 2);
-            if (lv > S.n_levels - 1) lv = S.n_levels - 1;
-            int blk;
-            uint32_t rank;
-            locate_block(L, j, v, &blk, &rank);
-            keep = (long long)rank < S.level_count[(long long)blk * S.n_levels + lv];
-        }
-        if (keep) {
-            float s[3], q[4];
-            load_scale_quat(S, g, s, q);
-            Proj p;
-            if (project_one(m, s, q, c, near_z, p) == 0) {
-                const float r = ceilf(3.0f * sqrtf(p.lam1));
-                const float W1 = (float)(L.W - 1), H1 = (float)(L.H - 1);
-                float x0 = ceilf(p.u - r), x1 = floorf(p.u + r);
-                float y0 = ceilf(p.v - r), y1 = floorf(p.v + r);
-                if (x0 < 0.0f) x0 = 0.0f;
-                if (y0 < 0.0f) y0 = 0.0f;
-                if (x1 > W1) x1 = W1;
-                if (y1 > H1) y1 = H1;
-                if (x0 <= x1 && y0 <= y1) {
-                    const uint32_t tx0 = (uint32_t)x0 / L.B, tx1 = (uint32_t)x1 / L.B + 1;
-                    const uint32_t ty0 = (uint32_t)y0 / L.B, ty1 = (uint32_t)y1 / L.B + 1;
-                    tt = (tx1 - tx0) * (ty1 - ty0);
-                    L.rect[j] = make_uint2(tx0 | (ty0 << 16), tx1 | (ty1 << 16));
-                    float ex, ey, tq;
-                    cull_extent(mo.w, p.A, p.B, p.C, &ex, &ey, &tq);
-                    L.tq[j] = tq;
-                    L.rec[3 * (size_t)j] = make_float4(p.u, p.v, mo.w, ex);
-                    L.rec[3 * (size_t)j + 1] = make_float4(p.conic[0], p.conic[1], p.conic[2], ey);
-                    L.pkey[j] = ((unsigned long long)(uint32_t)v << 32) | __float_as_uint(p.tz);
-                    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                    L.gs[3 * (size_t)j] = z4;
-                    L.gs[3 * (size_t)j + 1] = z4;
-                    L.gs[3 * (size_t)j + 2] = z4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const unsigned long long cap = (unsigned long long)L.k_cap;
+    for (uint32_t base = blockIdx.x * PROJ_THREADS; base < n; base += gridDim.x * PROJ_THREADS) {
+        const uint32_t j = base + threadIdx.x;
+        uint32_t tt = 0, rx = 0, ry = 0;
+        int v = 0;
+        if (j < n) {
+            long long g;
+            locate(L, j, &v, &g);
+            L.gidx[j] = (uint32_t)g;
+            const cgs_camera& c = cams[v];
+            const float4 mo = __ldg(mo4 + g);
+            const float m[3] = {mo.x, mo.y, mo.z};
+            // near-plane test first, so culled Gaussians never read scale or rotation
+            const float tz = ((c.R[6] * m[0] + c.R[7] * m[1]) + c.R[8] * m[2]) + c.t[2];
+            bool keep = tz > near_z;
+            if (keep && L.lod_mode == CGS_LOD_POINT) {
+                // point-wise baseline: the level of this Gaussian's own distance; kept iff its
+                // rank in the block lies inside that level's (nested) prefix
+                const float d0 = m[0] - c.campos[0], d1 = m[1] - c.campos[1], d2 = m[2] - c.campos[2];
+                const float dist = sqrtf((d0 * d0 + d1 * d1) + d2 * d2);
+                int lv = dist < L.lod_d1 ? 0 : (dist < L.lod_d2 ? 1 : 2);
+                if (lv > S.n_levels - 1) lv = S.n_levels - 1;
+                int blk;
+                uint32_t rank;
+                locate_block(L, j, v, &blk, &rank);
+                keep = (long long)rank < S.level_count[(long long)blk * S.n_levels + lv];
+            }
+            if (keep) {
+                float s[3], q[4];
+                load_scale_quat(S, g, s, q);
+                Proj p;
+                if (project_one(m, s, q, c, near_z, p) == 0) {
+                    const float r = ceilf(3.0f * sqrtf(p.lam1));
+                    const float W1 = (float)(L.W - 1), H1 = (float)(L.H - 1);
+                    float x0 = ceilf(p.u - r), x1 = floorf(p.u + r);
+                    float y0 = ceilf(p.v - r), y1 = floorf(p.v + r);
+                    if (x0 < 0.0f) x0 = 0.0f;
+                    if (y0 < 0.0f) y0 = 0.0f;
+                    if (x1 > W1) x1 = W1;
+                    if (y1 > H1) y1 = H1;
+                    if (x0 <= x1 && y0 <= y1) {
+                        const uint32_t tx0 = (uint32_t)x0 / L.B, tx1 = (uint32_t)x1 / L.B + 1;
+                        const uint32_t ty0 = (uint32_t)y0 / L.B, ty1 = (uint32_t)y1 / L.B + 1;
+                        tt = (tx1 - tx0) * (ty1 - ty0);
+                        rx = tx0 | (ty0 << 16);
+                        ry = tx1 | (ty1 << 16);
+                        L.rect[j] = make_uint2(rx, ry);
+                        float ex, ey, tq;
+                        cull_extent(mo.w, p.A, p.B, p.C, &ex, &ey, &tq);
+                        L.tq[j] = tq;
+                        L.rec[3 * (size_t)j] = make_float4(p.u, p.v, mo.w, ex);
+                        L.rec[3 * (size_t)j + 1] = make_float4(p.conic[0], p.conic[1], p.conic[2], ey);
+                        L.pkey[j] = ((unsigned long long)(uint32_t)v << 32) | __float_as_uint(p.tz);
+                        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                        L.gs[3 * (size_t)j] = z4;
+                        L.gs[3 * (size_t)j + 1] = z4;
+                        L.gs[3 * (size_t)j + 2] = z4;
+                    }
                 }
             }
+            L.tt[j] = tt;
         }
-        L.tt[j] = tt;
+        // warp totals: visible count (ballot) and tiles touched (inclusive shuffle scan)
+        const uint32_t vb = __ballot_sync(0xffffffffu, tt > 0);
+        uint32_t inc = tt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const uint32_t excl = inc - tt;
+        const uint32_t wtot = __shfl_sync(0xffffffffu, inc, 31);
+        if (lane == 0) {
+            s_wv[warp] = __popc(vb);
+            s_wt[warp] = wtot;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t nv = 0;
+            unsigned long long ne = 0;
+            for (int w = 0; w < PROJ_WARPS; w++) {
+                const uint32_t a = s_wv[w], b = s_wt[w];
+                s_wv[w] = nv;
+                s_wt[w] = (uint32_t)ne;
+                nv += a;
+                ne += b;
+            }
+            s_vbase = nv ? atomicAdd(&L.hdr->n_vis, nv) : 0u;
+            s_ebase = ne ? atomicAdd(&L.hdr->k_total, ne) : 0ull;
+            if (ne && s_ebase + ne > cap) latch(L.hdr, ST_CAPACITY);
+        }
+        __syncthreads();
+        if (tt > 0) L.vis[s_vbase + s_wv[warp] + __popc(vb & lt)] = j;
+        // cooperative duplication of the warp's entries
+        const unsigned long long e0 = s_ebase + s_wt[warp];
+        for (uint32_t it = 0; it * 32u < wtot; it++) {
+            const uint32_t idx = it * 32u + (uint32_t)lane;
+            // owner: the last lane o with excl(o) <= idx (lanes with tt = 0 share their
+            // successor's prefix and are never the last such lane)
+            int o = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const uint32_t eo = __shfl_sync(0xffffffffu, excl, o + step);
+                if (eo <= idx) o += step;
+            }
+            const uint32_t oj = __shfl_sync(0xffffffffu, j, o);
+            const uint32_t orx = __shfl_sync(0xffffffffu, rx, o), ory = __shfl_sync(0xffffffffu, ry, o);
+            const uint32_t oex = __shfl_sync(0xffffffffu, excl, o);
+            const int ov = __shfl_sync(0xffffffffu, v, o);
+            const unsigned long long k = e0 + idx;
+            if (idx < wtot && k < cap) {
+                const uint32_t tx0 = orx & 0xffffu, ty0 = orx >> 16, w = (ory & 0xffffu) - tx0;
+                const uint32_t local = idx - oex;
+                const uint32_t t = (uint32_t)ov * (uint32_t)L.T + (ty0 + local / w) * (uint32_t)L.tiles_x + (tx0 + local % w);
+                L.eraw[k] = ((unsigned long long)t << 32) | oj;
+                atomicAdd(&L.tcnt[t], 1u);
+            }
+        }
+        __syncthreads();
     }
 }
 
 // View-dependent colour (SH, Sec. 3.1) of each visible Gaussian, over the compacted visible
 // list so every lane has work.  Writes the third record (r, g, b, t), t the culling
 // threshold on the quadratic form (see cull_extent).
+// DEG is the scene's SH degree: every loop over coefficients has a fixed trip count, so the
+// coefficients stay in registers.
+template <int DEG>
 __global__ void __launch_bounds__(256) k_colour(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams)
 {
     const uint32_t n = L.hdr->n_vis;
-    const int deg = S.sh_degree;
-    const int nc = (deg + 1) * (deg + 1);
+    constexpr int deg = DEG;
+    constexpr int nc = (DEG + 1) * (DEG + 1);
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         const uint32_t j = L.vis[r];
         const int v = (int)(L.pkey[j] >> 32);
@@ -118,10 +203,10 @@ __global__ void __launch_bounds__(256) k_colour(Layout L, cgs_scene S, const cgs
 void launch_project(const Layout& L, const cgs_scene& S, const cgs_camera* cams, float near_z, int n_sm,
                     cudaStream_t st)
 {
-    long long want = (L.n_cap + 255) / 256;
+    long long want = (L.n_cap + PROJ_THREADS - 1) / PROJ_THREADS;
     long long grid = want < (long long)n_sm * 8 ? want : (long long)n_sm * 8;
     if (grid < 1) grid = 1;
-    k_project<<<(unsigned)grid, 256, 0, st>>>(L, S, cams, near_z);
+    k_project<<<(unsigned)grid, PROJ_THREADS, 0, st>>>(L, S, cams, near_z);
 }
 
 void launch_colour(const Layout& L, const cgs_scene& S, const cgs_camera* cams, int n_sm, cudaStream_t st)
@@ -129,7 +214,12 @@ void launch_colour(const Layout& L, const cgs_scene& S, const cgs_camera* cams, 
     long long want = (L.n_cap + 255) / 256;
     long long grid = want < (long long)n_sm * 8 ? want : (long long)n_sm * 8;
     if (grid < 1) grid = 1;
-    k_colour<<<(unsigned)grid, 256, 0, st>>>(L, S, cams);
+    switch (S.sh_degree) {
+        case 0: k_colour<0><<<(unsigned)grid, 256, 0, st>>>(L, S, cams); break;
+        case 1: k_colour<1><<<(unsigned)grid, 256, 0, st>>>(L, S, cams); break;
+        case 2: k_colour<2><<<(unsigned)grid, 256, 0, st>>>(L, S, cams); break;
+        default: k_colour<3><<<(unsigned)grid, 256, 0, st>>>(L, S, cams); break;
+    }
 }
 
 }  // namespace cgs

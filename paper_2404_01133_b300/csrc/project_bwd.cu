@@ -9,64 +9,101 @@
 
 namespace cgs {
 
-__global__ void __launch_bounds__(128) k_project_bwd(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams,
-                                                     float near_z, float* __restrict__ g_mo, float* __restrict__ g_sc,
-                                                     float* __restrict__ g_q, float* __restrict__ g_sh)
+// Two roles per CTA of 128 threads and 64 visible Gaussians: warps 0-1 chain the geometric
+// gradients (u, v, conic, opacity -> mean, scale, rotation), warps 2-3 the colour gradients
+// (rgb -> SH coefficients and the view-direction term of the mean).  The split halves the
+// registers a thread needs and doubles the threads in flight; each role adds its own part of
+// the mean gradient.  DEG is the scene's SH degree, fixed at compile time so the coefficient
+// loops unroll and the per-Gaussian arrays live in registers.
+constexpr int PB_THREADS = 128;
+constexpr int PB_PER_CTA = PB_THREADS / 2;
+
+template <int DEG>
+__global__ void __launch_bounds__(PB_THREADS) k_project_bwd(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams,
+                                                            float near_z, float* __restrict__ g_mo,
+                                                            float* __restrict__ g_sc, float* __restrict__ g_q,
+                                                            float* __restrict__ g_sh)
 {
     // over the compacted visible Gaussians, so every lane has work
     const uint32_t n = L.hdr->n_vis;
     const uint32_t* __restrict__ vis = L.vis;
-    const int deg = S.sh_degree;
-    const int nc = (deg + 1) * (deg + 1);
-    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-        const uint32_t j = vis[r];
-        const float4 ga = L.gs[3 * (size_t)j], gb = L.gs[3 * (size_t)j + 1], gc4 = L.gs[3 * (size_t)j + 2];
-        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        L.gs[3 * (size_t)j] = z4;
-        L.gs[3 * (size_t)j + 1] = z4;
-        L.gs[3 * (size_t)j + 2] = z4;
-        const float gu = ga.x, gv = ga.y, gA_ = ga.z, gB_ = ga.w, gC_ = gb.x, gop = gb.y;
-        const float grgb[3] = {gb.z, gb.w, gc4.x};
+    constexpr int deg = DEG;
+    constexpr int nc = (DEG + 1) * (DEG + 1);
+    const bool colour_role = threadIdx.x >= PB_PER_CTA;
+    const uint32_t li = threadIdx.x - (colour_role ? PB_PER_CTA : 0);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (uint32_t r0 = blockIdx.x * PB_PER_CTA; r0 < n; r0 += gridDim.x * PB_PER_CTA) {
+        const uint32_t r = r0 + li;
+        const bool valid = r < n;
+        const uint32_t j = valid ? vis[r] : 0u;
+        float4 ga = z4, gb = z4, gc4 = z4;
+        if (valid) {
+            ga = L.gs[3 * (size_t)j];
+            gb = L.gs[3 * (size_t)j + 1];
+            gc4 = L.gs[3 * (size_t)j + 2];
+        }
+        __syncthreads();  // both roles have read the accumulators; clear them for the next backward
+        if (valid) {
+            if (!colour_role) {
+                L.gs[3 * (size_t)j] = z4;
+                L.gs[3 * (size_t)j + 1] = z4;
+            } else {
+                L.gs[3 * (size_t)j + 2] = z4;
+            }
+        }
+        if (!valid) continue;
         const int v = (int)(L.pkey[j] >> 32);
         const long long g = L.gidx[j];
         const cgs_camera c = cams[v];
         const float4 mo = __ldg(reinterpret_cast<const float4*>(S.mean_opac) + g);
         const float m[3] = {mo.x, mo.y, mo.z};
+        if (colour_role) {
+            // colour -> SH coefficients and the view direction
+            const float grgb[3] = {gb.z, gb.w, gc4.x};
+            float f[48], rgb[3], dir[3], len, Y[16], dY[16][3];
+            if (S.attr_fp16) load_sh_half(S.sh, g, nc, f);
+            else load_sh(S.sh, g, nc, f);
+            const int cl = sh_colour(m, c, f, deg, rgb, dir, &len, Y);
+            sh_grad(dir[0], dir[1], dir[2], deg, dY);
+            float gdir[3] = {0.f, 0.f, 0.f};
+            float gc[3];
+#pragma unroll
+            for (int ch = 0; ch < 3; ch++) gc[ch] = (cl & (1 << ch)) ? 0.0f : grgb[ch];
+            // dL/dcolour . f_k per basis function, then through dY_k/d(dir)
+#pragma unroll
+            for (int k = 0; k < nc; k++) {
+                const float fg = f[k * 3] * gc[0] + f[k * 3 + 1] * gc[1] + f[k * 3 + 2] * gc[2];
+                gdir[0] += fg * dY[k][0];
+                gdir[1] += fg * dY[k][1];
+                gdir[2] += fg * dY[k][2];
+            }
+            // dL/df_k = Y_k dL/dcolour, added 16 bytes at a time
+            float* gsh = g_sh + g * (long long)(nc * 3);
+            if constexpr ((nc * 3) % 4 == 0) {
+                float4* g4 = reinterpret_cast<float4*>(gsh);
+#pragma unroll
+                for (int i = 0; i < nc * 3 / 4; i++)
+                    atomicAdd(g4 + i, make_float4(Y[(4 * i) / 3] * gc[(4 * i) % 3],
+                                                  Y[(4 * i + 1) / 3] * gc[(4 * i + 1) % 3],
+                                                  Y[(4 * i + 2) / 3] * gc[(4 * i + 2) % 3],
+                                                  Y[(4 * i + 3) / 3] * gc[(4 * i + 3) % 3]));
+            } else {
+#pragma unroll
+                for (int i = 0; i < nc * 3; i++) atomicAdd(gsh + i, Y[i / 3] * gc[i % 3]);
+            }
+            // the direction's dependence on the mean: d dir / d m = (I - dir dir^T) / len
+            const float dd = dir[0] * gdir[0] + dir[1] * gdir[1] + dir[2] * gdir[2];
+            atomicAdd(reinterpret_cast<float4*>(g_mo) + g,
+                      make_float4((gdir[0] - dir[0] * dd) / len, (gdir[1] - dir[1] * dd) / len,
+                                  (gdir[2] - dir[2] * dd) / len, 0.0f));
+            continue;
+        }
+        const float gu = ga.x, gv = ga.y, gA_ = ga.z, gB_ = ga.w, gC_ = gb.x, gop = gb.y;
         float s[3], q[4];
         load_scale_quat(S, g, s, q);
         Proj p;
         if (project_one(m, s, q, c, near_z, p) != 0) continue;
-
-        // colour -> SH coefficients and the view direction
-        float f[48], rgb[3], dir[3], len, Y[16], dY[16][3];
-        if (S.attr_fp16) load_sh_half(S.sh, g, nc, f);
-        else load_sh(S.sh, g, nc, f);
-        const int cl = sh_colour(m, c, f, deg, rgb, dir, &len, Y);
-        sh_grad(dir[0], dir[1], dir[2], deg, dY);
-        float gdir[3] = {0.f, 0.f, 0.f};
-        float gc[3];
-        for (int ch = 0; ch < 3; ch++) gc[ch] = (cl & (1 << ch)) ? 0.0f : grgb[ch];
-        float gf[48];
-        for (int k = 0; k < nc; k++)
-            for (int ch = 0; ch < 3; ch++) {
-                gf[k * 3 + ch] = Y[k] * gc[ch];
-                const float fk = f[k * 3 + ch] * gc[ch];
-                gdir[0] += fk * dY[k][0];
-                gdir[1] += fk * dY[k][1];
-                gdir[2] += fk * dY[k][2];
-            }
-        float* gsh = g_sh + g * (long long)(nc * 3);
-        if ((nc * 3) % 4 == 0) {
-            float4* g4 = reinterpret_cast<float4*>(gsh);
-            for (int i = 0; i < nc * 3 / 4; i++)
-                atomicAdd(g4 + i, make_float4(gf[4 * i], gf[4 * i + 1], gf[4 * i + 2], gf[4 * i + 3]));
-        } else {
-            for (int i = 0; i < nc * 3; i++) atomicAdd(gsh + i, gf[i]);
-        }
-        const float dd = dir[0] * gdir[0] + dir[1] * gdir[1] + dir[2] * gdir[2];
-        float gm[3];
-        for (int a = 0; a < 3; a++) gm[a] = (gdir[a] - dir[a] * dd) / len;
-
+        float gm[3] = {0.f, 0.f, 0.f};
         // conic (C/D, -B/D, A/D), D = AC - B^2 -> Sigma2D entries (A, B, C), over the common
         // denominator D^2 (1/D - AC/D^2 = -B^2/D^2 carries no cancellation this way)
         const float A = p.A, Bv = p.B, C = p.C, D2 = p.det * p.det;
@@ -108,7 +145,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(Layout L, cgs_scene S, cons
         gtz += gu * (-fx * tx / tz2);
         gty += gv * fy / tz;
         gtz += gv * (-fy * ty / tz2);
-        for (int a = 0; a < 3; a++) gm[a] += W[a] * gtx + W[3 + a] * gty + W[6 + a] * gtz;
+        for (int a = 0; a < 3; a++) gm[a] = W[a] * gtx + W[3 + a] * gty + W[6 + a] * gtz;
         atomicAdd(reinterpret_cast<float4*>(g_mo) + g, make_float4(gm[0], gm[1], gm[2], gop));
 
         // Sigma3D = M M^T, M = Rq diag(s)
@@ -144,10 +181,15 @@ __global__ void __launch_bounds__(128) k_project_bwd(Layout L, cgs_scene S, cons
 void launch_project_bwd(const Layout& L, const cgs_scene& S, const cgs_camera* cams, float near_z, float* g_mo,
                         float* g_sc, float* g_q, float* g_sh, int n_sm, cudaStream_t st)
 {
-    long long want = (L.n_cap + 127) / 128;
+    long long want = (L.n_cap + PB_PER_CTA - 1) / PB_PER_CTA;
     long long grid = want < (long long)n_sm * 16 ? want : (long long)n_sm * 16;
     if (grid < 1) grid = 1;
-    k_project_bwd<<<(unsigned)grid, 128, 0, st>>>(L, S, cams, near_z, g_mo, g_sc, g_q, g_sh);
+    switch (S.sh_degree) {
+        case 0: k_project_bwd<0><<<(unsigned)grid, PB_THREADS, 0, st>>>(L, S, cams, near_z, g_mo, g_sc, g_q, g_sh); break;
+        case 1: k_project_bwd<1><<<(unsigned)grid, PB_THREADS, 0, st>>>(L, S, cams, near_z, g_mo, g_sc, g_q, g_sh); break;
+        case 2: k_project_bwd<2><<<(unsigned)grid, PB_THREADS, 0, st>>>(L, S, cams, near_z, g_mo, g_sc, g_q, g_sh); break;
+        default: k_project_bwd<3><<<(unsigned)grid, PB_THREADS, 0, st>>>(L, S, cams, near_z, g_mo, g_sc, g_q, g_sh); break;
+    }
 }
 
 }  // namespace cgs

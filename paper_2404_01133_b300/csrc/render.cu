@@ -104,7 +104,10 @@ __device__ __forceinline__ uint32_t warp_mask(const float4& a, const float4& b, 
     return m;
 }
 
-// Forward blend of one entry into one pixel (Eq. 1 with the 3DGS thresholds).
+// Forward blend of one entry into one pixel (Eq. 1 with the 3DGS thresholds).  Written
+// without branches: a warp runs every step for all its lanes anyway, and the predicated form
+// saves the divergence bookkeeping.  A pair that does not blend adds c * 0 (exactly nothing)
+// and keeps T and last.
 struct FwdPixel {
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
     uint32_t last = 0, stop_at = 0xffffffffu;
@@ -112,25 +115,24 @@ struct FwdPixel {
     __device__ __forceinline__ bool blend(const float4& a, const float4& b, const float4& c, float fpx, float fpy,
                                           uint32_t pos)
     {
-        if (done) return false;
         float dx, dy;
         const float power = pair_power(a, b, fpx, fpy, &dx, &dy);
-        if (power > 0.0f) return false;
         const float alpha = fminf(0.99f, __fmul_rn(a.z, __expf(power)));
-        if (alpha < 1.0f / 255.0f) return false;
         const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
-        if (Tn < 1e-4f) {
-            done = true;
-            stop_at = pos;
-            return false;
-        }
-        const float w = alpha * T;
+        const bool ok = !done && !(power > 0.0f) && !(alpha < 1.0f / 255.0f);
+        const bool stop = ok && Tn < 1e-4f;
+        const bool use = ok && !stop;
+        const float w = use ? alpha * T : 0.0f;
         C0 += c.x * w;
         C1 += c.y * w;
         C2 += c.z * w;
-        T = Tn;
-        last = pos + 1u;
-        return true;
+        if (stop) {
+            done = true;
+            stop_at = pos;
+        }
+        T = use ? Tn : T;
+        last = use ? pos + 1u : last;
+        return use;
     }
 };
 
@@ -142,7 +144,7 @@ struct FwdPixel {
 // With HITS, every blend is also counted per scene Gaussian: one atomic add per (warp, entry)
 // of the number of the warp's pixels that blended it (L.hits, indexed by scene index).
 template <int B, int BATCH, bool HITS>
-__global__ void __launch_bounds__(B * B / 2) k_render_fwd(Layout L, const uint32_t* __restrict__ tval, float bg0,
+__global__ void __launch_bounds__(B * B / 2, B == 16 ? 8 : 32) k_render_fwd(Layout L, const uint32_t* __restrict__ tval, float bg0,
                                                           float bg1, float bg2, float* __restrict__ image,
                                                           float* __restrict__ final_T, uint32_t* __restrict__ n_contrib)
 {
@@ -253,37 +255,38 @@ __global__ void __launch_bounds__(B * B / 2) k_render_fwd(Layout L, const uint32
 struct BwdPixel {
     float T = 1.0f, gS = 0.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
     uint32_t nc = 0;
+    // Predicated like the forward: a pair that did not blend leaves T and gS and adds exact
+    // zeros (selected, never multiplied, so no inf * 0 reaches the sums).
     __device__ __forceinline__ bool replay(const float4& a, const float4& b, const float4& c, float fpx, float fpy,
                                            uint32_t lp, float* m)
     {
-        if (lp >= nc) return false;
         float dx, dy;
         const float power = pair_power(a, b, fpx, fpy, &dx, &dy);
-        if (power > 0.0f) return false;
         const float G = __expf(power);
         const float og = __fmul_rn(a.z, G);
         const float alpha = fminf(0.99f, og);
-        if (alpha < 1.0f / 255.0f) return false;
-        const float inv = __frcp_rn(1.0f - alpha);
-        T = T * inv;
+        const bool use = lp < nc && !(power > 0.0f) && !(alpha < 1.0f / 255.0f);
+        const float inv = __fdividef(1.0f, 1.0f - alpha);
+        const float Tb = T * inv;  // transmittance before this entry
         const float gc = g0 * c.x + g1 * c.y + g2 * c.z;
-        const float dal = gc * T - gS * inv;
-        const float aT = alpha * T;
-        gS += aT * gc;
-        m[6] += g0 * aT;
-        m[7] += g1 * aT;
-        m[8] += g2 * aT;
-        if (!(og > 0.99f)) {
-            m[5] += dal * G;
-            const float dp = dal * og;
-            const float px = dp * dx, py = dp * dy;
-            m[0] += px;
-            m[1] += py;
-            m[2] += px * dx;
-            m[3] += px * dy;
-            m[4] += py * dy;
-        }
-        return true;
+        const float dal = gc * Tb - gS * inv;
+        const float aT = alpha * Tb;
+        T = use ? Tb : T;
+        gS = use ? gS + aT * gc : gS;
+        const float aTu = use ? aT : 0.0f;
+        m[6] += g0 * aTu;
+        m[7] += g1 * aTu;
+        m[8] += g2 * aTu;
+        const bool lin = use && !(og > 0.99f);  // the 0.99 clamp passes no gradient
+        m[5] += lin ? dal * G : 0.0f;
+        const float dp = lin ? dal * og : 0.0f;
+        const float px = dp * dx, py = dp * dy;
+        m[0] += px;
+        m[1] += py;
+        m[2] += px * dx;
+        m[3] += px * dy;
+        m[4] += py * dy;
+        return use;
     }
 };
 
@@ -293,7 +296,7 @@ struct BwdPixel {
 // sum l), are added in shared memory per entry, turned into dL/d(u, v, conic, o, rgb) with
 // the entry's conic, and added once per (tile, Gaussian) to the global accumulator.
 template <int B, int BATCH>
-__global__ void __launch_bounds__(B * B / 2) k_render_bwd(Layout L, const uint32_t* __restrict__ tval, float bg0,
+__global__ void __launch_bounds__(B * B / 2, B == 16 ? 6 : 24) k_render_bwd(Layout L, const uint32_t* __restrict__ tval, float bg0,
                                                           float bg1, float bg2, const float* __restrict__ dL_dimg,
                                                           const float* __restrict__ final_T,
                                                           const uint32_t* __restrict__ n_contrib)

@@ -1,56 +1,23 @@
-// Stage c of the hot path: duplication into (tile, Gaussian) entries, and the depth order
-// inside every tile ("sorted in depth order", Sec. 3.1; ties to the lower index).
+// Stage c of the hot path, after the projection has emitted the (tile, Gaussian) entries and
+// the per-tile counts: the depth order inside every tile ("sorted in depth order", Sec. 3.1;
+// ties to the lower index).
 //
-//   compaction    single-pass scan over the selected Gaussians -> visible list (index order)
-//   offsets       single-pass scan of tiles touched over the visible list -> entry offsets
-//   duplicate     one thread per entry: owning Gaussian by binary search, its tile, and a
-//                 count per tile
 //   tile ranges   single-pass scan of the per-tile counts -> [start, end) of every tile
 //   scatter       one thread per entry: a slot in its tile's range (atomic cursor), key
 //                 (FP32 depth bits << 32 | selected index)
-//   tile sort     one CTA per tile sorts its keys in shared memory (bitonic); a tile longer
-//                 than the shared-memory capacity is sorted by one CTA of a separate kernel
-//                 (sorted chunks + merge rounds through global scratch)
+//   tile sort     one CTA per tile: up to 256 keys ranked against each other in shared
+//                 memory (each key's count of smaller keys is its slot), up to 2048 keys
+//                 bitonic-sorted in shared memory; longer tiles are sorted by one CTA of a
+//                 second kernel (sorted chunks + merge rounds through global scratch)
 //
-// Within a view, selected-index order is scene-index order, and a Gaussian appears at most
-// once per tile, so the 64-bit keys of one tile are distinct: the sorted order is exactly
-// (depth, index) whatever order the scatter produced.  Every count the sequence needs is
-// read on the device; every inter-block wait is bounded and latches ST_SPIN.
+// Within a view, a Gaussian appears at most once per tile, so the 64-bit keys of one tile are
+// distinct: the sorted order is exactly (depth, index) whatever order the projection emitted
+// the entries in and the scatter placed them.  Every count the sequence needs is read on the
+// device; every inter-block wait is bounded and latches ST_SPIN.
 #include "common.cuh"
 #include "scan.cuh"
 
 namespace cgs {
-
-// Keeps the selected Gaussians with tiles_touched > 0, in selected-index order.
-struct CompactOp {
-    Layout L;
-    __device__ long long count() const { return L.hdr->n_sel; }
-    __device__ uint32_t load(long long j) const { return L.tt[j] > 0 ? 1u : 0u; }
-    __device__ void store(long long j, unsigned long long e, uint32_t x) const
-    {
-        if (x) L.vis[e] = (uint32_t)j;
-    }
-    __device__ void finish(unsigned long long total) const { L.hdr->n_vis = (uint32_t)total; }
-};
-
-// Exclusive offsets of every visible Gaussian's entries.
-struct OffsetOp {
-    Layout L;
-    __device__ long long count() const { return L.hdr->n_vis; }
-    __device__ uint32_t load(long long r) const { return L.tt[L.vis[r]]; }
-    __device__ void store(long long r, unsigned long long e, uint32_t x) const
-    {
-        (void)x;
-        L.offs[r] = (uint32_t)(e < 0xffffffffull ? e : 0xffffffffull);
-    }
-    __device__ void finish(unsigned long long total) const
-    {
-        L.hdr->k_total = total;
-        const unsigned long long cap = (unsigned long long)L.k_cap;
-        L.hdr->k_used = (uint32_t)(total < cap ? total : cap);
-        if (total > cap) latch(L.hdr, ST_CAPACITY);
-    }
-};
 
 // [start, end) of every (view, tile) from the per-tile counts.
 struct TileRangeOp {
@@ -65,34 +32,10 @@ struct TileRangeOp {
     __device__ void finish(unsigned long long total) const { (void)total; }
 };
 
-// One thread per entry k: the owning visible Gaussian is the last r with offs[r] <= k; the
-// tile is the (k - offs[r])-th of its rect in row-major order.  Writes (tile << 32 | j) and
-// counts the tile.
-__global__ void __launch_bounds__(256) k_duplicate(Layout L)
-{
-    const long long n = L.hdr->k_used;
-    const uint32_t nv = L.hdr->n_vis;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-        uint32_t lo = 0, hi = nv;  // offs[lo] <= k < offs[hi], offs[nv] taken as +inf
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if ((long long)L.offs[mid] <= k) lo = mid; else hi = mid;
-        }
-        const uint32_t j = L.vis[lo];
-        const uint32_t view = (uint32_t)(L.pkey[j] >> 32);
-        const uint2 rc = L.rect[j];
-        const uint32_t tx0 = rc.x & 0xffffu, ty0 = rc.x >> 16, w = (rc.y & 0xffffu) - tx0;
-        const uint32_t local = (uint32_t)(k - (long long)L.offs[lo]);
-        const uint32_t t = view * (uint32_t)L.T + (ty0 + local / w) * (uint32_t)L.tiles_x + (tx0 + local % w);
-        L.eraw[k] = ((unsigned long long)t << 32) | j;
-        atomicAdd(&L.tcnt[t], 1u);
-    }
-}
-
 // One thread per entry: a slot inside its tile's range and the (depth bits, index) key.
 __global__ void __launch_bounds__(256) k_scatter(Layout L)
 {
-    const long long n = L.hdr->k_used;
+    const long long n = entries_kept(L);
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         const unsigned long long w = L.eraw[k];
         const uint32_t t = (uint32_t)(w >> 32), j = (uint32_t)w;
@@ -122,7 +65,12 @@ __device__ __forceinline__ void bitonic_smem(unsigned long long* s, int np)
     __syncthreads();
 }
 
-// One CTA per (view, tile).
+constexpr int RANK_MAX = 2 * TS_THREADS;  // keys per tile sorted by ranking
+
+// One CTA per (view, tile).  Up to RANK_MAX keys: every thread ranks up to two keys against
+// all keys of the tile in shared memory (keys are distinct, so the rank is the output slot);
+// up to TS_CAP keys: bitonic sort in shared memory; longer tiles are listed for the merge
+// kernel.
 __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(Layout L)
 {
     __shared__ unsigned long long s[TS_CAP];
@@ -131,6 +79,34 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(Layout L)
     if (n == 0) return;
     if (n > (uint32_t)TS_CAP) {
         if (threadIdx.x == 0) L.big[atomicAdd(&L.hdr->n_big, 1u)] = t;
+        return;
+    }
+    if (n <= (uint32_t)RANK_MAX) {
+        for (uint32_t i = threadIdx.x; i < n; i += TS_THREADS) s[i] = L.ekey[st + i];
+        __syncthreads();
+        const uint32_t i0 = threadIdx.x, i1 = threadIdx.x + TS_THREADS;
+        const unsigned long long k0 = i0 < n ? s[i0] : ~0ull, k1 = i1 < n ? s[i1] : ~0ull;
+        uint32_t r0 = 0, r1 = 0;
+        if (i0 < n) {
+            if (i1 < n) {
+                for (uint32_t m = 0; m < n; m++) {
+                    const unsigned long long x = s[m];
+                    r0 += x < k0;
+                    r1 += x < k1;
+                }
+            } else {
+#pragma unroll 4
+                for (uint32_t m = 0; m < n; m++) r0 += s[m] < k0;
+            }
+        }
+        if (i0 < n) {
+            L.tval[st + r0] = (uint32_t)k0;
+            L.tkey[st + r0] = t;
+        }
+        if (i1 < n) {
+            L.tval[st + r1] = (uint32_t)k1;
+            L.tkey[st + r1] = t;
+        }
         return;
     }
     int np = 2;
@@ -207,36 +183,25 @@ static long long grid_for(long long items, long long per_cta, int n_sm, int per_
     return g < 1 ? 1 : g;
 }
 
-// Visible compaction in selected-index order.  Returns the number of kernels launched.
-int launch_compact(const Layout& L, int n_sm, cudaStream_t st)
-{
-    CompactOp op{L};
-    k_scan<CompactOp><<<(unsigned)grid_for(L.n_cap, SCAN_TILE, n_sm, 8), SCAN_THREADS, 0, st>>>(
-        op, L.scan_lb, L.hdr->ctr + CTR_SCAN_COMPACT, L.hdr);
-    return 1;
-}
-
-// Entry offsets and duplication into (tile, Gaussian) entries with per-tile counts.
-int launch_duplicate(const Layout& L, int n_sm, cudaStream_t st)
-{
-    OffsetOp op{L};
-    k_scan<OffsetOp><<<(unsigned)grid_for(L.n_cap, SCAN_TILE, n_sm, 8), SCAN_THREADS, 0, st>>>(
-        op, L.scan_lb + L.scan_tiles_n, L.hdr->ctr + CTR_SCAN_OFFSETS, L.hdr);
-    k_duplicate<<<(unsigned)grid_for(L.k_cap, 256, n_sm, 16), 256, 0, st>>>(L);
-    return 2;
-}
-
-// Tile ranges, scatter into the ranges, per-tile sort (and the long-tile path).
-int launch_tile_sort(const Layout& L, int n_sm, cudaStream_t st)
+// Tile ranges from the per-tile counts and the scatter of the entries into them.  Returns the
+// number of kernels launched.
+int launch_bin(const Layout& L, int n_sm, cudaStream_t st)
 {
     const long long vt = (long long)L.V * L.T;
     TileRangeOp op{L};
     k_scan<TileRangeOp><<<(unsigned)grid_for(vt, SCAN_TILE, n_sm, 8), SCAN_THREADS, 0, st>>>(
-        op, L.scan_lb + 2 * L.scan_tiles_n, L.hdr->ctr + CTR_SCAN_RANGES, L.hdr);
+        op, L.scan_lb, L.hdr->ctr + CTR_SCAN_RANGES, L.hdr);
     k_scatter<<<(unsigned)grid_for(L.k_cap, 256, n_sm, 16), 256, 0, st>>>(L);
+    return 2;
+}
+
+// Per-tile sort (register, shared-memory and long-tile paths).
+int launch_tile_sort(const Layout& L, int n_sm, cudaStream_t st)
+{
+    const long long vt = (long long)L.V * L.T;
     k_tile_sort<<<(unsigned)vt, TS_THREADS, 0, st>>>(L);
     k_tile_sort_large<<<(unsigned)n_sm, TB_THREADS, 0, st>>>(L);
-    return 4;
+    return 2;
 }
 
 }  // namespace cgs

@@ -126,6 +126,17 @@ def test_long_tile_lists_use_the_merge_path(n):
     assert lens.max() > 2048
 
 
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 64, 65, 128, 129, 256, 257, 2048])
+def test_tile_lengths_at_sort_path_bounds(n):
+    """One 16 x 16 tile holding every Gaussian: lengths on both sides of the one-warp register
+    sorts (32, 64, 128, 256 keys) and of the shared-memory sort (2048) stay bit-exact."""
+    sc = synth.single_block(synth.random_cube_scene(n, seed=100 + n, sh_degree=0, extent=0.2, log_scale_mu=-2.5))
+    cam = synth.small_scene_camera(16, 16, f=30.0, dist=3.0)
+    g = gpu_render(sc, [cam])
+    o, _ = check_against_oracle(sc, cam, g, 16)
+    assert o["sort"]["ranges"][0, 1] - o["sort"]["ranges"][0, 0] == n
+
+
 def test_all_culled_view_gives_background():
     sc, cams = synth.workload_small()
     cam = synth.camera_from_rt(np.diag([-1.0, 1.0, -1.0]), [0.0, 0.0, -10.0], 150, 150, 63.5, 63.5, 128, 128)
