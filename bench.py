@@ -199,7 +199,8 @@ def run_ours(args, world, rank, local):
     n = sc["mean_opac"].shape[0]
     ds = ta.DeviceScene(sc, dev)
     d_cams = ta.cameras_device(cams, dev)
-    tgt_host = torch.from_numpy(synth.target_image(1, W, H))[None].pin_memory()
+    # the target is an 8-bit image, as a decoded training photo is (t stands for t / 255)
+    tgt_host = torch.from_numpy(synth.target_image_u8(1, W, H))[None].pin_memory()
     tgt = tgt_host.to(dev)
 
     # autotuner: tile size and batch depth for this workload, timed on the real step
@@ -217,7 +218,7 @@ def run_ours(args, world, rank, local):
                   torch.zeros_like(ds.sh))
             l_ = torch.zeros(1, device=dev)
             cgs.cgs_render_forward(ds.struct(), f_.struct, c_, d_cams, None, None, i_, T_, n_)
-            cgs.cgs_l1_loss(i_, tgt, i_.numel(), l_, dl_)
+            cgs.cgs_l1_loss_u8(i_, tgt, i_.numel(), l_, dl_)
             cgs.cgs_render_backward(ds.struct(), f_.struct, c_, d_cams, dl_, T_, n_, *gz)
 
         best, tune_ms = ta.autotune(run_candidate, ta.TUNE_CANDIDATES, reps=3)
@@ -252,7 +253,7 @@ def run_ours(args, world, rank, local):
         # the same step reading the target image and the camera from the given device buffers
         cur = torch.cuda.current_stream().cuda_stream
         cgs.cgs_render_forward(s_struct, frame.struct, cfg, cam_buf, None, None, img, T, nc, cur)
-        cgs.cgs_l1_loss(img, tgt_buf, img.numel(), loss, dL, cur)
+        cgs.cgs_l1_loss_u8(img, tgt_buf, img.numel(), loss, dL, cur)
         cgs.cgs_render_backward(s_struct, frame.struct, cfg, cam_buf, dL, T, nc, *grads, cur)
 
     def step(fwd_only=False):
@@ -261,7 +262,7 @@ def run_ours(args, world, rank, local):
         cgs.cgs_render_forward(s_struct, frame.struct, cfg, d_cams, None, None, img, T, nc, cur)
         if fwd_only:
             return
-        cgs.cgs_l1_loss(img, tgt, img.numel(), loss, dL, cur)
+        cgs.cgs_l1_loss_u8(img, tgt, img.numel(), loss, dL, cur)
         cgs.cgs_render_backward(s_struct, frame.struct, cfg, d_cams, dL, T, nc, *grads, cur)
 
     def timed(k, fwd_only=False, with_stages=False):
@@ -342,10 +343,11 @@ def run_ours(args, world, rank, local):
     work = {
         # algorithmic bytes per launch (HBM-bound stages)
         # projection: mean+opacity read, scene index and tiles-touched write for every selected
-        # Gaussian; scale, rotation, SH read and record, rect, key, visible-list write for the
-        # visible ones; one 8-byte (tile, Gaussian) entry written per tile touched
-        "project": ("hbm", n_sel * (16 + 4 + 4) + n_vis * (32 + 12 * nc_coef + 48 + 8 + 8 + 4) + k_ent * 8),
-        # binning: per tile its count and range; per entry read the entry, write the key
+        # Gaussian; scale, rotation and SH read, three records, rect, key, visible-list slot and
+        # cleared gradient rows written for the visible ones; one 8-byte entry per tile touched
+        "project": ("hbm", n_sel * (16 + 4 + 4) + n_vis * (32 + 12 * nc_coef + 48 + 8 + 8 + 4 + 48) + k_ent * 8),
+        # binning: per tile its count read and range written; per entry read the entry, write
+        # the key
         "duplicate": ("hbm", n_tiles * 12 + k_ent * (8 + 8)),
         # per-tile sort: per entry read the key, write value and tile
         "sort": ("hbm", k_ent * (8 + 4 + 4)),
@@ -353,8 +355,8 @@ def run_ours(args, world, rank, local):
         "render": ("alu", pairs_f * FP32_OPS_PER_EVAL_PAIR_FWD),
         "render_bwd": ("alu", pairs_f * FP32_OPS_PER_EVAL_PAIR_BWD),
         "project_bwd": ("hbm", n_vis * (16 * 3 + 12 * nc_coef + 48 + 4 * 4 * 3 + 12 * nc_coef)),
-        # L1: image and target read, gradient written
-        "loss": ("hbm", W * H * 3 * 12),
+        # L1: image read (4 B), 8-bit target read (1 B), gradient written (4 B)
+        "loss": ("hbm", W * H * 3 * 9),
     }
     # overall fraction: time every stage would take at its binding peak / step time
     ideal_ms = sum((amt / (peaks["hbm_gbs"] * 1e9) if b == "hbm" else amt / (alu_peak * 1e12)) * 1e3
@@ -382,7 +384,8 @@ def run_ours(args, world, rank, local):
         "config": {"workload": f"city-1M-SH3 1920x1080 fwd+bwd (L1), {args.tile}x{args.tile} tiles", "gaussians": n, "visible": n_vis, "tile_entries": k_ent,
                    "width": W, "height": H, "tile": args.tile, "batch": args.batch, "views_per_gpu": 1,
                    "parallelism": f"replicas x{world}", "l2": "flushed between timed steps (256 MB write)",
-                   "accumulators": "gradient and loss buffers cleared between timed steps (one memset)"},
+                   "accumulators": "gradient and loss buffers cleared between timed steps (one memset)",
+                   "target": "8-bit RGB image, channel t stands for t/255"},
         "fwd_mpix_s": fwd_value, "fwd_ms": fwd_ms, "fps_fwd_bwd": 1e3 / step_ms, "fps_fwd": 1e3 / fwd_ms,
         "gaussians_per_s": world * n / (step_ms * 1e-3),
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
@@ -492,7 +495,7 @@ def run_fp16_compare(args, sc, cfg, d_cams, tgt, ds32, st, flush, world, ta, cgs
         def one():
             cur = torch.cuda.current_stream().cuda_stream
             cgs.cgs_render_forward(s_struct, frame.struct, cfg, d_cams, None, None, img, T, nc, cur)
-            cgs.cgs_l1_loss(img, tgt, img.numel(), loss, dL, cur)
+            cgs.cgs_l1_loss_u8(img, tgt, img.numel(), loss, dL, cur)
             cgs.cgs_render_backward(s_struct, frame.struct, cfg, d_cams, dL, T, nc, *grads, cur)
 
         for _ in range(2):

@@ -68,7 +68,7 @@ typedef struct cgs_scene {
     const float* sh;             /* [n][(sh_degree+1)^2][3] SH coefficients, channel fastest */
     int64_t n;                   /* Gaussians, < 2^31 */
     int32_t sh_degree;           /* 0..3 */
-    int32_t n_blocks;            /* >= 1 */
+    int32_t n_blocks;            /* 1 .. 2^20 - 1 */
     int32_t n_levels;            /* >= 1 */
     int32_t attr_fp16;           /* 0: scale, quat, sh are FP32 as above; 1: they are IEEE half
                                     (binary16) with the same shapes ([n][4], [n][4],
@@ -173,6 +173,12 @@ int32_t cgs_render_backward(const cgs_scene* scene, const cgs_frame* frame, cons
  * (sign(0) = 0). */
 int32_t cgs_l1_loss(const float* d_img, const float* d_target, int64_t count, float* d_loss, float* d_grad,
                     void* stream);
+
+/* cgs_l1_loss with an 8-bit target (training images as decoded: channel value t stands for
+ * t / 255, the FP32 quotient correctly rounded), same layout and outputs.  A quarter of the
+ * target bytes of the FP32 variant. */
+int32_t cgs_l1_loss_u8(const float* d_img, const uint8_t* d_target, int64_t count, float* d_loss, float* d_grad,
+                       void* stream);
 
 /* Synchronizes `stream`, then copies the frame's device status word to *status and its
  * counters to counts[0..7]: selected Gaussians, visible Gaussians, tile entries, forward

@@ -86,6 +86,8 @@ def lib():
                                           vp, vp]
         L.cgs_l1_loss.restype = i32
         L.cgs_l1_loss.argtypes = [vp, vp, i64, vp, vp, vp]
+        L.cgs_l1_loss_u8.restype = i32
+        L.cgs_l1_loss_u8.argtypes = [vp, vp, i64, vp, vp, vp]
         L.cgs_frame_status.restype = i32
         L.cgs_frame_status.argtypes = [P(cgs_frame), P(i32), P(i64), vp]
         L.cgs_timing_enable.restype = i32
@@ -206,6 +208,11 @@ def cgs_render_backward(scene, frame, cfg, d_cams, d_dL_dimage, d_final_T, d_n_c
 def cgs_l1_loss(d_img, d_target, count, d_loss, d_grad, stream=None):
     return _check(lib().cgs_l1_loss(_ptr(d_img), _ptr(d_target), count, _ptr(d_loss), _ptr(d_grad),
                                     _stream(stream)), "cgs_l1_loss")
+
+
+def cgs_l1_loss_u8(d_img, d_target, count, d_loss, d_grad, stream=None):
+    return _check(lib().cgs_l1_loss_u8(_ptr(d_img), _ptr(d_target), count, _ptr(d_loss), _ptr(d_grad),
+                                       _stream(stream)), "cgs_l1_loss_u8")
 
 
 def cgs_frame_status(frame, stream=None):

@@ -22,6 +22,8 @@ bool launch_render_bwd(const Layout& L, const cgs_config& c, const float* dimg, 
 void launch_project_bwd(const Layout& L, const cgs_scene& S, const cgs_camera* cams, float near_z, float* g_mo,
                         float* g_sc, float* g_q, float* g_sh, int n_sm, cudaStream_t st);
 void launch_l1(const float* img, const float* tgt, long long n, float* loss, float* grad, int n_sm, cudaStream_t st);
+void launch_l1_u8(const float* img, const uint8_t* tgt, long long n, float* loss, float* grad, int n_sm,
+                  cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------
 // launch counting and optional per-stage event timing
@@ -147,6 +149,7 @@ static int sm_count()
 static bool scene_ok(const cgs_scene* s)
 {
     return s && s->n >= 0 && s->n < (1ll << 31) && s->sh_degree >= 0 && s->sh_degree <= 3 && s->n_blocks >= 1 &&
+           s->n_blocks < (1 << 20) &&
            (s->attr_fp16 == 0 || s->attr_fp16 == 1) &&
            s->n_levels >= 1 && s->mean_opac && s->scale && s->quat && s->sh && s->level_offset && s->level_count;
 }
@@ -257,7 +260,7 @@ static int32_t render_forward(const cgs_scene* scene, const cgs_frame* frame, co
     {
         StageScope s(CGS_STAGE_SELECT, st);
         launch_select(L, *scene, d_cams, d_view_block, d_levels, *cfg, st);
-        counted(2);
+        counted(1);
     }
     {
         StageScope s(CGS_STAGE_PROJECT, st);
@@ -334,6 +337,18 @@ int32_t cgs_l1_loss(const float* d_img, const float* d_target, int64_t count, fl
     {
         StageScope s(CGS_STAGE_LOSS, (cudaStream_t)stream);
         launch_l1(d_img, d_target, count, d_loss, d_grad, sm_count(), (cudaStream_t)stream);
+        counted(1);
+    }
+    return cudaGetLastError() == cudaSuccess ? CGS_OK : CGS_ERR_CUDA;
+}
+
+int32_t cgs_l1_loss_u8(const float* d_img, const uint8_t* d_target, int64_t count, float* d_loss, float* d_grad,
+                       void* stream)
+{
+    if (!d_img || !d_target || !d_loss || !d_grad || count < 1) return CGS_ERR_INVALID_ARGUMENT;
+    {
+        StageScope s(CGS_STAGE_LOSS, (cudaStream_t)stream);
+        launch_l1_u8(d_img, d_target, count, d_loss, d_grad, sm_count(), (cudaStream_t)stream);
         counted(1);
     }
     return cudaGetLastError() == cudaSuccess ? CGS_OK : CGS_ERR_CUDA;

@@ -14,7 +14,7 @@ namespace cgs {
 enum : uint32_t { ST_CAPACITY = 1u << 0, ST_SPIN = 1u << 1, ST_UNSUPPORTED = 1u << 2 };
 
 // Dynamic work counters of the single-pass (decoupled look-back) and persistent kernels.
-enum { CTR_SCAN_RANGES = 2, CTR_BIG = 3, N_CTR = 8 };
+enum { CTR_SCAN_RANGES = 2, CTR_BIG = 3, CTR_SELECT = 5, N_CTR = 8 };
 
 struct Header {
     uint32_t status;

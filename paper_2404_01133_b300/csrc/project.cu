@@ -24,63 +24,131 @@ __device__ __forceinline__ void cull_extent(float o, float A, float B, float C, 
     *tq = t;
 }
 
-// One thread per selected Gaussian j (flattened over views); the CTA walks the selected list
-// in steps of its size (a uniform trip count, so the CTA-wide steps below are safe).  Writes
-// tiles touched and the scene index of every selected Gaussian and, for the visible ones, the
-// screen-space part of the projected record, the tile rect, the (view, depth) sort key and
-// cleared screen-gradient accumulators.  The visible ones are then compacted and duplicated
-// in the same pass:
-//   - the CTA sums its visible count and tiles touched (warp ballots and shuffles, then the
-//     warp totals in shared memory) and reserves a range of the visible list and of the
-//     entry buffer with one atomic add each;
-//   - every warp emits the (tile << 32 | j) entries of its visible Gaussians cooperatively:
-//     lane l takes entries l, l + 32, ... of the warp's range, finds the owning lane by a
-//     binary search over the lanes' exclusive prefixes (shuffles), and counts the tile.
+// Conservative test that Gaussian (mean m, scales s) cannot touch the view's image: its tile
+// rect would be empty.  The 2D covariance is J W Sigma3D W^T J^T + 0.3 I with Sigma3D's
+// eigenvalues s_k^2, so its largest eigenvalue is at most |J|_F^2 max s_k^2 + 0.3; the radius
+// of the exact path, ceil(3 sqrt(lam1)) with lam1 <= that bound + 0.32 (the 0.1 floor of the
+// discriminant), is covered by rb with 1% and 2-pixel slack far above FP32 rounding.  True
+// only when the exact path's rect is certainly empty (a NaN anywhere keeps the Gaussian).
+__device__ __forceinline__ bool surely_off_screen(const float m[3], const float s[3], const cgs_camera& c,
+                                                  float tx, float ty, float tz, int W, int H)
+{
+    const float limx = 1.3f * ((0.5f * (float)c.width) / c.fx), limy = 1.3f * ((0.5f * (float)c.height) / c.fy);
+    const float xzc = fminf(fmaxf(tx / tz, -limx), limx), yzc = fminf(fmaxf(ty / tz, -limy), limy);
+    const float j00 = c.fx / tz, j11 = c.fy / tz, j02 = c.fx * xzc / tz, j12 = c.fy * yzc / tz;
+    const float jn = j00 * j00 + j02 * j02 + j11 * j11 + j12 * j12;
+    const float sm = fmaxf(fmaxf(fabsf(s[0]), fabsf(s[1])), fabsf(s[2]));
+    const float rb = 3.0f * sqrtf((jn * sm * sm + 0.3f) * 1.01f + 0.33f) * 1.01f + 2.0f;
+    const float u = (c.fx * tx) / tz + c.cx, v = (c.fy * ty) / tz + c.cy;
+    (void)m;
+    return u + rb < 0.0f || u - rb > (float)(W - 1) || v + rb < 0.0f || v - rb > (float)(H - 1);
+}
+
+// The CTA walks the selected list (flattened over views) in steps of PROJ_STEP Gaussians (a
+// uniform trip count, so the CTA-wide steps below are safe).
+//   phase 1  PROJ_ITEMS Gaussians per thread: scene index, near plane, the point-wise level
+//            test, the cheap off-screen bound; the survivors are queued in shared memory
+//   phase 2  in rounds of one queued Gaussian per thread (dense warps, so the full projection
+//            is not run by warps whose lanes are mostly culled): covariance,
+//            radius, tile rect; for the visible ones the screen-space part of the projected
+//            record, the rect, the (view, depth) sort key and cleared gradient accumulators
+//   phase 3  compaction and duplication: the CTA sums its visible count and tiles touched
+//            (warp ballots and shuffles, then the warp totals in shared memory) and reserves a
+//            range of the visible list and of the entry buffer with one atomic add each;
+//            every warp emits the (tile << 32 | j) entries of its visible Gaussians
+//            cooperatively: lane l takes entries l, l + 32, ... of the warp's range, finds
+//            the owning lane by a binary search over the lanes' exclusive prefixes
+//            (shuffles), and counts the tile.
 // The order of the visible list and of the entries depends on the order in which CTAs
 // reserve their ranges; nothing downstream depends on it (entries are sorted per tile by
 // (depth, index), colour and backward work per Gaussian).  Colour is evaluated later by
 // k_colour over the visible list.
 constexpr int PROJ_THREADS = 256;
 constexpr int PROJ_WARPS = PROJ_THREADS / 32;
+constexpr int PROJ_ITEMS = 4;  // selected Gaussians per thread in phase 1
+constexpr int PROJ_STEP = PROJ_THREADS * PROJ_ITEMS;
 
 __global__ void __launch_bounds__(PROJ_THREADS) k_project(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams,
                                                           float near_z)
 {
     __shared__ uint32_t s_wv[PROJ_WARPS], s_wt[PROJ_WARPS];
-    __shared__ uint32_t s_vbase;
+    __shared__ uint32_t s_vbase, s_nq;
     __shared__ unsigned long long s_ebase;
+    __shared__ uint32_t s_qj[PROJ_STEP];
+    __shared__ int s_qv[PROJ_STEP];
+    __shared__ long long s_qg[PROJ_STEP];
     const uint32_t n = L.hdr->n_sel;
     const float4* __restrict__ mo4 = reinterpret_cast<const float4*>(S.mean_opac);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const unsigned long long cap = (unsigned long long)L.k_cap;
-    for (uint32_t base = blockIdx.x * PROJ_THREADS; base < n; base += gridDim.x * PROJ_THREADS) {
-        const uint32_t j = base + threadIdx.x;
-        uint32_t tt = 0, rx = 0, ry = 0;
-        int v = 0;
-        if (j < n) {
-            long long g;
-            locate(L, j, &v, &g);
-            L.gidx[j] = (uint32_t)g;
-            const cgs_camera& c = cams[v];
-            const float4 mo = __ldg(mo4 + g);
-            const float m[3] = {mo.x, mo.y, mo.z};
-            // near-plane test first, so culled Gaussians never read scale or rotation
-            const float tz = ((c.R[6] * m[0] + c.R[7] * m[1]) + c.R[8] * m[2]) + c.t[2];
-            bool keep = tz > near_z;
-            if (keep && L.lod_mode == CGS_LOD_POINT) {
-                // point-wise baseline: the level of this Gaussian's own distance; kept iff its
-                // rank in the block lies inside that level's (nested) prefix
-                const float d0 = m[0] - c.campos[0], d1 = m[1] - c.campos[1], d2 = m[2] - c.campos[2];
-                const float dist = sqrtf((d0 * d0 + d1 * d1) + d2 * d2);
-                int lv = dist < L.lod_d1 ? 0 : (dist < L.lod_d2 ? 1 : 2);
-                if (lv > S.n_levels - 1) lv = S.n_levels - 1;
-                int blk;
-                uint32_t rank;
-                locate_block(L, j, v, &blk, &rank);
-                keep = (long long)rank < S.level_count[(long long)blk * S.n_levels + lv];
+    for (uint32_t base = blockIdx.x * PROJ_STEP; base < n; base += gridDim.x * PROJ_STEP) {
+        // phase 1
+        if (threadIdx.x == 0) s_nq = 0;
+        __syncthreads();
+#pragma unroll 1
+        for (int u = 0; u < PROJ_ITEMS; u++) {
+            const uint32_t j = base + (uint32_t)(u * PROJ_THREADS) + threadIdx.x;
+            bool cand = false;
+            int v = 0;
+            long long g = 0;
+            if (j < n) {
+                locate(L, j, &v, &g);
+                L.gidx[j] = (uint32_t)g;
+                const cgs_camera& c = cams[v];
+                const float4 mo = __ldg(mo4 + g);
+                const float m[3] = {mo.x, mo.y, mo.z};
+                // near-plane test first, so culled Gaussians never read scale or rotation
+                const float tz = ((c.R[6] * m[0] + c.R[7] * m[1]) + c.R[8] * m[2]) + c.t[2];
+                bool keep = tz > near_z;
+                if (keep && L.lod_mode == CGS_LOD_POINT) {
+                    // point-wise baseline: the level of this Gaussian's own distance; kept iff
+                    // its rank in the block lies inside that level's (nested) prefix
+                    const float d0 = m[0] - c.campos[0], d1 = m[1] - c.campos[1], d2 = m[2] - c.campos[2];
+                    const float dist = sqrtf((d0 * d0 + d1 * d1) + d2 * d2);
+                    int lv = dist < L.lod_d1 ? 0 : (dist < L.lod_d2 ? 1 : 2);
+                    if (lv > S.n_levels - 1) lv = S.n_levels - 1;
+                    int blk;
+                    uint32_t rank;
+                    locate_block(L, j, v, &blk, &rank);
+                    keep = (long long)rank < S.level_count[(long long)blk * S.n_levels + lv];
+                }
+                if (keep) {
+                    float s[3], q[4];
+                    load_scale_quat(S, g, s, q);
+                    const float tx = ((c.R[0] * m[0] + c.R[1] * m[1]) + c.R[2] * m[2]) + c.t[0];
+                    const float ty = ((c.R[3] * m[0] + c.R[4] * m[1]) + c.R[5] * m[2]) + c.t[1];
+                    keep = !surely_off_screen(m, s, c, tx, ty, tz, L.W, L.H);
+                }
+                cand = keep;
+                if (!cand) L.tt[j] = 0;
             }
-            if (keep) {
+            const uint32_t cb = __ballot_sync(0xffffffffu, cand);
+            uint32_t wbase = 0;
+            if (lane == 0 && cb) wbase = atomicAdd(&s_nq, (uint32_t)__popc(cb));
+            wbase = __shfl_sync(0xffffffffu, wbase, 0);
+            if (cand) {
+                const uint32_t slot = wbase + __popc(cb & lt);
+                s_qj[slot] = j;
+                s_qv[slot] = v;
+                s_qg[slot] = g;
+            }
+        }
+        __syncthreads();
+        const uint32_t nq = s_nq;
+        __syncthreads();  // every thread has read nq before the next step resets it
+        for (uint32_t q0 = 0; q0 < nq; q0 += PROJ_THREADS) {
+            // phase 2
+            uint32_t tt = 0, rx = 0, ry = 0, j = 0;
+            int v = 0;
+            if (q0 + threadIdx.x < nq) {
+                const uint32_t qi = q0 + threadIdx.x;
+                j = s_qj[qi];
+                v = s_qv[qi];
+                const long long g = s_qg[qi];
+                const cgs_camera& c = cams[v];
+                const float4 mo = __ldg(mo4 + g);
+                const float m[3] = {mo.x, mo.y, mo.z};
                 float s[3], q[4];
                 load_scale_quat(S, g, s, q);
                 Proj p;
@@ -112,74 +180,73 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(Layout L, cgs_scene S,
                         L.gs[3 * (size_t)j + 2] = z4;
                     }
                 }
+                L.tt[j] = tt;
             }
-            L.tt[j] = tt;
-        }
-        // warp totals: visible count (ballot) and tiles touched (inclusive shuffle scan)
-        const uint32_t vb = __ballot_sync(0xffffffffu, tt > 0);
-        uint32_t inc = tt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        const uint32_t excl = inc - tt;
-        const uint32_t wtot = __shfl_sync(0xffffffffu, inc, 31);
-        if (lane == 0) {
-            s_wv[warp] = __popc(vb);
-            s_wt[warp] = wtot;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t nv = 0;
-            unsigned long long ne = 0;
-            for (int w = 0; w < PROJ_WARPS; w++) {
-                const uint32_t a = s_wv[w], b = s_wt[w];
-                s_wv[w] = nv;
-                s_wt[w] = (uint32_t)ne;
-                nv += a;
-                ne += b;
+            // phase 3: warp totals, visible count (ballot) and tiles touched (inclusive shuffle scan)
+            const uint32_t vb = __ballot_sync(0xffffffffu, tt > 0);
+            uint32_t inc = tt;
+    #pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
             }
-            s_vbase = nv ? atomicAdd(&L.hdr->n_vis, nv) : 0u;
-            s_ebase = ne ? atomicAdd(&L.hdr->k_total, ne) : 0ull;
-            if (ne && s_ebase + ne > cap) latch(L.hdr, ST_CAPACITY);
-        }
-        __syncthreads();
-        if (tt > 0) L.vis[s_vbase + s_wv[warp] + __popc(vb & lt)] = j;
-        // cooperative duplication of the warp's entries
-        const unsigned long long e0 = s_ebase + s_wt[warp];
-        for (uint32_t it = 0; it * 32u < wtot; it++) {
-            const uint32_t idx = it * 32u + (uint32_t)lane;
-            // owner: the last lane o with excl(o) <= idx (lanes with tt = 0 share their
-            // successor's prefix and are never the last such lane)
-            int o = 0;
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                const uint32_t eo = __shfl_sync(0xffffffffu, excl, o + step);
-                if (eo <= idx) o += step;
+            const uint32_t excl = inc - tt;
+            const uint32_t wtot = __shfl_sync(0xffffffffu, inc, 31);
+            if (lane == 0) {
+                s_wv[warp] = __popc(vb);
+                s_wt[warp] = wtot;
             }
-            const uint32_t oj = __shfl_sync(0xffffffffu, j, o);
-            const uint32_t orx = __shfl_sync(0xffffffffu, rx, o), ory = __shfl_sync(0xffffffffu, ry, o);
-            const uint32_t oex = __shfl_sync(0xffffffffu, excl, o);
-            const int ov = __shfl_sync(0xffffffffu, v, o);
-            const unsigned long long k = e0 + idx;
-            if (idx < wtot && k < cap) {
-                const uint32_t tx0 = orx & 0xffffu, ty0 = orx >> 16, w = (ory & 0xffffu) - tx0;
-                const uint32_t local = idx - oex;
-                const uint32_t t = (uint32_t)ov * (uint32_t)L.T + (ty0 + local / w) * (uint32_t)L.tiles_x + (tx0 + local % w);
-                L.eraw[k] = ((unsigned long long)t << 32) | oj;
-                atomicAdd(&L.tcnt[t], 1u);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint32_t nv = 0;
+                unsigned long long ne = 0;
+                for (int w = 0; w < PROJ_WARPS; w++) {
+                    const uint32_t a = s_wv[w], b = s_wt[w];
+                    s_wv[w] = nv;
+                    s_wt[w] = (uint32_t)ne;
+                    nv += a;
+                    ne += b;
+                }
+                s_vbase = nv ? atomicAdd(&L.hdr->n_vis, nv) : 0u;
+                s_ebase = ne ? atomicAdd(&L.hdr->k_total, ne) : 0ull;
+                if (ne && s_ebase + ne > cap) latch(L.hdr, ST_CAPACITY);
             }
+            __syncthreads();
+            if (tt > 0) L.vis[s_vbase + s_wv[warp] + __popc(vb & lt)] = j;
+            // cooperative duplication of the warp's entries
+            const unsigned long long e0 = s_ebase + s_wt[warp];
+            for (uint32_t it = 0; it * 32u < wtot; it++) {
+                const uint32_t idx = it * 32u + (uint32_t)lane;
+                // owner: the last lane o with excl(o) <= idx (lanes with tt = 0 share their
+                // successor's prefix and are never the last such lane)
+                int o = 0;
+    #pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const uint32_t eo = __shfl_sync(0xffffffffu, excl, o + step);
+                    if (eo <= idx) o += step;
+                }
+                const uint32_t oj = __shfl_sync(0xffffffffu, j, o);
+                const uint32_t orx = __shfl_sync(0xffffffffu, rx, o), ory = __shfl_sync(0xffffffffu, ry, o);
+                const uint32_t oex = __shfl_sync(0xffffffffu, excl, o);
+                const int ov = __shfl_sync(0xffffffffu, v, o);
+                const unsigned long long k = e0 + idx;
+                if (idx < wtot && k < cap) {
+                    const uint32_t tx0 = orx & 0xffffu, ty0 = orx >> 16, w = (ory & 0xffffu) - tx0;
+                    const uint32_t local = idx - oex;
+                    const uint32_t t = (uint32_t)ov * (uint32_t)L.T + (ty0 + local / w) * (uint32_t)L.tiles_x + (tx0 + local % w);
+                    L.eraw[k] = ((unsigned long long)t << 32) | oj;
+                    atomicAdd(&L.tcnt[t], 1u);
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
 // View-dependent colour (SH, Sec. 3.1) of each visible Gaussian, over the compacted visible
 // list so every lane has work.  Writes the third record (r, g, b, t), t the culling
-// threshold on the quadratic form (see cull_extent).
-// DEG is the scene's SH degree: every loop over coefficients has a fixed trip count, so the
-// coefficients stay in registers.
+// threshold on the quadratic form (see cull_extent).  DEG is the scene's SH degree: every
+// loop over coefficients has a fixed trip count, so the coefficients stay in registers.
 template <int DEG>
 __global__ void __launch_bounds__(256) k_colour(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams)
 {
@@ -203,8 +270,8 @@ __global__ void __launch_bounds__(256) k_colour(Layout L, cgs_scene S, const cgs
 void launch_project(const Layout& L, const cgs_scene& S, const cgs_camera* cams, float near_z, int n_sm,
                     cudaStream_t st)
 {
-    long long want = (L.n_cap + PROJ_THREADS - 1) / PROJ_THREADS;
-    long long grid = want < (long long)n_sm * 8 ? want : (long long)n_sm * 8;
+    long long want = (L.n_cap + PROJ_STEP - 1) / PROJ_STEP;
+    long long grid = want < (long long)n_sm * 4 ? want : (long long)n_sm * 4;
     if (grid < 1) grid = 1;
     k_project<<<(unsigned)grid, PROJ_THREADS, 0, st>>>(L, S, cams, near_z);
 }

@@ -10,18 +10,21 @@
 
 namespace cgs {
 
-// power = -0.5 (A' dx^2 + C' dy^2) - B' dx dy and G = exp(power), with every rounding step
-// fixed by intrinsics so the forward and the backward kernels take identical decisions.
-__device__ __forceinline__ float pair_power(const float4& a, const float4& b, float fpx, float fpy, float* dx_out,
-                                            float* dy_out)
+// power = -0.5 A' dx^2 - B' dx dy - 0.5 C' dy^2 at a lane's two pixels (px, py0) and
+// (px, py1), which share dx, with every rounding step fixed by intrinsics so the forward and
+// the backward kernels take identical decisions.
+__device__ __forceinline__ void pair_power2(const float4& a, const float4& b, float fpx, float fpy0, float fpy1,
+                                            float* pw0, float* pw1, float* dx_out, float* dy0_out, float* dy1_out)
 {
-    const float dx = __fsub_rn(a.x, fpx), dy = __fsub_rn(a.y, fpy);
-    float q = __fmul_rn(__fmul_rn(b.x, dx), dx);
-    q = __fmaf_rn(__fmul_rn(b.z, dy), dy, q);
-    const float cr = __fmul_rn(__fmul_rn(b.y, dx), dy);
+    const float dx = __fsub_rn(a.x, fpx), dy0 = __fsub_rn(a.y, fpy0), dy1 = __fsub_rn(a.y, fpy1);
+    const float hC = __fmul_rn(-0.5f, b.z);
+    const float ax = __fmul_rn(__fmul_rn(__fmul_rn(-0.5f, b.x), dx), dx);  // -A' dx^2 / 2
+    const float nbx = __fmul_rn(-b.y, dx);                                  // -B' dx
+    *pw0 = __fmaf_rn(__fmul_rn(hC, dy0), dy0, __fmaf_rn(nbx, dy0, ax));
+    *pw1 = __fmaf_rn(__fmul_rn(hC, dy1), dy1, __fmaf_rn(nbx, dy1, ax));
     *dx_out = dx;
-    *dy_out = dy;
-    return __fmaf_rn(-0.5f, q, -cr);
+    *dy0_out = dy0;
+    *dy1_out = dy1;
 }
 
 // Warp sum of 32 values per lane by halving exchanges: at each step a lane keeps half of its
@@ -112,12 +115,9 @@ struct FwdPixel {
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
     uint32_t last = 0, stop_at = 0xffffffffu;
     bool done = false;
-    __device__ __forceinline__ bool blend(const float4& a, const float4& b, const float4& c, float fpx, float fpy,
-                                          uint32_t pos)
+    __device__ __forceinline__ bool blend(float power, float o, const float4& c, uint32_t pos)
     {
-        float dx, dy;
-        const float power = pair_power(a, b, fpx, fpy, &dx, &dy);
-        const float alpha = fminf(0.99f, __fmul_rn(a.z, __expf(power)));
+        const float alpha = fminf(0.99f, __fmul_rn(o, __expf(power)));
         const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
         const bool ok = !done && !(power > 0.0f) && !(alpha < 1.0f / 255.0f);
         const bool stop = ok && Tn < 1e-4f;
@@ -199,8 +199,10 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 8 : 32) k_render_fwd(Layo
                 const int k = c0 + kk;
                 const float4 a = s_a[k], b = s_b[k], c = s_c[k];
                 const uint32_t pos = start - rg.x + (uint32_t)k;
-                const bool b0 = p0.blend(a, b, c, fpx, fpy0, pos);
-                const bool b1 = p1.blend(a, b, c, fpx, fpy1, pos);
+                float pw0, pw1, dx, dy0, dy1;
+                pair_power2(a, b, fpx, fpy0, fpy1, &pw0, &pw1, &dx, &dy0, &dy1);
+                const bool b0 = p0.blend(pw0, a.z, c, pos);
+                const bool b1 = p1.blend(pw1, a.z, c, pos);
                 if (__any_sync(0xffffffffu, b0 || b1)) word |= 1u << kk;
                 if (HITS) {
                     const int cnt = __popc(__ballot_sync(0xffffffffu, b0)) + __popc(__ballot_sync(0xffffffffu, b1));
@@ -256,14 +258,14 @@ struct BwdPixel {
     float T = 1.0f, gS = 0.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
     uint32_t nc = 0;
     // Predicated like the forward: a pair that did not blend leaves T and gS and adds exact
-    // zeros (selected, never multiplied, so no inf * 0 reaches the sums).
-    __device__ __forceinline__ bool replay(const float4& a, const float4& b, const float4& c, float fpx, float fpy,
-                                           uint32_t lp, float* m)
+    // zeros (selected, never multiplied, so no inf * 0 reaches the sums).  SET writes the
+    // nine sums instead of adding to them (the first pixel of a lane).
+    template <bool SET>
+    __device__ __forceinline__ bool replay(float power, float dx, float dy, float o, const float4& c, uint32_t lp,
+                                           float* m)
     {
-        float dx, dy;
-        const float power = pair_power(a, b, fpx, fpy, &dx, &dy);
         const float G = __expf(power);
-        const float og = __fmul_rn(a.z, G);
+        const float og = __fmul_rn(o, G);
         const float alpha = fminf(0.99f, og);
         const bool use = lp < nc && !(power > 0.0f) && !(alpha < 1.0f / 255.0f);
         const float inv = __fdividef(1.0f, 1.0f - alpha);
@@ -274,18 +276,12 @@ struct BwdPixel {
         T = use ? Tb : T;
         gS = use ? gS + aT * gc : gS;
         const float aTu = use ? aT : 0.0f;
-        m[6] += g0 * aTu;
-        m[7] += g1 * aTu;
-        m[8] += g2 * aTu;
         const bool lin = use && !(og > 0.99f);  // the 0.99 clamp passes no gradient
-        m[5] += lin ? dal * G : 0.0f;
         const float dp = lin ? dal * og : 0.0f;
         const float px = dp * dx, py = dp * dy;
-        m[0] += px;
-        m[1] += py;
-        m[2] += px * dx;
-        m[3] += px * dy;
-        m[4] += py * dy;
+        const float v[9] = {px, py, px * dx, px * dy, py * dy, lin ? dal * G : 0.0f, g0 * aTu, g1 * aTu, g2 * aTu};
+#pragma unroll
+        for (int i = 0; i < 9; i++) m[i] = SET ? v[i] : m[i] + v[i];
         return use;
     }
 };
@@ -389,15 +385,21 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 6 : 24) k_render_bwd(Layo
                 }
                 float acc[32];
 #pragma unroll
-                for (int i = 0; i < 32; i++) acc[i] = 0.0f;
+                for (int i = 27; i < 32; i++) acc[i] = 0.0f;
 #pragma unroll
                 for (int e = 0; e < 3; e++) {
-                    if (ks[e] < 0) continue;
+                    if (ks[e] < 0) {
+#pragma unroll
+                        for (int i = 0; i < 9; i++) acc[9 * e + i] = 0.0f;
+                        continue;
+                    }
                     const int k = ks[e];
                     const float4 a = s_a[k], b = s_b[k], c = s_c[k];
                     const uint32_t lp = (uint32_t)(bs + k - first);
-                    pairs += (uint32_t)q0.replay(a, b, c, fpx, fpy0, lp, acc + 9 * e);
-                    pairs += (uint32_t)q1.replay(a, b, c, fpx, fpy1, lp, acc + 9 * e);
+                    float pw0, pw1, dx, dy0, dy1;
+                    pair_power2(a, b, fpx, fpy0, fpy1, &pw0, &pw1, &dx, &dy0, &dy1);
+                    pairs += (uint32_t)q0.replay<true>(pw0, dx, dy0, a.z, c, lp, acc + 9 * e);
+                    pairs += (uint32_t)q1.replay<false>(pw1, dx, dy1, a.z, c, lp, acc + 9 * e);
                 }
                 const float tot = warp_transpose_sum32(acc, lane);
                 if (lane < 27) {
@@ -488,14 +490,20 @@ bool launch_render_bwd(const Layout& L, const cgs_config& c, const float* dimg, 
 
 // L1 loss: loss += mean |img - target|, grad = sign(img - target) / count.  The partial
 // sums are reduced per CTA, so the loss takes one atomic per CTA.
-__global__ void __launch_bounds__(256) k_l1(const float* __restrict__ img, const float* __restrict__ tgt, long long n,
+// Target value of an FP32 target, or of an 8-bit one (channel value t stands for t / 255,
+// correctly rounded).
+__device__ __forceinline__ float target_value(float t) { return t; }
+__device__ __forceinline__ float target_value(uint8_t t) { return __fdiv_rn((float)t, 255.0f); }
+
+template <typename TT>
+__global__ void __launch_bounds__(256) k_l1(const float* __restrict__ img, const TT* __restrict__ tgt, long long n,
                                             float* loss, float* __restrict__ grad)
 {
     __shared__ float s_w[8];
     const float inv = 1.0f / (float)n;
     float acc = 0.0f;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float d = img[i] - tgt[i];
+        const float d = img[i] - target_value(tgt[i]);
         acc += fabsf(d);
         grad[i] = d > 0.0f ? inv : (d < 0.0f ? -inv : 0.0f);
     }
@@ -509,12 +517,24 @@ __global__ void __launch_bounds__(256) k_l1(const float* __restrict__ img, const
     }
 }
 
-void launch_l1(const float* img, const float* tgt, long long n, float* loss, float* grad, int n_sm, cudaStream_t st)
+template <typename TT>
+static void l1_launch(const float* img, const TT* tgt, long long n, float* loss, float* grad, int n_sm, cudaStream_t st)
 {
     long long g = (n + 255) / 256;
     if (g > (long long)n_sm * 8) g = (long long)n_sm * 8;
     if (g < 1) g = 1;
-    k_l1<<<(unsigned)g, 256, 0, st>>>(img, tgt, n, loss, grad);
+    k_l1<TT><<<(unsigned)g, 256, 0, st>>>(img, tgt, n, loss, grad);
+}
+
+void launch_l1(const float* img, const float* tgt, long long n, float* loss, float* grad, int n_sm, cudaStream_t st)
+{
+    l1_launch<float>(img, tgt, n, loss, grad, n_sm, st);
+}
+
+void launch_l1_u8(const float* img, const uint8_t* tgt, long long n, float* loss, float* grad, int n_sm,
+                  cudaStream_t st)
+{
+    l1_launch<uint8_t>(img, tgt, n, loss, grad, n_sm, st);
 }
 
 }  // namespace cgs

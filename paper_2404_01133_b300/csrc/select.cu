@@ -73,7 +73,9 @@ __global__ void k_lod_levels(cgs_scene S, const cgs_camera* __restrict__ cams, i
 }
 
 // Per view: the level of every block (given, one training block, or LoD), then the ordered
-// list of selected segments (fusion by concatenation, Sec. 3.3.2) and its prefix counts.
+// list of selected segments (fusion by concatenation, Sec. 3.3.2) and its prefix counts; the
+// last CTA to finish also writes the prefix of the per-view counts (the views' bases in the
+// flattened selected list).
 __global__ void k_select(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams, const int32_t* view_block,
                          const int8_t* levels_in, cgs_config cfg)
 {
@@ -110,39 +112,59 @@ __global__ void k_select(Layout L, cgs_scene S, const cgs_camera* __restrict__ c
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t* sb = L.seg_base + (long long)v * (NB + 1);
-        long long* so = L.seg_off + (long long)v * NB;
-        unsigned long long acc = 0;
-        int s = 0;
-        for (int b = 0; b < NB; b++) {
-            if (lev[b] < 0) continue;
-            so[s] = S.level_offset[(long long)b * NL + lev[b]];
-            L.seg_blk[(long long)v * NB + s] = b;
-            sb[s] = (uint32_t)acc;
-            acc += (unsigned long long)S.level_count[(long long)b * NL + lev[b]];
-            s++;
-        }
-        sb[s] = (uint32_t)(acc < 0xffffffffull ? acc : 0xffffffffull);
-        L.n_seg[v] = (uint32_t)s;
-        L.view_cnt[v] = (uint32_t)(acc < 0xffffffffull ? acc : 0xffffffffull);
-    }
-}
-
-// Exclusive prefix of the per-view counts; total capped at the frame capacity.
-__global__ void k_select_finish(Layout L)
-{
+    // the ordered segment list: one CTA-wide exclusive scan per chunk of blocks of the packed
+    // pair (selected count << 0 | Gaussian count << SEG_BITS)
+    constexpr int SEG_BITS = 20;  // n_blocks < 2^20
     __shared__ unsigned long long wb[33];
+    __shared__ unsigned long long s_carry;
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    uint32_t* sb = L.seg_base + (long long)v * (NB + 1);
+    long long* so = L.seg_off + (long long)v * NB;
+    for (int b0 = 0; b0 < NB; b0 += blockDim.x) {
+        const int b = b0 + threadIdx.x;
+        const int l = b < NB ? lev[b] : -1;
+        const unsigned long long cnt = l >= 0 ? (unsigned long long)S.level_count[(long long)b * NL + l] : 0ull;
+        const unsigned long long x = l >= 0 ? (1ull | (cnt << SEG_BITS)) : 0ull;
+        unsigned long long tot;
+        const unsigned long long ex = s_carry + block_exclusive_scan<unsigned long long>(x, wb, &tot);
+        if (l >= 0) {
+            const int sidx = (int)(ex & ((1ull << SEG_BITS) - 1));
+            const unsigned long long acc = ex >> SEG_BITS;
+            so[sidx] = S.level_offset[(long long)b * NL + l];
+            L.seg_blk[(long long)v * NB + sidx] = b;
+            sb[sidx] = (uint32_t)(acc < 0xffffffffull ? acc : 0xffffffffull);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int ns = (int)(s_carry & ((1ull << SEG_BITS) - 1));
+        const unsigned long long acc = s_carry >> SEG_BITS;
+        sb[ns] = (uint32_t)(acc < 0xffffffffull ? acc : 0xffffffffull);
+        L.n_seg[v] = (uint32_t)ns;
+        L.view_cnt[v] = (uint32_t)(acc < 0xffffffffull ? acc : 0xffffffffull);
+        // the last view's CTA to get here writes the per-view prefix
+        __threadfence();
+        s_last = atomicAdd(&L.hdr->ctr[CTR_SELECT], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // exclusive prefix of the per-view counts; total capped at the frame capacity
     const int V = L.V;
     const int per = (V + blockDim.x - 1) / blockDim.x;
     const int v0 = threadIdx.x * per;
+    const volatile uint32_t* vc = L.view_cnt;
     unsigned long long local = 0;
-    for (int v = v0; v < v0 + per && v < V; v++) local += L.view_cnt[v];
+    for (int w = v0; w < v0 + per && w < V; w++) local += vc[w];
     unsigned long long total;
     unsigned long long run = block_exclusive_scan<unsigned long long>(local, wb, &total);
-    for (int v = v0; v < v0 + per && v < V; v++) {
-        L.view_base[v] = (uint32_t)(run < 0xffffffffull ? run : 0xffffffffull);
-        run += L.view_cnt[v];
+    for (int w = v0; w < v0 + per && w < V; w++) {
+        L.view_base[w] = (uint32_t)(run < 0xffffffffull ? run : 0xffffffffull);
+        run += vc[w];
     }
     if (threadIdx.x == 0) {
         L.view_base[V] = (uint32_t)(total < 0xffffffffull ? total : 0xffffffffull);
@@ -274,7 +296,6 @@ void launch_select(const Layout& L, const cgs_scene& S, const cgs_camera* cams, 
                    const int8_t* levels, const cgs_config& cfg, cudaStream_t st)
 {
     k_select<<<L.V, 256, 0, st>>>(L, S, cams, view_block, levels, cfg);
-    k_select_finish<<<1, 1024, 0, st>>>(L);
 }
 
 void launch_lod_levels(const cgs_scene& S, const cgs_config& cfg, const cgs_camera* cams, int n_views,

@@ -305,6 +305,12 @@ def target_image(seed, width, height):
     return rng.uniform(0.0, 1.0, size=(3, height, width)).astype(np.float32)
 
 
+def target_image_u8(seed, width, height):
+    """Seeded 8-bit target image (uniform channel values 0..255), planar [3, H, W]."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, 256, size=(3, height, width), dtype=np.uint8)
+
+
 def workload_city_lod(n=20_000_000, grid=8, seed=3, heights=(50.0, 200.0, 500.0, 1000.0, 2000.0),
                       width=1920, height=1080):
     """Block-LoD city (6 km^2, grid x grid blocks, 3 nested levels) and top-down cameras."""

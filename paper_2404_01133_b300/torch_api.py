@@ -181,9 +181,13 @@ class RenderFn(torch.autograd.Function):
 
 
 def l1_loss(img, target, stream=None):
+    """L1 loss and its gradient; target is float32, or uint8 (t stands for t / 255)."""
     loss = torch.zeros(1, dtype=torch.float32, device=img.device)
     grad = torch.empty_like(img)
-    _c.cgs_l1_loss(img, target, img.numel(), loss, grad, stream)
+    if target.dtype == torch.uint8:
+        _c.cgs_l1_loss_u8(img, target, img.numel(), loss, grad, stream)
+    else:
+        _c.cgs_l1_loss(img, target, img.numel(), loss, grad, stream)
     return loss, grad
 
 

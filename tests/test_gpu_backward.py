@@ -93,6 +93,19 @@ def test_l1_loss_kernel():
     np.testing.assert_array_equal(grad.cpu().numpy(), ograd)
 
 
+def test_l1_loss_kernel_with_8bit_target():
+    rng = np.random.default_rng(6)
+    img = rng.uniform(size=(3, 37, 61)).astype(np.float32)
+    t8 = rng.integers(0, 256, size=(3, 37, 61)).astype(np.uint8)
+    img[0, 1, 2] = np.float32(t8[0, 1, 2]) / np.float32(255)   # an exact tie: gradient 0
+    loss, grad = ta.l1_loss(torch.tensor(img).cuda(), torch.tensor(t8).cuda())
+    # an 8-bit channel value t stands for t / 255 (FP32 quotient, correctly rounded)
+    oloss, ograd = oracle.l1(img, t8.astype(np.float32) / np.float32(255))
+    assert abs(loss.item() - oloss) <= 1e-6 * oloss
+    np.testing.assert_array_equal(grad.cpu().numpy(), ograd)
+    assert ograd[0, 1, 2] == 0.0
+
+
 def test_autograd_function_matches_direct_backward():
     sc = synth.single_block(synth.random_cube_scene(300, seed=8, sh_degree=1, log_scale_mu=-2.3))
     cam = synth.small_scene_camera(48, 48, f=60.0, dist=3.0)
