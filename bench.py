@@ -49,7 +49,8 @@ FP32_OPS_PER_CONTRIB_PAIR_BWD = 45
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels on this
 # workload (profiles/k_render_city1m.md).  A kernel absent here reports traffic null; an entry
 # must be removed when its kernel changes.
-NCU_TRAFFIC_BYTES = {"render": 14.700800e6 + 0.808192e6, "render_bwd": 65.559552e6 + 2.001152e6}
+NCU_TRAFFIC_BYTES = {"render": 14.714624e6 + 0.716544e6, "render_bwd": 65.620224e6 + 1.495808e6,
+                     "project_bwd": 104.624896e6 + 8.114688e6, "loss": 31.121152e6 + 0.040960e6}
 
 
 def parse_args():
@@ -361,6 +362,8 @@ def run_ours(args, world, rank, local):
     # overall fraction: time every stage would take at its binding peak / step time
     ideal_ms = sum((amt / (peaks["hbm_gbs"] * 1e9) if b == "hbm" else amt / (alu_peak * 1e12)) * 1e3
                    for b, amt in work.values())
+    ideal_fwd_ms = sum((amt / (peaks["hbm_gbs"] * 1e9) if b == "hbm" else amt / (alu_peak * 1e12)) * 1e3
+                       for k, (b, amt) in work.items() if k in ("project", "duplicate", "sort", "render"))
     strict = {"render": pairs_b * FP32_OPS_PER_CONTRIB_PAIR_FWD / (stage_ms["render"] * 1e-3) / 1e12 / alu_peak,
               "render_bwd": pairs_b * FP32_OPS_PER_CONTRIB_PAIR_BWD / (stage_ms["render_bwd"] * 1e-3) / 1e12 / alu_peak}
     dom = max(work, key=lambda k: stage_ms.get(k, 0.0))
@@ -395,6 +398,9 @@ def run_ours(args, world, rank, local):
         "roofline": roof,
         "roofline_overall": {"ideal_ms": ideal_ms, "frac": ideal_ms / step_ms,
                              "definition": "sum over stages of algorithmic work / binding peak, over the step time"},
+        "roofline_overall_fwd": {"ideal_ms": ideal_fwd_ms, "frac": ideal_fwd_ms / fwd_ms,
+                                 "definition": "the same over the forward stages and the forward time"},
+        "ms_per_step_median": statistics.median(ms),
         "roofline_stage_frac": {k: ((amt / (peaks["hbm_gbs"] * 1e9) if b == "hbm" else amt / (alu_peak * 1e12)) * 1e3
                                     / stage_ms[k]) for k, (b, amt) in work.items() if stage_ms.get(k)},
         "roofline_contributing_pairs_frac": strict,

@@ -67,8 +67,9 @@ constexpr int PROJ_THREADS = 256;
 constexpr int PROJ_WARPS = PROJ_THREADS / 32;
 constexpr int PROJ_ITEMS = 4;  // selected Gaussians per thread in phase 1
 constexpr int PROJ_STEP = PROJ_THREADS * PROJ_ITEMS;
+constexpr int PROJ_CTAS_PER_SM = 5;  // latency-bound: registers capped so five CTAs fit an SM
 
-__global__ void __launch_bounds__(PROJ_THREADS) k_project(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams,
+__global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM) k_project(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams,
                                                           float near_z)
 {
     __shared__ uint32_t s_wv[PROJ_WARPS], s_wt[PROJ_WARPS];
@@ -271,7 +272,7 @@ void launch_project(const Layout& L, const cgs_scene& S, const cgs_camera* cams,
                     cudaStream_t st)
 {
     long long want = (L.n_cap + PROJ_STEP - 1) / PROJ_STEP;
-    long long grid = want < (long long)n_sm * 4 ? want : (long long)n_sm * 4;
+    long long grid = want < (long long)n_sm * PROJ_CTAS_PER_SM ? want : (long long)n_sm * PROJ_CTAS_PER_SM;
     if (grid < 1) grid = 1;
     k_project<<<(unsigned)grid, PROJ_THREADS, 0, st>>>(L, S, cams, near_z);
 }

@@ -12,14 +12,15 @@ namespace cgs {
 // Two roles per CTA of 128 threads and 64 visible Gaussians: warps 0-1 chain the geometric
 // gradients (u, v, conic, opacity -> mean, scale, rotation), warps 2-3 the colour gradients
 // (rgb -> SH coefficients and the view-direction term of the mean).  The split halves the
-// registers a thread needs and doubles the threads in flight; each role adds its own part of
-// the mean gradient.  DEG is the scene's SH degree, fixed at compile time so the coefficient
+// registers a thread needs and doubles the threads in flight (registers are further capped
+// so six CTAs fit an SM: the kernel is bound by memory latency); each role adds its own part
+// of the mean gradient.  DEG is the scene's SH degree, fixed at compile time so the coefficient
 // loops unroll and the per-Gaussian arrays live in registers.
 constexpr int PB_THREADS = 128;
 constexpr int PB_PER_CTA = PB_THREADS / 2;
 
 template <int DEG>
-__global__ void __launch_bounds__(PB_THREADS) k_project_bwd(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams,
+__global__ void __launch_bounds__(PB_THREADS, 6) k_project_bwd(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams,
                                                             float near_z, float* __restrict__ g_mo,
                                                             float* __restrict__ g_sc, float* __restrict__ g_q,
                                                             float* __restrict__ g_sh)

@@ -491,22 +491,69 @@ bool launch_render_bwd(const Layout& L, const cgs_config& c, const float* dimg, 
 // L1 loss: loss += mean |img - target|, grad = sign(img - target) / count.  The partial
 // sums are reduced per CTA, so the loss takes one atomic per CTA.
 // Target value of an FP32 target, or of an 8-bit one (channel value t stands for t / 255,
-// correctly rounded).
-__device__ __forceinline__ float target_value(float t) { return t; }
-__device__ __forceinline__ float target_value(uint8_t t) { return __fdiv_rn((float)t, 255.0f); }
+// correctly rounded: a 256-entry table of __fdiv_rn(t, 255) per CTA).
+template <typename TT>
+struct TargetMap;
+template <>
+struct TargetMap<float> {
+    __device__ __forceinline__ void init() {}
+    __device__ __forceinline__ float operator()(float t) const { return t; }
+};
+template <>
+struct TargetMap<uint8_t> {
+    float* tab;
+    __device__ __forceinline__ void init()
+    {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) tab[i] = __fdiv_rn((float)i, 255.0f);
+        __syncthreads();
+    }
+    __device__ __forceinline__ float operator()(uint8_t t) const { return tab[t]; }
+};
 
 template <typename TT>
+__device__ __forceinline__ float l1_term(float x, TT t, const TargetMap<TT>& map, float inv, float* g)
+{
+    const float d = x - map(t);
+    *g = d > 0.0f ? inv : (d < 0.0f ? -inv : 0.0f);
+    return fabsf(d);
+}
+
+// With VEC (all three arrays aligned for it), four values per thread (16-byte image and
+// gradient accesses) over the bulk, then a tail; otherwise one value per thread.
+template <typename TT, bool VEC>
 __global__ void __launch_bounds__(256) k_l1(const float* __restrict__ img, const TT* __restrict__ tgt, long long n,
                                             float* loss, float* __restrict__ grad)
 {
     __shared__ float s_w[8];
+    __shared__ float s_tab[256];
+    TargetMap<TT> map;
+    if constexpr (sizeof(TT) == 1) map.tab = s_tab;
+    map.init();
     const float inv = 1.0f / (float)n;
     float acc = 0.0f;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float d = img[i] - target_value(tgt[i]);
-        acc += fabsf(d);
-        grad[i] = d > 0.0f ? inv : (d < 0.0f ? -inv : 0.0f);
+    const long long n4 = VEC ? n / 4 : 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const float4* img4 = reinterpret_cast<const float4*>(img);
+    float4* grad4 = reinterpret_cast<float4*>(grad);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const float4 x = img4[i];
+        TT t[4];
+        if constexpr (sizeof(TT) == 1) {
+            const uchar4 u = reinterpret_cast<const uchar4*>(tgt)[i];
+            t[0] = u.x; t[1] = u.y; t[2] = u.z; t[3] = u.w;
+        } else {
+            const float4 u = reinterpret_cast<const float4*>(tgt)[i];
+            t[0] = u.x; t[1] = u.y; t[2] = u.z; t[3] = u.w;
+        }
+        float4 g;
+        acc += l1_term(x.x, t[0], map, inv, &g.x);
+        acc += l1_term(x.y, t[1], map, inv, &g.y);
+        acc += l1_term(x.z, t[2], map, inv, &g.z);
+        acc += l1_term(x.w, t[3], map, inv, &g.w);
+        grad4[i] = g;
     }
+    for (long long i = 4 * n4 + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        acc += l1_term(img[i], tgt[i], map, inv, &grad[i]);
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
     __syncthreads();
@@ -520,10 +567,12 @@ __global__ void __launch_bounds__(256) k_l1(const float* __restrict__ img, const
 template <typename TT>
 static void l1_launch(const float* img, const TT* tgt, long long n, float* loss, float* grad, int n_sm, cudaStream_t st)
 {
-    long long g = (n + 255) / 256;
+    const bool vec = ((uintptr_t)img % 16 == 0) && ((uintptr_t)grad % 16 == 0) && ((uintptr_t)tgt % (4 * sizeof(TT)) == 0);
+    long long g = ((vec ? n / 4 : n) + 255) / 256;
     if (g > (long long)n_sm * 8) g = (long long)n_sm * 8;
     if (g < 1) g = 1;
-    k_l1<TT><<<(unsigned)g, 256, 0, st>>>(img, tgt, n, loss, grad);
+    if (vec) k_l1<TT, true><<<(unsigned)g, 256, 0, st>>>(img, tgt, n, loss, grad);
+    else k_l1<TT, false><<<(unsigned)g, 256, 0, st>>>(img, tgt, n, loss, grad);
 }
 
 void launch_l1(const float* img, const float* tgt, long long n, float* loss, float* grad, int n_sm, cudaStream_t st)

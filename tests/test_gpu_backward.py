@@ -104,6 +104,14 @@ def test_l1_loss_kernel_with_8bit_target():
     assert abs(loss.item() - oloss) <= 1e-6 * oloss
     np.testing.assert_array_equal(grad.cpu().numpy(), ograd)
     assert ograd[0, 1, 2] == 0.0
+    # unaligned views take the one-value-per-thread path, with the same results
+    big = torch.zeros(img.size + 1, device="cuda")
+    big[1:] = torch.tensor(img.ravel()).cuda()
+    t8b = torch.zeros(t8.size + 1, dtype=torch.uint8, device="cuda")
+    t8b[1:] = torch.tensor(t8.ravel()).cuda()
+    loss2, grad2 = ta.l1_loss(big[1:], t8b[1:])
+    assert abs(loss2.item() - oloss) <= 1e-6 * oloss
+    np.testing.assert_array_equal(grad2.cpu().numpy().reshape(img.shape), ograd)
 
 
 def test_autograd_function_matches_direct_backward():
