@@ -91,6 +91,8 @@ def lib(real="f32"):
         L.orc_partition_order.argtypes = [i64, vp, i32, vp, vp]
         L.orc_hit_counts.argtypes = [i64, vp, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp]
         L.orc_generate_levels.argtypes = [i32, vp, vp, vp, vp, vp, i32, vp, vp, vp]
+        L.orc_ssim.restype = C.c_double
+        L.orc_ssim.argtypes = [i32, i32, i32, vp, vp, vp]
         L.orc_real_bytes.restype = i32
         _LIBS[real] = L
     return _LIBS[real]
@@ -379,3 +381,22 @@ def generate_levels(scene, rates, hits=None):
     h = None if hits is None else np.ascontiguousarray(hits, np.int64)
     lib("f32").orc_generate_levels(nb, _p(off), _p(cnt), _p(mo), _p(sc), _p(h), len(r), _p(r), _p(perm), _p(lc))
     return perm, lc
+
+
+# ---- SSIM (Eq. 3) --------------------------------------------------------------------------
+
+def ssim(a, b, with_map=False):
+    """Mean SSIM of two [C, H, W] images (11x11 Gaussian window, sigma 1.5, zero padding),
+    FP64; with_map also returns the per-pixel map averaged over channels."""
+    A = np.ascontiguousarray(a, np.float32)
+    B = np.ascontiguousarray(b, np.float32)
+    c, h, w = A.shape
+    m = np.zeros((h, w), np.float64) if with_map else None
+    v = lib("f32").orc_ssim(c, w, h, _p(A), _p(B), _p(m))
+    return (v, m) if with_map else v
+
+
+def pose_assign_b1(full, without, eps):
+    """Eq. 3: B1 = 1 where the SSIM loss 1 - SSIM(render with all blocks, render without block
+    j) exceeds eps; `without` is a sequence of renders, one per block."""
+    return np.array([1 - ssim(full, w) > eps for w in without], dtype=bool)

@@ -17,7 +17,7 @@ def lib_path(real):
 
 def build(force=False, extra=()):
     src = os.path.join(HERE, "oracle.c")
-    deps = [src] + [os.path.join(HERE, f) for f in ("oracle_project.inc", "oracle_partition.inc", "oracle_levels.inc")]
+    deps = [src] + [os.path.join(HERE, f) for f in ("oracle_project.inc", "oracle_partition.inc", "oracle_levels.inc", "oracle_ssim.inc")]
     for real, ctype in (("f32", "float"), ("f64", "double")):
         out = lib_path(real)
         if (not force and os.path.exists(out)

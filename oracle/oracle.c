@@ -16,6 +16,7 @@
  *   - Sec. 3.2.2 and Eqs. 2 and 4: foreground normalisation, contraction, the uniform block
  *     grid over the contracted cube, stable grouping by block, the block of a camera pose
  *     (oracle_partition.inc).
+ *   - Eq. 3 (Sec. 3.2.2): the SSIM loss of two renders (oracle_ssim.inc).
  *   - Sec. 3.3.1: nested detail levels per block from a significance ranking (opacity x
  *     volume, optionally weighted by per-pixel hit counts), oracle_levels.inc.
  *   - Eq. 7 (Sec. 3.3.2): MAD block bounds; block frustum test by projecting the corners
@@ -785,5 +786,6 @@ int64_t orc_pointwise_select(int32_t n_blocks, int32_t n_levels, const int64_t* 
 
 #include "oracle_partition.inc"
 #include "oracle_levels.inc"
+#include "oracle_ssim.inc"
 
 int32_t orc_real_bytes(void) { return (int32_t)sizeof(REAL); }
