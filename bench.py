@@ -65,7 +65,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-fp16-compare", action="store_true")
-    ap.add_argument("--workload", default="city1m", choices=["city1m", "lod20m", "lodqueue", "train32", "partition", "levels"])
+    ap.add_argument("--workload", default="city1m", choices=["city1m", "lod20m", "lodqueue", "train32", "partition", "levels", "assign"])
     ap.add_argument("--batched-views", type=int, default=8)
     return ap.parse_args()
 
@@ -949,6 +949,55 @@ def run_levels(args, world):
                                 "frac": g_bytes / (tg * 1e-3) / 1e9 / peaks["hbm_gbs"]}}
 
 
+def run_assign(args, world):
+    """Pose-to-block assignment of Sec. 3.2.2 on the 20M-Gaussian SH-3 unbounded city,
+    partitioned into the 8x8 contracted grid: per pose, B1 (Eq. 3: SSIM loss between the render
+    with every block and the render without block j, threshold 0.05 as Table S3 sets for
+    MatrixCity), B2 (Eq. 4) and B (Eq. 5); aerial poses at 150-400 m, 800x450 renders (one
+    batched frame of 65 views per pose, split into waves)."""
+    import torch
+    from paper_2404_01133_b300 import build as libbuild, cgs, synth
+    from paper_2404_01133_b300 import torch_api as ta
+    libbuild.build()
+    t0 = time.time()
+    sc, box = synth.unbounded_city(20_000_000, seed=3)
+    t_gen = time.time() - t0
+    grid, nb = (8, 8, 1), 64
+    dev = torch.device("cuda")
+    keys = ("mean_opac", "scale", "quat", "sh")
+    src = {k: torch.from_numpy(np.ascontiguousarray(sc[k], np.float32)).to(dev) for k in keys}
+    _, off, perm, _ = ta.partition(src["mean_opac"], box[0], box[1], grid)
+    grouped = {k: ta.gather_rows(src[k], perm) for k in keys}
+    del src
+    o = off.cpu().numpy()
+    gsc = {"sh_degree": sc["sh_degree"], "level_offset": o[:nb, None], "level_count": np.diff(o)[:, None],
+           "block_cell": np.zeros((nb, 4), np.float32)}
+    ds = ta.DeviceScene(gsc, dev, attrs=grouped)
+    pos = synth.aerial_poses(sc["side"], 4 + args.steps, seed=11)
+    cams = [synth.pitched_camera(tuple(p), math.atan2(p[0], -p[1]), math.radians(45.0), 600.0, 600.0, 800, 450)
+            for p in pos]
+    ta.pose_assign(ds, cams[:2], box[0], box[1], grid, 0.05)  # warm-up
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    barrier(world)
+    t1 = time.perf_counter()
+    b1, b2, b, s = ta.pose_assign(ds, cams[4:], box[0], box[1], grid, 0.05)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t1
+    clk = clocks.stop()
+    P = len(cams) - 4
+    return {"metric": "poses assigned to blocks per second (B1 SSIM renders + B2, Eqs. 3-5), 20M SH3, 64 blocks",
+            "value": world * P / max_over_ranks(wall, world), "unit": "poses/s", "n_gpus": world, "steps": P,
+            "higher_is_better": True, "scaling": "weak", "dtype": "f32", "data": "synthetic", "clocks": clk,
+            "timing": "host wall clock around the whole assignment (renders, SSIM, B2), synchronised",
+            "config": {"workload": "unbounded city 20M SH3, 8x8x1 contracted blocks, 800x450 aerial poses, eps 0.05",
+                       "generation_s": t_gen},
+            "ms_per_pose": 1e3 * wall / P, "renders_per_pose": nb + 1,
+            "assigned_blocks_per_pose": {"b1": float(b1.sum().item()) / P, "b2": float(b2.sum().item()) / P,
+                                         "b": float(b.sum().item()) / P}}
+
+
 def run_lodqueue(args, world):
     """64 seeded top-down poses over the 20M-Gaussian LoD city: batched frames (views grouped
     to fit the frame capacity, one CUDA graph) against 64 sequential one-view renders."""
@@ -1096,6 +1145,8 @@ def main():
         out = run_partition(args, world)
     elif args.workload == "levels":
         out = run_levels(args, world)
+    elif args.workload == "assign":
+        out = run_assign(args, world)
     else:
         out = run_ours(args, world, rank, local)
     if rank == 0:

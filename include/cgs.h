@@ -292,6 +292,19 @@ int32_t cgs_generate_levels(const float* d_mean_opac, const void* d_scale, int32
 /* Synchronises the stream; CGS_OK or CGS_ERR_SPIN_TIMEOUT for the last call on d_ws. */
 int32_t cgs_levels_status(const void* d_ws, void* stream);
 
+/* ---- SSIM of renders (Eq. 3, B1 pose assignment) ------------------------------------------
+ * Mean SSIM of n_pairs image pairs ([channels][height][width] FP32 each, planar like the
+ * render output): pair i compares a_i = d_a + i * a_stride (floats; a_stride = 0 compares
+ * every b_i with the same a) and b_i = d_b + i * channels * height * width.  Per channel:
+ * local means, variances and covariance under an 11 x 11 Gaussian window of sigma 1.5
+ * (weights summing to 1, zero outside the image), the SSIM map
+ * ((2 ma mb + C1)(2 sab + C2)) / ((ma^2 + mb^2 + C1)(sa^2 + sb^2 + C2)), C1 = 0.01^2,
+ * C2 = 0.03^2, averaged over every pixel and channel -> d_ssim[i] (written).  d_map (may be
+ * NULL) receives the per-pixel map averaged over channels, [n_pairs][height][width].  The
+ * SSIM loss of Eq. 3 is 1 - d_ssim[i].  Asynchronous; n_pairs <= 65535. */
+int32_t cgs_ssim(const float* d_a, int64_t a_stride, const float* d_b, int32_t n_pairs, int32_t channels,
+                 int32_t width, int32_t height, float* d_ssim, float* d_map, void* stream);
+
 /* ---- Block partition of a scene (Sec. 3.2.2, Eqs. 2 and 4) --------------------------------
  * Positions are rows of `stride` floats with x, y, z first (stride 4 reads the mean_opac rows
  * of a scene directly; stride 3 reads plain xyz).  pmin, pmax (3 floats each) and grid

@@ -18,7 +18,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
           "-I", CSRC, "--expt-relaxed-constexpr"]
 NO_FMA = {"project.cu", "project_bwd.cu", "select.cu", "partition.cu", "levels.cu"}
-SOURCES = ["api.cu", "select.cu", "project.cu", "sort.cu", "render.cu", "project_bwd.cu", "static_ws.cu", "partition.cu", "levels.cu"]
+SOURCES = ["api.cu", "select.cu", "project.cu", "sort.cu", "render.cu", "project_bwd.cu", "static_ws.cu", "partition.cu", "levels.cu", "ssim.cu"]
 
 
 def _nvcc():

@@ -108,6 +108,8 @@ def lib():
         L.cgs_generate_levels.argtypes = [vp, vp, i32, i64, vp, i32, vp, vp, i32, vp, vp, vp, i64, vp]
         L.cgs_levels_status.restype = i32
         L.cgs_levels_status.argtypes = [vp, vp]
+        L.cgs_ssim.restype = i32
+        L.cgs_ssim.argtypes = [vp, i64, vp, i32, i32, i32, i32, vp, vp, vp]
         L.cgs_contract.restype = i32
         L.cgs_contract.argtypes = [vp, i64, i64, vp, vp, vp, vp]
         L.cgs_pose_blocks.restype = i32
@@ -329,3 +331,8 @@ def cgs_generate_levels(d_mean_opac, d_scale, attr_fp16, n, d_block_offset, n_bl
 
 def cgs_levels_status(d_ws, stream=None):
     return lib().cgs_levels_status(_ptr(d_ws), _stream(stream))
+
+
+def cgs_ssim(d_a, a_stride, d_b, n_pairs, channels, width, height, d_ssim, d_map=None, stream=None):
+    return _check(lib().cgs_ssim(_ptr(d_a), a_stride, _ptr(d_b), n_pairs, channels, width, height, _ptr(d_ssim),
+                                 _ptr(d_map), _stream(stream)), "cgs_ssim")

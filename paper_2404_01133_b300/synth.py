@@ -190,8 +190,8 @@ def unbounded_city(n, seed, area_km2=6.0, bg_frac=0.1, sh_degree=3, defer_sh=Fal
     """An unbounded scene for the block partition: the aerial city of ``city_scene`` with a
     fraction ``bg_frac`` of its Gaussians moved to a far background (directions uniform on
     the upper hemisphere, distances log-uniform from 1 to 30 km), as an optimised global
-    prior of a real capture has.  Returns the scene and its foreground box (the city square,
-    z from -10 m to 100 m)."""
+    prior of a real capture has.  Returns the scene and its foreground box: the city square in
+    x and y and, as Table S3 sets it, the minimum and maximum z of all Gaussians."""
     sc = city_scene(n, area_km2, seed, sh_degree=sh_degree, defer_sh=defer_sh)
     rng = np.random.default_rng(seed + 1000)
     nb = int(round(bg_frac * n))
@@ -202,7 +202,8 @@ def unbounded_city(n, seed, area_km2=6.0, bg_frac=0.1, sh_degree=3, defer_sh=Fal
     r = np.exp(rng.uniform(math.log(1000.0), math.log(30000.0), size=(nb, 1)))
     sc["mean_opac"][idx, :3] = (d * r).astype(np.float32)
     h = sc["side"] / 2.0
-    box = (np.array([-h, -h, -10.0], np.float32), np.array([h, h, 100.0], np.float32))
+    z = sc["mean_opac"][:, 2]
+    box = (np.array([-h, -h, z.min()], np.float32), np.array([h, h, z.max()], np.float32))
     return sc, box
 
 

@@ -363,3 +363,61 @@ def scatter_rows(src, rank, n_out, out=None, stream=None):
     row_bytes = src[0].numel() * src.element_size() if src.shape[0] else 4
     _c.cgs_scatter_rows(src, out, row_bytes, rank, src.shape[0], stream)
     return out
+
+
+def ssim(a, b, with_map=False, stream=None):
+    """Mean SSIM of image pairs: a [C, H, W] (compared with every b) or [n, C, H, W], b
+    [n, C, H, W] (float32 device tensors); returns [n] (and the [n, H, W] map)."""
+    if b.dim() == 3:
+        b = b[None]
+    n, c, h, w = b.shape
+    a_stride = 0 if a.dim() == 3 else c * h * w
+    out = torch.empty(n, dtype=torch.float32, device=b.device)
+    m = torch.empty((n, h, w), dtype=torch.float32, device=b.device) if with_map else None
+    _c.cgs_ssim(a.contiguous(), a_stride, b.contiguous(), n, c, w, h, out, m, stream)
+    return (out, m) if with_map else out
+
+
+def pose_assign(dscene, cams, pmin, pmax, grid, eps, tile=16, batch=None):
+    """Pose-to-block assignment of Sec. 3.2.2: B1 (Eq. 3) where the SSIM loss between the render
+    with every block and the render without block j exceeds eps; B2 (Eq. 4) where the camera
+    centre lies in block j after normalisation and contraction; B = B1 + B2 (Eq. 5, read as a
+    logical or).  The scene's blocks are its block table (level 0 of each block); the renders of
+    one pose are one batched frame of n_blocks + 1 views, split into waves that fit the frame
+    capacities.  Returns (B1, B2, B) as [n_poses, n_blocks] bool tensors and the SSIM values."""
+    nb = dscene.n_blocks
+    P = len(cams)
+    W, H = cams[0]["width"], cams[0]["height"]
+    dev = dscene.device
+    cfg = make_config(tile=tile, batch=batch)
+    campos = torch.tensor(np.asarray([c["campos"] for c in cams], np.float32), device=dev)
+    pb = torch.empty(P, dtype=torch.int32, device=dev)
+    _c.cgs_pose_blocks(campos, P, 3, pmin, pmax, grid, pb)
+    b2 = torch.zeros((P, nb), dtype=torch.bool, device=dev)
+    ok = pb >= 0
+    b2[torch.arange(P, device=dev)[ok], pb[ok].long()] = True
+    lv_all = torch.zeros((nb + 1, nb), dtype=torch.int8, device=dev)
+    lv_all[torch.arange(1, nb + 1), torch.arange(nb)] = -1
+    s_all = torch.empty((P, nb), dtype=torch.float32, device=dev)
+    for i, cam in enumerate(cams):
+        sel, ent = frame_counts(dscene, [cam], W, H, tile=tile, levels=lv_all[:1], cfg=cfg)
+        per_sel, per_ent = sel[0], ent[0]
+        full = None
+        # frames of at most ~64M selected Gaussians (a few GB of workspace), at least one view
+        groups = waves([per_sel] * (nb + 1), [per_ent] * (nb + 1), n_cap_max=max(1 << 26, 2 * per_sel + 4096),
+                       k_cap_max=min((1 << 30) - 1, max(1 << 28, 2 * per_ent + 8192)))
+        for views, n_cap, k_cap in groups:
+            views = list(views)
+            fr = Frame(len(views), W, H, tile, nb, n_cap, k_cap, dev)
+            d_cams = cameras_device([cam] * len(views), dev)
+            img, T, nc = render_forward(dscene, fr, cfg, d_cams, None, lv_all[views].contiguous())
+            st, _ = fr.status()
+            if st != _c.CGS_OK:
+                raise _c.CgsError(st, "pose_assign")
+            if views[0] == 0:
+                full = img[0].clone()
+                img, views = img[1:], views[1:]
+            if views:
+                s_all[i, torch.tensor(views, device=dev) - 1] = ssim(full, img)
+    b1 = (1.0 - s_all) > eps
+    return b1, b2, b1 | b2, s_all
