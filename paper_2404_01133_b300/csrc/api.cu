@@ -13,7 +13,6 @@ void launch_lod_levels(const cgs_scene& S, const cgs_config& cfg, const cgs_came
 void launch_block_bounds(const cgs_scene& S, double n_mad, float* aabb, cudaStream_t st);
 void launch_project(const Layout& L, const cgs_scene& S, const cgs_camera* cams, float near_z, int n_sm,
                     cudaStream_t st);
-void launch_colour(const Layout& L, const cgs_scene& S, const cgs_camera* cams, int n_sm, cudaStream_t st);
 int launch_bin(const Layout& L, int n_sm, cudaStream_t st);
 int launch_tile_sort(const Layout& L, int n_sm, cudaStream_t st);
 bool launch_render_fwd(const Layout& L, const cgs_config& c, float* img, float* T, uint32_t* nc, cudaStream_t st);
@@ -265,8 +264,6 @@ static int32_t render_forward(const cgs_scene* scene, const cgs_frame* frame, co
     {
         StageScope s(CGS_STAGE_PROJECT, st);
         launch_project(L, *scene, d_cams, cfg->near_z, n_sm, st);
-        counted(1);
-        launch_colour(L, *scene, d_cams, n_sm, st);
         counted(1);
     }
     {

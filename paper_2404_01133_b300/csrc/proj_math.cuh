@@ -264,6 +264,43 @@ __device__ __forceinline__ int sh_colour(const float m[3], const cgs_camera& c, 
     return clamp;
 }
 
+// sh_colour with the coefficients read from the scene as they are used (three per basis
+// function) instead of staged in registers: the same operations in the same order, so the
+// same colour bit for bit, in far fewer registers.
+template <int DEG>
+__device__ __forceinline__ void sh_colour_streamed(const float m[3], const cgs_camera& c, const cgs_scene& S,
+                                                   long long g, float rgb[3])
+{
+    constexpr int nc = (DEG + 1) * (DEG + 1);
+    const float d0 = m[0] - c.campos[0], d1 = m[1] - c.campos[1], d2 = m[2] - c.campos[2];
+    const float len = sqrtf((d0 * d0 + d1 * d1) + d2 * d2);
+    float Y[16];
+    sh_eval(d0 / len, d1 / len, d2 / len, DEG, Y);
+    float acc[3];
+    if (S.attr_fp16) {
+        const unsigned short* f = reinterpret_cast<const unsigned short*>(S.sh) + g * (long long)(nc * 3);
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) acc[ch] = Y[0] * h2f(__ldg(f + ch));
+#pragma unroll
+        for (int k = 1; k < nc; k++)
+#pragma unroll
+            for (int ch = 0; ch < 3; ch++) acc[ch] = acc[ch] + Y[k] * h2f(__ldg(f + k * 3 + ch));
+    } else {
+        const float* f = S.sh + g * (long long)(nc * 3);
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) acc[ch] = Y[0] * __ldg(f + ch);
+#pragma unroll
+        for (int k = 1; k < nc; k++)
+#pragma unroll
+            for (int ch = 0; ch < 3; ch++) acc[ch] = acc[ch] + Y[k] * __ldg(f + k * 3 + ch);
+    }
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        const float v = acc[ch] + 0.5f;
+        rgb[ch] = v < 0.0f ? 0.0f : v;
+    }
+}
+
 // Maps a flattened selected index j to (view, scene index) through the per-view segment
 // lists built by the selection kernel (binary searches over short prefix arrays).
 __device__ __forceinline__ void locate(const Layout& L, uint32_t j, int* view_out, long long* g_out)

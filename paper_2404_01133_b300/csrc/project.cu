@@ -50,8 +50,9 @@ __device__ __forceinline__ bool surely_off_screen(const float m[3], const float 
 //            test, the cheap off-screen bound; the survivors are queued in shared memory
 //   phase 2  in rounds of one queued Gaussian per thread (dense warps, so the full projection
 //            is not run by warps whose lanes are mostly culled): covariance,
-//            radius, tile rect; for the visible ones the screen-space part of the projected
-//            record, the rect, the (view, depth) sort key and cleared gradient accumulators
+//            radius, tile rect; for the visible ones the projected record (screen-space part
+//            and the view-dependent SH colour, Sec. 3.1, its coefficients read as they are
+//            used), the rect, the (view, depth) sort key and cleared gradient accumulators
 //   phase 3  compaction and duplication: the CTA sums its visible count and tiles touched
 //            (warp ballots and shuffles, then the warp totals in shared memory) and reserves a
 //            range of the visible list and of the entry buffer with one atomic add each;
@@ -61,16 +62,16 @@ __device__ __forceinline__ bool surely_off_screen(const float m[3], const float 
 //            (shuffles), and counts the tile.
 // The order of the visible list and of the entries depends on the order in which CTAs
 // reserve their ranges; nothing downstream depends on it (entries are sorted per tile by
-// (depth, index), colour and backward work per Gaussian).  Colour is evaluated later by
-// k_colour over the visible list.
+// (depth, index), the backward works per Gaussian).  DEG is the scene's SH degree.
 constexpr int PROJ_THREADS = 256;
 constexpr int PROJ_WARPS = PROJ_THREADS / 32;
 constexpr int PROJ_ITEMS = 4;  // selected Gaussians per thread in phase 1
 constexpr int PROJ_STEP = PROJ_THREADS * PROJ_ITEMS;
 constexpr int PROJ_CTAS_PER_SM = 5;  // latency-bound: registers capped so five CTAs fit an SM
 
-__global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM) k_project(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams,
-                                                          float near_z)
+template <int DEG>
+__global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM)
+    k_project(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams, float near_z)
 {
     __shared__ uint32_t s_wv[PROJ_WARPS], s_wt[PROJ_WARPS];
     __shared__ uint32_t s_vbase, s_nq;
@@ -174,6 +175,9 @@ __global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM) k_project(Layo
                         L.tq[j] = tq;
                         L.rec[3 * (size_t)j] = make_float4(p.u, p.v, mo.w, ex);
                         L.rec[3 * (size_t)j + 1] = make_float4(p.conic[0], p.conic[1], p.conic[2], ey);
+                        float rgb[3];
+                        sh_colour_streamed<DEG>(m, c, S, g, rgb);
+                        L.rec[3 * (size_t)j + 2] = make_float4(rgb[0], rgb[1], rgb[2], tq);
                         L.pkey[j] = ((unsigned long long)(uint32_t)v << 32) | __float_as_uint(p.tz);
                         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
                         L.gs[3 * (size_t)j] = z4;
@@ -244,50 +248,20 @@ __global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM) k_project(Layo
     }
 }
 
-// View-dependent colour (SH, Sec. 3.1) of each visible Gaussian, over the compacted visible
-// list so every lane has work.  Writes the third record (r, g, b, t), t the culling
-// threshold on the quadratic form (see cull_extent).  DEG is the scene's SH degree: every
-// loop over coefficients has a fixed trip count, so the coefficients stay in registers.
-template <int DEG>
-__global__ void __launch_bounds__(256) k_colour(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams)
-{
-    const uint32_t n = L.hdr->n_vis;
-    constexpr int deg = DEG;
-    constexpr int nc = (DEG + 1) * (DEG + 1);
-    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-        const uint32_t j = L.vis[r];
-        const int v = (int)(L.pkey[j] >> 32);
-        const long long g = L.gidx[j];
-        const float4 mo = __ldg(reinterpret_cast<const float4*>(S.mean_opac) + g);
-        const float m[3] = {mo.x, mo.y, mo.z};
-        float f[48], rgb[3], dir[3], len, Y[16];
-        if (S.attr_fp16) load_sh_half(S.sh, g, nc, f);
-        else load_sh(S.sh, g, nc, f);
-        sh_colour(m, cams[v], f, deg, rgb, dir, &len, Y);
-        L.rec[3 * (size_t)j + 2] = make_float4(rgb[0], rgb[1], rgb[2], L.tq[j]);
-    }
-}
-
 void launch_project(const Layout& L, const cgs_scene& S, const cgs_camera* cams, float near_z, int n_sm,
                     cudaStream_t st)
 {
     long long want = (L.n_cap + PROJ_STEP - 1) / PROJ_STEP;
     long long grid = want < (long long)n_sm * PROJ_CTAS_PER_SM ? want : (long long)n_sm * PROJ_CTAS_PER_SM;
     if (grid < 1) grid = 1;
-    k_project<<<(unsigned)grid, PROJ_THREADS, 0, st>>>(L, S, cams, near_z);
-}
-
-void launch_colour(const Layout& L, const cgs_scene& S, const cgs_camera* cams, int n_sm, cudaStream_t st)
-{
-    long long want = (L.n_cap + 255) / 256;
-    long long grid = want < (long long)n_sm * 8 ? want : (long long)n_sm * 8;
-    if (grid < 1) grid = 1;
     switch (S.sh_degree) {
-        case 0: k_colour<0><<<(unsigned)grid, 256, 0, st>>>(L, S, cams); break;
-        case 1: k_colour<1><<<(unsigned)grid, 256, 0, st>>>(L, S, cams); break;
-        case 2: k_colour<2><<<(unsigned)grid, 256, 0, st>>>(L, S, cams); break;
-        default: k_colour<3><<<(unsigned)grid, 256, 0, st>>>(L, S, cams); break;
+        case 0: k_project<0><<<(unsigned)grid, PROJ_THREADS, 0, st>>>(L, S, cams, near_z); break;
+        case 1: k_project<1><<<(unsigned)grid, PROJ_THREADS, 0, st>>>(L, S, cams, near_z); break;
+        case 2: k_project<2><<<(unsigned)grid, PROJ_THREADS, 0, st>>>(L, S, cams, near_z); break;
+        default: k_project<3><<<(unsigned)grid, PROJ_THREADS, 0, st>>>(L, S, cams, near_z); break;
     }
 }
+
+
 
 }  // namespace cgs
