@@ -742,11 +742,21 @@ def run_lod20m(args, world):
             sel, ent = ta.frame_counts(ds, [cam], 1920, 1080, levels=lv, cfg=c_)
             fr = ta.Frame(1, 1920, 1080, 16, nb, max(1, int(sel[0] * 1.02) + 1024),
                           min((1 << 30) - 1, int(ent[0] * 1.05) + 65536))
-            ms = _graph_ms(_fwd_runner(ds, fr, c_, d_cam, None, lv), args.steps, flush, world)
+            run = _fwd_runner(ds, fr, c_, d_cam, None, lv)
+            ms = _graph_ms(run, args.steps, flush, world)
             st, c = fr.status()
             t = max_over_ranks(sum(ms) / len(ms), world)
             row[name] = {"fps": 1e3 / t, "ms": t, "selected": c[0], "visible": c[1], "entries": c[2],
                          "status": cgs.cgs_status_string(st)}
+            if name == "lod":
+                # per-stage times of the LoD frame (library events, eager launches)
+                cgs.cgs_timing_enable(True)
+                for _ in range(3):
+                    run()
+                torch.cuda.synchronize()
+                stg = cgs.cgs_timing_read()
+                cgs.cgs_timing_enable(False)
+                row[name]["stage_ms"] = {k: round(v[0] / v[1], 4) for k, v in stg.items() if v[1]}
             del fr
         rows.append(row)
     mean = lambda k: float(np.mean([r[k]["fps"] for r in rows]))

@@ -264,35 +264,63 @@ __device__ __forceinline__ int sh_colour(const float m[3], const cgs_camera& c, 
     return clamp;
 }
 
-// sh_colour with the coefficients read from the scene as they are used (three per basis
-// function) instead of staged in registers: the same operations in the same order, so the
-// same colour bit for bit, in far fewer registers.
+// sh_colour with the coefficients read from the scene in chunks of four basis functions (12
+// values, three 16-byte loads issued together) instead of staged all at once in registers:
+// the same operations in the same order, so the same colour bit for bit, in far fewer
+// registers, with one memory latency per chunk rather than per coefficient.
 template <int DEG>
 __device__ __forceinline__ void sh_colour_streamed(const float m[3], const cgs_camera& c, const cgs_scene& S,
                                                    long long g, float rgb[3])
 {
     constexpr int nc = (DEG + 1) * (DEG + 1);
+    constexpr int nchunk = (nc + 3) / 4;
     const float d0 = m[0] - c.campos[0], d1 = m[1] - c.campos[1], d2 = m[2] - c.campos[2];
     const float len = sqrtf((d0 * d0 + d1 * d1) + d2 * d2);
     float Y[16];
     sh_eval(d0 / len, d1 / len, d2 / len, DEG, Y);
-    float acc[3];
-    if (S.attr_fp16) {
-        const unsigned short* f = reinterpret_cast<const unsigned short*>(S.sh) + g * (long long)(nc * 3);
+    float acc[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-        for (int ch = 0; ch < 3; ch++) acc[ch] = Y[0] * h2f(__ldg(f + ch));
+    for (int ck = 0; ck < nchunk; ck++) {
+        float f[12];
+        constexpr int per = 12;
+        const int k0 = 4 * ck;
+        const int cnt = (nc - k0) < 4 ? 3 * (nc - k0) : per;  // values in this chunk
+        if (S.attr_fp16) {
+            const unsigned short* src = reinterpret_cast<const unsigned short*>(S.sh) + g * (long long)(nc * 3) + 3 * k0;
+            if (nc == 16) {
+                const uint2* s2 = reinterpret_cast<const uint2*>(src);  // 24-byte aligned rows: 8-byte loads
+                const uint2 u0 = __ldg(s2), u1 = __ldg(s2 + 1), u2 = __ldg(s2 + 2);
+                const uint32_t w[6] = {u0.x, u0.y, u1.x, u1.y, u2.x, u2.y};
 #pragma unroll
-        for (int k = 1; k < nc; k++)
+                for (int i = 0; i < 6; i++) {
+                    f[2 * i] = h2f(w[i] & 0xffffu);
+                    f[2 * i + 1] = h2f(w[i] >> 16);
+                }
+            } else {
 #pragma unroll
-            for (int ch = 0; ch < 3; ch++) acc[ch] = acc[ch] + Y[k] * h2f(__ldg(f + k * 3 + ch));
-    } else {
-        const float* f = S.sh + g * (long long)(nc * 3);
+                for (int i = 0; i < per; i++) f[i] = i < cnt ? h2f(__ldg(src + i)) : 0.0f;
+            }
+        } else {
+            const float* src = S.sh + g * (long long)(nc * 3) + 3 * k0;
+            if (nc == 16 || nc == 4) {
+                const float4* s4 = reinterpret_cast<const float4*>(src);
+                const float4 a = __ldg(s4), b = __ldg(s4 + 1), cc = __ldg(s4 + 2);
+                f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
+                f[4] = b.x; f[5] = b.y; f[6] = b.z; f[7] = b.w;
+                f[8] = cc.x; f[9] = cc.y; f[10] = cc.z; f[11] = cc.w;
+            } else {
 #pragma unroll
-        for (int ch = 0; ch < 3; ch++) acc[ch] = Y[0] * __ldg(f + ch);
+                for (int i = 0; i < per; i++) f[i] = i < cnt ? __ldg(src + i) : 0.0f;
+            }
+        }
 #pragma unroll
-        for (int k = 1; k < nc; k++)
+        for (int kk = 0; kk < 4; kk++) {
+            const int k = k0 + kk;
+            if (k >= nc) break;
 #pragma unroll
-            for (int ch = 0; ch < 3; ch++) acc[ch] = acc[ch] + Y[k] * __ldg(f + k * 3 + ch);
+            for (int ch = 0; ch < 3; ch++)
+                acc[ch] = k == 0 ? Y[0] * f[ch] : acc[ch] + Y[k] * f[3 * kk + ch];
+        }
     }
 #pragma unroll
     for (int ch = 0; ch < 3; ch++) {
