@@ -8,7 +8,8 @@
 //   tile sort     one CTA per tile: up to 256 keys ranked against each other in shared
 //                 memory (each key's count of smaller keys is its slot), up to 2048 keys
 //                 bitonic-sorted in shared memory; longer tiles are sorted by one CTA of a
-//                 second kernel (sorted chunks + merge rounds through global scratch)
+//                 second kernel (bitonic in shared memory up to 4096 keys, beyond that
+//                 sorted chunks + merge rounds through global scratch)
 //
 // Within a view, a Gaussian appears at most once per tile, so the 64-bit keys of one tile are
 // distinct: the sorted order is exactly (depth, index) whatever order the projection emitted
@@ -44,8 +45,9 @@ __global__ void __launch_bounds__(256) k_scatter(Layout L)
     }
 }
 
-constexpr int TS_THREADS = 128;
-constexpr int TS_CAP = 2048;  // keys per tile sorted entirely in shared memory
+constexpr int TS_THREADS = 256;
+constexpr int TS_CAP = 2048;  // keys per tile sorted entirely in shared memory by k_tile_sort
+constexpr int LT_CAP = 4096;  // keys per chunk of the long-tile kernel
 
 // In-place ascending bitonic sort of s[0, np) (np a power of two) by the threads of a CTA.
 __device__ __forceinline__ void bitonic_smem(unsigned long long* s, int np)
@@ -65,11 +67,11 @@ __device__ __forceinline__ void bitonic_smem(unsigned long long* s, int np)
     __syncthreads();
 }
 
-constexpr int RANK_MAX = 2 * TS_THREADS;  // keys per tile sorted by ranking
+constexpr int RANK_MAX = TS_THREADS;  // keys per tile sorted by ranking
 
-// One CTA per (view, tile).  Up to RANK_MAX keys: every thread ranks up to two keys against
-// all keys of the tile in shared memory (keys are distinct, so the rank is the output slot);
-// up to TS_CAP keys: bitonic sort in shared memory; longer tiles are listed for the merge
+// One CTA per (view, tile).  Up to RANK_MAX keys: every thread ranks one key against all keys
+// of the tile in shared memory (keys are distinct, so the rank is the output slot); up to
+// TS_CAP keys: bitonic sort in shared memory; longer tiles are listed for the long-tile
 // kernel.
 __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(Layout L)
 {
@@ -82,30 +84,16 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(Layout L)
         return;
     }
     if (n <= (uint32_t)RANK_MAX) {
-        for (uint32_t i = threadIdx.x; i < n; i += TS_THREADS) s[i] = L.ekey[st + i];
+        const uint32_t i = threadIdx.x;
+        const unsigned long long key = i < n ? L.ekey[st + i] : ~0ull;
+        if (i < n) s[i] = key;
         __syncthreads();
-        const uint32_t i0 = threadIdx.x, i1 = threadIdx.x + TS_THREADS;
-        const unsigned long long k0 = i0 < n ? s[i0] : ~0ull, k1 = i1 < n ? s[i1] : ~0ull;
-        uint32_t r0 = 0, r1 = 0;
-        if (i0 < n) {
-            if (i1 < n) {
-                for (uint32_t m = 0; m < n; m++) {
-                    const unsigned long long x = s[m];
-                    r0 += x < k0;
-                    r1 += x < k1;
-                }
-            } else {
+        if (i < n) {
+            uint32_t r = 0;
 #pragma unroll 4
-                for (uint32_t m = 0; m < n; m++) r0 += s[m] < k0;
-            }
-        }
-        if (i0 < n) {
-            L.tval[st + r0] = (uint32_t)k0;
-            L.tkey[st + r0] = t;
-        }
-        if (i1 < n) {
-            L.tval[st + r1] = (uint32_t)k1;
-            L.tkey[st + r1] = t;
+            for (uint32_t m = 0; m < n; m++) r += s[m] < key;
+            L.tval[st + r] = (uint32_t)key;
+            L.tkey[st + r] = t;
         }
         return;
     }
@@ -120,13 +108,14 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(Layout L)
 }
 
 // Tiles longer than TS_CAP: one CTA per tile (persistent over the device list) sorts chunks
-// of TS_CAP keys in shared memory, then merges runs pairwise through global scratch (the
-// entry buffer, free after the scatter).  With distinct keys, an element's output position
-// is its rank in its own run plus the number of smaller keys in the other run.
+// of LT_CAP keys in shared memory (the whole tile when it fits), then merges runs pairwise
+// through global scratch (the entry buffer, free after the scatter).  With distinct keys, an
+// element's output position is its rank in its own run plus the number of smaller keys in
+// the other run.
 constexpr int TB_THREADS = 512;
 __global__ void __launch_bounds__(TB_THREADS) k_tile_sort_large(Layout L)
 {
-    __shared__ unsigned long long s[TS_CAP];
+    __shared__ unsigned long long s[LT_CAP];
     __shared__ uint32_t s_item;
     const uint32_t nbig = L.hdr->n_big;
     while (true) {
@@ -139,8 +128,8 @@ __global__ void __launch_bounds__(TB_THREADS) k_tile_sort_large(Layout L)
         const uint32_t st = L.ranges[2 * (size_t)t], n = L.ranges[2 * (size_t)t + 1] - st;
         unsigned long long* a = L.ekey + st;
         unsigned long long* b = L.eraw + st;
-        for (uint32_t c0 = 0; c0 < n; c0 += TS_CAP) {
-            const int m = (int)min((uint32_t)TS_CAP, n - c0);
+        for (uint32_t c0 = 0; c0 < n; c0 += LT_CAP) {
+            const int m = (int)min((uint32_t)LT_CAP, n - c0);
             int np = 2;
             while (np < m) np <<= 1;
             for (int i = threadIdx.x; i < np; i += blockDim.x) s[i] = i < m ? a[c0 + i] : ~0ull;
@@ -148,7 +137,7 @@ __global__ void __launch_bounds__(TB_THREADS) k_tile_sort_large(Layout L)
             for (int i = threadIdx.x; i < m; i += blockDim.x) a[c0 + i] = s[i];
             __syncthreads();
         }
-        for (uint32_t width = TS_CAP; width < n; width <<= 1) {
+        for (uint32_t width = LT_CAP; width < n; width <<= 1) {
             for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
                 const uint32_t base = i - i % (2 * width);
                 const bool in_first = (i - base) < width;
@@ -200,7 +189,7 @@ int launch_tile_sort(const Layout& L, int n_sm, cudaStream_t st)
 {
     const long long vt = (long long)L.V * L.T;
     k_tile_sort<<<(unsigned)vt, TS_THREADS, 0, st>>>(L);
-    k_tile_sort_large<<<(unsigned)n_sm, TB_THREADS, 0, st>>>(L);
+    k_tile_sort_large<<<(unsigned)(4 * n_sm), TB_THREADS, 0, st>>>(L);  // four 512-thread CTAs fit an SM
     return 2;
 }
 
