@@ -28,7 +28,7 @@ struct Header {
     unsigned long long steps_fwd;     // forward (warp, entry) steps visited
     unsigned long long steps_useful;  // of those, steps where an entry blended into a warp pixel
     uint32_t spin_giveups;
-    uint32_t n_big;        // tiles too long for the shared-memory sort
+    uint32_t n_big;        // tiles too long for the ranking sort
     uint32_t ctr[N_CTR];
 };
 

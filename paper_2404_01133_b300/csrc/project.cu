@@ -55,11 +55,11 @@ __device__ __forceinline__ bool surely_off_screen(const float m[3], const float 
 //            used), the rect, the (view, depth) sort key and cleared gradient accumulators
 //   phase 3  compaction and duplication: the CTA sums its visible count and tiles touched
 //            (warp ballots and shuffles, then the warp totals in shared memory) and reserves a
-//            range of the visible list and of the entry buffer with one atomic add each;
-//            every warp emits the (tile << 32 | j) entries of its visible Gaussians
-//            cooperatively: lane l takes entries l, l + 32, ... of the warp's range, finds
-//            the owning lane by a binary search over the lanes' exclusive prefixes
-//            (shuffles), and counts the tile.
+//            range of the visible list and of the entry buffer with one atomic add each; the
+//            whole CTA then emits the round's (tile << 32 | j) entries: thread t takes entries
+//            t, t + 256, ..., finds the owning Gaussian by a binary search over the round's
+//            exclusive offsets in shared memory, and counts the tile.  A round of large
+//            Gaussians (hundreds of tiles each, near the camera) is spread over all warps.
 // The order of the visible list and of the entries depends on the order in which CTAs
 // reserve their ranges; nothing downstream depends on it (entries are sorted per tile by
 // (depth, index), the backward works per Gaussian).  DEG is the scene's SH degree.
@@ -74,7 +74,9 @@ __global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM)
     k_project(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams, float near_z)
 {
     __shared__ uint32_t s_wv[PROJ_WARPS], s_wt[PROJ_WARPS];
-    __shared__ uint32_t s_vbase, s_nq;
+    __shared__ uint32_t s_vbase, s_nq, s_rtot;
+    __shared__ uint32_t s_ex[PROJ_THREADS], s_ej[PROJ_THREADS], s_rx[PROJ_THREADS], s_ry[PROJ_THREADS];
+    __shared__ int s_ev[PROJ_THREADS];
     __shared__ unsigned long long s_ebase;
     __shared__ uint32_t s_qj[PROJ_STEP];
     __shared__ int s_qv[PROJ_STEP];
@@ -190,7 +192,7 @@ __global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM)
             // phase 3: warp totals, visible count (ballot) and tiles touched (inclusive shuffle scan)
             const uint32_t vb = __ballot_sync(0xffffffffu, tt > 0);
             uint32_t inc = tt;
-    #pragma unroll
+#pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
                 if (lane >= o) inc += y;
@@ -214,32 +216,35 @@ __global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM)
                 }
                 s_vbase = nv ? atomicAdd(&L.hdr->n_vis, nv) : 0u;
                 s_ebase = ne ? atomicAdd(&L.hdr->k_total, ne) : 0ull;
+                s_rtot = (uint32_t)ne;
                 if (ne && s_ebase + ne > cap) latch(L.hdr, ST_CAPACITY);
             }
             __syncthreads();
             if (tt > 0) L.vis[s_vbase + s_wv[warp] + __popc(vb & lt)] = j;
-            // cooperative duplication of the warp's entries
-            const unsigned long long e0 = s_ebase + s_wt[warp];
-            for (uint32_t it = 0; it * 32u < wtot; it++) {
-                const uint32_t idx = it * 32u + (uint32_t)lane;
-                // owner: the last lane o with excl(o) <= idx (lanes with tt = 0 share their
-                // successor's prefix and are never the last such lane)
+            // the round's entries, emitted by the whole CTA: each thread's Gaussian in shared
+            // memory with its exclusive entry offset in the round
+            s_ex[threadIdx.x] = s_wt[warp] + excl;
+            s_ej[threadIdx.x] = j;
+            s_ev[threadIdx.x] = v;
+            s_rx[threadIdx.x] = rx;
+            s_ry[threadIdx.x] = ry;
+            __syncthreads();
+            const uint32_t rtot = s_rtot;
+            for (uint32_t idx = threadIdx.x; idx < rtot; idx += PROJ_THREADS) {
+                // owner: the last slot o with s_ex[o] <= idx (a slot with no entries shares its
+                // successor's offset and is never the last such slot)
                 int o = 0;
-    #pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const uint32_t eo = __shfl_sync(0xffffffffu, excl, o + step);
-                    if (eo <= idx) o += step;
-                }
-                const uint32_t oj = __shfl_sync(0xffffffffu, j, o);
-                const uint32_t orx = __shfl_sync(0xffffffffu, rx, o), ory = __shfl_sync(0xffffffffu, ry, o);
-                const uint32_t oex = __shfl_sync(0xffffffffu, excl, o);
-                const int ov = __shfl_sync(0xffffffffu, v, o);
-                const unsigned long long k = e0 + idx;
-                if (idx < wtot && k < cap) {
+#pragma unroll
+                for (int step = PROJ_THREADS / 2; step >= 1; step >>= 1)
+                    if (s_ex[o + step] <= idx) o += step;
+                const unsigned long long k = s_ebase + idx;
+                if (k < cap) {
+                    const uint32_t orx = s_rx[o], ory = s_ry[o];
                     const uint32_t tx0 = orx & 0xffffu, ty0 = orx >> 16, w = (ory & 0xffffu) - tx0;
-                    const uint32_t local = idx - oex;
-                    const uint32_t t = (uint32_t)ov * (uint32_t)L.T + (ty0 + local / w) * (uint32_t)L.tiles_x + (tx0 + local % w);
-                    L.eraw[k] = ((unsigned long long)t << 32) | oj;
+                    const uint32_t local = idx - s_ex[o];
+                    const uint32_t t = (uint32_t)s_ev[o] * (uint32_t)L.T + (ty0 + local / w) * (uint32_t)L.tiles_x +
+                                       (tx0 + local % w);
+                    L.eraw[k] = ((unsigned long long)t << 32) | s_ej[o];
                     atomicAdd(&L.tcnt[t], 1u);
                 }
             }

@@ -6,10 +6,11 @@
 //   scatter       one thread per entry: a slot in its tile's range (atomic cursor), key
 //                 (FP32 depth bits << 32 | selected index)
 //   tile sort     one CTA per tile: up to 256 keys ranked against each other in shared
-//                 memory (each key's count of smaller keys is its slot), up to 2048 keys
-//                 bitonic-sorted in shared memory; longer tiles are sorted by one CTA of a
-//                 second kernel (bitonic in shared memory up to 4096 keys, beyond that
-//                 sorted chunks + merge rounds through global scratch)
+//                 memory (each key's count of smaller keys is its slot); longer tiles go to a
+//                 second kernel: up to 2048 keys a bitonic sort held in registers (shuffles
+//                 within warps, shared memory only for the strides that cross warps), up to
+//                 4096 a bitonic sort in shared memory, beyond that sorted chunks + merge
+//                 rounds through global scratch
 //
 // Within a view, a Gaussian appears at most once per tile, so the 64-bit keys of one tile are
 // distinct: the sorted order is exactly (depth, index) whatever order the projection emitted
@@ -46,7 +47,7 @@ __global__ void __launch_bounds__(256) k_scatter(Layout L)
 }
 
 constexpr int TS_THREADS = 256;
-constexpr int TS_CAP = 2048;  // keys per tile sorted entirely in shared memory by k_tile_sort
+constexpr int TS_CAP = 2048;  // keys per tile sorted in registers by the long-tile kernel
 constexpr int LT_CAP = 4096;  // keys per chunk of the long-tile kernel
 
 // In-place ascending bitonic sort of s[0, np) (np a power of two) by the threads of a CTA.
@@ -67,23 +68,103 @@ __device__ __forceinline__ void bitonic_smem(unsigned long long* s, int np)
     __syncthreads();
 }
 
+// Ascending bitonic sort of np = THREADS * E keys held by the CTA in registers: warp w
+// holds keys [32 E w, 32 E (w + 1)), lane l's x[e] being key 32 E w + 32 e + l.  Exchanges
+// between lanes of a warp are shuffles, between a lane's own registers are moves; only the
+// strides that cross warps go through shared memory (a store, one synchronised pass per
+// stride, a load), so a sort of 2048 keys takes 6 shared-memory passes instead of 66.
+template <int THREADS, int E>
+__device__ __forceinline__ void cta_bitonic(unsigned long long (&x)[E], unsigned long long* s)
+{
+    constexpr int NP = THREADS * E, WS = 32 * E;
+    const int lane = threadIdx.x & 31;
+    const int base = (threadIdx.x >> 5) * WS;
+#pragma unroll
+    for (int size = 2; size <= NP; size <<= 1) {
+        int stride = size >> 1;
+        if (stride >= WS) {
+#pragma unroll
+            for (int e = 0; e < E; e++) s[base + 32 * e + lane] = x[e];
+            __syncthreads();
+            for (; stride >= WS; stride >>= 1) {
+                for (int i = threadIdx.x; i < NP / 2; i += THREADS) {
+                    const int lo = 2 * i - (i & (stride - 1));
+                    const int hi = lo + stride;
+                    const bool up = (lo & size) == 0;
+                    const unsigned long long a = s[lo], b = s[hi];
+                    if ((a > b) == up) { s[lo] = b; s[hi] = a; }
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int e = 0; e < E; e++) x[e] = s[base + 32 * e + lane];
+            __syncthreads();
+        }
+#pragma unroll
+        for (int d = WS / 2; d > 0; d >>= 1) {
+            if (d > stride) continue;
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                const bool up = ((base + 32 * e + lane) & size) == 0;
+                if (d >= 32) {
+                    const int pe = e ^ (d >> 5);
+                    if (pe > e) {
+                        const unsigned long long a = x[e], b = x[pe];
+                        const bool sw = (a > b) == up;
+                        x[e] = sw ? b : a;
+                        x[pe] = sw ? a : b;
+                    }
+                } else {
+                    const unsigned long long y = __shfl_xor_sync(0xffffffffu, x[e], d);
+                    const unsigned long long mn = x[e] < y ? x[e] : y, mx = x[e] < y ? y : x[e];
+                    x[e] = (((lane & d) == 0) == up) ? mn : mx;
+                }
+            }
+        }
+    }
+}
+
+template <int THREADS, int E>
+__device__ __forceinline__ void tile_sort_regs(const Layout& L, unsigned long long* s, uint32_t t, uint32_t st,
+                                               uint32_t n)
+{
+    constexpr int WS = 32 * E;
+    const int lane = threadIdx.x & 31;
+    const int base = (threadIdx.x >> 5) * WS;
+    unsigned long long x[E];
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+        const uint32_t i = (uint32_t)(base + 32 * e + lane);
+        x[e] = i < n ? L.ekey[st + i] : ~0ull;
+    }
+    cta_bitonic<THREADS, E>(x, s);
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+        const uint32_t i = (uint32_t)(base + 32 * e + lane);
+        if (i < n) {
+            L.tval[st + i] = (uint32_t)x[e];
+            L.tkey[st + i] = t;
+        }
+    }
+}
+
 constexpr int RANK_MAX = TS_THREADS;  // keys per tile sorted by ranking
 
 // One CTA per (view, tile).  Up to RANK_MAX keys: every thread ranks one key against all keys
-// of the tile in shared memory (keys are distinct, so the rank is the output slot); up to
-// TS_CAP keys: bitonic sort in shared memory; longer tiles are listed for the long-tile
-// kernel.
+// of the tile in shared memory (keys are distinct, so the rank is the output slot); longer
+// tiles are listed for the long-tile kernel, kept apart so the common short tiles run at full
+// occupancy.
 __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(Layout L)
 {
-    __shared__ unsigned long long s[TS_CAP];
+    __shared__ unsigned long long s[RANK_MAX];
     const uint32_t t = blockIdx.x;
     const uint32_t st = L.ranges[2 * (size_t)t], n = L.ranges[2 * (size_t)t + 1] - st;
     if (n == 0) return;
-    if (n > (uint32_t)TS_CAP) {
+    if (n > (uint32_t)RANK_MAX) {
         if (threadIdx.x == 0) L.big[atomicAdd(&L.hdr->n_big, 1u)] = t;
         return;
     }
-    if (n <= (uint32_t)RANK_MAX) {
+    {
         const uint32_t i = threadIdx.x;
         const unsigned long long key = i < n ? L.ekey[st + i] : ~0ull;
         if (i < n) s[i] = key;
@@ -95,23 +176,15 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(Layout L)
             L.tval[st + r] = (uint32_t)key;
             L.tkey[st + r] = t;
         }
-        return;
-    }
-    int np = 2;
-    while (np < (int)n) np <<= 1;
-    for (int i = threadIdx.x; i < np; i += blockDim.x) s[i] = i < (int)n ? L.ekey[st + i] : ~0ull;
-    bitonic_smem(s, np);
-    for (int i = threadIdx.x; i < (int)n; i += blockDim.x) {
-        L.tval[st + i] = (uint32_t)s[i];
-        L.tkey[st + i] = t;
     }
 }
 
-// Tiles longer than TS_CAP: one CTA per tile (persistent over the device list) sorts chunks
-// of LT_CAP keys in shared memory (the whole tile when it fits), then merges runs pairwise
-// through global scratch (the entry buffer, free after the scatter).  With distinct keys, an
-// element's output position is its rank in its own run plus the number of smaller keys in
-// the other run.
+// Tiles longer than RANK_MAX: one CTA per listed tile (persistent over the device list).  Up
+// to TS_CAP keys: bitonic sort held in registers (cta_bitonic).  Longer: chunks of LT_CAP keys
+// sorted in shared memory (the whole tile when it fits), then runs merged pairwise through
+// global scratch (the entry buffer, free after the scatter); with distinct keys, an element's
+// output position is its rank in its own run plus the number of smaller keys in the other
+// run.
 constexpr int TB_THREADS = 512;
 __global__ void __launch_bounds__(TB_THREADS) k_tile_sort_large(Layout L)
 {
@@ -126,6 +199,13 @@ __global__ void __launch_bounds__(TB_THREADS) k_tile_sort_large(Layout L)
         if (item >= nbig) break;
         const uint32_t t = L.big[item];
         const uint32_t st = L.ranges[2 * (size_t)t], n = L.ranges[2 * (size_t)t + 1] - st;
+        if (n <= (uint32_t)TS_CAP) {
+            if (n <= (uint32_t)TB_THREADS) tile_sort_regs<TB_THREADS, 1>(L, s, t, st, n);
+            else if (n <= 2u * TB_THREADS) tile_sort_regs<TB_THREADS, 2>(L, s, t, st, n);
+            else tile_sort_regs<TB_THREADS, 4>(L, s, t, st, n);
+            __syncthreads();
+            continue;
+        }
         unsigned long long* a = L.ekey + st;
         unsigned long long* b = L.eraw + st;
         for (uint32_t c0 = 0; c0 < n; c0 += LT_CAP) {
@@ -189,7 +269,7 @@ int launch_tile_sort(const Layout& L, int n_sm, cudaStream_t st)
 {
     const long long vt = (long long)L.V * L.T;
     k_tile_sort<<<(unsigned)vt, TS_THREADS, 0, st>>>(L);
-    k_tile_sort_large<<<(unsigned)(4 * n_sm), TB_THREADS, 0, st>>>(L);  // four 512-thread CTAs fit an SM
+    k_tile_sort_large<<<(unsigned)(3 * n_sm), TB_THREADS, 0, st>>>(L);  // three 512-thread CTAs fit an SM
     return 2;
 }
 
