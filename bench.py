@@ -49,8 +49,8 @@ FP32_OPS_PER_CONTRIB_PAIR_BWD = 45
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels on this
 # workload (profiles/k_render_city1m.md).  A kernel absent here reports traffic null; an entry
 # must be removed when its kernel changes.
-NCU_TRAFFIC_BYTES = {"render": 14.714624e6 + 0.716544e6, "render_bwd": 65.620224e6 + 1.495808e6,
-                     "project_bwd": 104.624896e6 + 8.114688e6, "loss": 31.121152e6 + 0.040960e6}
+NCU_TRAFFIC_BYTES = {"render": 14.701568e6 + 0.719360e6, "render_bwd": 65.589760e6 + 1.506560e6,
+                     "project_bwd": 69.176064e6 + 3.756288e6, "loss": 31.120896e6 + 0.033024e6}
 
 
 def parse_args():
@@ -67,6 +67,8 @@ def parse_args():
     ap.add_argument("--no-fp16-compare", action="store_true")
     ap.add_argument("--workload", default="city1m", choices=["city1m", "lod20m", "lodqueue", "train32", "partition", "levels", "assign"])
     ap.add_argument("--batched-views", type=int, default=8)
+    ap.add_argument("--lod-n", type=int, default=20_000_000, help="Gaussians of the LoD city (lod20m)")
+    ap.add_argument("--lod-heights", default="50,200,500,1000,2000", help="camera heights in m (lod20m)")
     return ap.parse_args()
 
 
@@ -206,8 +208,14 @@ def run_ours(args, world, rank, local):
 
     # autotuner: tile size and batch depth for this workload, timed on the real step
     tune = None
+    f32 = torch.float32
+    tune_rows = (torch.empty((n, 4), dtype=f32, device=dev), torch.empty((n, 4), dtype=f32, device=dev),
+                 torch.empty((n, 4), dtype=f32, device=dev),
+                 torch.empty((n,) + tuple(ds.sh.shape[1:]), dtype=f32, device=dev),
+                 torch.empty(n, dtype=torch.int64, device=dev))
     if args.tile == 0:
         tframes = {}
+        l_ = torch.zeros(1, device=dev)
 
         def run_candidate(tile, batch):
             if tile not in tframes:
@@ -215,12 +223,10 @@ def run_ours(args, world, rank, local):
                 tframes[tile] = (f_, f_.outputs(), torch.empty((1, 3, H, W), device=dev))
             f_, (i_, T_, n_), dl_ = tframes[tile]
             c_ = ta.make_config(tile=tile, batch=batch)
-            gz = (torch.zeros_like(ds.mean_opac), torch.zeros_like(ds.scale), torch.zeros_like(ds.quat),
-                  torch.zeros_like(ds.sh))
-            l_ = torch.zeros(1, device=dev)
             cgs.cgs_render_forward(ds.struct(), f_.struct, c_, d_cams, None, None, i_, T_, n_)
+            l_.zero_()
             cgs.cgs_l1_loss_u8(i_, tgt, i_.numel(), l_, dl_)
-            cgs.cgs_render_backward(ds.struct(), f_.struct, c_, d_cams, dl_, T_, n_, *gz)
+            ta.render_backward_packed(ds, f_, c_, d_cams, dl_, T_, n_, rows=tune_rows)
 
         best, tune_ms = ta.autotune(run_candidate, ta.TUNE_CANDIDATES, reps=3)
         tune = {"choice": f"{best[0]}x{best[1]}", "ms": tune_ms}
@@ -244,18 +250,22 @@ def run_ours(args, world, rank, local):
         off += gbuf.numel()
     grads = tuple(views)
     loss = grad_flat[off:off + 1]
+    # the step's gradients: one packed row per visible Gaussian (cgs_render_backward_packed),
+    # written in full every step, so nothing is cleared outside the timed region
+    rows = tune_rows
 
     def zero_accumulators():
-        # gradient buffers are accumulated into (+=); a training loop clears them when it
-        # applies the optimizer -- one memset, outside the timed step
-        grad_flat.zero_()
+        # nothing outside the step: the loss accumulator is cleared inside it, the packed
+        # gradient rows are overwritten
+        pass
 
     def step_with(tgt_buf, cam_buf):
         # the same step reading the target image and the camera from the given device buffers
         cur = torch.cuda.current_stream().cuda_stream
         cgs.cgs_render_forward(s_struct, frame.struct, cfg, cam_buf, None, None, img, T, nc, cur)
+        loss.zero_()
         cgs.cgs_l1_loss_u8(img, tgt_buf, img.numel(), loss, dL, cur)
-        cgs.cgs_render_backward(s_struct, frame.struct, cfg, cam_buf, dL, T, nc, *grads, cur)
+        cgs.cgs_render_backward_packed(s_struct, frame.struct, cfg, cam_buf, dL, T, nc, *rows, cur)
 
     def step(fwd_only=False):
         # the current stream at call time (the capture stream while a CUDA graph is recorded)
@@ -263,6 +273,16 @@ def run_ours(args, world, rank, local):
         cgs.cgs_render_forward(s_struct, frame.struct, cfg, d_cams, None, None, img, T, nc, cur)
         if fwd_only:
             return
+        loss.zero_()
+        cgs.cgs_l1_loss_u8(img, tgt, img.numel(), loss, dL, cur)
+        cgs.cgs_render_backward_packed(s_struct, frame.struct, cfg, d_cams, dL, T, nc, *rows, cur)
+
+    def step_dense():
+        # the scene-indexed form: gradients added into arrays laid out like the scene, which
+        # the step clears first (236 MB)
+        cur = torch.cuda.current_stream().cuda_stream
+        grad_flat.zero_()
+        cgs.cgs_render_forward(s_struct, frame.struct, cfg, d_cams, None, None, img, T, nc, cur)
         cgs.cgs_l1_loss_u8(img, tgt, img.numel(), loss, dL, cur)
         cgs.cgs_render_backward(s_struct, frame.struct, cfg, d_cams, dL, T, nc, *grads, cur)
 
@@ -323,6 +343,10 @@ def run_ours(args, world, rank, local):
         ms, launches, _ = timed(args.steps)
     clk = clocks.stop()
     ms_fwd, _, stages_fwd = timed(args.steps, fwd_only=True, with_stages=True)
+    # the scene-indexed gradient form, its arrays cleared inside the step
+    g_dense = ta.capture(step_dense, warmup=1)
+    ms_dense, _ = timed_fn(g_dense.replay, max(3, args.steps // 2), st, flush, world)
+    del g_dense
     step()  # one full step so the frame's counters hold both the forward and the backward
     status, counts = frame.status()
     if status != cgs.CGS_OK:
@@ -355,7 +379,12 @@ def run_ours(args, world, rank, local):
         # algorithmic FP32 operations per launch (issue-bound stages)
         "render": ("alu", pairs_f * FP32_OPS_PER_EVAL_PAIR_FWD),
         "render_bwd": ("alu", pairs_f * FP32_OPS_PER_EVAL_PAIR_BWD),
-        "project_bwd": ("hbm", n_vis * (16 * 3 + 12 * nc_coef + 48 + 4 * 4 * 3 + 12 * nc_coef)),
+        # projection backward, per visible Gaussian: read the visible-list slot, key, scene
+        # index, screen-space gradients, mean+opacity, scale, rotation and SH; write the packed
+        # gradient row (mean+opacity, scale, rotation, SH, scene index) and clear the
+        # screen-space gradients
+        "project_bwd": ("hbm", n_vis * ((4 + 8 + 4 + 48 + 16 + 16 + 16 + 12 * nc_coef) +
+                                        (16 + 16 + 16 + 12 * nc_coef + 8 + 48))),
         # L1: image read (4 B), 8-bit target read (1 B), gradient written (4 B)
         "loss": ("hbm", W * H * 3 * 9),
     }
@@ -387,7 +416,8 @@ def run_ours(args, world, rank, local):
         "config": {"workload": f"city-1M-SH3 1920x1080 fwd+bwd (L1), {args.tile}x{args.tile} tiles", "gaussians": n, "visible": n_vis, "tile_entries": k_ent,
                    "width": W, "height": H, "tile": args.tile, "batch": args.batch, "views_per_gpu": 1,
                    "parallelism": f"replicas x{world}", "l2": "flushed between timed steps (256 MB write)",
-                   "accumulators": "gradient and loss buffers cleared between timed steps (one memset)",
+                   "gradients": "packed rows per visible Gaussian, written in full by every step; the loss "
+                                "accumulator cleared inside the step; nothing cleared between steps",
                    "target": "8-bit RGB image, channel t stands for t/255"},
         "fwd_mpix_s": fwd_value, "fwd_ms": fwd_ms, "fps_fwd_bwd": 1e3 / step_ms, "fps_fwd": 1e3 / fwd_ms,
         "gaussians_per_s": world * n / (step_ms * 1e-3),
@@ -401,6 +431,8 @@ def run_ours(args, world, rank, local):
         "roofline_overall_fwd": {"ideal_ms": ideal_fwd_ms, "frac": ideal_fwd_ms / fwd_ms,
                                  "definition": "the same over the forward stages and the forward time"},
         "ms_per_step_median": statistics.median(ms),
+        "dense_gradients": {"ms_per_step": max_over_ranks(sum(ms_dense) / len(ms_dense), world),
+                            "form": "scene-indexed gradient arrays (atomic adds), cleared (236 MB) inside the step"},
         "roofline_stage_frac": {k: ((amt / (peaks["hbm_gbs"] * 1e9) if b == "hbm" else amt / (alu_peak * 1e12)) * 1e3
                                     / stage_ms[k]) for k, (b, amt) in work.items() if stage_ms.get(k)},
         "roofline_contributing_pairs_frac": strict,
@@ -443,27 +475,37 @@ def run_batched_compare(args, ds, sc, cfg, st, flush, world, synth, ta, cgs):
     tgt = torch.rand((V, 3, H, W), device=ds.device)
     dL = torch.empty_like(img)
     loss = torch.zeros(1, device=ds.device)
-    grads = (torch.zeros_like(ds.mean_opac), torch.zeros_like(ds.scale), torch.zeros_like(ds.quat),
-             torch.zeros_like(ds.sh))
     s_struct = ds.struct()
+
+    def packed_rows(cap):
+        f32, dev = torch.float32, ds.device
+        return (torch.empty((cap, 4), dtype=f32, device=dev), torch.empty((cap, 4), dtype=f32, device=dev),
+                torch.empty((cap, 4), dtype=f32, device=dev),
+                torch.empty((cap,) + tuple(ds.sh.shape[1:]), dtype=f32, device=dev),
+                torch.empty(cap, dtype=torch.int64, device=dev))
+
+    rows = packed_rows(n_cap)
 
     def batched():
         cur = torch.cuda.current_stream().cuda_stream
         cgs.cgs_render_forward(s_struct, frame.struct, cfg, d_cams, None, None, img, T, nc, cur)
+        loss.zero_()
         cgs.cgs_l1_loss(img, tgt, img.numel(), loss, dL, cur)
-        cgs.cgs_render_backward(s_struct, frame.struct, cfg, d_cams, dL, T, nc, *grads, cur)
+        cgs.cgs_render_backward_packed(s_struct, frame.struct, cfg, d_cams, dL, T, nc, *rows, cur)
 
     f1 = ta.Frame(1, W, H, cfg.tile, ds.n_blocks, max(sel) + 1024, min((1 << 30) - 1, max(ent) * 2 + 65536))
     d1 = [ta.cameras_device([c]) for c in cams]
     i1, T1, n1 = f1.outputs()
     dL1 = torch.empty_like(i1)
+    rows1 = [packed_rows(f1.n_cap) for _ in range(V)]  # one set of rows per view, as the batched frame has
 
     def sequential():
         cur = torch.cuda.current_stream().cuda_stream
+        loss.zero_()
         for v in range(V):
             cgs.cgs_render_forward(s_struct, f1.struct, cfg, d1[v], None, None, i1, T1, n1, cur)
             cgs.cgs_l1_loss(i1, tgt[v:v + 1].contiguous(), i1.numel(), loss, dL1, cur)
-            cgs.cgs_render_backward(s_struct, f1.struct, cfg, d1[v], dL1, T1, n1, *grads, cur)
+            cgs.cgs_render_backward_packed(s_struct, f1.struct, cfg, d1[v], dL1, T1, n1, *rows1[v], cur)
 
     g_b = ta.capture(batched, warmup=1)
     g_s = ta.capture(sequential, warmup=1)
@@ -476,7 +518,7 @@ def run_batched_compare(args, ds, sc, cfg, st, flush, world, synth, ta, cgs):
     return {"views": V, "status": cgs.cgs_status_string(status),
             "batched_mpix_s": world * V * W * H / (tb * 1e-3) / 1e6, "batched_ms": tb,
             "sequential_mpix_s": world * V * W * H / (ts * 1e-3) / 1e6, "sequential_ms": ts,
-            "speedup": ts / tb, "both": "fwd+L1+bwd, CUDA graph replay"}
+            "speedup": ts / tb, "both": "fwd+L1+bwd (packed gradient rows), CUDA graph replay"}
 
 
 def run_fp16_compare(args, sc, cfg, d_cams, tgt, ds32, st, flush, world, ta, cgs):
@@ -492,17 +534,19 @@ def run_fp16_compare(args, sc, cfg, d_cams, tgt, ds32, st, flush, world, ta, cgs
         img, T, nc = frame.outputs()
         dL = torch.empty_like(img)
         loss = torch.zeros(1, device=ds.device)
-        f32 = torch.float32
-        grads = (torch.zeros_like(ds.mean_opac), torch.zeros(ds.scale.shape, dtype=f32, device=ds.device),
-                 torch.zeros(ds.quat.shape, dtype=f32, device=ds.device),
-                 torch.zeros(ds.sh.shape, dtype=f32, device=ds.device))
+        f32, cap = torch.float32, ds.n
+        rows = (torch.empty((cap, 4), dtype=f32, device=ds.device), torch.empty((cap, 4), dtype=f32, device=ds.device),
+                torch.empty((cap, 4), dtype=f32, device=ds.device),
+                torch.empty((cap,) + tuple(ds.sh.shape[1:]), dtype=f32, device=ds.device),
+                torch.empty(cap, dtype=torch.int64, device=ds.device))
         s_struct = ds.struct()
 
         def one():
             cur = torch.cuda.current_stream().cuda_stream
             cgs.cgs_render_forward(s_struct, frame.struct, cfg, d_cams, None, None, img, T, nc, cur)
+            loss.zero_()
             cgs.cgs_l1_loss_u8(img, tgt, img.numel(), loss, dL, cur)
-            cgs.cgs_render_backward(s_struct, frame.struct, cfg, d_cams, dL, T, nc, *grads, cur)
+            cgs.cgs_render_backward_packed(s_struct, frame.struct, cfg, d_cams, dL, T, nc, *rows, cur)
 
         for _ in range(2):
             one()
@@ -724,7 +768,8 @@ def run_lod20m(args, world):
     from paper_2404_01133_b300 import torch_api as ta
     libbuild.build()
     t0 = time.time()
-    sc, cams = synth.workload_city_lod()
+    heights = tuple(float(h) for h in args.lod_heights.split(","))
+    sc, cams = synth.workload_city_lod(n=args.lod_n, heights=heights)
     t_gen = time.time() - t0
     ds = ta.DeviceScene(sc)
     ds.compute_block_bounds(4.0)
@@ -760,10 +805,12 @@ def run_lod20m(args, world):
             del fr
         rows.append(row)
     mean = lambda k: float(np.mean([r[k]["fps"] for r in rows]))
-    return {"metric": "20M-Gaussian LoD FPS at 1080p (block LoD vs point-wise LoD vs fixed levels)", "value": mean("lod"),
+    mn = f"{args.lod_n / 1e6:g}M"
+    return {"metric": f"{mn}-Gaussian LoD FPS at 1080p (block LoD vs point-wise LoD vs fixed levels)", "value": mean("lod"),
             "unit": "FPS", "n_gpus": world, "steps": args.steps, "higher_is_better": True, "dtype": "f32",
-            "data": "synthetic", "config": {"workload": "city-20M-SH3 6 km^2, 8x8 blocks, levels 100/50/25%, "
+            "data": "synthetic", "config": {"workload": f"city-{mn}-SH3 6 km^2, 8x8 blocks, levels 100/50/25%, "
                                                         "top-down 1920x1080, f=1200, 16x16 tiles",
+                                            "heights_m": list(heights),
                                             "lod_dist_m": [200, 600], "generation_s": t_gen},
             "mean_fps": {"lod": mean("lod"), "pointwise_lod": mean("pointwise"), "no_lod_level0": mean("level0"),
                          "only_level1": mean("level1"), "only_level2": mean("level2")},

@@ -168,6 +168,21 @@ int32_t cgs_render_backward(const cgs_scene* scene, const cgs_frame* frame, cons
                             const uint32_t* d_n_contrib, float* d_g_mean_opac, float* d_g_scale,
                             float* d_g_quat, float* d_g_sh, void* stream);
 
+/* The same backward with the gradients of each visible (view, Gaussian) pair in its own
+ * row instead of added into scene-indexed arrays.  Rows r = 0 .. n_vis-1 (n_vis: the
+ * visible count of the frame, cgs_frame_status counts[1]) are WRITTEN, in the order of the
+ * visible list (frame buffer 7): d_g_mean_opac [rows][4] (x, y, z, opacity), d_g_scale
+ * [rows][4] (x, y, z, 0), d_g_quat [rows][4], d_g_sh [rows][(deg+1)^2][3] and d_g_index
+ * [rows] (int64 scene index of the row's Gaussian).  Arrays hold frame->n_cap rows; rows
+ * from n_vis on are left as they are.  Nothing needs clearing between calls, and with one
+ * view per frame every scene index appears at most once; with several views the caller
+ * sums rows of equal index.  Results equal cgs_render_backward's up to the order of
+ * floating-point additions. */
+int32_t cgs_render_backward_packed(const cgs_scene* scene, const cgs_frame* frame, const cgs_config* cfg,
+                                   const cgs_camera* d_cams, const float* d_dL_dimage, const float* d_final_T,
+                                   const uint32_t* d_n_contrib, float* d_g_mean_opac, float* d_g_scale,
+                                   float* d_g_quat, float* d_g_sh, int64_t* d_g_index, void* stream);
+
 /* L1 photometric loss (the L1 term of the training loss, Sec. 3.2.3) over `count` values:
  * ADDS mean|img - target| into *d_loss and writes d_grad = sign(img - target) / count
  * (sign(0) = 0). */

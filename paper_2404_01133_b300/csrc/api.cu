@@ -19,7 +19,7 @@ bool launch_render_fwd(const Layout& L, const cgs_config& c, float* img, float* 
 bool launch_render_bwd(const Layout& L, const cgs_config& c, const float* dimg, const float* T, const uint32_t* nc,
                        cudaStream_t st);
 void launch_project_bwd(const Layout& L, const cgs_scene& S, const cgs_camera* cams, float near_z, float* g_mo,
-                        float* g_sc, float* g_q, float* g_sh, int n_sm, cudaStream_t st);
+                        float* g_sc, float* g_q, float* g_sh, long long* g_index, int n_sm, cudaStream_t st);
 void launch_l1(const float* img, const float* tgt, long long n, float* loss, float* grad, int n_sm, cudaStream_t st);
 void launch_l1_u8(const float* img, const uint8_t* tgt, long long n, float* loss, float* grad, int n_sm,
                   cudaStream_t st);
@@ -109,7 +109,6 @@ static bool make_layout(const cgs_frame* f, Layout* L, size_t* bytes)
     l.seg_blk = c.take<int32_t>((long long)l.V * l.NB);
     l.levels = c.take<int8_t>((long long)l.V * l.NB);
     l.rec = c.take<float4>(3 * l.n_cap);
-    l.tq = c.take<float>(l.n_cap);
     l.rect = c.take<uint2>(l.n_cap);
     l.tt = c.take<uint32_t>(l.n_cap);
     l.gidx = c.take<uint32_t>(l.n_cap);
@@ -300,10 +299,10 @@ int32_t cgs_render_forward_hits(const cgs_scene* scene, const cgs_frame* frame, 
                           d_hits, stream);
 }
 
-int32_t cgs_render_backward(const cgs_scene* scene, const cgs_frame* frame, const cgs_config* cfg,
-                            const cgs_camera* d_cams, const float* d_dL_dimage, const float* d_final_T,
-                            const uint32_t* d_n_contrib, float* d_g_mean_opac, float* d_g_scale, float* d_g_quat,
-                            float* d_g_sh, void* stream)
+static int32_t render_backward(const cgs_scene* scene, const cgs_frame* frame, const cgs_config* cfg,
+                               const cgs_camera* d_cams, const float* d_dL_dimage, const float* d_final_T,
+                               const uint32_t* d_n_contrib, float* d_g_mean_opac, float* d_g_scale, float* d_g_quat,
+                               float* d_g_sh, int64_t* d_g_index, void* stream)
 {
     Layout L;
     size_t bytes = 0;
@@ -321,10 +320,30 @@ int32_t cgs_render_backward(const cgs_scene* scene, const cgs_frame* frame, cons
     }
     {
         StageScope s(CGS_STAGE_PROJECT_BWD, st);
-        launch_project_bwd(L, *scene, d_cams, cfg->near_z, d_g_mean_opac, d_g_scale, d_g_quat, d_g_sh, n_sm, st);
+        launch_project_bwd(L, *scene, d_cams, cfg->near_z, d_g_mean_opac, d_g_scale, d_g_quat, d_g_sh,
+                           reinterpret_cast<long long*>(d_g_index), n_sm, st);
         counted(1);
     }
     return cudaGetLastError() == cudaSuccess ? CGS_OK : CGS_ERR_CUDA;
+}
+
+int32_t cgs_render_backward(const cgs_scene* scene, const cgs_frame* frame, const cgs_config* cfg,
+                            const cgs_camera* d_cams, const float* d_dL_dimage, const float* d_final_T,
+                            const uint32_t* d_n_contrib, float* d_g_mean_opac, float* d_g_scale, float* d_g_quat,
+                            float* d_g_sh, void* stream)
+{
+    return render_backward(scene, frame, cfg, d_cams, d_dL_dimage, d_final_T, d_n_contrib, d_g_mean_opac, d_g_scale,
+                           d_g_quat, d_g_sh, nullptr, stream);
+}
+
+int32_t cgs_render_backward_packed(const cgs_scene* scene, const cgs_frame* frame, const cgs_config* cfg,
+                                   const cgs_camera* d_cams, const float* d_dL_dimage, const float* d_final_T,
+                                   const uint32_t* d_n_contrib, float* d_g_mean_opac, float* d_g_scale,
+                                   float* d_g_quat, float* d_g_sh, int64_t* d_g_index, void* stream)
+{
+    if (!d_g_index) return CGS_ERR_INVALID_ARGUMENT;
+    return render_backward(scene, frame, cfg, d_cams, d_dL_dimage, d_final_T, d_n_contrib, d_g_mean_opac, d_g_scale,
+                           d_g_quat, d_g_sh, d_g_index, stream);
 }
 
 int32_t cgs_l1_loss(const float* d_img, const float* d_target, int64_t count, float* d_loss, float* d_grad,

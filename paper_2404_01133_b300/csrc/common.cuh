@@ -20,7 +20,7 @@ struct Header {
     uint32_t status;
     uint32_t n_sel;        // selected Gaussians summed over views, capped at n_cap
     uint32_t n_vis;        // visible (tiles touched > 0)
-    uint32_t _unused;
+    uint32_t reserved;
     unsigned long long n_sel_raw;
     unsigned long long k_total;
     unsigned long long pairs_fwd;
@@ -58,7 +58,6 @@ struct Layout {
     float lod_d1, lod_d2;        // FP32 thresholds of the point mode
     int8_t* levels;              // [V][NB]
     float4* rec;                 // [n_cap][3] (u, v, o, ext_x) (A', B', C', ext_y) (r, g, b, t)
-    float* tq;                   // [n_cap] culling threshold t on the quadratic form
     uint2* rect;                 // [n_cap] (x0 | y0 << 16, x1 | y1 << 16), tile units, end exclusive
     uint32_t* tt;                // [n_cap] tiles touched
     uint32_t* gidx;              // [n_cap] scene index

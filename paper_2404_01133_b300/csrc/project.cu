@@ -174,7 +174,6 @@ __global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM)
                         L.rect[j] = make_uint2(rx, ry);
                         float ex, ey, tq;
                         cull_extent(mo.w, p.A, p.B, p.C, &ex, &ey, &tq);
-                        L.tq[j] = tq;
                         L.rec[3 * (size_t)j] = make_float4(p.u, p.v, mo.w, ex);
                         L.rec[3 * (size_t)j + 1] = make_float4(p.conic[0], p.conic[1], p.conic[2], ey);
                         float rgb[3];

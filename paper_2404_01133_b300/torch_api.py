@@ -151,6 +151,23 @@ def render_backward(dscene, frame, cfg, d_cams, dL_dimage, final_T, n_contrib, g
     return grads
 
 
+def render_backward_packed(dscene, frame, cfg, d_cams, dL_dimage, final_T, n_contrib, rows=None, attrs=None,
+                           stream=None):
+    """Backward with one gradient row per visible (view, Gaussian) pair (cgs_render_backward_packed):
+    returns (g_mean_opac, g_scale, g_quat, g_sh, g_index), each with frame.n_cap rows of which the
+    first n_vis (frame.status()[1][1]) are written."""
+    if rows is None:
+        f32, dev, cap = torch.float32, dscene.device, frame.n_cap
+        rows = (torch.empty((cap, 4), dtype=f32, device=dev), torch.empty((cap, 4), dtype=f32, device=dev),
+                torch.empty((cap, 4), dtype=f32, device=dev),
+                torch.empty((cap,) + tuple(dscene.sh.shape[1:]), dtype=f32, device=dev),
+                torch.empty(cap, dtype=torch.int64, device=dev))
+    g_mo, g_sc, g_q, g_sh, g_idx = rows
+    _c.cgs_render_backward_packed(dscene.struct(attrs), frame.struct, cfg, d_cams, dL_dimage.contiguous(), final_T,
+                                  n_contrib, g_mo, g_sc, g_q, g_sh, g_idx, stream)
+    return rows
+
+
 class RenderFn(torch.autograd.Function):
     """image = render(mean_opac, scale, quat, sh) for the views of `frame`.
 
@@ -198,9 +215,11 @@ def frame_counts(dscene, cams, width, height, tile=16, view_block=None, levels=N
                  n_cap=None, k_cap=None, cfg=None):
     """Selected Gaussians and tile entries of each view, rendered one view at a time.
 
-    Used to size batched frames: returns two lists (selected, entries) per view."""
+    Used to size batched frames: returns two lists (selected, entries) per view.  The entry
+    count is exact even past the counting frame's capacity (the projection counts every entry
+    and drops the ones that do not fit), so the counting frame stays small."""
     n_cap = n_cap or max(1, dscene.n)
-    k_cap = k_cap or min((1 << 30) - 1, 64 * n_cap)
+    k_cap = k_cap or min((1 << 30) - 1, 4 * n_cap + (1 << 20))
     fr = Frame(1, width, height, tile, dscene.n_blocks, n_cap, k_cap, device)
     cfg = cfg or make_config(tile=tile)
     sel, ent = [], []
@@ -215,6 +234,8 @@ def frame_counts(dscene, cams, width, height, tile=16, view_block=None, levels=N
             raise _c.CgsError(st, "frame_counts")
         sel.append(int(c[0]))
         ent.append(int(c[2]))
+    del fr, out
+    torch.cuda.empty_cache()
     return sel, ent
 
 

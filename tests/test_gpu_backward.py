@@ -36,6 +36,34 @@ def gpu_grads(g, dL):
             "quat": gq.cpu().numpy(), "sh": gsh.cpu().numpy()}
 
 
+def gpu_grads_packed(g, dL, sentinel=None):
+    """Packed backward rows, and the same gradients scattered into scene-indexed arrays by
+    summing rows of equal index (float64 sums)."""
+    d = torch.as_tensor(dL, dtype=torch.float32).cuda().reshape(g["image"].shape).contiguous()
+    rows = None
+    if sentinel is not None:
+        fr, ds = g["frame"], g["ds"]
+        cap = fr.n_cap
+        rows = tuple(torch.full(sh, sentinel, dtype=torch.float32, device="cuda")
+                     for sh in ((cap, 4), (cap, 4), (cap, 4), (cap,) + tuple(ds.sh.shape[1:])))
+        rows = rows + (torch.full((cap,), -7, dtype=torch.int64, device="cuda"),)
+    rows = ta.render_backward_packed(g["ds"], g["frame"], g["cfg"], g["cams"], d, g["final_T"], g["n_contrib"],
+                                     rows=rows)
+    torch.cuda.synchronize()
+    st, counts = g["frame"].status()
+    n_vis = int(counts[1])
+    gm, gs_, gq, gsh, gi = (t.cpu().numpy() for t in rows)
+    n = g["ds"].n
+    dense = {}
+    for k, src in (("mo", gm), ("sc", gs_), ("q", gq), ("sh", gsh)):
+        acc = np.zeros((n,) + src.shape[1:], np.float64)
+        np.add.at(acc, gi[:n_vis], src[:n_vis].astype(np.float64))
+        dense[k] = acc
+    out = {"mean": dense["mo"][:, :3], "opac": dense["mo"][:, 3], "scale": dense["sc"][:, :3], "quat": dense["q"],
+           "sh": dense["sh"]}
+    return out, (gm, gs_, gq, gsh, gi), n_vis
+
+
 def compare_grads(gg, og, rows=None, rtol=G_RTOL, elem=G_ELEM):
     for k in ("mean", "opac", "scale", "quat", "sh"):
         a = gg[k].astype(np.float64)
@@ -165,3 +193,53 @@ def test_full_size_city_1m_forward_backward():
     og64 = oracle.render_backward(sc, cam, dL.astype(np.float64), real="f64")
     for k in ("mean", "opac", "scale", "quat", "sh"):
         assert np.linalg.norm(gg[k] - og64[k]) <= G_RTOL * np.linalg.norm(og64[k]), k
+
+
+@pytest.mark.parametrize("deg", [3, 1])
+def test_packed_backward_rows_match_dense_backward(deg):
+    """One view: every visible Gaussian owns one packed row, whose values are the dense
+    backward's row (up to the order in which the compositing backward adds each Gaussian's
+    screen-space gradient, which differs between runs in the last bits); rows past the visible
+    count are left as they were; the row indices follow the visible list."""
+    sc = synth.single_block(synth.random_cube_scene(900, seed=30 + deg, sh_degree=deg, log_scale_mu=-2.4))
+    cam = synth.small_scene_camera(96, 80, f=80.0, dist=3.0)
+    cfg = oracle.make_config(tile=16)
+    o = oracle.render(sc, cam, cfg)
+    w = np.random.default_rng(12).normal(size=(3, 80, 96)).astype(np.float32)
+    w[:, o["ambiguous"].astype(bool)] = 0.0
+    g = gpu_render(sc, [cam])
+    dense = gpu_grads(g, w)
+    packed, rows, n_vis = gpu_grads_packed(g, w, sentinel=np.float32(1234.5))
+    gm, gs_, gq, gsh, gi = rows
+    assert n_vis > 100
+    # rows past n_vis untouched
+    assert (gi[n_vis:] == -7).all() and (gm[n_vis:] == 1234.5).all() and (gsh[n_vis:] == 1234.5).all()
+    # the visible list's scene indices, each once
+    vis = g["frame"].buffer(cgs.BUF_VISIBLE, torch.int32, count=n_vis).cpu().numpy()
+    sidx = g["frame"].buffer(cgs.BUF_SCENE_INDEX, torch.int32, count=g["counts"][0]).cpu().numpy()
+    np.testing.assert_array_equal(gi[:n_vis], sidx[vis])
+    assert len(np.unique(gi[:n_vis])) == n_vis
+    for k in ("mean", "opac", "scale", "quat", "sh"):
+        b = dense[k].astype(np.float64)
+        np.testing.assert_allclose(packed[k], b, rtol=1e-5, atol=1e-6 * np.abs(b).max(), err_msg=k)
+        assert ((packed[k] != 0) == (b != 0)).mean() > 0.999, k   # the same rows carry gradient
+    assert (gs_[:n_vis, 3] == 0).all()
+    # and the oracle's gradient
+    og = oracle.render_backward(sc, cam, w, cfg, real="f32", fwd=o)
+    compare_grads({k: v.astype(np.float32) for k, v in packed.items()}, og)
+
+
+def test_packed_backward_multi_view_sums_to_dense():
+    """Several views in one frame: a Gaussian seen by k views owns k rows; their sum is the
+    dense backward's accumulated gradient (up to the order of FP32 additions)."""
+    sc = synth.single_block(synth.random_cube_scene(700, seed=41, sh_degree=3, log_scale_mu=-2.4))
+    cams = [synth.look_at((x, 0.4, -3.2), (0, 0, 0), (0, -1, 0), 60.0, 60.0, 64, 48) for x in (-0.8, 0.0, 0.9)]
+    g = gpu_render(sc, cams)
+    w = np.random.default_rng(13).normal(size=(3, 3, 48, 64)).astype(np.float32)
+    dense = gpu_grads(g, w)
+    packed, rows, n_vis = gpu_grads_packed(g, w)
+    gi = rows[4][:n_vis]
+    assert n_vis > len(np.unique(gi))  # some Gaussians are visible in more than one view
+    for k in ("mean", "opac", "scale", "quat", "sh"):
+        a, b = packed[k], dense[k].astype(np.float64)
+        np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max(), err_msg=k)
