@@ -44,6 +44,20 @@ __device__ __forceinline__ bool surely_off_screen(const float m[3], const float 
     return u + rb < 0.0f || u - rb > (float)(W - 1) || v + rb < 0.0f || v - rb > (float)(H - 1);
 }
 
+// L2 prefetch of the rows phase 2 reads for a candidate: its SH coefficients (one 192-byte
+// row at degree 3 in FP32, which spans two 128-byte lines) and its rotation.
+template <int DEG>
+__device__ __forceinline__ void prefetch_rows(const cgs_scene& S, long long g)
+{
+    constexpr int nc = (DEG + 1) * (DEG + 1);
+    const size_t row = (size_t)(nc * 3) * (S.attr_fp16 ? 2u : 4u);
+    const char* p = reinterpret_cast<const char*>(S.sh) + (size_t)g * row;
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+    if (row > 64) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + row - 1));
+    const char* q = reinterpret_cast<const char*>(S.quat) + (size_t)g * (S.attr_fp16 ? 8u : 16u);
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
+}
+
 // The CTA walks the selected list (flattened over views) in steps of PROJ_STEP Gaussians (a
 // uniform trip count, so the CTA-wide steps below are safe).
 //   phase 1  PROJ_ITEMS Gaussians per thread: scene index, near plane, the point-wise level
@@ -136,6 +150,8 @@ __global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM)
                 s_qj[slot] = j;
                 s_qv[slot] = v;
                 s_qg[slot] = g;
+                // the rows of phase 2's first round, fetched into L2 while phase 1 goes on
+                if (slot < PROJ_THREADS) prefetch_rows<DEG>(S, g);
             }
         }
         __syncthreads();
