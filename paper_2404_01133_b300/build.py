@@ -2,8 +2,8 @@
 
 Each .cu file is compiled to an object with nvcc; the files whose floating-point results
 decide integers (the projection key path, LoD selection, MAD bounds) are compiled with
--fmad=false so that no multiply-add is contracted.  The objects are linked into one shared
-library next to this file.
+-fmad=false so that no multiply-add is contracted; the compositing backward is built with
+flush-to-zero.  The objects are linked into one shared library next to this file.
 """
 import os
 import subprocess
@@ -18,7 +18,9 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
           "-I", CSRC, "--expt-relaxed-constexpr"]
 NO_FMA = {"project.cu", "project_bwd.cu", "select.cu", "partition.cu", "levels.cu"}
-SOURCES = ["api.cu", "select.cu", "project.cu", "sort.cu", "render.cu", "project_bwd.cu", "static_ws.cu", "partition.cu", "levels.cu", "ssim.cu"]
+FTZ = {"render_bwd.cu"}  # gradient arithmetic only; the decisions it shares with the forward are pinned in PTX
+SOURCES = ["api.cu", "select.cu", "project.cu", "sort.cu", "render.cu", "render_bwd.cu", "project_bwd.cu",
+           "static_ws.cu", "partition.cu", "levels.cu", "ssim.cu"]
 
 
 def _nvcc():
@@ -41,6 +43,8 @@ def build(force=False, verbose=False, extra=()):
         flags = list(COMMON) + list(extra)
         if src in NO_FMA:
             flags.append("-fmad=false")
+        if src in FTZ:
+            flags.append("-ftz=true")
         cmd = [nvcc, *ARCH, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd))

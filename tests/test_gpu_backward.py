@@ -243,3 +243,28 @@ def test_packed_backward_multi_view_sums_to_dense():
     for k in ("mean", "opac", "scale", "quat", "sh"):
         a, b = packed[k], dense[k].astype(np.float64)
         np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max(), err_msg=k)
+
+
+@pytest.mark.parametrize("case", ["small16", "small8", "city1m"])
+def test_backward_replays_exactly_the_forward_blends(case):
+    """The compositing backward (built with flush-to-zero) replays exactly the forward's blends:
+    the number of (pixel, Gaussian) pairs its replay takes equals the forward's per-Gaussian
+    blended-pixel counts summed (the two kernels take every skip and stop decision alike)."""
+    if case == "city1m":
+        sc, cams = synth.workload_city_1m()
+        tile, batch, n_cap, k_cap = 16, 128, 1_000_000, 4_000_000
+    else:
+        sc = synth.single_block(synth.random_cube_scene(1500, seed=77, sh_degree=2, log_scale_mu=-2.2))
+        cams = [synth.small_scene_camera(120, 90, f=90.0, dist=3.0)]
+        tile, batch = (16, 64) if case == "small16" else (8, 32)
+        n_cap, k_cap = None, None
+    g = gpu_render(sc, cams, tile=tile, batch=batch, n_cap=n_cap, k_cap=k_cap)
+    hits = torch.zeros(g["ds"].n, dtype=torch.int32, device="cuda")
+    img, T, nc = ta.render_forward_hits(g["ds"], g["frame"], g["cfg"], g["cams"], hits)
+    dL = torch.randn_like(img)
+    ta.render_backward_packed(g["ds"], g["frame"], g["cfg"], g["cams"], dL, T, nc)
+    torch.cuda.synchronize()
+    st, counts = g["frame"].status()
+    assert st == 0
+    blends = int(hits.to(torch.int64).sum().item())
+    assert blends > 0 and counts[4] == blends, (counts[4], blends)
