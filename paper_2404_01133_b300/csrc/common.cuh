@@ -45,6 +45,7 @@ struct Layout {
     // zeroed at every forward (one memset from hdr over zero_bytes)
     unsigned long long* scan_lb; // [scan tiles of V*T] look-back words of the tile-range scan
     uint32_t* tcnt;              // [V * T] entries per tile
+    uint32_t* sel_done;          // [V] CTAs of the view that finished the selection's first phase
     uint32_t* tcur;              // [V * T] scatter cursors
     // not zeroed
     uint32_t* ranges;            // [V * T][2] [start, end) of every tile's entries

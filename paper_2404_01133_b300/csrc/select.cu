@@ -72,19 +72,26 @@ __global__ void k_lod_levels(cgs_scene S, const cgs_camera* __restrict__ cams, i
     }
 }
 
-// Per view: the level of every block (given, one training block, or LoD), then the ordered
-// list of selected segments (fusion by concatenation, Sec. 3.3.2) and its prefix counts; the
-// last CTA to finish also writes the prefix of the per-view counts (the views' bases in the
-// flattened selected list).
-__global__ void k_select(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams, const int32_t* view_block,
-                         const int8_t* levels_in, cgs_config cfg)
+// Per view, in two phases.  Phase 1, spread over ceil(n_blocks / SEL_BLOCKS) CTAs per view so
+// that the FP64 corner arithmetic of many blocks runs on many SMs: the level of each block
+// (given, one training block, or LoD).  Phase 2, in the last CTA of the view to finish phase 1:
+// the ordered list of selected segments (fusion by concatenation, Sec. 3.3.2) and its prefix
+// counts; the last view to finish also writes the prefix of the per-view counts (the views'
+// bases in the flattened selected list).
+constexpr int SEL_BLOCKS = 8;                // blocks per CTA in phase 1 (one 8-lane group each)
+constexpr int SEL_THREADS = SEL_BLOCKS * 8;  // 64
+
+__global__ void __launch_bounds__(SEL_THREADS) k_select(Layout L, cgs_scene S, const cgs_camera* __restrict__ cams,
+                                                        const int32_t* view_block, const int8_t* levels_in,
+                                                        cgs_config cfg)
 {
-    const int v = blockIdx.x;
+    const int v = blockIdx.y;
     const int NB = S.n_blocks, NL = S.n_levels;
     int8_t* lev = L.levels + (long long)v * NB;
-    const cgs_camera c = cams[v];
+    const int b0 = blockIdx.x * SEL_BLOCKS;
     if (levels_in || view_block) {
-        for (int b = threadIdx.x; b < NB; b += blockDim.x) {
+        const int b = b0 + (int)threadIdx.x;
+        if (threadIdx.x < SEL_BLOCKS && b < NB) {
             int l;
             if (levels_in) {
                 l = levels_in[(long long)v * NB + b];
@@ -99,32 +106,39 @@ __global__ void k_select(Layout L, cgs_scene S, const cgs_camera* __restrict__ c
     } else if (L.lod_mode == CGS_LOD_POINT) {
         // point-wise baseline: every non-empty block at its finest level; k_project applies the
         // per-Gaussian distance test
-        for (int b = threadIdx.x; b < NB; b += blockDim.x) lev[b] = S.level_count[(long long)b * NL] > 0 ? 0 : -1;
+        const int b = b0 + (int)threadIdx.x;
+        if (threadIdx.x < SEL_BLOCKS && b < NB) lev[b] = S.level_count[(long long)b * NL] > 0 ? 0 : -1;
     } else {
-        const int groups = blockDim.x >> 3;
-        for (int b0 = 0; b0 < NB; b0 += groups) {
-            const int b = b0 + (threadIdx.x >> 3);
-            int l = lod_level8(S, b < NB ? b : -1, c, (double)cfg.near_z, cfg.lod_dist[0], cfg.lod_dist[1]);
-            if (b < NB && (threadIdx.x & 7) == 0) {
-                if (l >= 0 && S.level_count[(long long)b * NL + l] <= 0) l = -1;
-                lev[b] = (int8_t)l;
-            }
+        const cgs_camera c = cams[v];
+        const int b = b0 + (int)(threadIdx.x >> 3);
+        int l = lod_level8(S, b < NB ? b : -1, c, (double)cfg.near_z, cfg.lod_dist[0], cfg.lod_dist[1]);
+        if (b < NB && (threadIdx.x & 7) == 0) {
+            if (l >= 0 && S.level_count[(long long)b * NL + l] <= 0) l = -1;
+            lev[b] = (int8_t)l;
         }
     }
+    __shared__ bool s_last;
     __syncthreads();
-    // the ordered segment list: one CTA-wide exclusive scan per chunk of blocks of the packed
-    // pair (selected count << 0 | Gaussian count << SEG_BITS)
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&L.sel_done[v], 1u) == gridDim.x - 1u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // phase 2: the ordered segment list, one CTA-wide exclusive scan per chunk of blocks of the
+    // packed pair (selected count << 0 | Gaussian count << SEG_BITS); the levels written by the
+    // other CTAs are read past L1
     constexpr int SEG_BITS = 20;  // n_blocks < 2^20
     __shared__ unsigned long long wb[33];
     __shared__ unsigned long long s_carry;
-    __shared__ bool s_last;
     if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
     uint32_t* sb = L.seg_base + (long long)v * (NB + 1);
     long long* so = L.seg_off + (long long)v * NB;
-    for (int b0 = 0; b0 < NB; b0 += blockDim.x) {
-        const int b = b0 + threadIdx.x;
-        const int l = b < NB ? lev[b] : -1;
+    for (int c0 = 0; c0 < NB; c0 += blockDim.x) {
+        const int b = c0 + threadIdx.x;
+        const int l = b < NB ? (int)__ldcg(lev + b) : -1;
         const unsigned long long cnt = l >= 0 ? (unsigned long long)S.level_count[(long long)b * NL + l] : 0ull;
         const unsigned long long x = l >= 0 ? (1ull | (cnt << SEG_BITS)) : 0ull;
         unsigned long long tot;
@@ -146,9 +160,9 @@ __global__ void k_select(Layout L, cgs_scene S, const cgs_camera* __restrict__ c
         sb[ns] = (uint32_t)(acc < 0xffffffffull ? acc : 0xffffffffull);
         L.n_seg[v] = (uint32_t)ns;
         L.view_cnt[v] = (uint32_t)(acc < 0xffffffffull ? acc : 0xffffffffull);
-        // the last view's CTA to get here writes the per-view prefix
+        // the last view to get here writes the per-view prefix
         __threadfence();
-        s_last = atomicAdd(&L.hdr->ctr[CTR_SELECT], 1u) == gridDim.x - 1;
+        s_last = atomicAdd(&L.hdr->ctr[CTR_SELECT], 1u) == (uint32_t)L.V - 1u;
     }
     __syncthreads();
     if (!s_last) return;
@@ -295,7 +309,8 @@ __global__ void __launch_bounds__(256) k_block_bounds(cgs_scene S, double n_mad,
 void launch_select(const Layout& L, const cgs_scene& S, const cgs_camera* cams, const int32_t* view_block,
                    const int8_t* levels, const cgs_config& cfg, cudaStream_t st)
 {
-    k_select<<<L.V, 256, 0, st>>>(L, S, cams, view_block, levels, cfg);
+    const dim3 grid((unsigned)((S.n_blocks + SEL_BLOCKS - 1) / SEL_BLOCKS), (unsigned)L.V);
+    k_select<<<grid, SEL_THREADS, 0, st>>>(L, S, cams, view_block, levels, cfg);
 }
 
 void launch_lod_levels(const cgs_scene& S, const cgs_config& cfg, const cgs_camera* cams, int n_views,
