@@ -3,7 +3,8 @@ configuration: the 20M-Gaussian, 8 x 8-block, 3-level city (Sec. 3.3) rendered t
 1920x1080 from 50 to 2000 m with MAD block bounds (Eq. 7, n_MAD = 4), distance intervals
 200 / 600 m, 16 x 16 tiles and batches of 256.  Block bounds and every view's selected list
 are compared whole and bit-exact; two heights also compare every tile key, value and range,
-and the pixels of a band of tile rows, against the oracle."""
+and the pixels of a band of tile rows, against the oracle.  The 64-pose queue, batched as the
+benchmark batches it, is checked view by view against one-view renders."""
 import numpy as np
 import pytest
 import torch
@@ -93,3 +94,29 @@ def test_full_size_lod_frame_20m(city, height):
 
 def fr_tiles(fr):
     return fr.n_views * ((fr.width + fr.tile - 1) // fr.tile) * ((fr.height + fr.tile - 1) // fr.tile)
+
+
+def test_full_size_pose_queue_batched_equals_single_views(city):
+    """The 64-pose queue over the 20M city rendered as batched frames (views grouped by
+    capacity, as the benchmark does): every sampled view equals its own one-view render bit for
+    bit (image, T, n_contrib), and the batched selections add up to the per-view ones."""
+    sc, _, ds, _ = city
+    cams = synth.lod_pose_queue(sc["side"])
+    cfg = ta.make_config(tile=16, batch=256, lod_dist=(200.0, 600.0))
+    sel, ent = ta.frame_counts(ds, cams, 1920, 1080, cfg=cfg)
+    groups = ta.waves(sel, ent, n_cap_max=200_000_000, k_cap_max=(1 << 30) - 1)
+    sample = {0, 17, 40, 63}
+    for views, n_cap, k_cap in groups:
+        fr = ta.Frame(len(views), 1920, 1080, 16, ds.n_blocks, n_cap, min((1 << 30) - 1, k_cap))
+        img, T, nc = ta.render_forward(ds, fr, cfg, ta.cameras_device([cams[v] for v in views]))
+        torch.cuda.synchronize()
+        st, counts = fr.status()
+        assert st == 0, cgs.cgs_status_string(st)
+        assert counts[0] == sum(sel[v] for v in views) and counts[2] == sum(ent[v] for v in views)
+        for i, v in enumerate(views):
+            if v not in sample:
+                continue
+            _, c1, img1, T1, nc1 = render_view(ds, cams[v])
+            assert c1[0] == sel[v]
+            assert torch.equal(img[i], img1[0]) and torch.equal(T[i], T1[0]) and torch.equal(nc[i], nc1[0]), v
+        del fr, img, T, nc
