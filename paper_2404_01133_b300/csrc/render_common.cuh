@@ -35,6 +35,18 @@ __device__ __forceinline__ float ieee_fma(float a, float b, float c)
     asm("fma.rn.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
     return r;
 }
+// G = e^power = 2^(power log2 e), with log2 e rounded to FP32 and the hardware base-2
+// exponential (PTX ex2.approx), both with flush-to-zero, written in PTX so the forward and the
+// backward evaluate it identically whatever their files' floating-point flags.  A result that
+// would be denormal becomes zero; o G is then below 1/255 either way.
+__device__ __forceinline__ float gauss_exp(float power)
+{
+    float x, g;
+    asm("mul.ftz.f32 %0, %1, 0f3FB8AA3B;" : "=f"(x) : "f"(power));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(g) : "f"(x));
+    return g;
+}
+
 __device__ __forceinline__ void pair_power2(const float4& a, const float4& b, float fpx, float fpy0, float fpy1,
                                             float* pw0, float* pw1, float* dx_out, float* dy0_out, float* dy1_out)
 {
@@ -139,7 +151,7 @@ struct FwdPixel {
     bool done = false;
     __device__ __forceinline__ bool blend(float power, float o, const float4& c, uint32_t pos)
     {
-        const float alpha = fminf(0.99f, __fmul_rn(o, __expf(power)));
+        const float alpha = fminf(0.99f, __fmul_rn(o, gauss_exp(power)));
         const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
         const bool ok = !done && !(power > 0.0f) && !(alpha < 1.0f / 255.0f);
         const bool stop = ok && Tn < 1e-4f;
@@ -178,7 +190,7 @@ struct BwdPixel {
     __device__ __forceinline__ bool replay(float power, float dx, float dy, float o, const float4& c, uint32_t lp,
                                            float* m)
     {
-        const float G = __expf(power);
+        const float G = gauss_exp(power);
         const float og = __fmul_rn(o, G);
         const float alpha = fminf(0.99f, og);
         const bool use = lp < nc && !(power > 0.0f) && !(alpha < 1.0f / 255.0f);
