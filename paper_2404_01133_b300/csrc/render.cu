@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 8 : 32) k_render_fwd(Layo
                 const size_t j = tval[start + i];
                 const float4 a = L.rec[3 * j], b = L.rec[3 * j + 1], c = L.rec[3 * j + 2];
                 s_a[i] = a;
-                s_b[i] = b;
+                s_b[i] = power_factors(b);
                 s_c[i] = c;
                 m = warp_mask<B>(a, b, c.w, tx0, ty0);
                 if (HITS) s_g[i] = L.gidx[j];
@@ -66,10 +66,10 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 8 : 32) k_render_fwd(Layo
                 const int kk = __ffs(bits) - 1;
                 bits &= bits - 1;
                 const int k = c0 + kk;
-                const float4 a = s_a[k], b = s_b[k], c = s_c[k];
+                const float4 a = s_a[k], nf = s_b[k], c = s_c[k];
                 const uint32_t pos = start - rg.x + (uint32_t)k;
                 float pw0, pw1, dx, dy0, dy1;
-                pair_power2(a, b, fpx, fpy0, fpy1, &pw0, &pw1, &dx, &dy0, &dy1);
+                pair_power2(a, nf, fpx, fpy0, fpy1, &pw0, &pw1, &dx, &dy0, &dy1);
                 const bool b0 = p0.blend(pw0, a.z, c, pos);
                 const bool b1 = p1.blend(pw1, a.z, c, pos);
                 if (__any_sync(0xffffffffu, b0 || b1)) word |= 1u << kk;

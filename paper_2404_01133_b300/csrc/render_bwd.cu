@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 6 : 24) k_render_bwd(Layo
 {
     constexpr int NT = B * B / 2;
     constexpr int NW = B * B / 64;
-    __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
+    __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH], s_f[BATCH];
     __shared__ uint32_t s_j[BATCH];
     __shared__ float s_g[BATCH][9];
     __shared__ uint32_t s_maxnc;
@@ -81,7 +81,9 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 6 : 24) k_render_bwd(Layo
             const uint32_t j = tval[bs + i];
             s_j[i] = j;
             s_a[i] = L.rec[3 * (size_t)j];
-            s_b[i] = L.rec[3 * (size_t)j + 1];
+            const float4 cb = L.rec[3 * (size_t)j + 1];
+            s_b[i] = cb;
+            s_f[i] = power_factors(cb);
             s_c[i] = L.rec[3 * (size_t)j + 2];
         }
         for (int i = threadIdx.x; i < 9 * BATCH; i += NT) (&s_g[0][0])[i] = 0.0f;
@@ -115,10 +117,10 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 6 : 24) k_render_bwd(Layo
                         continue;
                     }
                     const int k = ks[e];
-                    const float4 a = s_a[k], b = s_b[k], c = s_c[k];
+                    const float4 a = s_a[k], nf = s_f[k], c = s_c[k];
                     const uint32_t lp = (uint32_t)(bs + k - first);
                     float pw0, pw1, dx, dy0, dy1;
-                    pair_power2(a, b, fpx, fpy0, fpy1, &pw0, &pw1, &dx, &dy0, &dy1);
+                    pair_power2(a, nf, fpx, fpy0, fpy1, &pw0, &pw1, &dx, &dy0, &dy1);
                     pairs += (uint32_t)q0.replay<true>(pw0, dx, dy0, a.z, c, lp, acc + 9 * e);
                     pairs += (uint32_t)q1.replay<false>(pw1, dx, dy1, a.z, c, lp, acc + 9 * e);
                 }

@@ -13,7 +13,7 @@
 namespace cgs {
 
 // power = -0.5 A' dx^2 - B' dx dy - 0.5 C' dy^2 at a lane's two pixels (px, py0) and
-// (px, py1), which share dx.  Every operation is written as an explicit IEEE instruction in
+// (px, py1), which share dx, from the entry's staged factors (power_factors).  Every operation is written as an explicit IEEE instruction in
 // PTX (round to nearest, denormals kept), so the forward and the backward kernels compute the
 // same bits whatever their translation units' floating-point flags (the backward is built
 // with flush-to-zero) and take identical skip and stop decisions.
@@ -47,13 +47,20 @@ __device__ __forceinline__ float gauss_exp(float power)
     return g;
 }
 
-__device__ __forceinline__ void pair_power2(const float4& a, const float4& b, float fpx, float fpy0, float fpy1,
+// The per-entry factors of the power, -A'/2, -B', -C'/2, computed once when an entry is
+// staged (exact scalings and a negation of the record's conic).
+__device__ __forceinline__ float4 power_factors(const float4& conic)
+{
+    return make_float4(ieee_mul(-0.5f, conic.x), ieee_mul(-1.0f, conic.y), ieee_mul(-0.5f, conic.z), 0.0f);
+}
+
+__device__ __forceinline__ void pair_power2(const float4& a, const float4& nf, float fpx, float fpy0, float fpy1,
                                             float* pw0, float* pw1, float* dx_out, float* dy0_out, float* dy1_out)
 {
     const float dx = ieee_sub(a.x, fpx), dy0 = ieee_sub(a.y, fpy0), dy1 = ieee_sub(a.y, fpy1);
-    const float hC = ieee_mul(-0.5f, b.z);
-    const float ax = ieee_mul(ieee_mul(ieee_mul(-0.5f, b.x), dx), dx);  // -A' dx^2 / 2
-    const float nbx = ieee_mul(-b.y, dx);                               // -B' dx
+    const float hC = nf.z;                               // -C'/2
+    const float ax = ieee_mul(ieee_mul(nf.x, dx), dx);   // -A' dx^2 / 2
+    const float nbx = ieee_mul(nf.y, dx);                // -B' dx
     *pw0 = ieee_fma(ieee_mul(hC, dy0), dy0, ieee_fma(nbx, dy0, ax));
     *pw1 = ieee_fma(ieee_mul(hC, dy1), dy1, ieee_fma(nbx, dy1, ax));
     *dx_out = dx;
