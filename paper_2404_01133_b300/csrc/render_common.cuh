@@ -12,11 +12,10 @@
 
 namespace cgs {
 
-// power = -0.5 A' dx^2 - B' dx dy - 0.5 C' dy^2 at a lane's two pixels (px, py0) and
-// (px, py1), which share dx, from the entry's staged factors (power_factors).  Every operation is written as an explicit IEEE instruction in
-// PTX (round to nearest, denormals kept), so the forward and the backward kernels compute the
-// same bits whatever their translation units' floating-point flags (the backward is built
-// with flush-to-zero) and take identical skip and stop decisions.
+// Every operation of the per-pair power is written as an explicit IEEE instruction in PTX
+// (round to nearest, denormals kept), so the forward and the backward kernels compute the same
+// bits whatever their translation units' floating-point flags (the backward is built with
+// flush-to-zero) and take identical skip and stop decisions.
 __device__ __forceinline__ float ieee_sub(float a, float b)
 {
     float r;
@@ -35,32 +34,35 @@ __device__ __forceinline__ float ieee_fma(float a, float b, float c)
     asm("fma.rn.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
     return r;
 }
-// G = e^power = 2^(power log2 e), with log2 e rounded to FP32 and the hardware base-2
-// exponential (PTX ex2.approx), both with flush-to-zero, written in PTX so the forward and the
-// backward evaluate it identically whatever their files' floating-point flags.  A result that
-// would be denormal becomes zero; o G is then below 1/255 either way.
-__device__ __forceinline__ float gauss_exp(float power)
+// The falloff G = e^q, q = -0.5 A' dx^2 - B' dx dy - 0.5 C' dy^2, is evaluated as 2^p with
+// p = q log2 e: the per-entry factors (-A'/2, -B', -C'/2) are scaled by log2 e (rounded to
+// FP32) once when the entry is staged, p is assembled per pixel from them, and 2^p is the
+// hardware base-2 exponential (PTX ex2.approx, flush-to-zero: a result that would be denormal
+// becomes zero, and o G is then below 1/255 either way).  p has the sign of q, so the
+// "power > 0" guard reads p.
+__device__ __forceinline__ float4 power_factors(const float4& conic)
 {
-    float x, g;
-    asm("mul.ftz.f32 %0, %1, 0f3FB8AA3B;" : "=f"(x) : "f"(power));
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(g) : "f"(x));
+    const float l2e = 1.44269502f;  // log2(e) rounded to FP32
+    return make_float4(ieee_mul(ieee_mul(-0.5f, conic.x), l2e), ieee_mul(ieee_mul(-1.0f, conic.y), l2e),
+                       ieee_mul(ieee_mul(-0.5f, conic.z), l2e), 0.0f);
+}
+
+__device__ __forceinline__ float gauss_exp2(float p)
+{
+    float g;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(g) : "f"(p));
     return g;
 }
 
-// The per-entry factors of the power, -A'/2, -B', -C'/2, computed once when an entry is
-// staged (exact scalings and a negation of the record's conic).
-__device__ __forceinline__ float4 power_factors(const float4& conic)
-{
-    return make_float4(ieee_mul(-0.5f, conic.x), ieee_mul(-1.0f, conic.y), ieee_mul(-0.5f, conic.z), 0.0f);
-}
-
+// p at a lane's two pixels (px, py0) and (px, py1), which share dx, from the entry's staged
+// factors nf (power_factors).
 __device__ __forceinline__ void pair_power2(const float4& a, const float4& nf, float fpx, float fpy0, float fpy1,
                                             float* pw0, float* pw1, float* dx_out, float* dy0_out, float* dy1_out)
 {
     const float dx = ieee_sub(a.x, fpx), dy0 = ieee_sub(a.y, fpy0), dy1 = ieee_sub(a.y, fpy1);
-    const float hC = nf.z;                               // -C'/2
-    const float ax = ieee_mul(ieee_mul(nf.x, dx), dx);   // -A' dx^2 / 2
-    const float nbx = ieee_mul(nf.y, dx);                // -B' dx
+    const float hC = nf.z;                               // -C'/2 log2 e
+    const float ax = ieee_mul(ieee_mul(nf.x, dx), dx);   // -A' dx^2 / 2 log2 e
+    const float nbx = ieee_mul(nf.y, dx);                // -B' dx log2 e
     *pw0 = ieee_fma(ieee_mul(hC, dy0), dy0, ieee_fma(nbx, dy0, ax));
     *pw1 = ieee_fma(ieee_mul(hC, dy1), dy1, ieee_fma(nbx, dy1, ax));
     *dx_out = dx;
@@ -158,7 +160,7 @@ struct FwdPixel {
     bool done = false;
     __device__ __forceinline__ bool blend(float power, float o, const float4& c, uint32_t pos)
     {
-        const float alpha = fminf(0.99f, __fmul_rn(o, gauss_exp(power)));
+        const float alpha = fminf(0.99f, __fmul_rn(o, gauss_exp2(power)));
         const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
         const bool ok = !done && !(power > 0.0f) && !(alpha < 1.0f / 255.0f);
         const bool stop = ok && Tn < 1e-4f;
@@ -197,7 +199,7 @@ struct BwdPixel {
     __device__ __forceinline__ bool replay(float power, float dx, float dy, float o, const float4& c, uint32_t lp,
                                            float* m)
     {
-        const float G = gauss_exp(power);
+        const float G = gauss_exp2(power);
         const float og = __fmul_rn(o, G);
         const float alpha = fminf(0.99f, og);
         const bool use = lp < nc && !(power > 0.0f) && !(alpha < 1.0f / 255.0f);
