@@ -161,7 +161,7 @@ struct FwdPixel {
     __device__ __forceinline__ bool blend(float power, float o, const float4& c, uint32_t pos)
     {
         const float alpha = fminf(0.99f, __fmul_rn(o, gauss_exp2(power)));
-        const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+        const float Tn = ieee_fma(-alpha, T, T);  // T (1 - alpha), rounded once
         const bool ok = !done && !(power > 0.0f) && !(alpha < 1.0f / 255.0f);
         const bool stop = ok && Tn < 1e-4f;
         const bool use = ok && !stop;
