@@ -107,7 +107,10 @@ typedef struct cgs_config {
 /* A batch of n_views equally sized views rendered together, and the caller-owned device
  * workspace holding its intermediate state (kept for the backward).  n_cap bounds the
  * selected Gaussians summed over the views (< 2^31); k_cap bounds the (tile, Gaussian)
- * entries summed over the views (< 2^30).  Size ws with cgs_frame_workspace_bytes. */
+ * entries summed over the views (< 2^30).  Size ws with cgs_frame_workspace_bytes and fill
+ * it with zeros once, before its first use: the backward's per-Gaussian accumulators are
+ * kept at zero between backwards by the library (each backward clears what it added), not
+ * cleared by every forward. */
 typedef struct cgs_frame {
     void* ws;
     int64_t ws_bytes;

@@ -66,7 +66,7 @@ __device__ __forceinline__ void prefetch_rows(const cgs_scene& S, long long g)
 //            is not run by warps whose lanes are mostly culled): covariance,
 //            radius, tile rect; for the visible ones the projected record (screen-space part
 //            and the view-dependent SH colour, Sec. 3.1, its coefficients read as they are
-//            used), the rect, the (view, depth) sort key and cleared gradient accumulators
+//            used), the rect and the (view, depth) sort key
 //   phase 3  compaction and duplication: the CTA sums its visible count and tiles touched
 //            (warp ballots and shuffles, then the warp totals in shared memory) and reserves a
 //            range of the visible list and of the entry buffer with one atomic add each; the
@@ -196,10 +196,6 @@ __global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM)
                         sh_colour_streamed<DEG>(m, c, S, g, rgb);
                         L.rec[3 * (size_t)j + 2] = make_float4(rgb[0], rgb[1], rgb[2], tq);
                         L.pkey[j] = ((unsigned long long)(uint32_t)v << 32) | __float_as_uint(p.tz);
-                        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                        L.gs[3 * (size_t)j] = z4;
-                        L.gs[3 * (size_t)j + 1] = z4;
-                        L.gs[3 * (size_t)j + 2] = z4;
                     }
                 }
                 L.tt[j] = tt;

@@ -102,7 +102,7 @@ class Frame:
         nbytes = _c.cgs_frame_workspace_bytes(n_views, width, height, tile, n_blocks, n_cap, k_cap)
         if nbytes <= 0:
             raise ValueError("invalid frame dimensions")
-        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.ws = torch.zeros(nbytes, dtype=torch.uint8, device=device)  # zero-filled once (cgs_frame)
         f = _c.cgs_frame()
         f.ws = self.ws.data_ptr()
         f.ws_bytes = nbytes
