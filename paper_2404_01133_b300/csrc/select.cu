@@ -120,8 +120,13 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Layout L, cgs_scene S, c
     __shared__ bool s_last;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = atomicAdd(&L.sel_done[v], 1u) == gridDim.x - 1u;
+        // a view handled by one CTA needs no hand-off
+        if (gridDim.x > 1) {
+            __threadfence();
+            s_last = atomicAdd(&L.sel_done[v], 1u) == gridDim.x - 1u;
+        } else {
+            s_last = true;
+        }
     }
     __syncthreads();
     if (!s_last) return;
@@ -161,8 +166,12 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Layout L, cgs_scene S, c
         L.n_seg[v] = (uint32_t)ns;
         L.view_cnt[v] = (uint32_t)(acc < 0xffffffffull ? acc : 0xffffffffull);
         // the last view to get here writes the per-view prefix
-        __threadfence();
-        s_last = atomicAdd(&L.hdr->ctr[CTR_SELECT], 1u) == (uint32_t)L.V - 1u;
+        if (L.V > 1) {
+            __threadfence();
+            s_last = atomicAdd(&L.hdr->ctr[CTR_SELECT], 1u) == (uint32_t)L.V - 1u;
+        } else {
+            s_last = true;
+        }
     }
     __syncthreads();
     if (!s_last) return;
