@@ -69,6 +69,8 @@ def parse_args():
     ap.add_argument("--batched-views", type=int, default=8)
     ap.add_argument("--lod-n", type=int, default=20_000_000, help="Gaussians of the LoD city (lod20m)")
     ap.add_argument("--lod-heights", default="50,200,500,1000,2000", help="camera heights in m (lod20m)")
+    ap.add_argument("--lod-batch", type=int, default=128,
+                    help="compositing batch depth of the LoD workloads (128 measured best over the height sweep)")
     return ap.parse_args()
 
 
@@ -782,8 +784,8 @@ def run_lod20m(args, world):
     t_gen = time.time() - t0
     ds = ta.DeviceScene(sc)
     ds.compute_block_bounds(4.0)
-    cfg = ta.make_config(tile=16, batch=256, lod_dist=(200.0, 600.0))
-    cfg_pt = ta.make_config(tile=16, batch=256, lod_dist=(200.0, 600.0), lod_mode=cgs.CGS_LOD_POINT)
+    cfg = ta.make_config(tile=16, batch=args.lod_batch, lod_dist=(200.0, 600.0))
+    cfg_pt = ta.make_config(tile=16, batch=args.lod_batch, lod_dist=(200.0, 600.0), lod_mode=cgs.CGS_LOD_POINT)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     nb = ds.n_blocks
     rows = []
@@ -1075,7 +1077,7 @@ def run_lodqueue(args, world):
     cams = synth.lod_pose_queue(sc["side"])
     ds = ta.DeviceScene(sc)
     ds.compute_block_bounds(4.0)
-    cfg = ta.make_config(tile=16, batch=256, lod_dist=(200.0, 600.0))
+    cfg = ta.make_config(tile=16, batch=args.lod_batch, lod_dist=(200.0, 600.0))
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     sel, ent = ta.frame_counts(ds, cams, 1920, 1080)
     V = len(cams)

@@ -1,7 +1,7 @@
 """GPU parity of the block-LoD workload at its full size, in the benchmark's launch
 configuration: the 20M-Gaussian, 8 x 8-block, 3-level city (Sec. 3.3) rendered top-down at
 1920x1080 from 50 to 2000 m with MAD block bounds (Eq. 7, n_MAD = 4), distance intervals
-200 / 600 m, 16 x 16 tiles and batches of 256.  Block bounds and every view's selected list
+200 / 600 m, 16 x 16 tiles and batches of 128.  Block bounds and every view's selected list
 are compared whole and bit-exact; two heights also compare every tile key, value and range,
 and the pixels of a band of tile rows, against the oracle.  The 64-pose queue, batched as the
 benchmark batches it, is checked view by view against one-view renders."""
@@ -28,7 +28,7 @@ def city():
 
 
 def render_view(ds, cam):
-    cfg = ta.make_config(tile=16, batch=256, lod_dist=(200.0, 600.0))
+    cfg = ta.make_config(tile=16, batch=128, lod_dist=(200.0, 600.0))
     sel, ent = ta.frame_counts(ds, [cam], 1920, 1080, cfg=cfg)
     fr = ta.Frame(1, 1920, 1080, 16, ds.n_blocks, int(sel[0] * 1.02) + 1024, int(ent[0] * 1.05) + 65536)
     img, T, nc = ta.render_forward(ds, fr, cfg, ta.cameras_device([cam]))
@@ -102,7 +102,7 @@ def test_full_size_pose_queue_batched_equals_single_views(city):
     bit (image, T, n_contrib), and the batched selections add up to the per-view ones."""
     sc, _, ds, _ = city
     cams = synth.lod_pose_queue(sc["side"])
-    cfg = ta.make_config(tile=16, batch=256, lod_dist=(200.0, 600.0))
+    cfg = ta.make_config(tile=16, batch=128, lod_dist=(200.0, 600.0))
     sel, ent = ta.frame_counts(ds, cams, 1920, 1080, cfg=cfg)
     groups = ta.waves(sel, ent, n_cap_max=200_000_000, k_cap_max=(1 << 30) - 1)
     sample = {0, 17, 40, 63}
