@@ -24,24 +24,44 @@ __device__ __forceinline__ void cull_extent(float o, float A, float B, float C, 
     *tq = t;
 }
 
-// Conservative test that Gaussian (mean m, scales s) cannot touch the view's image: its tile
-// rect would be empty.  The 2D covariance is J W Sigma3D W^T J^T + 0.3 I with Sigma3D's
-// eigenvalues s_k^2, so its largest eigenvalue is at most |J|_F^2 max s_k^2 + 0.3; the radius
-// of the exact path, ceil(3 sqrt(lam1)) with lam1 <= that bound + 0.32 (the 0.1 floor of the
-// discriminant), is covered by rb with 1% and 2-pixel slack far above FP32 rounding.  True
-// only when the exact path's rect is certainly empty (a NaN anywhere keeps the Gaussian).
-__device__ __forceinline__ bool surely_off_screen(const float m[3], const float s[3], const cgs_camera& c,
-                                                  float tx, float ty, float tz, int W, int H)
+// Conservative test that a Gaussian (camera-space centre t, largest absolute scale sm) cannot
+// touch the view's image: its tile rect would be empty.  The 2D covariance is
+// J W Sigma3D W^T J^T + 0.3 I with Sigma3D's eigenvalues s_k^2, so its largest eigenvalue is
+// at most |J|_F^2 max s_k^2 + 0.3; the radius of the exact path, ceil(3 sqrt(lam1)) with
+// lam1 <= that bound + 0.32 (the 0.1 floor of the discriminant), is covered by rb with 1% and
+// 2-pixel slack.  The test multiplies by one reciprocal of tz instead of dividing: its error
+// and FP32 rounding, a few units in the last place, lie far inside that slack.  True only when
+// the exact path's rect is certainly empty (a NaN anywhere keeps the Gaussian).
+__device__ __forceinline__ bool surely_off_screen(float sm, const cgs_camera& c, float tx, float ty, float tz, int W,
+                                                  int H)
 {
+    const float itz = __frcp_rn(tz);
     const float limx = 1.3f * ((0.5f * (float)c.width) / c.fx), limy = 1.3f * ((0.5f * (float)c.height) / c.fy);
-    const float xzc = fminf(fmaxf(tx / tz, -limx), limx), yzc = fminf(fmaxf(ty / tz, -limy), limy);
-    const float j00 = c.fx / tz, j11 = c.fy / tz, j02 = c.fx * xzc / tz, j12 = c.fy * yzc / tz;
+    const float xzc = fminf(fmaxf(tx * itz, -limx), limx), yzc = fminf(fmaxf(ty * itz, -limy), limy);
+    const float j00 = c.fx * itz, j11 = c.fy * itz, j02 = j00 * xzc, j12 = j11 * yzc;
     const float jn = j00 * j00 + j02 * j02 + j11 * j11 + j12 * j12;
-    const float sm = fmaxf(fmaxf(fabsf(s[0]), fabsf(s[1])), fabsf(s[2]));
     const float rb = 3.0f * sqrtf((jn * sm * sm + 0.3f) * 1.01f + 0.33f) * 1.01f + 2.0f;
-    const float u = (c.fx * tx) / tz + c.cx, v = (c.fy * ty) / tz + c.cy;
-    (void)m;
+    const float u = j00 * tx + c.cx, v = j11 * ty + c.cy;
     return u + rb < 0.0f || u - rb > (float)(W - 1) || v + rb < 0.0f || v - rb > (float)(H - 1);
+}
+
+// Largest absolute scale of Gaussian g (FP32 or FP16 storage): the only attribute the
+// off-screen test reads besides the mean.
+__device__ __forceinline__ float load_max_scale(const cgs_scene& S, long long g)
+{
+    float s0, s1, s2;
+    if (S.attr_fp16) {
+        const uint2 a = __ldg(reinterpret_cast<const uint2*>(S.scale) + g);
+        s0 = h2f(a.x & 0xffffu);
+        s1 = h2f(a.x >> 16);
+        s2 = h2f(a.y & 0xffffu);
+    } else {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(S.scale) + g);
+        s0 = a.x;
+        s1 = a.y;
+        s2 = a.z;
+    }
+    return fmaxf(fmaxf(fabsf(s0), fabsf(s1)), fabsf(s2));
 }
 
 // L2 prefetch of the rows phase 2 reads for a candidate: its SH coefficients (one 192-byte
@@ -132,11 +152,10 @@ __global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM)
                     keep = (long long)rank < S.level_count[(long long)blk * S.n_levels + lv];
                 }
                 if (keep) {
-                    float s[3], q[4];
-                    load_scale_quat(S, g, s, q);
+                    const float sm = load_max_scale(S, g);
                     const float tx = ((c.R[0] * m[0] + c.R[1] * m[1]) + c.R[2] * m[2]) + c.t[0];
                     const float ty = ((c.R[3] * m[0] + c.R[4] * m[1]) + c.R[5] * m[2]) + c.t[1];
-                    keep = !surely_off_screen(m, s, c, tx, ty, tz, L.W, L.H);
+                    keep = !surely_off_screen(sm, c, tx, ty, tz, L.W, L.H);
                 }
                 cand = keep;
                 if (!cand) L.tt[j] = 0;
