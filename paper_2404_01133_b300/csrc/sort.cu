@@ -148,12 +148,14 @@ __device__ __forceinline__ void tile_sort_regs(const Layout& L, unsigned long lo
     }
 }
 
-constexpr int RANK_MAX = TS_THREADS;  // keys per tile sorted by ranking
+constexpr int RANK_MAX = TS_THREADS;  // keys per tile sorted by this kernel
+constexpr int RANK_ONLY = 128;        // up to this many keys by ranking, above by a bitonic sort
 
-// One CTA per (view, tile).  Up to RANK_MAX keys: every thread ranks one key against all keys
-// of the tile in shared memory (keys are distinct, so the rank is the output slot); longer
-// tiles are listed for the long-tile kernel, kept apart so the common short tiles run at full
-// occupancy.
+// One CTA per (view, tile).  Up to RANK_ONLY keys: every thread ranks one key against all keys
+// of the tile in shared memory (keys are distinct, so the rank is the output slot; n^2
+// comparisons); up to RANK_MAX keys: a bitonic sort of 256 keys held one per thread (n log^2 n,
+// fewer operations above about 128 keys); longer tiles are listed for the long-tile kernel,
+// kept apart so the common short tiles run at full occupancy.
 __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(Layout L)
 {
     __shared__ unsigned long long s[RANK_MAX];
@@ -162,6 +164,10 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(Layout L)
     if (n == 0) return;
     if (n > (uint32_t)RANK_MAX) {
         if (threadIdx.x == 0) L.big[atomicAdd(&L.hdr->n_big, 1u)] = t;
+        return;
+    }
+    if (n > (uint32_t)RANK_ONLY) {
+        tile_sort_regs<TS_THREADS, 1>(L, s, t, st, n);
         return;
     }
     {

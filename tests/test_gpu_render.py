@@ -126,11 +126,11 @@ def test_long_tile_lists_use_the_merge_path(n):
     assert lens.max() > 2048
 
 
-@pytest.mark.parametrize("n", [1, 31, 32, 33, 255, 256, 257, 2048, 2049, 4096, 4097])
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 128, 129, 255, 256, 257, 2048, 2049, 4096, 4097])
 def test_tile_lengths_at_sort_path_bounds(n):
-    """One 16 x 16 tile holding every Gaussian: lengths on both sides of the ranking sort (256
-    keys), the per-tile shared-memory sort (2048) and the long-tile kernel's shared-memory
-    sort (4096, beyond which it merges chunks) stay bit-exact."""
+    """One 16 x 16 tile holding every Gaussian: lengths on both sides of the ranking sort (128
+    keys), the short-tile bitonic sort (256), the long-tile kernel's register sort (2048) and
+    its shared-memory sort (4096, beyond which it merges chunks) stay bit-exact."""
     sc = synth.single_block(synth.random_cube_scene(n, seed=100 + n, sh_degree=0, extent=0.2, log_scale_mu=-2.5))
     cam = synth.small_scene_camera(16, 16, f=30.0, dist=3.0)
     g = gpu_render(sc, [cam])
