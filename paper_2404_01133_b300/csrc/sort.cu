@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(Layout L)
 // global scratch (the entry buffer, free after the scatter); with distinct keys, an element's
 // output position is its rank in its own run plus the number of smaller keys in the other
 // run.
-constexpr int TB_THREADS = 512;
+constexpr int TB_THREADS = 256;
 __global__ void __launch_bounds__(TB_THREADS) k_tile_sort_large(Layout L)
 {
     __shared__ unsigned long long s[LT_CAP];
@@ -206,9 +206,10 @@ __global__ void __launch_bounds__(TB_THREADS) k_tile_sort_large(Layout L)
         const uint32_t t = L.big[item];
         const uint32_t st = L.ranges[2 * (size_t)t], n = L.ranges[2 * (size_t)t + 1] - st;
         if (n <= (uint32_t)TS_CAP) {
-            if (n <= (uint32_t)TB_THREADS) tile_sort_regs<TB_THREADS, 1>(L, s, t, st, n);
-            else if (n <= 2u * TB_THREADS) tile_sort_regs<TB_THREADS, 2>(L, s, t, st, n);
-            else tile_sort_regs<TB_THREADS, 4>(L, s, t, st, n);
+            // listed tiles hold more than 256 keys: two, four or eight keys per thread
+            if (n <= 2u * TB_THREADS) tile_sort_regs<TB_THREADS, 2>(L, s, t, st, n);
+            else if (n <= 4u * TB_THREADS) tile_sort_regs<TB_THREADS, 4>(L, s, t, st, n);
+            else tile_sort_regs<TB_THREADS, 8>(L, s, t, st, n);
             __syncthreads();
             continue;
         }
@@ -275,7 +276,7 @@ int launch_tile_sort(const Layout& L, int n_sm, cudaStream_t st)
 {
     const long long vt = (long long)L.V * L.T;
     k_tile_sort<<<(unsigned)vt, TS_THREADS, 0, st>>>(L);
-    k_tile_sort_large<<<(unsigned)(3 * n_sm), TB_THREADS, 0, st>>>(L);  // three 512-thread CTAs fit an SM
+    k_tile_sort_large<<<(unsigned)(6 * n_sm), TB_THREADS, 0, st>>>(L);  // six 256-thread CTAs fit an SM
     return 2;
 }
 
