@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256) k_scatter(Layout L)
     }
 }
 
-constexpr int TS_THREADS = 256;
+constexpr int TS_THREADS = 128;
 constexpr int TS_CAP = 2048;  // keys per tile sorted in registers by the long-tile kernel
 constexpr int LT_CAP = 4096;  // keys per chunk of the long-tile kernel
 
@@ -148,12 +148,12 @@ __device__ __forceinline__ void tile_sort_regs(const Layout& L, unsigned long lo
     }
 }
 
-constexpr int RANK_MAX = TS_THREADS;  // keys per tile sorted by this kernel
-constexpr int RANK_ONLY = 128;        // up to this many keys by ranking, above by a bitonic sort
+constexpr int RANK_MAX = 2 * TS_THREADS;  // keys per tile sorted by this kernel
+constexpr int RANK_ONLY = TS_THREADS;     // up to this many keys by ranking, above by a bitonic sort
 
 // One CTA per (view, tile).  Up to RANK_ONLY keys: every thread ranks one key against all keys
 // of the tile in shared memory (keys are distinct, so the rank is the output slot; n^2
-// comparisons); up to RANK_MAX keys: a bitonic sort of 256 keys held one per thread (n log^2 n,
+// comparisons); up to RANK_MAX keys: a bitonic sort of 256 keys held two per thread (n log^2 n,
 // fewer operations above about 128 keys); longer tiles are listed for the long-tile kernel,
 // kept apart so the common short tiles run at full occupancy.
 __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(Layout L)
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(Layout L)
         return;
     }
     if (n > (uint32_t)RANK_ONLY) {
-        tile_sort_regs<TS_THREADS, 1>(L, s, t, st, n);
+        tile_sort_regs<TS_THREADS, 2>(L, s, t, st, n);
         return;
     }
     {
