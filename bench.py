@@ -49,8 +49,8 @@ FP32_OPS_PER_CONTRIB_PAIR_BWD = 45
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels on this
 # workload (profiles/k_render_city1m.md).  A kernel absent here reports traffic null; an entry
 # must be removed when its kernel changes.
-NCU_TRAFFIC_BYTES = {"render": 14.699520e6 + 0.794368e6, "render_bwd": 65.581312e6 + 1.374208e6,
-                     "project_bwd": 69.170688e6 + 3.620352e6, "loss": 31.120896e6 + 0.033024e6}
+NCU_TRAFFIC_BYTES = {"render": 14.700032e6 + 0.851712e6, "render_bwd": 65.590016e6 + 1.423872e6,
+                     "project_bwd": 69.171968e6 + 3.555584e6, "loss": 31.120896e6 + 0.033024e6}
 
 
 def parse_args():
