@@ -378,9 +378,9 @@ def run_ours(args, world, rank, local):
     work = {
         # algorithmic bytes per launch (HBM-bound stages)
         # projection: mean+opacity read, scene index and tiles-touched write for every selected
-        # Gaussian; scale, rotation and SH read, three records, rect, key, visible-list slot and
-        # cleared gradient rows written for the visible ones; one 8-byte entry per tile touched
-        "project": ("hbm", n_sel * (16 + 4 + 4) + n_vis * (32 + 12 * nc_coef + 48 + 8 + 8 + 4 + 48) + k_ent * 8),
+        # Gaussian; scale, rotation and SH read, three records, rect, key and visible-list slot
+        # written for the visible ones; one 8-byte entry per tile touched
+        "project": ("hbm", n_sel * (16 + 4 + 4) + n_vis * (32 + 12 * nc_coef + 48 + 8 + 8 + 4) + k_ent * 8),
         # binning: per tile its count read and range written; per entry read the entry, write
         # the key
         "duplicate": ("hbm", n_tiles * 12 + k_ent * (8 + 8)),
