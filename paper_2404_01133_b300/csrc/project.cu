@@ -99,7 +99,7 @@ __device__ __forceinline__ void prefetch_rows(const cgs_scene& S, long long g)
 // (depth, index), the backward works per Gaussian).  DEG is the scene's SH degree.
 constexpr int PROJ_THREADS = 256;
 constexpr int PROJ_WARPS = PROJ_THREADS / 32;
-constexpr int PROJ_ITEMS = 4;  // selected Gaussians per thread in phase 1
+constexpr int PROJ_ITEMS = 2;  // selected Gaussians per thread in phase 1
 constexpr int PROJ_STEP = PROJ_THREADS * PROJ_ITEMS;
 constexpr int PROJ_CTAS_PER_SM = 5;  // latency-bound: registers capped so five CTAs fit an SM
 
