@@ -158,7 +158,8 @@ __global__ void __launch_bounds__(PB_THREADS, 6) k_project_bwd(Layout L, cgs_sce
             gb = L.gs[3 * (size_t)j + 1];
             gc4 = L.gs[3 * (size_t)j + 2];
         }
-        __syncthreads();  // both roles have read the accumulators; clear them for the next backward
+        __syncthreads();  // both roles have read the accumulators; clear them (no forward does: each
+                          // backward leaves every row the compositing backward added to at zero)
         float gm[3] = {0.f, 0.f, 0.f}, gsv[3] = {0.f, 0.f, 0.f}, gqn[4] = {0.f, 0.f, 0.f, 0.f};
         long long g = 0;
         if (valid) {
