@@ -34,7 +34,7 @@ METRIC = "fwd / fwd+bwd Mpix/s at 1080p, 20M-Gaussian LoD FPS, batched vs plain"
 UNIT = "Mpix/s"
 WORKLOAD = "city-1M-SH3 1920x1080 fwd+bwd (L1), 16x16 tiles"
 L2_FLUSH_BYTES = 256 << 20
-# Algorithmic work per unit (SURVEY 8d).  Compositing: the unit is the EVALUATED pair, an
+# Algorithmic work per unit.  Compositing: the unit is the EVALUATED pair, an
 # entry of a pixel's tile list visited up to and including the pixel's stop (as the plain
 # per-pixel loop of Eq. 1 visits them); ~17 FP32-pipe instructions per pair forward and ~45
 # backward, plus one SFU exp each.  The kernels skip, per warp, entries that cannot pass the
@@ -398,7 +398,7 @@ def run_ours(args, world, rank, local):
         # L1: image read (4 B), 8-bit target read (1 B), gradient written (4 B)
         "loss": ("hbm", W * H * 3 * 9),
     }
-    # overall fraction (SURVEY 8d): time every stage would take at its binding peak / step time
+    # overall fraction: time every stage would take at its binding peak / step time
     ideal_ms = sum((amt / (peaks["hbm_gbs"] * 1e9) if b == "hbm" else amt / (alu_peak * 1e12)) * 1e3
                    for b, amt in work.values())
     ideal_fwd_ms = sum((amt / (peaks["hbm_gbs"] * 1e9) if b == "hbm" else amt / (alu_peak * 1e12)) * 1e3
