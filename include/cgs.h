@@ -271,6 +271,22 @@ int32_t cgs_frame_buffer(const cgs_frame* frame, int32_t which, void** d_ptr, in
 int32_t cgs_timing_enable(int32_t on);
 int32_t cgs_timing_read(double* ms /*[CGS_N_STAGES]*/, int64_t* count /*[CGS_N_STAGES]*/);
 
+/* Measured issue-rate peaks of the current device, for roofline denominators (instrumentation;
+ * the paper has no counterpart).  Runs three loops on every SM -- scalar FP32 fused
+ * multiply-adds, packed FP32x2 fused multiply-adds, and base-2 exponentials (ex2.approx, the
+ * compositing kernels' one transcendental per pair) -- each timed with CUDA events on
+ * `stream` (best of three after a warm-up), and SYNCHRONISES the stream.  rates[0] = FP32 lane
+ * operations per second (one FMA instruction of one lane = 1), rates[1] = the same counted
+ * from the packed loop (one packed instruction of one lane = 2), rates[2] = exponentials per
+ * second.  n_rates >= 3.  d_scratch is a device array of at least (SM count x 2048) floats
+ * that the loops overwrite. */
+int32_t cgs_measure_peaks(double* rates, int32_t n_rates, float* d_scratch, int64_t scratch_floats, void* stream);
+
+/* Test hook: d_g[i] = 2^d_p[i] evaluated exactly as both compositing kernels evaluate the
+ * Gaussian falloff of Eq. 1 (the hardware base-2 exponential, results below the smallest normal
+ * FP32 value flushed to zero), so that tests can bound its error.  n >= 0 values; asynchronous. */
+int32_t cgs_debug_exp2(const float* d_p, int64_t n, float* d_g, void* stream);
+
 /* Number of CUDA kernels this library has launched in the process so far (host counter). */
 int64_t cgs_kernel_launches(void);
 

@@ -127,6 +127,10 @@ def lib():
         L.cgs_partition_status.argtypes = [vp, vp]
         L.cgs_gather_rows.restype = i32
         L.cgs_gather_rows.argtypes = [vp, vp, i64, vp, i64, vp]
+        L.cgs_debug_exp2.restype = i32
+        L.cgs_debug_exp2.argtypes = [vp, i64, vp, vp]
+        L.cgs_measure_peaks.restype = i32
+        L.cgs_measure_peaks.argtypes = [P(C.c_double), i32, vp, i64, vp]
         _lib = L
     return _lib
 
@@ -348,3 +352,18 @@ def cgs_levels_status(d_ws, stream=None):
 def cgs_ssim(d_a, a_stride, d_b, n_pairs, channels, width, height, d_ssim, d_map=None, stream=None):
     return _check(lib().cgs_ssim(_ptr(d_a), a_stride, _ptr(d_b), n_pairs, channels, width, height, _ptr(d_ssim),
                                  _ptr(d_map), _stream(stream)), "cgs_ssim")
+
+
+# ---------------------------------------------------------------------------------------
+# instrumentation
+# ---------------------------------------------------------------------------------------
+def cgs_debug_exp2(d_p, n, d_g, stream=None):
+    return _check(lib().cgs_debug_exp2(_ptr(d_p), n, _ptr(d_g), _stream(stream)), "cgs_debug_exp2")
+
+
+def cgs_measure_peaks(d_scratch, stream=None):
+    """Measured issue rates of the current device (synchronises): FP32 lane operations per
+    second from the scalar and the packed FMA loops, and base-2 exponentials per second."""
+    r = (C.c_double * 3)()
+    _check(lib().cgs_measure_peaks(r, 3, _ptr(d_scratch), d_scratch.numel(), _stream(stream)), "cgs_measure_peaks")
+    return {"fp32_lane_ops_s": r[0], "fp32x2_lane_ops_s": r[1], "ex2_s": r[2]}

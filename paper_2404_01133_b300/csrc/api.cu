@@ -23,6 +23,7 @@ void launch_project_bwd(const Layout& L, const cgs_scene& S, const cgs_camera* c
 void launch_l1(const float* img, const float* tgt, long long n, float* loss, float* grad, int n_sm, cudaStream_t st);
 void launch_l1_u8(const float* img, const uint8_t* tgt, long long n, float* loss, float* grad, int n_sm,
                   cudaStream_t st);
+void launch_debug_exp2(const float* p, long long n, float* g, int n_sm, cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------
 // launch counting and optional per-stage event timing
@@ -429,6 +430,15 @@ int32_t cgs_timing_read(double* ms, int64_t* count)
 }
 
 int64_t cgs_kernel_launches(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+int32_t cgs_debug_exp2(const float* d_p, int64_t n, float* d_g, void* stream)
+{
+    if (!d_p || !d_g || n < 0) return CGS_ERR_INVALID_ARGUMENT;
+    if (n == 0) return CGS_OK;
+    launch_debug_exp2(d_p, n, d_g, sm_count(), (cudaStream_t)stream);
+    counted(1);
+    return cudaGetLastError() == cudaSuccess ? CGS_OK : CGS_ERR_CUDA;
+}
 
 int32_t cgs_frame_buffer(const cgs_frame* frame, int32_t which, void** d_ptr, int64_t* count)
 {

@@ -142,6 +142,22 @@ bool launch_render_fwd(const Layout& L, const cgs_config& c, float* img, float* 
     return false;
 }
 
+// The falloff exponential of both compositing kernels (gauss_exp2) over an array, for the
+// tests that bound its error.
+__global__ void __launch_bounds__(256) k_debug_exp2(const float* __restrict__ p, long long n, float* __restrict__ g)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        g[i] = gauss_exp2(p[i]);
+}
+
+void launch_debug_exp2(const float* p, long long n, float* g, int n_sm, cudaStream_t st)
+{
+    long long grid = (n + 255) / 256;
+    if (grid > (long long)n_sm * 16) grid = (long long)n_sm * 16;
+    if (grid < 1) grid = 1;
+    k_debug_exp2<<<(unsigned)grid, 256, 0, st>>>(p, n, g);
+}
+
 // L1 loss: loss += mean |img - target|, grad = sign(img - target) / count.  The partial
 // sums are reduced per CTA, so the loss takes one atomic per CTA.
 // Target value of an FP32 target, or of an 8-bit one (channel value t stands for t / 255,
