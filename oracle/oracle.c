@@ -310,8 +310,27 @@ void orc_tile_ranges(int64_t k, const uint64_t* keys, int32_t n_tiles, int64_t* 
 /* ------------------------------------------------------------------------------------- */
 /* Compositing, Eq. 1, one pixel at a time over its tile's sorted list.                    */
 /* ------------------------------------------------------------------------------------- */
-#define AMB_ALPHA_REL 1e-4   /* |o exp(power) - 1/255| below this relative margin: ambiguous */
-#define AMB_T_REL 2e-3       /* |T (1 - alpha) - 1e-4| below this relative margin: ambiguous */
+/* Decision margins for the parity comparison (not part of Eq. 1).  Another FP32 evaluation of
+ * the same pair -- the power assembled in a different rounding order (from per-entry factors
+ * pre-scaled by log2 e), the falloff by a hardware base-2 exponential, the transmittance by one
+ * fused multiply-add -- agrees with this one only up to bounded rounding, so a pixel whose
+ * discrete decisions (the sign test, the 1/255 skip, the 1e-4 stop) lie within twice these
+ * bounds of their thresholds may legitimately take the other branch: it is flagged ambiguous.
+ *   power:  |d power| <= AMB_POW_U * u * S, S = |A'dx^2/2| + |B'dx dy| + |C'dy^2/2|, u = 2^-24:
+ *           here each term takes two product roundings, the sums and the final difference
+ *           one each (at most 4u S); the other order takes at most three and a half per term
+ *           (the factor's scaling by log2 e, its two products, half a unit for log2 e itself)
+ *           and two fused sums (at most 5.5u S);
+ *   alpha:  |d(o exp(power))| / (o exp(power)) <= |d power| + AMB_EXP2_REL + 4u (the
+ *           exponential's relative error and the roundings of the exponential and the opacity
+ *           product on either side);
+ *   T:      relative error of the transmittance after k blends <= sum over blends of
+ *           alpha e_alpha / (1 - alpha) + 3u (a relative error e_alpha of alpha is amplified by
+ *           alpha / (1 - alpha) in 1 - alpha; the product rounds once or twice); a clamped
+ *           alpha (o exp(power) above 0.99 by more than its margin) is exactly 0.99. */
+#define AMB_U 5.9604644775390625e-8      /* 2^-24 */
+#define AMB_POW_U 10.0
+#define AMB_EXP2_REL 4.76837158203125e-7 /* 2^-21: bound assumed for the device's ex2.approx */
 
 typedef struct {
     REAL alpha, G, T;        /* per blended entry: alpha, exp(power), transmittance before it */
@@ -330,6 +349,7 @@ static int64_t pixel_walk(const int64_t* list, int64_t len, REAL px, REAL py, co
     const REAL thr = (REAL)1 / (REAL)255;
     const REAL tmin = (REAL)0.0001;
     REAL Tr = 1;
+    double eT = 0.0; /* relative error bound of Tr (decision margins only) */
     C[0] = C[1] = C[2] = 0;
     int64_t nb = 0, last = 0, vis = 0;
     for (int64_t p = 0; p < len; p++) {
@@ -338,16 +358,30 @@ static int64_t pixel_walk(const int64_t* list, int64_t len, REAL px, REAL py, co
         REAL dx = xy[2 * g] - px, dy = xy[2 * g + 1] - py;
         REAL a = conic[3 * g], b = conic[3 * g + 1], c = conic[3 * g + 2];
         REAL power = (REAL)-0.5 * ((a * dx) * dx + (c * dy) * dy) - (b * dx) * dy;
+        double epow = 0.0, ea = 0.0;
+        if (amb) {
+            double ddx = (double)dx, ddy = (double)dy;
+            epow = AMB_POW_U * AMB_U *
+                   (fabs(0.5 * (double)a * ddx * ddx) + fabs((double)b * ddx * ddy) + fabs(0.5 * (double)c * ddy * ddy));
+            ea = epow + AMB_EXP2_REL + 4.0 * AMB_U;
+            if (fabs((double)power) <= 2.0 * epow) *amb = 1;
+        }
         if (power > 0) { if (hash) *hash = fnv(*hash, 1); continue; }
         REAL o = mean_opac[4 * g + 3];
         REAL G = exp(power);
         REAL og = o * G;
-        if (amb && fabs((double)o * exp((double)power) - 1.0 / 255.0) < AMB_ALPHA_REL / 255.0) *amb = 1;
+        if (amb && fabs((double)og - 1.0 / 255.0) <= 2.0 * ea * (double)og) *amb = 1;
         REAL alpha = og < (REAL)0.99 ? og : (REAL)0.99;
         if (alpha < thr) { if (hash) *hash = fnv(*hash, 2); continue; }
         REAL Tn = Tr * ((REAL)1 - alpha);
-        if (amb && fabs((double)Tn - 1e-4) < AMB_T_REL * 1e-4) *amb = 1;
+        double eTn = 0.0;
+        if (amb) {
+            const double ealpha = (double)og * (1.0 - 2.0 * ea) > 0.99 ? 0.0 : ea;
+            eTn = eT + (double)alpha * ealpha / (1.0 - (double)alpha) + 3.0 * AMB_U;
+            if (fabs((double)Tn - 1e-4) <= 2.0 * eTn * (double)Tn) *amb = 1;
+        }
         if (Tn < tmin) { if (hash) *hash = fnv(*hash, 3); break; }
+        eT = eTn;
         if (hash) *hash = fnv(*hash, og > (REAL)0.99 ? 5 : 4);
         if (out) {
             out[nb].alpha = alpha; out[nb].G = G; out[nb].T = Tr; out[nb].clamped = og > (REAL)0.99;

@@ -10,9 +10,31 @@ from paper_2404_01133_b300 import torch_api as ta
 # Pixel tolerance in FP32 (spec bound) for pixels whose skip/stop decisions are not
 # within the oracle's ambiguity margins.
 PIX_ATOL = 1e-4
-# An ambiguous pixel can differ by one entry at the 1/255 threshold or one blend at the
-# 1e-4 transmittance stop: alpha * T * c <= 0.99 * 0.01 * c behind the stop, 1/255 at the skip.
-AMB_ATOL = 0.03
+# An ambiguous pixel may take the other branch of one near-threshold decision.  A flipped 1/255
+# skip changes the pixel by at most alpha T c_max <= c_max / 255 (the entry's own colour and
+# the 1 - alpha scaling of everything behind it, each at most that, with opposite signs), and
+# the 1 - 1/255 change of T it causes can flip a later 1e-4 stop, one blend of at most
+# 0.99 * 0.01 * c_max (the stop happens only once T < 1e-2).  Per unit of the largest colour:
+AMB_ATOL_PER_C = 1.0 / 255.0 + 0.0099 + 1e-4
+# Most ambiguous pixels a frame may have, per pair its compositing evaluates.  The oracle's
+# margins are rigorous rounding bounds (oracle.c): near 1/255 about 7e-6 relative on alpha for
+# these scenes, so a pair is flagged when ln(alpha) lies in a window about 1.4e-5 wide around
+# ln(1/255); measured on a B300, 0.3e-6 to 5.8e-6 of the evaluated pairs flag their pixel
+# (1.0e-6 on the 1080p city frame: 141 of its 2,073,600 pixels; the most, 5.8e-6, on scenes
+# of needle-like Gaussians, whose power terms cancel and so widen the margin).  The bound
+# keeps the margins honest: a looser margin would exempt more pixels from the 1e-4 check and
+# fail it.
+AMB_PER_PAIR_MAX = 1e-5
+AMB_MIN_ALLOWED = 4  # small frames: at most this many pixels whatever the pair count
+
+
+def amb_atol(rgb):
+    """Error bound of an ambiguous pixel for projected colours rgb (any shape)."""
+    return AMB_ATOL_PER_C * max(1.0, float(np.max(rgb))) if np.size(rgb) else AMB_ATOL_PER_C
+
+
+# backwards compatible name: the bound for colours at most 1
+AMB_ATOL = AMB_ATOL_PER_C
 
 
 def fp16_rounded(scene):
@@ -69,9 +91,10 @@ def canonical_ranges(r, first=0):
     return np.where(r[:, 1:] > r[:, :1], r - first, 0)
 
 
-def compare_image(gimg, gT, gnc, o):
+def compare_image(gimg, gT, gnc, o, rgb_max=None, label=""):
     """Pixels within PIX_ATOL and n_contrib equal where the oracle saw no near-threshold
-    decision; ambiguous pixels within AMB_ATOL.  Returns the number of ambiguous pixels."""
+    decision; ambiguous pixels within amb_atol and at most AMB_PER_PAIR_MAX per evaluated pair.  Prints
+    and returns the counts: ambiguous pixels, and those among them that actually differ."""
     amb = o["ambiguous"].astype(bool)
     img = gimg.detach().cpu().numpy()
     T = gT.detach().cpu().numpy()
@@ -83,6 +106,17 @@ def compare_image(gimg, gT, gnc, o):
     assert np.abs(T - o["final_T"])[ok].max(initial=0.0) <= PIX_ATOL
     bad = (nc != o["n_contrib"]) & ok
     assert not bad.any(), np.argwhere(bad)[:5]
-    if amb.any():
-        assert err[amb].max() <= AMB_ATOL
-    return int(amb.sum())
+    n_amb = int(amb.sum())
+    if rgb_max is None:
+        rgb_max = o["proj"]["rgb"] if "proj" in o else 1.0
+    lim = amb_atol(rgb_max)
+    differ = amb & ((err > PIX_ATOL) | (nc != o["n_contrib"]))
+    if n_amb:
+        assert err[amb].max() <= lim, (err[amb].max(), lim)
+        assert np.abs(T - o["final_T"])[amb].max() <= lim
+    assert n_amb <= max(AMB_MIN_ALLOWED, AMB_PER_PAIR_MAX * o["pairs"]), (n_amb, o["pairs"])
+    print(f"[parity{(' ' + label) if label else ''}] pixels {amb.size}, ambiguous {n_amb} "
+          f"({n_amb / amb.size:.2e} of pixels, {n_amb / max(1, o['pairs']):.2e} per evaluated pair), "
+          f"of which differing {int(differ.sum())}, "
+          f"max error there {err[amb].max(initial=0.0):.3g} (bound {lim:.3g})")
+    return n_amb

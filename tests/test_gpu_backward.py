@@ -178,7 +178,8 @@ def test_full_size_city_1m_forward_backward():
     np.testing.assert_array_equal(a["records"][vis, 8:11], pr["rgb"][vis])
     # full oracle composite (seconds), compare every pixel
     o = oracle.composite(pr, srt, cam)
-    compare_image(g["image"][0], g["final_T"][0], g["n_contrib"][0], o)
+    n_amb = compare_image(g["image"][0], g["final_T"][0], g["n_contrib"][0], o, rgb_max=pr["rgb"][vis],
+                          label="1920x1080 city, 1M Gaussians")
     # backward of the L1 loss against the seeded target; the upstream gradient is the oracle's
     tgt = synth.target_image(1, cam["width"], cam["height"])
     _, dL = oracle.l1(o["image"], tgt)

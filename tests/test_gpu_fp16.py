@@ -83,4 +83,5 @@ def test_fp16_full_size_city_1m_forward():
     np.testing.assert_array_equal(a["vals"].astype(np.int64), srt["vals"].astype(np.int64))
     np.testing.assert_array_equal(canonical_ranges(a["ranges"]), srt["ranges"])
     o = oracle.composite(pr, srt, cam)
-    compare_image(g["image"][0], g["final_T"][0], g["n_contrib"][0], o)
+    compare_image(g["image"][0], g["final_T"][0], g["n_contrib"][0], o, rgb_max=pr["rgb"],
+                  label="1920x1080 city, FP16 attributes")

@@ -12,7 +12,7 @@ import torch
 import oracle
 from paper_2404_01133_b300 import cgs, synth
 from paper_2404_01133_b300 import torch_api as ta
-from gpu_common import AMB_ATOL, PIX_ATOL, canonical_ranges
+from gpu_common import AMB_MIN_ALLOWED, AMB_PER_PAIR_MAX, PIX_ATOL, amb_atol, canonical_ranges
 
 pytestmark = pytest.mark.gpu
 
@@ -86,10 +86,19 @@ def test_full_size_lod_frame_20m(city, height):
     gi = img[0, :, y0:y1].cpu().numpy()
     err = np.abs(gi - o["image"][:, y0:y1]).max(axis=0)
     assert err[~amb].max(initial=0.0) <= PIX_ATOL
-    assert err[amb].max(initial=0.0) <= AMB_ATOL
+    lim = amb_atol(pr["rgb"][pr["tiles_touched"] > 0])
+    assert err[amb].max(initial=0.0) <= lim
     assert np.abs(T[0, y0:y1].cpu().numpy() - o["final_T"][y0:y1])[~amb].max(initial=0.0) <= PIX_ATOL
-    bad = (nc[0, y0:y1].cpu().numpy() != o["n_contrib"][y0:y1]) & ~amb
+    ncb = nc[0, y0:y1].cpu().numpy()
+    bad = (ncb != o["n_contrib"][y0:y1]) & ~amb
     assert not bad.any(), np.argwhere(bad)[:5]
+    n_amb = int(amb.sum())
+    assert n_amb <= max(AMB_MIN_ALLOWED, AMB_PER_PAIR_MAX * o["pairs"]), (n_amb, o["pairs"])
+    differ = amb & ((err > PIX_ATOL) | (ncb != o["n_contrib"][y0:y1]))
+    print(f"[parity 20M LoD frame at {height:g} m, central band] pixels {amb.size}, ambiguous {n_amb} "
+          f"({n_amb / amb.size:.2e} of pixels, {n_amb / max(1, o['pairs']):.2e} per evaluated pair), "
+          f"of which differing {int(differ.sum())}, "
+          f"max error there {err[amb].max(initial=0.0):.3g} (bound {lim:.3g})")
 
 
 def fr_tiles(fr):
