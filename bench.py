@@ -1,17 +1,29 @@
 #!/usr/bin/env python
 """Benchmark of the CityGaussian rendering hot path on B300.
 
-Default workload: one training step on the 1,000,000-Gaussian SH-3 synthetic city viewed at
-1920x1080 from 150 m, pitched 45 degrees: block LoD selection (one block), projection, depth
-sort, tile duplication, tile sort, compositing, L1 loss against a seeded target and the
-full backward.  Prints ONE JSON line.
+Default run (one JSON line): one training step on the 1,000,000-Gaussian SH-3 synthetic city
+viewed at 1920x1080 from 150 m, pitched 45 degrees (block LoD selection of one block,
+projection, duplication into tile entries, per-tile depth sort, compositing, L1 loss against a
+seeded target, full backward), and nested in the same line the other workloads of the
+benchmark's metric:
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  lod20m    block-LoD forward of the 20M-Gaussian, 8x8-block, 3-level city at 1920x1080,
+            straight down from 50 / 200 / 500 / 1000 / 2000 m: block-wise LoD against
+            point-wise LoD and against no LoD (every block at its finest level)
+  lodqueue  64 seeded poses (30-2500 m) over the same city: batched frames against 64
+            sequential one-view renders, per-frame latency p50 / p99
+  train32   batched differentiable step: 32 blocks of log-uniform 200k-3M Gaussians, 8 views
+            each at 1600x900, every view forward + L1 + backward, against one-view steps
+
+Each carries per-stage times, a roofline for its dominant kernel, the clocks of its timed
+region and a CPU baseline (the oracle, as it stands, on the host's cores).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--headline-only]
 
 N > 1 runs one independent replica per GPU (launched with torch.distributed.run): each rank
 renders the same workload; only the timing is combined (barrier + max over ranks).
-`--impl reference` times the CPU oracle (plain C, single thread) on a bounded sample of the
-same workload instead.
+`--impl reference` times the CPU oracle (plain C, threads over tile rows) on the headline
+workload instead.
 """
 from __future__ import annotations
 
@@ -23,6 +35,7 @@ import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 import numpy as np
@@ -34,23 +47,27 @@ METRIC = "fwd / fwd+bwd Mpix/s at 1080p, 20M-Gaussian LoD FPS, batched vs plain"
 UNIT = "Mpix/s"
 WORKLOAD = "city-1M-SH3 1920x1080 fwd+bwd (L1), 16x16 tiles"
 L2_FLUSH_BYTES = 256 << 20
-# Algorithmic work per unit.  Compositing: the unit is the EVALUATED pair, an
-# entry of a pixel's tile list visited up to and including the pixel's stop (as the plain
-# per-pixel loop of Eq. 1 visits them); ~17 FP32-pipe instructions per pair forward and ~45
-# backward, plus one SFU exp each.  The kernels skip, per warp, entries that cannot pass the
-# 1/255 test, so they execute fewer than this; the stricter count over CONTRIBUTING pairs
-# (19 / 45 operations per blended pair) is reported beside it.
-FP32_OPS_PER_EVAL_PAIR_FWD = 17
-FP32_OPS_PER_EVAL_PAIR_BWD = 45
-FP32_OPS_PER_CONTRIB_PAIR_FWD = 19
-FP32_OPS_PER_CONTRIB_PAIR_BWD = 45
 
+# Algorithmic FP32 work of compositing, counted as the plain per-pixel loop of Eq. 1 performs
+# it (one FP32 instruction of one lane = one operation):
+#   forward   every EVALUATED pair (the entries of a pixel's tile list up to and including
+#             its stop): offset (2), power (9), sign test (1), exponential and its scaling (2),
+#             opacity product (1), clamp (1), 1/255 test (1) = 17; a pair that blends adds the
+#             transmittance update and stop test (2), alpha T (1) and the colour (3) = 6
+#   backward  the loop walks each pixel's list from n_contrib down to the front, so it
+#             evaluates alpha again (17) for every pair before n_contrib; a pair that blended
+#             adds the gradient: T recovery (2), g.c (5), dL/dalpha (3), the running sum (2),
+#             dL/drgb (4), dL/dpower (2), the five second moments (5) and their sums with
+#             dL/do (5) = 28
+OPS_FWD_EVAL = 17
+OPS_FWD_BLEND = 6
+OPS_BWD_EVAL = 17
+OPS_BWD_GRAD = 28
 
-# DRAM bytes (read + write) per launch from one ncu capture of the current kernels on this
-# workload (profiles/k_render_city1m.md).  A kernel absent here reports traffic null; an entry
-# must be removed when its kernel changes.
-NCU_TRAFFIC_BYTES = {"render": 14.700032e6 + 0.851712e6, "render_bwd": 65.590016e6 + 1.423872e6,
-                     "project_bwd": 69.171968e6 + 3.555584e6, "loss": 31.120896e6 + 0.033024e6}
+# DRAM bytes (read + write) per launch of a kernel of the headline workload, from one ncu
+# capture of the current build (the summary committed beside the kernel profiles); a kernel
+# absent here reports traffic null.  An entry is removed when its kernel changes.
+NCU_TRAFFIC_BYTES = {}
 
 
 def parse_args():
@@ -61,16 +78,19 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, default=0, help="16 or 8; 0 = autotune tile and batch")
     ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--headline-only", action="store_true", help="skip the nested lod20m / lodqueue / train32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-fp16-compare", action="store_true")
-    ap.add_argument("--workload", default="city1m", choices=["city1m", "lod20m", "lodqueue", "train32", "partition", "levels", "assign"])
+    ap.add_argument("--workload", default="city1m",
+                    choices=["city1m", "lod20m", "lodqueue", "train32", "partition", "levels", "assign"])
     ap.add_argument("--batched-views", type=int, default=8)
-    ap.add_argument("--lod-n", type=int, default=20_000_000, help="Gaussians of the LoD city (lod20m)")
+    ap.add_argument("--lod-n", type=int, default=20_000_000, help="Gaussians of the LoD city")
     ap.add_argument("--lod-heights", default="50,200,500,1000,2000", help="camera heights in m (lod20m)")
     ap.add_argument("--lod-batch", type=int, default=128,
                     help="compositing batch depth of the LoD workloads (128 measured best over the height sweep)")
+    ap.add_argument("--train-scale", type=float, default=1.0, help="scales the Gaussian counts of train32")
     return ap.parse_args()
 
 
@@ -138,6 +158,7 @@ class ClockSampler:
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+        return self
 
     def stop(self):
         if self.proc is None:
@@ -187,8 +208,112 @@ def timed_fn(fn, k, st, flush, world, zero=None):
     return [a.elapsed_time(b) for a, b in ev], cgs.cgs_kernel_launches() - launches0
 
 
+def stage_times(fn, reps, flush=None):
+    """Per-stage milliseconds per launch (library events around every stage) over `reps` eager
+    calls of fn."""
+    import torch
+    from paper_2404_01133_b300 import cgs
+    torch.cuda.synchronize()
+    cgs.cgs_timing_enable(True)
+    for _ in range(reps):
+        if flush is not None:
+            flush.fill_(3)
+        fn()
+    torch.cuda.synchronize()
+    stg = cgs.cgs_timing_read()
+    cgs.cgs_timing_enable(False)
+    return {k: v[0] / v[1] for k, v in stg.items() if v[1]}, {k: v for k, v in stg.items() if v[1]}
+
+
 # -----------------------------------------------------------------------------------------
-# our arm
+# rooflines
+# -----------------------------------------------------------------------------------------
+def device_peaks(dev, index):
+    """Roofline denominators: HBM from the measured copy bandwidth of the B300s, FP32
+    and exponential issue rates measured on this device by the library's FMA / ex2 loops."""
+    import torch
+    from paper_2404_01133_b300 import cgs
+    p, src = load_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm = props.multi_processor_count
+    scratch = torch.empty(sm * 2048, dtype=torch.float32, device=dev)
+    clk = ClockSampler(index).start()
+    r = cgs.cgs_measure_peaks(scratch)
+    c = clk.stop()
+    del scratch
+    fp32 = max(r["fp32_lane_ops_s"], r["fp32x2_lane_ops_s"])
+    mhz = float(p.get("sm_max_mhz", 2032.0))
+    return {"hbm_gbs": float(p["hbm_gbs"]),
+            "hbm_source": f"{src}: copy bandwidth (MEASURED_PEAKS.json)" if src == "measured" else "fallback",
+            "fp32_tops": fp32 / 1e12, "fp32_scalar_tops": r["fp32_lane_ops_s"] / 1e12,
+            "fp32_packed_tops": r["fp32x2_lane_ops_s"] / 1e12, "ex2_tops": r["ex2_s"] / 1e12,
+            "fp32_source": "measured on this device: FP32 FMA loops (scalar and packed), lane operations per second",
+            "sm_count": sm, "nominal_fp32_tops": sm * 128 * mhz * 1e6 / 1e12, "clocks_during_peaks": c}
+
+
+def stage_work(counts, sum_nc, n_tiles, pixels, deg, backward=False, loss_bytes=9, packed=True):
+    """Algorithmic work per launch of every stage of a frame: (bound, amount), HBM bytes or
+    FP32 operations.  counts: the frame counters (selected, visible, entries, evaluated
+    pairs, contributing pairs); sum_nc: the sum of n_contrib over the frame's pixels."""
+    n_sel, n_vis, k, pf, pb = (int(x) for x in counts[:5])
+    nco = (deg + 1) ** 2
+    w = {
+        # projection: mean+opacity read, scene index and tiles-touched write for every selected
+        # Gaussian; scale, rotation and SH read, three records, rect, key and visible-list slot
+        # written for the visible ones; one 8-byte entry per tile touched
+        "project": ("hbm", n_sel * (16 + 4 + 4) + n_vis * (32 + 12 * nco + 48 + 8 + 8 + 4) + k * 8),
+        # tile ranges and scatter: per tile its count read and range written; per entry read
+        # the entry, write its key
+        "duplicate": ("hbm", n_tiles * 12 + k * (8 + 8)),
+        # per-tile sort: per entry read the key, write value and tile
+        "sort": ("hbm", k * (8 + 4 + 4)),
+        "render": ("alu", pf * OPS_FWD_EVAL + pb * OPS_FWD_BLEND),
+    }
+    if backward:
+        w["render_bwd"] = ("alu", int(sum_nc) * OPS_BWD_EVAL + pb * OPS_BWD_GRAD)
+        # projection backward, per visible Gaussian: read the visible-list slot, key, scene
+        # index, screen-space gradients, mean+opacity, scale, rotation and SH; write the
+        # gradient row (mean+opacity, scale, rotation, SH, and the scene index in the packed
+        # form) and clear the screen-space gradients
+        w["project_bwd"] = ("hbm", n_vis * ((4 + 8 + 4 + 48 + 16 + 16 + 16 + 12 * nco) +
+                                            (16 + 16 + 16 + 12 * nco + (8 if packed else 0) + 48)))
+        # L1: image read (4 B), target read (1 B 8-bit, 4 B FP32), gradient written (4 B)
+        w["loss"] = ("hbm", pixels * 3 * loss_bytes)
+    return w
+
+
+def ideal_ms(work, peaks, keys=None):
+    return sum((amt / (peaks["hbm_gbs"] * 1e9) if b == "hbm" else amt / (peaks["fp32_tops"] * 1e12)) * 1e3
+               for k, (b, amt) in work.items() if keys is None or k in keys)
+
+
+def stage_fracs(work, stage_ms, peaks):
+    return {k: round(ideal_ms({k: work[k]}, peaks) / stage_ms[k], 4) for k in work if stage_ms.get(k)}
+
+
+def roofline(kernel, stage_ms, work, peaks, kernel_name, traffic=None):
+    bound, amount = work[kernel]
+    t = stage_ms[kernel] * 1e-3
+    if bound == "hbm":
+        ach, peak, unit, src = amount / t / 1e9, peaks["hbm_gbs"], "GB/s", peaks["hbm_source"]
+        wdef = "algorithmic bytes per launch"
+    else:
+        ach, peak, unit, src = amount / t / 1e12, peaks["fp32_tops"], "T FP32 lane-ops/s", peaks["fp32_source"]
+        wdef = ("FP32 operations of the plain per-pixel loop: forward 17 per evaluated pair + 6 per blended pair; "
+                "backward 17 per pair before n_contrib + 28 per contributing pair")
+    return {"bound": "alu" if bound == "alu" else "hbm", "achieved": ach, "peak": peak, "unit": unit,
+            "frac": ach / peak, "traffic": traffic, "kernel": kernel_name, "stage": kernel,
+            "ms_per_launch": stage_ms[kernel], "work_per_launch": amount, "work_definition": wdef,
+            "peak_source": src}
+
+
+KERNEL_NAMES = {"select": "k_select", "project": "k_project<3>", "duplicate": "k_scan + k_scatter",
+                "sort": "k_tile_sort + k_tile_sort_large", "render": "k_render_fwd", "render_bwd": "k_render_bwd",
+                "project_bwd": "k_project_bwd<3>", "loss": "k_l1"}
+
+
+# -----------------------------------------------------------------------------------------
+# our arm: the headline training step (1M Gaussians, 1080p)
 # -----------------------------------------------------------------------------------------
 def run_ours(args, world, rank, local):
     import torch
@@ -198,6 +323,7 @@ def run_ours(args, world, rank, local):
     from paper_2404_01133_b300 import torch_api as ta
 
     dev = torch.device("cuda", local)
+    peaks = device_peaks(dev, local)
     sc, cams = synth.workload_city_1m()
     cam = cams[0]
     W, H = cam["width"], cam["height"]
@@ -207,6 +333,7 @@ def run_ours(args, world, rank, local):
     # the target is an 8-bit image, as a decoded training photo is (t stands for t / 255)
     tgt_host = torch.from_numpy(synth.target_image_u8(1, W, H))[None].pin_memory()
     tgt = tgt_host.to(dev)
+    tgt_f32 = torch.from_numpy(synth.target_image(1, W, H))[None].to(dev)
 
     # autotuner: tile size and batch depth for this workload, timed on the real step
     tune = None
@@ -239,27 +366,19 @@ def run_ours(args, world, rank, local):
     img, T, nc = frame.outputs()
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
     dL = torch.empty_like(img)
-    grads = (torch.zeros_like(ds.mean_opac), torch.zeros_like(ds.scale), torch.zeros_like(ds.quat),
-             torch.zeros_like(ds.sh))
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     st = torch.cuda.current_stream(dev)
     s_struct = ds.struct()
-
-    grad_flat = torch.zeros(sum(g.numel() for g in grads) + 1, dtype=torch.float32, device=dev)
-    views, off = [], 0
-    for gbuf in grads:
-        views.append(grad_flat[off:off + gbuf.numel()].view_as(gbuf))
-        off += gbuf.numel()
-    grads = tuple(views)
-    loss = grad_flat[off:off + 1]
+    grad_flat = torch.zeros(ds.mean_opac.numel() + ds.scale.numel() + ds.quat.numel() + ds.sh.numel(),
+                            dtype=torch.float32, device=dev)
+    grads, off = [], 0
+    for t_ in (ds.mean_opac, ds.scale, ds.quat, ds.sh):
+        grads.append(grad_flat[off:off + t_.numel()].view(t_.shape))
+        off += t_.numel()
+    grads = tuple(grads)
     # the step's gradients: one packed row per visible Gaussian (cgs_render_backward_packed),
     # written in full every step, so nothing is cleared outside the timed region
     rows = tune_rows
-
-    def zero_accumulators():
-        # nothing outside the step: the loss accumulator is cleared inside it, the packed
-        # gradient rows are overwritten
-        pass
 
     def step_with(tgt_buf, cam_buf):
         # the same step reading the target image and the camera from the given device buffers
@@ -279,43 +398,25 @@ def run_ours(args, world, rank, local):
         cgs.cgs_l1_loss_u8(img, tgt, img.numel(), loss, dL, cur)
         cgs.cgs_render_backward_packed(s_struct, frame.struct, cfg, d_cams, dL, T, nc, *rows, cur)
 
+    def step_f32_target():
+        # the same step with an FP32 target image (U[0,1]), 4 bytes per target value
+        cur = torch.cuda.current_stream().cuda_stream
+        cgs.cgs_render_forward(s_struct, frame.struct, cfg, d_cams, None, None, img, T, nc, cur)
+        loss.zero_()
+        cgs.cgs_l1_loss(img, tgt_f32, img.numel(), loss, dL, cur)
+        cgs.cgs_render_backward_packed(s_struct, frame.struct, cfg, d_cams, dL, T, nc, *rows, cur)
+
     def step_dense():
         # the scene-indexed form: gradients added into arrays laid out like the scene, which
         # the step clears first (236 MB)
         cur = torch.cuda.current_stream().cuda_stream
         grad_flat.zero_()
         cgs.cgs_render_forward(s_struct, frame.struct, cfg, d_cams, None, None, img, T, nc, cur)
+        loss.zero_()
         cgs.cgs_l1_loss_u8(img, tgt, img.numel(), loss, dL, cur)
         cgs.cgs_render_backward(s_struct, frame.struct, cfg, d_cams, dL, T, nc, *grads, cur)
 
-    def timed(k, fwd_only=False, with_stages=False):
-        if not with_stages:
-            ms_, l_ = timed_fn(lambda: step(fwd_only), k, st, flush, world,
-                               zero=None if fwd_only else zero_accumulators)
-            return ms_, l_, None
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
-        if with_stages:
-            cgs.cgs_timing_enable(True)
-        launches0 = cgs.cgs_kernel_launches()
-        barrier(world)
-        torch.cuda.synchronize()
-        for i in range(k):
-            flush.fill_(i & 0xff)  # evict L2 between timed steps (outside the event pair)
-            zero_accumulators()
-            ev[i][0].record(st)
-            step(fwd_only)
-            ev[i][1].record(st)
-        torch.cuda.synchronize()
-        barrier(world)
-        launches = cgs.cgs_kernel_launches() - launches0
-        stages = cgs.cgs_timing_read() if with_stages else None
-        if with_stages:
-            cgs.cgs_timing_enable(False)
-        ms = [a.elapsed_time(b) for a, b in ev]
-        return ms, launches, stages
-
     for _ in range(args.warmup):
-        zero_accumulators()
         step()
     torch.cuda.synchronize()
     l0 = cgs.cgs_kernel_launches()
@@ -326,126 +427,90 @@ def run_ours(args, world, rank, local):
     if status != cgs.CGS_OK:
         raise RuntimeError(f"frame status: {cgs.cgs_status_string(status)}")
 
-    # stage breakdown (library events) on an eager run, then the timed region
-    _, _, stages = timed(max(3, args.steps // 2), with_stages=True)
+    # stage breakdown (library events) on eager runs, then the timed region on CUDA graphs
+    stage_ms, _ = stage_times(step, max(3, args.steps // 2), flush)
     graph = None
     if not args.no_graph:
         graph = ta.capture(step, warmup=1)
         torch.cuda.synchronize()
-
-    def graph_step():
-        graph.replay()
-
-    clocks = ClockSampler(local)
-    clocks.start()
+    clocks = ClockSampler(local).start()
     if graph is not None:
-        ms, launches = timed_fn(graph_step, args.steps, st, flush, world, zero=zero_accumulators)
+        ms, _ = timed_fn(graph.replay, args.steps, st, flush, world)
         launches = per_step_launches * args.steps
     else:
-        ms, launches, _ = timed(args.steps)
+        ms, launches = timed_fn(step, args.steps, st, flush, world)
     clk = clocks.stop()
-    # forward only: stage times from an eager run with library events, the time itself from a
-    # CUDA graph of the forward (timed like the step)
-    _, _, stages_fwd = timed(max(3, args.steps // 2), fwd_only=True, with_stages=True)
+    # forward only: stage times from eager runs, the time itself from a CUDA graph of the forward
+    stage_ms_fwd, _ = stage_times(lambda: step(fwd_only=True), max(3, args.steps // 2), flush)
     if graph is not None:
         g_fwd = ta.capture(lambda: step(fwd_only=True), warmup=1)
         ms_fwd, _ = timed_fn(g_fwd.replay, args.steps, st, flush, world)
         del g_fwd
+        g32 = ta.capture(step_f32_target, warmup=1)
+        ms_f32t, _ = timed_fn(g32.replay, max(3, args.steps // 2), st, flush, world)
+        del g32
+        g_dense = ta.capture(step_dense, warmup=1)
+        ms_dense, _ = timed_fn(g_dense.replay, max(3, args.steps // 2), st, flush, world)
+        del g_dense
     else:
-        ms_fwd, _, _ = timed(args.steps, fwd_only=True)
-    # the scene-indexed gradient form, its arrays cleared inside the step
-    g_dense = ta.capture(step_dense, warmup=1)
-    ms_dense, _ = timed_fn(g_dense.replay, max(3, args.steps // 2), st, flush, world)
-    del g_dense
+        ms_fwd, _ = timed_fn(lambda: step(fwd_only=True), args.steps, st, flush, world)
+        ms_f32t, _ = timed_fn(step_f32_target, max(3, args.steps // 2), st, flush, world)
+        ms_dense, _ = timed_fn(step_dense, max(3, args.steps // 2), st, flush, world)
     step()  # one full step so the frame's counters hold both the forward and the backward
     status, counts = frame.status()
     if status != cgs.CGS_OK:
         raise RuntimeError(f"frame status: {cgs.cgs_status_string(status)}")
+    sum_nc = int(nc.to(torch.int64).sum().item())
 
     step_ms = max_over_ranks(sum(ms) / len(ms), world)
     fwd_ms = max_over_ranks(sum(ms_fwd) / len(ms_fwd), world)
     pix = W * H
     value = whole_job_mpix_s(world, pix, step_ms)
     fwd_value = whole_job_mpix_s(world, pix, fwd_ms)
-
-    # per-stage averages (ms per launch of the stage)
-    stage_ms = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in stages.items()}
-    n_sel, n_vis, k_ent, pairs_f, pairs_b = counts[0], counts[1], counts[2], counts[3], counts[4]
-    nc_coef = (sc["sh_degree"] + 1) ** 2
-    peaks, peak_src = load_peaks()
-    alu_peak = 148 * 128 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12  # FP32 lane-ops / s, in T/s
+    n_sel, n_vis, k_ent, pairs_f, pairs_b = counts[:5]
     n_tiles = ((W + args.tile - 1) // args.tile) * ((H + args.tile - 1) // args.tile)
-    work = {
-        # algorithmic bytes per launch (HBM-bound stages)
-        # projection: mean+opacity read, scene index and tiles-touched write for every selected
-        # Gaussian; scale, rotation and SH read, three records, rect, key and visible-list slot
-        # written for the visible ones; one 8-byte entry per tile touched
-        "project": ("hbm", n_sel * (16 + 4 + 4) + n_vis * (32 + 12 * nc_coef + 48 + 8 + 8 + 4) + k_ent * 8),
-        # binning: per tile its count read and range written; per entry read the entry, write
-        # the key
-        "duplicate": ("hbm", n_tiles * 12 + k_ent * (8 + 8)),
-        # per-tile sort: per entry read the key, write value and tile
-        "sort": ("hbm", k_ent * (8 + 4 + 4)),
-        # algorithmic FP32 operations per launch (issue-bound stages)
-        "render": ("alu", pairs_f * FP32_OPS_PER_EVAL_PAIR_FWD),
-        "render_bwd": ("alu", pairs_f * FP32_OPS_PER_EVAL_PAIR_BWD),
-        # projection backward, per visible Gaussian: read the visible-list slot, key, scene
-        # index, screen-space gradients, mean+opacity, scale, rotation and SH; write the packed
-        # gradient row (mean+opacity, scale, rotation, SH, scene index) and clear the
-        # screen-space gradients
-        "project_bwd": ("hbm", n_vis * ((4 + 8 + 4 + 48 + 16 + 16 + 16 + 12 * nc_coef) +
-                                        (16 + 16 + 16 + 12 * nc_coef + 8 + 48))),
-        # L1: image read (4 B), 8-bit target read (1 B), gradient written (4 B)
-        "loss": ("hbm", W * H * 3 * 9),
-    }
-    # overall fraction: time every stage would take at its binding peak / step time
-    ideal_ms = sum((amt / (peaks["hbm_gbs"] * 1e9) if b == "hbm" else amt / (alu_peak * 1e12)) * 1e3
-                   for b, amt in work.values())
-    ideal_fwd_ms = sum((amt / (peaks["hbm_gbs"] * 1e9) if b == "hbm" else amt / (alu_peak * 1e12)) * 1e3
-                       for k, (b, amt) in work.items() if k in ("project", "duplicate", "sort", "render"))
-    strict = {"render": pairs_b * FP32_OPS_PER_CONTRIB_PAIR_FWD / (stage_ms["render"] * 1e-3) / 1e12 / alu_peak,
-              "render_bwd": pairs_b * FP32_OPS_PER_CONTRIB_PAIR_BWD / (stage_ms["render_bwd"] * 1e-3) / 1e12 / alu_peak}
-    dom = max(work, key=lambda k: stage_ms.get(k, 0.0))
-    bound, amount = work[dom]
-    t = stage_ms[dom] * 1e-3
-    if bound == "hbm":
-        achieved = amount / t / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"]}
-    else:
-        achieved = amount / t / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFP32op/s",
-                "frac": achieved / alu_peak}
-    roof.update({"kernel": dom, "traffic": NCU_TRAFFIC_BYTES.get(dom) if args.tile == 16 else None,
-                 "peak_source": peak_src, "ms_per_launch": stage_ms[dom]})
+    work = stage_work(counts, sum_nc, n_tiles, pix, sc["sh_degree"], backward=True, loss_bytes=9)
+    fwd_keys = ("project", "duplicate", "sort", "render")
+    i_ms = ideal_ms(work, peaks)
+    i_fwd = ideal_ms(work, peaks, fwd_keys)
+    dom = max(work, key=lambda k_: stage_ms.get(k_, 0.0))
+    roof = roofline(dom, stage_ms, work, peaks, KERNEL_NAMES[dom],
+                    NCU_TRAFFIC_BYTES.get(dom) if args.tile == 16 else None)
+    strict = {"render": pairs_b * (OPS_FWD_EVAL + OPS_FWD_BLEND) / (stage_ms["render"] * 1e-3) / 1e12 / peaks["fp32_tops"],
+              "render_bwd": pairs_b * (OPS_BWD_EVAL + OPS_BWD_GRAD) / (stage_ms["render_bwd"] * 1e-3) / 1e12
+              / peaks["fp32_tops"]}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"city-1M-SH3 1920x1080 fwd+bwd (L1), {args.tile}x{args.tile} tiles", "gaussians": n, "visible": n_vis, "tile_entries": k_ent,
-                   "width": W, "height": H, "tile": args.tile, "batch": args.batch, "views_per_gpu": 1,
-                   "parallelism": f"replicas x{world}", "l2": "flushed between timed steps (256 MB write)",
+        "config": {"workload": f"city-1M-SH3 1920x1080 fwd+bwd (L1), {args.tile}x{args.tile} tiles", "gaussians": n,
+                   "visible": n_vis, "tile_entries": k_ent, "width": W, "height": H, "tile": args.tile,
+                   "batch": args.batch, "views_per_gpu": 1, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (256 MB write)",
                    "gradients": "packed rows per visible Gaussian, written in full by every step; the loss "
                                 "accumulator cleared inside the step; nothing cleared between steps",
                    "target": "8-bit RGB image, channel t stands for t/255"},
         "fwd_mpix_s": fwd_value, "fwd_ms": fwd_ms, "fps_fwd_bwd": 1e3 / step_ms, "fps_fwd": 1e3 / fwd_ms,
         "gaussians_per_s": world * n / (step_ms * 1e-3),
-        "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
-        "stage_ms_fwd_only": {k: round(v[0] / v[1], 4) for k, v in stages_fwd.items() if v[1]},
-        "pairs": {"fwd_evaluated": pairs_f, "bwd_contributing": pairs_b, "fwd_warp_steps": counts[6],
-                  "fwd_useful_warp_steps": counts[7]},
+        "stage_ms": {k_: round(v, 4) for k_, v in stage_ms.items()},
+        "stage_ms_fwd_only": {k_: round(v, 4) for k_, v in stage_ms_fwd.items()},
+        "pairs": {"fwd_evaluated": pairs_f, "bwd_contributing": pairs_b, "bwd_visited_sum_n_contrib": sum_nc,
+                  "fwd_warp_steps": counts[6], "fwd_useful_warp_steps": counts[7]},
+        "peaks": peaks,
         "roofline": roof,
-        "roofline_overall": {"ideal_ms": ideal_ms, "frac": ideal_ms / step_ms,
+        "roofline_overall": {"ideal_ms": i_ms, "frac": i_ms / step_ms,
                              "definition": "sum over stages of algorithmic work / binding peak, over the step time"},
-        "roofline_overall_fwd": {"ideal_ms": ideal_fwd_ms, "frac": ideal_fwd_ms / fwd_ms,
+        "roofline_overall_fwd": {"ideal_ms": i_fwd, "frac": i_fwd / fwd_ms,
                                  "definition": "the same over the forward stages and the forward time"},
+        "roofline_stage_frac": stage_fracs(work, stage_ms, peaks),
+        "roofline_contributing_pairs_frac": strict,
         "ms_per_step_median": statistics.median(ms),
+        "fp32_target": {"ms_per_step": max_over_ranks(sum(ms_f32t) / len(ms_f32t), world),
+                        "mpix_s": whole_job_mpix_s(world, pix, max_over_ranks(sum(ms_f32t) / len(ms_f32t), world)),
+                        "target": "FP32 U[0,1] image (seed 1)"},
         "dense_gradients": {"ms_per_step": max_over_ranks(sum(ms_dense) / len(ms_dense), world),
                             "form": "scene-indexed gradient arrays (atomic adds), cleared (236 MB) inside the step"},
-        "roofline_stage_frac": {k: ((amt / (peaks["hbm_gbs"] * 1e9) if b == "hbm" else amt / (alu_peak * 1e12)) * 1e3
-                                    / stage_ms[k]) for k, (b, amt) in work.items() if stage_ms.get(k)},
-        "roofline_contributing_pairs_frac": strict,
         "gpu_launches": launches,
         "kernels_per_step": per_step_launches,
         "timing": ("CUDA graph replay of the whole step (and of the forward for fwd_ms)" if graph is not None
@@ -455,16 +520,21 @@ def run_ours(args, world, rank, local):
     }
     if args.batched_views > 1:
         out["batched_vs_plain"] = run_batched_compare(args, ds, sc, cfg, st, flush, world, synth, ta, cgs)
-
     if not args.no_fp16_compare:
         out["fp16_attributes"] = run_fp16_compare(args, sc, cfg, d_cams, tgt, ds, st, flush, world, ta, cgs)
-
     if not args.no_e2e:
-        out["e2e"] = run_e2e(args, frame, cams, tgt_host, step_with, loss, zero_accumulators, st, world)
-        out["e2e_scene_upload"] = run_e2e_scene_upload(args, ds, frame, sc, tgt_host, tgt, step, loss,
-                                                       zero_accumulators, st, world)
+        out["e2e"] = run_e2e(args, frame, cams, tgt_host, step_with, loss, st, world)
+        out["e2e_scene_upload"] = run_e2e_scene_upload(args, ds, frame, sc, tgt_host, tgt, step, loss, st, world)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(sc, cam, full=True)
+        out["cpu_baseline"] = cpu_baseline_city1m(sc, cam)
+    del frame, ds, rows, tune_rows, grad_flat, grads, flush
+    torch.cuda.empty_cache()
+    if not args.headline_only:
+        extra_launches = [0]
+        out["lod20m"], out["lodqueue"] = run_lod_workloads(args, world, rank, local, peaks, extra_launches)
+        torch.cuda.empty_cache()
+        out["train32"] = run_train32(args, world, rank, local, peaks, extra_launches)
+        out["gpu_launches_nested"] = extra_launches[0]
     return out
 
 
@@ -517,7 +587,6 @@ def run_batched_compare(args, ds, sc, cfg, st, flush, world, synth, ta, cgs):
             cgs.cgs_render_forward(s_struct, f1.struct, cfg, d1[v], None, None, i1, T1, n1, cur)
             cgs.cgs_l1_loss(i1, tgt[v:v + 1].contiguous(), i1.numel(), loss, dL1, cur)
             cgs.cgs_render_backward_packed(s_struct, f1.struct, cfg, d1[v], dL1, T1, n1, *rows1[v], cur)
-
     g_b = ta.capture(batched, warmup=1)
     g_s = ta.capture(sequential, warmup=1)
     k = max(3, args.steps // 2)
@@ -561,22 +630,14 @@ def run_fp16_compare(args, sc, cfg, d_cams, tgt, ds32, st, flush, world, ta, cgs
 
         for _ in range(2):
             one()
-        torch.cuda.synchronize()
-        cgs.cgs_timing_enable(True)
-        for _ in range(5):
-            flush.fill_(1)
-            one()
-        torch.cuda.synchronize()
-        stg = cgs.cgs_timing_read()
-        cgs.cgs_timing_enable(False)
+        stg, _ = stage_times(one, 5, flush)
         g = ta.capture(one, warmup=1)
         k = max(3, args.steps // 2)
         ms, _ = timed_fn(g.replay, k, st, flush, world)
         status, _ = frame.status()
         attr_bytes = sum(t.numel() * t.element_size() for t in (ds.mean_opac, ds.scale, ds.quat, ds.sh))
         res[name] = {"ms_per_step": max_over_ranks(sum(ms) / len(ms), world), "attribute_bytes": attr_bytes,
-                     "project_ms": stg["project"][0] / max(1, stg["project"][1]),
-                     "project_bwd_ms": stg["project_bwd"][0] / max(1, stg["project_bwd"][1]),
+                     "project_ms": stg["project"], "project_bwd_ms": stg["project_bwd"],
                      "status": cgs.cgs_status_string(status)}
     res["step_speedup"] = res["fp32"]["ms_per_step"] / res["fp16"]["ms_per_step"]
     res["project_speedup"] = res["fp32"]["project_ms"] / res["fp16"]["project_ms"]
@@ -584,7 +645,7 @@ def run_fp16_compare(args, sc, cfg, d_cams, tgt, ds32, st, flush, world, ta, cgs
     return res
 
 
-def run_e2e(args, frame, cams, tgt_host, step_with, loss, zero_accumulators, st, world):
+def run_e2e(args, frame, cams, tgt_host, step_with, loss, st, world):
     """The training step end to end through the public API with its per-step inputs on the
     HOST: every step copies its camera and its target image from pinned host memory, runs
     forward + L1 + backward, and reads the loss back; the Gaussian parameters (the model) stay
@@ -625,7 +686,6 @@ def run_e2e(args, frame, cams, tgt_host, step_with, loss, zero_accumulators, st,
                 copy_in(i + 1)
             b = i % 2
             st.wait_event(ready[b])
-            zero_accumulators()
             graphs[b].replay()
             free[b].record(st)
             loss_host[i:i + 1].copy_(loss, non_blocking=True)
@@ -646,23 +706,22 @@ def run_e2e(args, frame, cams, tgt_host, step_with, loss, zero_accumulators, st,
             "step": "CUDA graph replay per input buffer"}
 
 
-def run_e2e_scene_upload(args, ds, frame, sc, tgt_host, tgt_dev, step, loss, zero_accumulators, st, world):
+def run_e2e_scene_upload(args, ds, frame, sc, tgt_host, tgt_dev, step, loss, st, world):
     """The step with the whole scene re-uploaded as well: every step copies the scene and the
-    target from pinned host memory to the device, clears the accumulators, runs the step and
-    reads the loss back; all of it inside the timed region (bound by the host link)."""
+    target from pinned host memory to the device, runs the step and reads the loss back; all
+    of it inside the timed region (bound by the host link)."""
     import torch
     host = {k: torch.from_numpy(np.ascontiguousarray(sc[k], np.float32)).pin_memory()
             for k in ("mean_opac", "scale", "quat", "sh")}
     dev_bufs = {"mean_opac": ds.mean_opac, "scale": ds.scale, "quat": ds.quat, "sh": ds.sh}
     loss_host = torch.empty(1, dtype=torch.float32).pin_memory()
-    h2d = sum(t.numel() * 4 for t in host.values()) + tgt_host.numel() * 4
+    h2d = sum(t.numel() * 4 for t in host.values()) + tgt_host.numel() * tgt_host.element_size()
     k = max(3, min(args.steps, 10))
 
     def one():
         for name, t in host.items():
             dev_bufs[name].copy_(t, non_blocking=True)
         tgt_dev.copy_(tgt_host, non_blocking=True)
-        zero_accumulators()
         step()
         loss_host.copy_(loss, non_blocking=True)
 
@@ -683,43 +742,113 @@ def run_e2e_scene_upload(args, ds, frame, sc, tgt_host, tgt_dev, step, loss, zer
 
 
 # -----------------------------------------------------------------------------------------
-# CPU oracle (baseline leg and the reference arm)
+# CPU oracle, as it stands, run by threads over disjoint pieces of a frame (the CPU-baseline
+# legs and the reference arm).  The oracle's C functions keep no global state, and ctypes
+# releases the interpreter lock during each call, so its projection runs on disjoint ranges
+# of Gaussians and its compositing (forward and backward) on disjoint tile rows, in parallel.
 # -----------------------------------------------------------------------------------------
-def band_mask(cam, tile, frac):
+def host_cores():
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
+
+
+def _in_threads(fns):
+    th = [threading.Thread(target=f) for f in fns]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+
+
+def oracle_project_par(scene, cam, idx, nt):
+    """oracle.project over ranges of the selected Gaussians, one range per thread, merged."""
+    import oracle
+    mo = np.ascontiguousarray(scene["mean_opac"] if idx is None else scene["mean_opac"][idx], np.float32)
+    sc = np.ascontiguousarray(scene["scale"] if idx is None else scene["scale"][idx], np.float32)
+    q = np.ascontiguousarray(scene["quat"] if idx is None else scene["quat"][idx], np.float32)
+    sh = np.ascontiguousarray(scene["sh"] if idx is None else scene["sh"][idx], np.float32)
+    n = mo.shape[0]
+    cuts = np.linspace(0, n, nt + 1).astype(np.int64)
+    parts = [None] * nt
+
+    def piece(i):
+        a, b = int(cuts[i]), int(cuts[i + 1])
+        parts[i] = oracle.project(scene, cam, arrays=(mo[a:b], sc[a:b], q[a:b], sh[a:b]))
+
+    _in_threads([lambda i=i: piece(i) for i in range(nt)])
+    pr = {k: np.concatenate([p[k] for p in parts]) for k in
+          ("depth", "radius", "rect", "tiles_touched", "xy", "cov2d", "conic", "rgb", "flags")}
+    pr["n_entries"] = sum(p["n_entries"] for p in parts)
+    pr["arrays"] = (mo, sc, q, sh)
+    return pr
+
+
+def tile_row_masks(cam, tile, nt):
+    """Per thread a tile mask of every nt-th row of tiles (interleaved, for balance)."""
     tx = (cam["width"] + tile - 1) // tile
     ty = (cam["height"] + tile - 1) // tile
-    rows = max(1, int(round(ty * frac)))
-    r0 = (ty - rows) // 2
-    m = np.zeros((ty, tx), np.uint8)
-    m[r0:r0 + rows] = 1
-    pix = sum(min(tile, cam["height"] - r * tile) for r in range(r0, r0 + rows)) * cam["width"]
-    return m.reshape(-1), pix
+    masks = []
+    for i in range(nt):
+        m = np.zeros((ty, tx), np.uint8)
+        m[i::nt] = 1
+        masks.append(m.reshape(-1))
+    return masks
 
 
-def oracle_step(sc, cam, tgt, mask):
+def oracle_frame_par(scene, cam, idx, nt, target=None):
+    """One frame of the oracle on nt threads: projection, sort (one thread), compositing over
+    interleaved tile rows, and with a target the L1 loss and the full backward.  Returns
+    (seconds per stage, evaluated pairs)."""
     import oracle
+    t = {}
     t0 = time.perf_counter()
-    pr = oracle.project(sc, cam)
+    pr = oracle_project_par(scene, cam, idx, nt)
+    t["project"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
     srt = oracle.bin_and_sort(pr, cam)
-    o = oracle.composite(pr, srt, cam, tile_mask=mask)
-    o["proj"], o["sort"] = pr, srt
-    _, dL = oracle.l1(o["image"], tgt)
-    oracle.render_backward(sc, cam, dL, fwd=o, tile_mask=mask)
-    return time.perf_counter() - t0
+    t["sort"] = time.perf_counter() - t0
+    masks = tile_row_masks(cam, 16, nt)
+    outs = [None] * nt
+    t0 = time.perf_counter()
+    _in_threads([lambda i=i: outs.__setitem__(i, oracle.composite(pr, srt, cam, tile_mask=masks[i]))
+                 for i in range(nt)])
+    t["composite"] = time.perf_counter() - t0
+    pairs = sum(o["pairs"] for o in outs)
+    if target is not None:
+        W, H = cam["width"], cam["height"]
+        img = np.zeros((3, H, W), np.float32)
+        ty_of = np.repeat(np.arange((H + 15) // 16), 16)[:H]
+        for i, o in enumerate(outs):
+            rows = (ty_of % nt) == i
+            img[:, rows] = o["image"][:, rows]
+        t0 = time.perf_counter()
+        _, dL = oracle.l1(img, target)
+        fwd = dict(outs[0])
+        fwd["proj"], fwd["sort"] = pr, srt
+        grads = [None] * nt
+        _in_threads([lambda i=i: grads.__setitem__(i, oracle.render_backward(scene, cam, dL, fwd=fwd,
+                                                                             tile_mask=masks[i]))
+                     for i in range(nt)])
+        for key in ("mean", "scale", "quat", "opac", "sh"):
+            s = grads[0][key]
+            for g in grads[1:]:
+                s = s + g[key]
+        t["loss_backward"] = time.perf_counter() - t0
+    return t, pairs
 
 
-def cpu_baseline(sc, cam, full):
+def cpu_baseline_city1m(sc, cam):
     from paper_2404_01133_b300 import synth
+    nt = host_cores()
     tgt = synth.target_image(1, cam["width"], cam["height"])
-    if full:
-        mask, pix = None, cam["width"] * cam["height"]
-        sample = "one full 1920x1080 frame: projection, sort, compositing, L1, backward (oracle as is)"
-    else:
-        mask, pix = band_mask(cam, 16, 0.125)
-        sample = "central band of 1/8 of the tile rows; full projection and sort"
-    t = oracle_step(sc, cam, tgt, mask)
-    return {"value": pix / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-            "seconds": t}
+    t, _ = oracle_frame_par(sc, cam, None, nt, target=tgt)
+    s = sum(t.values())
+    return {"value": cam["width"] * cam["height"] / s / 1e6, "unit": UNIT, "cores": nt, "kind": "oracle",
+            "sample": "one full 1920x1080 frame: projection, sort, compositing, L1, backward (oracle as is, "
+                      "threads over Gaussian ranges and tile rows)",
+            "seconds": s, "stage_s": {k: round(v, 3) for k, v in t.items()}}
 
 
 def run_reference(args, world, rank):
@@ -730,25 +859,25 @@ def run_reference(args, world, rank):
     oracle.lib("f32")
     sc, cams = synth.workload_city_1m()
     cam = cams[0]
+    nt = host_cores()
     tgt = synth.target_image(1, cam["width"], cam["height"])
-    mask, pix = band_mask(cam, 16, 0.125)
     for _ in range(args.warmup):
-        oracle_step(sc, cam, tgt, mask)
-    ts = [oracle_step(sc, cam, tgt, mask) for _ in range(args.steps)]
+        oracle_frame_par(sc, cam, None, nt, target=tgt)
+    ts = [sum(oracle_frame_par(sc, cam, None, nt, target=tgt)[0].values()) for _ in range(args.steps)]
     ms = 1e3 * sum(ts) / len(ts)
-    value = pix / (ms * 1e-3) / 1e6
-    sample = "central band of 1/8 of the tile rows per step (full projection and sort)"
+    value = cam["width"] * cam["height"] / (ms * 1e-3) / 1e6
+    sample = "one full 1920x1080 frame per step (projection, sort, compositing, L1, backward)"
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "gaussians": sc["mean_opac"].shape[0], "width": cam["width"],
-                       "height": cam["height"], "tile": 16, "parallelism": "cpu, 1 thread"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                       "height": cam["height"], "tile": 16, "parallelism": f"cpu, {nt} threads"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 # -----------------------------------------------------------------------------------------
-# LoD and batched workloads (separate JSON lines)
+# LoD workloads over the 20M-Gaussian, 8x8-block, 3-level city
 # -----------------------------------------------------------------------------------------
 def _fwd_runner(ds, frame, cfg, d_cams, view_block=None, levels=None):
     import torch
@@ -759,83 +888,357 @@ def _fwd_runner(ds, frame, cfg, d_cams, view_block=None, levels=None):
     def run():
         cgs.cgs_render_forward(s_struct, frame.struct, cfg, d_cams, view_block, levels, img, T, nc,
                                torch.cuda.current_stream().cuda_stream)
+    run.outputs = (img, T, nc)
     return run
 
 
 def _graph_ms(fn, k, flush, world):
+    """k timed replays of a CUDA graph of fn; returns (ms list, kernels launched by the
+    replays: the library's launches per call of fn, counted while capturing, times k)."""
     import torch
+    from paper_2404_01133_b300 import cgs
     from paper_2404_01133_b300 import torch_api as ta
-    g = ta.capture(fn, warmup=1)
+    l0 = cgs.cgs_kernel_launches()
+    g = ta.capture(fn, warmup=1)  # one warm-up call and the captured call
+    per_call = (cgs.cgs_kernel_launches() - l0) // 2
     ms, _ = timed_fn(g.replay, k, torch.cuda.current_stream(), flush, world)
-    return ms
+    return ms, per_call * k
 
 
-def run_lod20m(args, world):
-    """Block-LoD forward of the 20M-Gaussian, 8x8-block, 3-level city at 1920x1080, looking
-    straight down from several heights: LoD (block selection + culling, 200/600 m) against
-    every block at one fixed level without block culling (no LoD = level 0)."""
+def cpu_baseline_lod(sc, cams, aabb, lod_dist, label):
+    """The oracle on whole LoD frames: FP64 block selection, concatenation, then projection,
+    sort and compositing of the selected Gaussians on the host's cores."""
+    import oracle
+    nt = host_cores()
+    frames = []
+    for cam in cams:
+        t0 = time.perf_counter()
+        lev = oracle.lod_select(sc, aabb, cam, dist=lod_dist)
+        idx = oracle.concat(sc, lev)
+        t_sel = time.perf_counter() - t0
+        t, pairs = oracle_frame_par(sc, cam, idx, nt)
+        s = t_sel + sum(t.values())
+        frames.append({"height_m": float(cam["campos"][2]), "seconds": round(s, 3), "fps": 1.0 / s,
+                       "selected": int(idx.shape[0]), "evaluated_pairs": int(pairs),
+                       "stage_s": {"select": round(t_sel, 4), **{k: round(v, 3) for k, v in t.items()}}})
+    fps = len(frames) / sum(f["seconds"] for f in frames)
+    return {"value": fps, "unit": "FPS", "cores": nt, "kind": "oracle",
+            "sample": f"{label}: whole 1920x1080 frames (FP64 block LoD selection, projection, sort, compositing)",
+            "frames": frames}
+
+
+def run_lod_workloads(args, world, rank, local, peaks, launches_acc):
+    """lod20m (height sweep) and lodqueue (64 poses), sharing one device copy of the scene."""
     import torch
-    from paper_2404_01133_b300 import build as libbuild, cgs, synth
+    from paper_2404_01133_b300 import cgs, synth
     from paper_2404_01133_b300 import torch_api as ta
-    libbuild.build()
+    import oracle
     t0 = time.time()
     heights = tuple(float(h) for h in args.lod_heights.split(","))
     sc, cams = synth.workload_city_lod(n=args.lod_n, heights=heights)
     t_gen = time.time() - t0
     ds = ta.DeviceScene(sc)
     ds.compute_block_bounds(4.0)
-    cfg = ta.make_config(tile=16, batch=args.lod_batch, lod_dist=(200.0, 600.0))
-    cfg_pt = ta.make_config(tile=16, batch=args.lod_batch, lod_dist=(200.0, 600.0), lod_mode=cgs.CGS_LOD_POINT)
+    lod_dist = (200.0, 600.0)
+    cfg = ta.make_config(tile=16, batch=args.lod_batch, lod_dist=lod_dist)
+    cfg_pt = ta.make_config(tile=16, batch=args.lod_batch, lod_dist=lod_dist, lod_mode=cgs.CGS_LOD_POINT)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     nb = ds.n_blocks
+    W, H = 1920, 1080
+    n_tiles = 120 * 68
+    steps = max(5, args.steps // 2)
+
+    # ---- lod20m: height sweep -------------------------------------------------------------
     rows = []
+    clocks = ClockSampler(local).start()
     for cam in cams:
         d_cam = ta.cameras_device([cam])
         row = {"height_m": float(cam["campos"][2])}
-        variants = [("lod", None, cfg), ("pointwise", None, cfg_pt)] + \
-            [(f"level{l}", torch.full((1, nb), l, dtype=torch.int8, device="cuda"), cfg) for l in range(3)]
+        variants = [("lod", None, cfg), ("pointwise", None, cfg_pt),
+                    ("level0", torch.zeros((1, nb), dtype=torch.int8, device="cuda"), cfg)]
         for name, lv, c_ in variants:
-            sel, ent = ta.frame_counts(ds, [cam], 1920, 1080, levels=lv, cfg=c_)
-            fr = ta.Frame(1, 1920, 1080, 16, nb, max(1, int(sel[0] * 1.02) + 1024),
+            sel, ent = ta.frame_counts(ds, [cam], W, H, levels=lv, cfg=c_)
+            fr = ta.Frame(1, W, H, 16, nb, max(1, int(sel[0] * 1.02) + 1024),
                           min((1 << 30) - 1, int(ent[0] * 1.05) + 65536))
             run = _fwd_runner(ds, fr, c_, d_cam, None, lv)
-            ms = _graph_ms(run, args.steps, flush, world)
+            ms, l_ = _graph_ms(run, steps, flush, world)
+            launches_acc[0] += l_
             st, c = fr.status()
             t = max_over_ranks(sum(ms) / len(ms), world)
             row[name] = {"fps": 1e3 / t, "ms": t, "selected": c[0], "visible": c[1], "entries": c[2],
                          "status": cgs.cgs_status_string(st)}
             if name == "lod":
-                # per-stage times of the LoD frame (library events, eager launches)
-                cgs.cgs_timing_enable(True)
-                for _ in range(3):
-                    run()
-                torch.cuda.synchronize()
-                stg = cgs.cgs_timing_read()
-                cgs.cgs_timing_enable(False)
-                row[name]["stage_ms"] = {k: round(v[0] / v[1], 4) for k, v in stg.items() if v[1]}
-            del fr
+                sms, _ = stage_times(run, 3, flush)
+                work = stage_work(c, 0, n_tiles, W * H, sc["sh_degree"])
+                row[name]["stage_ms"] = {k: round(v, 4) for k, v in sms.items()}
+                row[name]["stage_frac"] = stage_fracs(work, sms, peaks)
+                row[name]["pairs"] = {"fwd_evaluated": c[3], "contributing": c[4]}
+                row[name]["roofline_overall"] = ideal_ms(work, peaks) / t
+                row[name]["_work"], row[name]["_stage_ms"] = work, sms
+            del fr, run
         rows.append(row)
+    clk = clocks.stop()
     mean = lambda k: float(np.mean([r[k]["fps"] for r in rows]))
+    worst = min(rows, key=lambda r: r["lod"]["fps"])
+    wdom = max(worst["lod"]["_stage_ms"], key=worst["lod"]["_stage_ms"].get)
+    roof = roofline(wdom, worst["lod"]["_stage_ms"], worst["lod"]["_work"], peaks, KERNEL_NAMES[wdom])
+    roof["frame"] = f"block-LoD frame at {worst['height_m']:g} m (the sweep's slowest)"
+    for r in rows:
+        del r["lod"]["_work"], r["lod"]["_stage_ms"]
     mn = f"{args.lod_n / 1e6:g}M"
-    return {"metric": f"{mn}-Gaussian LoD FPS at 1080p (block LoD vs point-wise LoD vs fixed levels)", "value": mean("lod"),
-            "unit": "FPS", "n_gpus": world, "steps": args.steps, "higher_is_better": True, "dtype": "f32",
-            "data": "synthetic", "config": {"workload": f"city-{mn}-SH3 6 km^2, 8x8 blocks, levels 100/50/25%, "
-                                                        "top-down 1920x1080, f=1200, 16x16 tiles",
-                                            "heights_m": list(heights),
-                                            "lod_dist_m": [200, 600], "generation_s": t_gen},
-            "mean_fps": {"lod": mean("lod"), "pointwise_lod": mean("pointwise"), "no_lod_level0": mean("level0"),
-                         "only_level1": mean("level1"), "only_level2": mean("level2")},
-            "per_height": rows}
+    lod = {"metric": f"{mn}-Gaussian LoD FPS at 1080p (block LoD vs point-wise LoD vs no LoD)", "value": mean("lod"),
+           "unit": "FPS", "higher_is_better": True,
+           "config": {"workload": f"city-{mn}-SH3 6 km^2, 8x8 blocks, levels 100/50/25%, top-down 1920x1080, "
+                                  "f=1200, 16x16 tiles", "heights_m": list(heights), "lod_dist_m": list(lod_dist),
+                      "batch": args.lod_batch, "generation_s": round(t_gen, 1),
+                      "timing": f"CUDA graph of one frame, {steps} replays per variant, L2 flushed between"},
+           "mean_fps": {"lod": mean("lod"), "pointwise_lod": mean("pointwise"), "no_lod_level0": mean("level0")},
+           "per_height": rows, "roofline": roof, "clocks": clk,
+           "paper_context": "53.7 FPS block LoD, 30.3 point-wise, 21.6 no LoD on MatrixCity (unnamed GPU, width "
+                            "1600; Table 4 and the LoD experiments)"}
+
+    # ---- lodqueue: 64 poses -----------------------------------------------------------------
+    qcams = synth.lod_pose_queue(sc["side"])
+    V = len(qcams)
+    sel, ent = ta.frame_counts(ds, qcams, W, H, cfg=cfg)
+    f1 = ta.Frame(1, W, H, 16, nb, int(max(sel) * 1.02) + 1024, min((1 << 30) - 1, int(max(ent) * 1.05) + 65536))
+    d1 = [ta.cameras_device([c]) for c in qcams]
+    runs = [_fwd_runner(ds, f1, cfg, d) for d in d1]
+
+    def seq_all():
+        for r in runs:
+            r()
+    lat = []
+    for v in range(V):
+        ms, _ = _graph_ms(runs[v], 3, flush, world)
+        lat.append(sorted(ms)[1])
+    groups = ta.waves(sel, ent, n_cap_max=200_000_000, k_cap_max=(1 << 30) - 1)
+    frames = []
+    for views, n_cap, k_cap in groups:
+        fr = ta.Frame(len(views), W, H, 16, nb, n_cap, min((1 << 30) - 1, k_cap))
+        frames.append((fr, _fwd_runner(ds, fr, cfg, ta.cameras_device([qcams[v] for v in views]))))
+
+    def batched_all():
+        for _, r in frames:
+            r()
+    clocks = ClockSampler(local).start()
+    ms_seq, l_s = _graph_ms(seq_all, max(2, args.steps // 4), flush, world)
+    ms_b, l_b = _graph_ms(batched_all, max(2, args.steps // 4), flush, world)
+    clk_q = clocks.stop()
+    launches_acc[0] += l_s + l_b
+    t_seq = max_over_ranks(sum(ms_seq) / len(ms_seq), world)
+    t_b = max_over_ranks(sum(ms_b) / len(ms_b), world)
+    # per-stage times and work of the batched frames (library events on eager runs)
+    sms, raw = stage_times(batched_all, 2, flush)
+    per_frame_stage = {k: v[0] / 2 for k, v in raw.items()}  # ms per batched pass, summed over its frames
+    counts = np.zeros(8, np.int64)
+    status = []
+    for fr, _ in frames:
+        s_, c_ = fr.status()
+        status.append(cgs.cgs_status_string(s_))
+        counts += np.asarray(c_, np.int64)
+    work = stage_work(counts, 0, n_tiles * V, W * H * V, sc["sh_degree"])
+    qdom = max(per_frame_stage, key=per_frame_stage.get)
+    qroof = roofline(qdom, per_frame_stage, work, peaks, KERNEL_NAMES[qdom])
+    qroof["frame"] = "the 64 poses' batched frames together (work and time summed over the frames)"
+    queue = {"metric": "LoD pose queue FPS, batched vs sequential (64 poses, 20M Gaussians, 1080p)",
+             "value": world * V / (t_b * 1e-3), "unit": "FPS", "higher_is_better": True,
+             "config": {"workload": f"city-{mn}-SH3 6 km^2, 8x8 blocks, 64 top-down poses 30-2500 m (seed 5), "
+                                    "1920x1080", "groups": [len(g[0]) for g in groups],
+                        "timing": "CUDA graphs (all batched frames in one graph; the 64 one-view renders in "
+                                  "another), L2 flushed between replays"},
+             "batched_fps": world * V / (t_b * 1e-3), "batched_ms": t_b,
+             "sequential_fps": world * V / (t_seq * 1e-3), "sequential_ms": t_seq, "speedup": t_seq / t_b,
+             "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+             "latency_definition": "per pose, one-view frame from its own CUDA graph (median of 3)",
+             "batched_group_latency_ms": t_b / max(1, len(groups)),
+             "stage_ms_batched": {k: round(v, 4) for k, v in per_frame_stage.items()},
+             "stage_frac_batched": stage_fracs(work, per_frame_stage, peaks), "roofline": qroof,
+             "status": status, "selected_per_view_mean": float(np.mean(sel)),
+             "entries_per_view_mean": float(np.mean(ent)), "clocks": clk_q}
+    del frames, runs, f1
+    # ---- CPU baselines ------------------------------------------------------------------------
+    if rank == 0 and not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        aabb = oracle.block_bounds(sc, 4.0)
+        t_bounds = time.perf_counter() - t0
+        pick = [c for c in cams if float(c["campos"][2]) in (200.0, 2000.0)] or cams[:1]
+        lod["cpu_baseline"] = cpu_baseline_lod(sc, pick, aabb, lod_dist, "Z = 200 m and 2000 m")
+        lod["cpu_baseline"]["scene_bounds_s"] = round(t_bounds, 2)
+        queue["cpu_baseline"] = cpu_baseline_lod(sc, qcams[:4], aabb, lod_dist, "the first 4 poses of the queue")
+    del ds, sc
+    torch.cuda.empty_cache()
+    return lod, queue
 
 
+# -----------------------------------------------------------------------------------------
+# train32: batched differentiable step over 32 blocks x 8 views
+# -----------------------------------------------------------------------------------------
+def run_train32(args, world, rank, local, peaks, launches_acc):
+    """Batched differentiable step: 32 blocks (log-uniform 200k-3M Gaussians), 8 views each at
+    1600x900, every view rendering its own block, forward + L1 + backward, views grouped into
+    frames by capacity and replayed from one CUDA graph; against one-view steps in sequence.
+    Tile size and batch depth from the autotuner, timed on one group."""
+    import torch
+    from paper_2404_01133_b300 import cgs, synth
+    from paper_2404_01133_b300 import torch_api as ta
+    t0 = time.time()
+    sc, cams, vb = synth.training_blocks(scale_counts=args.train_scale)
+    t_gen = time.time() - t0
+    ds = ta.DeviceScene(sc)
+    W, H = 1600, 900
+    vb_dev = torch.as_tensor(vb).cuda()
+    sel, ent = ta.frame_counts(ds, cams, W, H, view_block=vb_dev)
+    groups = ta.waves(sel, ent, n_cap_max=300_000_000, k_cap_max=(1 << 30) - 1)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    grads = (torch.zeros_like(ds.mean_opac), torch.zeros_like(ds.scale), torch.zeros_like(ds.quat),
+             torch.zeros_like(ds.sh))
+    loss = torch.zeros(1, device="cuda")
+
+    def clear():
+        # the scene-indexed gradients (summed over all views of all blocks) and the loss start
+        # from zero every step, inside the timed region
+        for g_ in grads:
+            g_.zero_()
+        loss.zero_()
+
+    # autotune tile and batch on the first 16 views (two blocks), each tile size with frame
+    # capacities counted for it; a candidate whose frame reports an error is not eligible
+    tv = list(range(min(16, len(cams))))
+    tv_dev = vb_dev[tv].contiguous()
+    tune_frames = {}
+    for tile_ in sorted({t for t, _ in ta.TUNE_CANDIDATES}):
+        s_, e_ = ta.frame_counts(ds, [cams[v] for v in tv], W, H, tile=tile_, view_block=tv_dev)
+        fr_ = ta.Frame(len(tv), W, H, tile_, ds.n_blocks, int(sum(s_) * 1.05) + 1024,
+                       min((1 << 30) - 1, int(sum(e_) * 1.1) + 65536))
+        img_, T_, nc_ = fr_.outputs()
+        tune_frames[tile_] = (fr_, img_, T_, nc_, torch.rand_like(img_), torch.empty_like(img_),
+                              ta.cameras_device([cams[v] for v in tv]))
+    tune_ok = {}
+
+    def run_candidate(tile, batch):
+        fr_, img_, T_, nc_, tg_, dl_, dc_ = tune_frames[tile]
+        c_ = ta.make_config(tile=tile, batch=batch)
+        s_ = ds.struct()
+        cgs.cgs_render_forward(s_, fr_.struct, c_, dc_, tv_dev, None, img_, T_, nc_)
+        cgs.cgs_l1_loss(img_, tg_, img_.numel(), loss, dl_)
+        cgs.cgs_render_backward(s_, fr_.struct, c_, dc_, dl_, T_, nc_, *grads)
+        tune_ok[(tile, batch)] = fr_.status()[0] == cgs.CGS_OK
+
+    _, tune_ms = ta.autotune(run_candidate, ta.TUNE_CANDIDATES, reps=2)
+    ok_ms = {c: tune_ms[f"{c[0]}x{c[1]}"] for c in ta.TUNE_CANDIDATES if tune_ok.get(c)}
+    tile, batch = min(ok_ms, key=ok_ms.get) if ok_ms else (16, 256)
+    del tune_frames
+    torch.cuda.empty_cache()
+    if tile != 16:
+        sel, ent = ta.frame_counts(ds, cams, W, H, tile=tile, view_block=vb_dev)
+        groups = ta.waves(sel, ent, n_cap_max=300_000_000, k_cap_max=(1 << 30) - 1)
+    cfg = ta.make_config(tile=tile, batch=batch)
+    parts = []
+    for views, n_cap, k_cap in groups:
+        fr = ta.Frame(len(views), W, H, tile, ds.n_blocks, n_cap, min((1 << 30) - 1, k_cap))
+        img, T, nc = fr.outputs()
+        tgt = torch.rand_like(img)
+        parts.append((fr, ta.cameras_device([cams[v] for v in views]), vb_dev[views].contiguous(), img, T, nc, tgt,
+                      torch.empty_like(img)))
+
+    def batched_all():
+        cur = torch.cuda.current_stream().cuda_stream
+        s_struct = ds.struct()
+        clear()
+        for fr, dc, vbd, img, T, nc, tgt, dL in parts:
+            cgs.cgs_render_forward(s_struct, fr.struct, cfg, dc, vbd, None, img, T, nc, cur)
+            cgs.cgs_l1_loss(img, tgt, img.numel(), loss, dL, cur)
+            cgs.cgs_render_backward(s_struct, fr.struct, cfg, dc, dL, T, nc, *grads, cur)
+    clocks = ClockSampler(local).start()
+    ms_b, l_b = _graph_ms(batched_all, max(2, args.steps // 4), flush, world)
+    clk = clocks.stop()
+    launches_acc[0] += l_b
+    t_b = max_over_ranks(sum(ms_b) / len(ms_b), world)
+    _, raw = stage_times(batched_all, 1, flush)
+    per_step_stage = {k: v[0] for k, v in raw.items()}
+    counts = np.zeros(8, np.int64)
+    sum_nc = 0
+    status = []
+    for p in parts:
+        s_, c_ = p[0].status()
+        status.append(cgs.cgs_status_string(s_))
+        counts += np.asarray(c_, np.int64)
+        sum_nc += int(p[5].to(torch.int64).sum().item())
+    V = len(cams)
+    n_tiles = ((W + tile - 1) // tile) * ((H + tile - 1) // tile) * V
+    work = stage_work(counts, sum_nc, n_tiles, W * H * V, sc["sh_degree"], backward=True, loss_bytes=12,
+                      packed=False)
+    dom = max(per_step_stage, key=per_step_stage.get)
+    roof = roofline(dom, per_step_stage, work, peaks, KERNEL_NAMES[dom])
+    roof["frame"] = "the batched step's frames together (work and time summed over the frames)"
+    del parts
+    torch.cuda.empty_cache()
+    f1 = ta.Frame(1, W, H, tile, ds.n_blocks, int(max(sel) * 1.02) + 1024,
+                  min((1 << 30) - 1, int(max(ent) * 1.05) + 65536))
+    i1, T1, n1 = f1.outputs()
+    t1 = torch.rand_like(i1)
+    dL1 = torch.empty_like(i1)
+    d1 = [ta.cameras_device([c]) for c in cams]
+
+    def seq_all():
+        cur = torch.cuda.current_stream().cuda_stream
+        s_struct = ds.struct()
+        clear()
+        for v in range(len(cams)):
+            cgs.cgs_render_forward(s_struct, f1.struct, cfg, d1[v], vb_dev[v:v + 1], None, i1, T1, n1, cur)
+            cgs.cgs_l1_loss(i1, t1, i1.numel(), loss, dL1, cur)
+            cgs.cgs_render_backward(s_struct, f1.struct, cfg, d1[v], dL1, T1, n1, *grads, cur)
+    ms_s, l_s = _graph_ms(seq_all, max(2, args.steps // 4), flush, world)
+    launches_acc[0] += l_s
+    t_s = max_over_ranks(sum(ms_s) / len(ms_s), world)
+    out = {"metric": "batched training step Mpix/s (32 blocks x 8 views, 1600x900, fwd+bwd)",
+           "value": world * V * W * H / (t_b * 1e-3) / 1e6, "unit": "Mpix/s", "higher_is_better": True,
+           "config": {"workload": "32 city blocks log-U[200k,3M] Gaussians SH3 (seed 4), 8 views/block 100-400 m, "
+                                  "1600x900, f=1000", "gaussians": ds.n, "groups": [len(g[0]) for g in groups],
+                      "tile": tile, "batch": batch, "generation_s": round(t_gen, 1),
+                      "gradients": "scene-indexed arrays, cleared inside every timed step",
+                      "timing": "CUDA graph of the whole step (all groups), L2 flushed between replays"},
+           "autotune": {"choice": f"{tile}x{batch}", "ms_16_views": tune_ms,
+                        "eligible": [f"{t}x{b}" for (t, b) in ok_ms]},
+           "batched_ms": t_b, "sequential_ms": t_s, "speedup": t_s / t_b,
+           "sequential_mpix_s": world * V * W * H / (t_s * 1e-3) / 1e6,
+           "stage_ms_step": {k: round(v, 4) for k, v in per_step_stage.items()},
+           "stage_frac": stage_fracs(work, per_step_stage, peaks), "roofline": roof,
+           "roofline_overall": ideal_ms(work, peaks) / t_b,
+           "status": status, "selected_per_view_mean": float(np.mean(sel)),
+           "entries_per_view_mean": float(np.mean(ent)), "clocks": clk}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        nt = host_cores()
+        v0 = 0
+        b0 = int(vb[v0])
+        off, cnt = int(sc["level_offset"][b0, 0]), int(sc["level_count"][b0, 0])
+        idx = np.arange(off, off + cnt, dtype=np.int64)
+        tgt0 = np.random.default_rng(7).uniform(0.0, 1.0, size=(3, H, W)).astype(np.float32)
+        t, _ = oracle_frame_par(sc, cams[v0], idx, nt, target=tgt0)
+        s = sum(t.values())
+        oracle.lib("f32")
+        out["cpu_baseline"] = {"value": W * H / s / 1e6, "unit": "Mpix/s", "cores": nt, "kind": "oracle",
+                               "sample": f"one 1600x900 training view of block {b0} ({cnt} Gaussians): projection, "
+                                         "sort, compositing, L1, backward",
+                               "seconds": round(s, 3), "stage_s": {k: round(v, 3) for k, v in t.items()}}
+    del ds, sc, grads
+    torch.cuda.empty_cache()
+    return out
+
+
+# -----------------------------------------------------------------------------------------
+# standalone workloads (--workload): the three above on their own, and the rows beyond the
+# hot path (block partition, detail-level generation, pose assignment)
+# -----------------------------------------------------------------------------------------
 def run_partition(args, world):
     """Block partition of the 20M-Gaussian SH-3 unbounded city (Sec. 3.2.2): block of every
     Gaussian after normalisation and contraction (Eq. 2), stable grouping by block, and the
-    gather of position, scale, rotation and SH rows into block segments; plus the block of
-    every pose of an aerial capture (Eq. 4)."""
+    move of position, scale, rotation and SH rows into block segments; plus the block of every
+    pose of an aerial capture (Eq. 4)."""
     import torch
     from paper_2404_01133_b300 import build as libbuild, cgs, synth
-    from paper_2404_01133_b300 import torch_api as ta
     libbuild.build()
     t0 = time.time()
     sc, box = synth.unbounded_city(20_000_000, seed=3)
@@ -885,8 +1288,7 @@ def run_partition(args, world):
     if cgs.cgs_partition_status(ws) != cgs.CGS_OK:
         raise RuntimeError("partition status")
     off = offset.cpu().numpy()
-    clocks = ClockSampler(0)
-    clocks.start()
+    clocks = ClockSampler(0).start()
     ms, launches = timed_fn(step, args.steps, st, flush, world)
     clk = clocks.stop()
     ms_a, _ = timed_fn(assign_group, args.steps, st, flush, world)
@@ -984,8 +1386,7 @@ def run_levels(args, world):
     status, counts = frame.status()
     if status != cgs.CGS_OK or cgs.cgs_levels_status(lws) != cgs.CGS_OK:
         raise RuntimeError("levels workload status")
-    clocks = ClockSampler(0)
-    clocks.start()
+    clocks = ClockSampler(0).start()
     ms_h, l1 = timed_fn(count_hits, args.steps, st, flush, world)
     ms_r, l2 = timed_fn(rank, args.steps, st, flush, world)
     ms_g, l3 = timed_fn(gather, args.steps, st, flush, world)
@@ -1024,7 +1425,7 @@ def run_assign(args, world):
     MatrixCity), B2 (Eq. 4) and B (Eq. 5); aerial poses at 150-400 m, 800x450 renders (one
     batched frame of 65 views per pose, split into waves)."""
     import torch
-    from paper_2404_01133_b300 import build as libbuild, cgs, synth
+    from paper_2404_01133_b300 import build as libbuild, synth
     from paper_2404_01133_b300 import torch_api as ta
     libbuild.build()
     t0 = time.time()
@@ -1046,8 +1447,7 @@ def run_assign(args, world):
             for p in pos]
     ta.pose_assign(ds, cams[:2], box[0], box[1], grid, 0.05)  # warm-up
     torch.cuda.synchronize()
-    clocks = ClockSampler(0)
-    clocks.start()
+    clocks = ClockSampler(0).start()
     barrier(world)
     t1 = time.perf_counter()
     b1, b2, b, s = ta.pose_assign(ds, cams[4:], box[0], box[1], grid, 0.05)
@@ -1066,141 +1466,21 @@ def run_assign(args, world):
                                          "b": float(b.sum().item()) / P}}
 
 
-def run_lodqueue(args, world):
-    """64 seeded top-down poses over the 20M-Gaussian LoD city: batched frames (views grouped
-    to fit the frame capacity, one CUDA graph) against 64 sequential one-view renders."""
+def run_nested_alone(args, world, rank, local, which):
     import torch
-    from paper_2404_01133_b300 import build as libbuild, cgs, synth
-    from paper_2404_01133_b300 import torch_api as ta
+    from paper_2404_01133_b300 import build as libbuild
     libbuild.build()
-    sc, _ = synth.workload_city_lod(heights=())
-    cams = synth.lod_pose_queue(sc["side"])
-    ds = ta.DeviceScene(sc)
-    ds.compute_block_bounds(4.0)
-    cfg = ta.make_config(tile=16, batch=args.lod_batch, lod_dist=(200.0, 600.0))
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    sel, ent = ta.frame_counts(ds, cams, 1920, 1080)
-    V = len(cams)
-    # sequential: one frame sized for the largest view, per-frame latency from events
-    f1 = ta.Frame(1, 1920, 1080, 16, ds.n_blocks, int(max(sel) * 1.02) + 1024,
-                  min((1 << 30) - 1, int(max(ent) * 1.05) + 65536))
-    d1 = [ta.cameras_device([c]) for c in cams]
-    runs = [_fwd_runner(ds, f1, cfg, d) for d in d1]
-
-    def seq_all():
-        for r in runs:
-            r()
-    seq_graph = ta.capture(seq_all, warmup=1)
-    lat = []
-    for v in range(V):
-        g = ta.capture(runs[v], warmup=1)
-        ms, _ = timed_fn(g.replay, 3, torch.cuda.current_stream(), flush, world)
-        lat.append(sorted(ms)[1])
-        del g
-    ms_seq, _ = timed_fn(seq_graph.replay, max(2, args.steps // 4), torch.cuda.current_stream(), flush, world)
-    t_seq = max_over_ranks(sum(ms_seq) / len(ms_seq), world)
-    # batched: views grouped by capacity, each group one frame; all groups in one graph
-    groups = ta.waves(sel, ent, n_cap_max=200_000_000, k_cap_max=(1 << 30) - 1)
-    frames = []
-    for views, n_cap, k_cap in groups:
-        fr = ta.Frame(len(views), 1920, 1080, 16, ds.n_blocks, n_cap, min((1 << 30) - 1, k_cap))
-        frames.append((fr, _fwd_runner(ds, fr, cfg, ta.cameras_device([cams[v] for v in views]))))
-
-    def batched_all():
-        for _, r in frames:
-            r()
-    ms_b, _ = timed_fn(ta.capture(batched_all, warmup=1).replay, max(2, args.steps // 4),
-                       torch.cuda.current_stream(), flush, world)
-    t_b = max_over_ranks(sum(ms_b) / len(ms_b), world)
-    status = [cgs.cgs_status_string(fr.status()[0]) for fr, _ in frames]
-    return {"metric": "LoD pose queue FPS, batched vs sequential (64 poses, 20M Gaussians, 1080p)",
-            "value": world * V / (t_b * 1e-3), "unit": "FPS", "n_gpus": world, "higher_is_better": True,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "city-20M-SH3 6 km^2, 8x8 blocks, 64 top-down poses 30-2500 m, 1920x1080",
-                       "groups": [len(g[0]) for g in groups]},
-            "batched_fps": world * V / (t_b * 1e-3), "batched_ms": t_b,
-            "sequential_fps": world * V / (t_seq * 1e-3), "sequential_ms": t_seq,
-            "speedup": t_seq / t_b, "latency_ms_p50": float(np.percentile(lat, 50)),
-            "latency_ms_p99": float(np.percentile(lat, 99)), "status": status,
-            "selected_per_view_mean": float(np.mean(sel)), "entries_per_view_mean": float(np.mean(ent))}
-
-
-def run_train32(args, world):
-    """Batched differentiable step: 32 blocks (log-uniform 200k-3M Gaussians), 8 views each at
-    1600x900, every view rendering its own block, forward + L1 + backward, views grouped into
-    frames by capacity and replayed from one CUDA graph; against one-view steps in sequence."""
-    import torch
-    from paper_2404_01133_b300 import build as libbuild, cgs, synth
-    from paper_2404_01133_b300 import torch_api as ta
-    libbuild.build()
-    t0 = time.time()
-    sc, cams, vb = synth.training_blocks()
-    t_gen = time.time() - t0
-    ds = ta.DeviceScene(sc)
-    cfg = ta.make_config(tile=16, batch=256)
-    W, H = 1600, 900
-    vb_dev = torch.as_tensor(vb).cuda()
-    sel, ent = ta.frame_counts(ds, cams, W, H, view_block=vb_dev)
-    groups = ta.waves(sel, ent, n_cap_max=300_000_000, k_cap_max=(1 << 30) - 1)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    grads = (torch.zeros_like(ds.mean_opac), torch.zeros_like(ds.scale), torch.zeros_like(ds.quat),
-             torch.zeros_like(ds.sh))
-    loss = torch.zeros(1, device="cuda")
-    parts = []
-    for views, n_cap, k_cap in groups:
-        fr = ta.Frame(len(views), W, H, 16, ds.n_blocks, n_cap, min((1 << 30) - 1, k_cap))
-        img, T, nc = fr.outputs()
-        tgt = torch.rand_like(img)
-        parts.append((fr, ta.cameras_device([cams[v] for v in views]), vb_dev[views].contiguous(), img, T, nc, tgt,
-                      torch.empty_like(img)))
-
-    def clear():
-        # the scene-indexed gradients (summed over all views of all blocks) and the loss start
-        # from zero every step, inside the timed region
-        for g_ in grads:
-            g_.zero_()
-        loss.zero_()
-
-    def batched_all():
-        cur = torch.cuda.current_stream().cuda_stream
-        s_struct = ds.struct()
-        clear()
-        for fr, dc, vbd, img, T, nc, tgt, dL in parts:
-            cgs.cgs_render_forward(s_struct, fr.struct, cfg, dc, vbd, None, img, T, nc, cur)
-            cgs.cgs_l1_loss(img, tgt, img.numel(), loss, dL, cur)
-            cgs.cgs_render_backward(s_struct, fr.struct, cfg, dc, dL, T, nc, *grads, cur)
-    ms_b, _ = timed_fn(ta.capture(batched_all, warmup=1).replay, max(2, args.steps // 4),
-                       torch.cuda.current_stream(), flush, world)
-    t_b = max_over_ranks(sum(ms_b) / len(ms_b), world)
-    status = [cgs.cgs_status_string(p[0].status()[0]) for p in parts]
-    del parts
-    f1 = ta.Frame(1, W, H, 16, ds.n_blocks, int(max(sel) * 1.02) + 1024, min((1 << 30) - 1, int(max(ent) * 1.05) + 65536))
-    i1, T1, n1 = f1.outputs()
-    t1 = torch.rand_like(i1)
-    dL1 = torch.empty_like(i1)
-    d1 = [ta.cameras_device([c]) for c in cams]
-
-    def seq_all():
-        cur = torch.cuda.current_stream().cuda_stream
-        s_struct = ds.struct()
-        clear()
-        for v in range(len(cams)):
-            cgs.cgs_render_forward(s_struct, f1.struct, cfg, d1[v], vb_dev[v:v + 1], None, i1, T1, n1, cur)
-            cgs.cgs_l1_loss(i1, t1, i1.numel(), loss, dL1, cur)
-            cgs.cgs_render_backward(s_struct, f1.struct, cfg, d1[v], dL1, T1, n1, *grads, cur)
-    ms_s, _ = timed_fn(ta.capture(seq_all, warmup=1).replay, max(2, args.steps // 4),
-                       torch.cuda.current_stream(), flush, world)
-    t_s = max_over_ranks(sum(ms_s) / len(ms_s), world)
-    V = len(cams)
-    return {"metric": "batched training step Mpix/s (32 blocks x 8 views, 1600x900, fwd+bwd)",
-            "value": world * V * W * H / (t_b * 1e-3) / 1e6, "unit": "Mpix/s", "n_gpus": world,
-            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "32 city blocks log-U[200k,3M] Gaussians SH3, 8 views/block 100-400 m, 1600x900",
-                       "gaussians": ds.n, "groups": [len(g[0]) for g in groups], "generation_s": t_gen,
-                       "gradients": "scene-indexed arrays, cleared inside every timed step"},
-            "batched_ms": t_b, "sequential_ms": t_s, "speedup": t_s / t_b,
-            "sequential_mpix_s": world * V * W * H / (t_s * 1e-3) / 1e6, "status": status,
-            "selected_per_view_mean": float(np.mean(sel)), "entries_per_view_mean": float(np.mean(ent))}
+    peaks = device_peaks(torch.device("cuda", local), local)
+    acc = [0]
+    if which == "train32":
+        out = run_train32(args, world, rank, local, peaks, acc)
+    else:
+        lod, queue = run_lod_workloads(args, world, rank, local, peaks, acc)
+        out = lod if which == "lod20m" else queue
+        out["other"] = queue if which == "lod20m" else lod
+    out.update({"n_gpus": world, "steps": args.steps, "dtype": "f32", "data": "synthetic", "gpu_launches": acc[0],
+                "peaks": peaks})
+    return out
 
 
 def main():
@@ -1213,12 +1493,8 @@ def main():
             print(json.dumps(out))
         return
     world, rank, local = dist_setup()
-    if args.workload == "lod20m":
-        out = run_lod20m(args, world)
-    elif args.workload == "lodqueue":
-        out = run_lodqueue(args, world)
-    elif args.workload == "train32":
-        out = run_train32(args, world)
+    if args.workload in ("lod20m", "lodqueue", "train32"):
+        out = run_nested_alone(args, world, rank, local, args.workload)
     elif args.workload == "partition":
         out = run_partition(args, world)
     elif args.workload == "levels":
