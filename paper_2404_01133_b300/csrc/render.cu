@@ -10,6 +10,12 @@ namespace cgs {
 // order.  n_contrib and the evaluated-pair count keep the semantics of a walk over the full
 // list: entries up to and including the stopping one, or the whole list.
 //
+// A lane's two pixels are packed pairs (render_common.cuh): the falloff, -alpha, the
+// transmittance update and the colour sums of both pixels take one packed instruction each.
+// The colour is accumulated negated (the staged opacity is -o), NC = -C, exactly.  Per pixel
+// and entry, written without branches: a warp runs every step for all its lanes anyway, and
+// a pair that does not blend adds c * 0 and keeps T and last.
+//
 // With HITS, every blend is also counted per scene Gaussian: one atomic add per (warp, entry)
 // of the number of the warp's pixels that blended it (L.hits, indexed by scene index).
 template <int B, int BATCH, bool HITS>
@@ -18,7 +24,7 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 8 : 32) k_render_fwd(Layo
                                                           float* __restrict__ final_T, uint32_t* __restrict__ n_contrib)
 {
     constexpr int NT = B * B / 2;
-    __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH];
+    __shared__ float4 s_e0[BATCH], s_e1[BATCH], s_e2[BATCH], s_e3[BATCH];
     __shared__ uint32_t s_m[BATCH];
     __shared__ uint32_t s_g[HITS ? BATCH : 1];
     const int v = blockIdx.z;
@@ -28,7 +34,8 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 8 : 32) k_render_fwd(Layo
     pixels_of<B>(threadIdx.x, &lx, &ly, &wx0, &wy0);
     const int px = blockIdx.x * B + lx, py0 = blockIdx.y * B + ly, py1 = py0 + 4;
     const bool in0 = px < L.W && py0 < L.H, in1 = px < L.W && py1 < L.H;
-    const float fpx = (float)px, fpy0 = (float)py0, fpy1 = (float)py1;
+    const float fpx = (float)px;
+    const float2 fpy = make_float2((float)py0, (float)py1);
     const float tx0 = (float)(blockIdx.x * B), ty0 = (float)(blockIdx.y * B);
     const int lane = threadIdx.x & 31;
     const uint32_t wbit = 1u << (threadIdx.x >> 5);
@@ -37,19 +44,23 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 8 : 32) k_render_fwd(Layo
     const size_t tg = (size_t)v * L.T + tile;
     uint32_t* cbits = L.cbits + (size_t)NW * (rg.x / 32 + tg) + (size_t)(threadIdx.x >> 5) * ((rg.y - rg.x) / 32 + 1);
     uint32_t steps = 0, useful = 0;  // warp steps visited / with a blend (lane 0 counts)
-    FwdPixel p0, p1;
-    p0.done = !in0;
-    p1.done = !in1;
+    float2 T = make_float2(1.0f, 1.0f);
+    float2 NC0 = make_float2(0.0f, 0.0f), NC1 = NC0, NC2 = NC0;  // minus the colour sums
+    uint32_t last0 = 0, last1 = 0, stop0 = 0xffffffffu, stop1 = 0xffffffffu;
+    bool done0 = !in0, done1 = !in1;
+    const float nthr = -1.0f / 255.0f;
     for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
-        if (__syncthreads_count(p0.done && p1.done) == NT) break;
+        if (__syncthreads_count(done0 && done1) == NT) break;
         for (int i = threadIdx.x; i < BATCH; i += NT) {
             uint32_t m = 0;
             if (start + i < rg.y) {
                 const size_t j = tval[start + i];
                 const float4 a = L.rec[3 * j], b = L.rec[3 * j + 1], c = L.rec[3 * j + 2];
-                s_a[i] = a;
-                s_b[i] = power_factors(b);
-                s_c[i] = c;
+                const Staged se = stage_entry(a, b, c);
+                s_e0[i] = se.e0;
+                s_e1[i] = se.e1;
+                s_e2[i] = se.e2;
+                s_e3[i] = se.e3;
                 m = warp_mask<B>(a, b, c.w, tx0, ty0);
                 if (HITS) s_g[i] = L.gidx[j];
             }
@@ -58,7 +69,7 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 8 : 32) k_render_fwd(Layo
         __syncthreads();
         const int nb = (int)min((uint32_t)BATCH, rg.y - start);
         for (int c0 = 0; c0 < nb; c0 += 32) {
-            if (__all_sync(0xffffffffu, p0.done && p1.done)) break;
+            if (__all_sync(0xffffffffu, done0 && done1)) break;
             uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < nb && (s_m[c0 + lane] & wbit));
             const uint32_t s_bits = bits;
             uint32_t word = 0;
@@ -66,12 +77,33 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 8 : 32) k_render_fwd(Layo
                 const int kk = __ffs(bits) - 1;
                 bits &= bits - 1;
                 const int k = c0 + kk;
-                const float4 a = s_a[k], nf = s_b[k], c = s_c[k];
+                const float4 e0 = s_e0[k], e1 = s_e1[k], e2 = s_e2[k], e3 = s_e3[k];
                 const uint32_t pos = start - rg.x + (uint32_t)k;
-                float pw0, pw1, dx, dy0, dy1;
-                pair_power2(a, nf, fpx, fpy0, fpy1, &pw0, &pw1, &dx, &dy0, &dy1);
-                const bool b0 = p0.blend(pw0, a.z, c, pos);
-                const bool b1 = p1.blend(pw1, a.z, c, pos);
+                float dx;
+                float2 dy;
+                const float2 p = staged_power2(e0, e1, fpx, fpy, &dx, &dy);
+                const float2 G = make_float2(gauss_exp2(p.x), gauss_exp2(p.y));
+                float2 nog;
+                const float2 na = neg_alpha2(e2, G, &nog);  // -alpha
+                const float2 Tn = ieee_fma2(na, T, T);      // T (1 - alpha), rounded once
+                const bool ok0 = !done0 && !(p.x > 0.0f) && !(na.x > nthr);
+                const bool ok1 = !done1 && !(p.y > 0.0f) && !(na.y > nthr);
+                const bool st0 = ok0 && Tn.x < 1e-4f, st1 = ok1 && Tn.y < 1e-4f;
+                const bool b0 = ok0 && !st0, b1 = ok1 && !st1;
+                // -alpha where the pixel blends, 0 where it does not: then T (1 - alpha) and the
+                // colour weight alpha T come out of the packed FMA pipe (fma(0, T, T) = T exactly)
+                const float2 nab = make_float2(b0 ? na.x : 0.0f, b1 ? na.y : 0.0f);
+                const float2 w = __fmul2_rn(nab, T);        // -alpha T, or 0
+                NC0 = __ffma2_rn(make_float2(e2.z, e2.w), w, NC0);
+                NC1 = __ffma2_rn(make_float2(e3.x, e3.y), w, NC1);
+                NC2 = __ffma2_rn(make_float2(e3.z, e3.w), w, NC2);
+                T = ieee_fma2(nab, T, T);
+                last0 = b0 ? pos + 1u : last0;
+                last1 = b1 ? pos + 1u : last1;
+                stop0 = st0 ? pos : stop0;
+                stop1 = st1 ? pos : stop1;
+                done0 = done0 || st0;
+                done1 = done1 || st1;
                 if (__any_sync(0xffffffffu, b0 || b1)) word |= 1u << kk;
                 if (HITS) {
                     const int cnt = __popc(__ballot_sync(0xffffffffu, b0)) + __popc(__ballot_sync(0xffffffffu, b1));
@@ -88,23 +120,23 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 8 : 32) k_render_fwd(Layo
     const size_t HW = (size_t)L.W * L.H;
     if (in0) {
         const size_t pix = (size_t)py0 * L.W + px;
-        image[(3 * (size_t)v + 0) * HW + pix] = p0.C0 + p0.T * bg0;
-        image[(3 * (size_t)v + 1) * HW + pix] = p0.C1 + p0.T * bg1;
-        image[(3 * (size_t)v + 2) * HW + pix] = p0.C2 + p0.T * bg2;
-        final_T[(size_t)v * HW + pix] = p0.T;
-        n_contrib[(size_t)v * HW + pix] = p0.last;
+        image[(3 * (size_t)v + 0) * HW + pix] = T.x * bg0 - NC0.x;
+        image[(3 * (size_t)v + 1) * HW + pix] = T.x * bg1 - NC1.x;
+        image[(3 * (size_t)v + 2) * HW + pix] = T.x * bg2 - NC2.x;
+        final_T[(size_t)v * HW + pix] = T.x;
+        n_contrib[(size_t)v * HW + pix] = last0;
     }
     if (in1) {
         const size_t pix = (size_t)py1 * L.W + px;
-        image[(3 * (size_t)v + 0) * HW + pix] = p1.C0 + p1.T * bg0;
-        image[(3 * (size_t)v + 1) * HW + pix] = p1.C1 + p1.T * bg1;
-        image[(3 * (size_t)v + 2) * HW + pix] = p1.C2 + p1.T * bg2;
-        final_T[(size_t)v * HW + pix] = p1.T;
-        n_contrib[(size_t)v * HW + pix] = p1.last;
+        image[(3 * (size_t)v + 0) * HW + pix] = T.y * bg0 - NC0.y;
+        image[(3 * (size_t)v + 1) * HW + pix] = T.y * bg1 - NC1.y;
+        image[(3 * (size_t)v + 2) * HW + pix] = T.y * bg2 - NC2.y;
+        final_T[(size_t)v * HW + pix] = T.y;
+        n_contrib[(size_t)v * HW + pix] = last1;
     }
     const uint32_t len = rg.y - rg.x;
-    const uint32_t visited = (in0 ? (p0.stop_at != 0xffffffffu ? p0.stop_at + 1u : len) : 0u) +
-                             (in1 ? (p1.stop_at != 0xffffffffu ? p1.stop_at + 1u : len) : 0u);
+    const uint32_t visited = (in0 ? (stop0 != 0xffffffffu ? stop0 + 1u : len) : 0u) +
+                             (in1 ? (stop1 != 0xffffffffu ? stop1 + 1u : len) : 0u);
     const uint32_t ws = __reduce_add_sync(0xffffffffu, visited);
     if (lane == 0) {
         if (ws) atomicAdd(&L.hdr->pairs_fwd, (unsigned long long)ws);

@@ -8,10 +8,24 @@
 namespace cgs {
 
 // Backward.  A warp visits exactly the entries that blended into at least one of its pixels
-// in the forward (the forward's contribution bits), three at a time: the 27 sums of the
-// three entries over the warp's 64 pixels come out of one transpose reduction (lane l holds
-// sum l), are added in shared memory per entry, turned into dL/d(u, v, conic, o, rgb) with
-// the entry's conic, and added once per (tile, Gaussian) to the global accumulator.
+// in the forward (the forward's contribution bits), last first.  Per entry, a lane replays its
+// two pixels as packed pairs and reduces them to nine values:
+//   w = dL/do of a pixel (dalpha/do = G when the 0.99 clamp is inactive, else 0); since
+//   dL/dpower = o w, the power moments are kept as moments of w and multiplied by o once per
+//   (tile, Gaussian):  m0 = sum w dx, m1 = sum w dy, m2 = sum w dx^2, m3 = sum w dx dy,
+//   m4 = sum w dy^2, m5 = sum w;  m6..m8 = sum (-alpha T) dL/d(r, g, b)  (negated colour
+//   gradient, the staged opacity being -o).
+// The two pixels of a lane share dx, so m0 = dx m5, m2 = dx m0, m3 = dx m1.  Up to three
+// entries' 27 values go through a per-warp shared-memory transpose (row = value, column =
+// lane; lane r then sums row r with eight 16-byte loads), are added in shared memory per
+// entry, turned into dL/d(u, v, conic, o, rgb) with the entry's conic and opacity, and added
+// once per (tile, Gaussian) to the global accumulator.
+//
+// Replay of one pixel: from its final transmittance T and gS = dL/dP . S, S the colour behind
+// the current entry (initially T_final bg), entry i with alpha = min(0.99, o G) recovers
+// T_before = T / (1 - alpha); dL/dalpha = (T (g . c) - gS) / (1 - alpha), dL/dc = g alpha
+// T_before; then T = T_before and gS += alpha T_before (g . c).  The running sum is kept
+// negated (ngS = -gS) and alpha enters as -alpha, so no step negates anything.
 template <int B, int BATCH>
 __global__ void __launch_bounds__(B * B / 2, B == 16 ? 6 : 24) k_render_bwd(Layout L, const uint32_t* __restrict__ tval, float bg0,
                                                           float bg1, float bg2, const float* __restrict__ dL_dimg,
@@ -20,9 +34,11 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 6 : 24) k_render_bwd(Layo
 {
     constexpr int NT = B * B / 2;
     constexpr int NW = B * B / 64;
-    __shared__ float4 s_a[BATCH], s_b[BATCH], s_c[BATCH], s_f[BATCH];
+    constexpr int RS = 36;  // transpose row stride: 32 lanes + 4, conflict-free 16-byte row reads
+    __shared__ float4 s_e0[BATCH], s_e1[BATCH], s_e2[BATCH], s_e3[BATCH], s_cn[BATCH];
     __shared__ uint32_t s_j[BATCH];
     __shared__ float s_g[BATCH][9];
+    __shared__ __align__(16) float s_red[NW][27][RS];
     __shared__ uint32_t s_maxnc;
     const int v = blockIdx.z;
     const int tile = blockIdx.y * L.tiles_x + blockIdx.x;
@@ -31,34 +47,35 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 6 : 24) k_render_bwd(Layo
     pixels_of<B>(threadIdx.x, &lx, &ly, &wx0, &wy0);
     const int px = blockIdx.x * B + lx, py0 = blockIdx.y * B + ly, py1 = py0 + 4;
     const bool in0 = px < L.W && py0 < L.H, in1 = px < L.W && py1 < L.H;
-    const float fpx = (float)px, fpy0 = (float)py0, fpy1 = (float)py1;
-    const int lane = threadIdx.x & 31;
+    const float fpx = (float)px;
+    const float2 fpy = make_float2((float)py0, (float)py1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const size_t tg = (size_t)v * L.T + tile;
-    const uint32_t* cbits =
-        L.cbits + (size_t)NW * (rg.x / 32 + tg) + (size_t)(threadIdx.x >> 5) * ((rg.y - rg.x) / 32 + 1);
+    const uint32_t* cbits = L.cbits + (size_t)NW * (rg.x / 32 + tg) + (size_t)warp * ((rg.y - rg.x) / 32 + 1);
     const size_t HW = (size_t)L.W * L.H;
-    BwdPixel q0, q1;
+    float2 T = make_float2(1.0f, 1.0f), g0 = make_float2(0.0f, 0.0f), g1 = g0, g2 = g0;
+    uint32_t nc0 = 0, nc1 = 0;
     if (in0) {
         const size_t pix = (size_t)py0 * L.W + px;
-        q0.T = final_T[(size_t)v * HW + pix];
-        q0.nc = n_contrib[(size_t)v * HW + pix];
-        q0.g0 = dL_dimg[(3 * (size_t)v + 0) * HW + pix];
-        q0.g1 = dL_dimg[(3 * (size_t)v + 1) * HW + pix];
-        q0.g2 = dL_dimg[(3 * (size_t)v + 2) * HW + pix];
+        T.x = final_T[(size_t)v * HW + pix];
+        nc0 = n_contrib[(size_t)v * HW + pix];
+        g0.x = dL_dimg[(3 * (size_t)v + 0) * HW + pix];
+        g1.x = dL_dimg[(3 * (size_t)v + 1) * HW + pix];
+        g2.x = dL_dimg[(3 * (size_t)v + 2) * HW + pix];
     }
     if (in1) {
         const size_t pix = (size_t)py1 * L.W + px;
-        q1.T = final_T[(size_t)v * HW + pix];
-        q1.nc = n_contrib[(size_t)v * HW + pix];
-        q1.g0 = dL_dimg[(3 * (size_t)v + 0) * HW + pix];
-        q1.g1 = dL_dimg[(3 * (size_t)v + 1) * HW + pix];
-        q1.g2 = dL_dimg[(3 * (size_t)v + 2) * HW + pix];
+        T.y = final_T[(size_t)v * HW + pix];
+        nc1 = n_contrib[(size_t)v * HW + pix];
+        g0.y = dL_dimg[(3 * (size_t)v + 0) * HW + pix];
+        g1.y = dL_dimg[(3 * (size_t)v + 1) * HW + pix];
+        g2.y = dL_dimg[(3 * (size_t)v + 2) * HW + pix];
     }
-    q0.gS = q0.T * (q0.g0 * bg0 + q0.g1 * bg1 + q0.g2 * bg2);
-    q1.gS = q1.T * (q1.g0 * bg0 + q1.g1 * bg1 + q1.g2 * bg2);
+    float2 ngS = make_float2(-(T.x * (g0.x * bg0 + g1.x * bg1 + g2.x * bg2)),
+                             -(T.y * (g0.y * bg0 + g1.y * bg1 + g2.y * bg2)));
     if (threadIdx.x == 0) s_maxnc = 0;
     __syncthreads();
-    const uint32_t mnc = max(q0.nc, q1.nc);
+    const uint32_t mnc = max(nc0, nc1);
     if (mnc) atomicMax(&s_maxnc, mnc);
     __syncthreads();
     const long long first = rg.x;
@@ -69,7 +86,10 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 6 : 24) k_render_bwd(Layo
     uint32_t wmax = mnc;
 #pragma unroll
     for (int o = 16; o; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+    const float nthr = -1.0f / 255.0f;
+    const float2 one = make_float2(1.0f, 1.0f);
     uint32_t pairs = 0;
+    float(*red)[RS] = s_red[warp];
     // batches at list positions that are multiples of BATCH (as in the forward), last first,
     // so contribution words line up with 32-entry chunks
     for (long long bi = (end - first - 1) / BATCH; end > first && bi >= 0; bi--) {
@@ -80,71 +100,119 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 6 : 24) k_render_bwd(Layo
         for (int i = threadIdx.x; i < nb; i += NT) {
             const uint32_t j = tval[bs + i];
             s_j[i] = j;
-            s_a[i] = L.rec[3 * (size_t)j];
-            const float4 cb = L.rec[3 * (size_t)j + 1];
-            s_b[i] = cb;
-            s_f[i] = power_factors(cb);
-            s_c[i] = L.rec[3 * (size_t)j + 2];
+            const float4 a = L.rec[3 * (size_t)j], cb = L.rec[3 * (size_t)j + 1], c = L.rec[3 * (size_t)j + 2];
+            const Staged se = stage_entry(a, cb, c);
+            s_e0[i] = se.e0;
+            s_e1[i] = se.e1;
+            s_e2[i] = se.e2;
+            s_e3[i] = se.e3;
+            s_cn[i] = make_float4(cb.x, cb.y, cb.z, a.z);
         }
         for (int i = threadIdx.x; i < 9 * BATCH; i += NT) (&s_g[0][0])[i] = 0.0f;
         __syncthreads();
         const int kmax = (int)min((long long)nb, (long long)wmax - (bs - first));  // entries k < kmax
-        for (int c0 = ((kmax - 1) & ~31); kmax > 0 && c0 >= 0; c0 -= 32) {
+        // this warp's set bits of the batch, highest first, across its 32-entry chunks
+        int c0 = (kmax - 1) & ~31;
+        uint32_t bits = 0;
+        if (kmax > 0) {
+            bits = cbits[(uint32_t)(bs - first + c0) >> 5];
             const int avail = kmax - c0;
-            uint32_t bits = cbits[(uint32_t)(bs - first + c0) >> 5];
             if (avail < 32) bits &= (1u << avail) - 1u;
-            while (bits) {
-                // up to three entries, in descending list order
-                int ks[3];
-#pragma unroll
-                for (int e = 0; e < 3; e++) {
-                    if (bits) {
-                        const int hb = 31 - __clz(bits);
-                        bits &= ~(1u << hb);
-                        ks[e] = c0 + hb;
-                    } else {
-                        ks[e] = -1;
-                    }
-                }
-                float acc[32];
-#pragma unroll
-                for (int i = 27; i < 32; i++) acc[i] = 0.0f;
-#pragma unroll
-                for (int e = 0; e < 3; e++) {
-                    if (ks[e] < 0) {
-#pragma unroll
-                        for (int i = 0; i < 9; i++) acc[9 * e + i] = 0.0f;
-                        continue;
-                    }
-                    const int k = ks[e];
-                    const float4 a = s_a[k], nf = s_f[k], c = s_c[k];
-                    const uint32_t lp = (uint32_t)(bs + k - first);
-                    float pw0, pw1, dx, dy0, dy1;
-                    pair_power2(a, nf, fpx, fpy0, fpy1, &pw0, &pw1, &dx, &dy0, &dy1);
-                    pairs += (uint32_t)q0.replay<true>(pw0, dx, dy0, a.z, c, lp, acc + 9 * e);
-                    pairs += (uint32_t)q1.replay<false>(pw1, dx, dy1, a.z, c, lp, acc + 9 * e);
-                }
-                const float tot = warp_transpose_sum32(acc, lane);
-                if (lane < 27) {
-                    const int e = lane / 9, comp = lane - 9 * e;
-                    const int k = e == 0 ? ks[0] : (e == 1 ? ks[1] : ks[2]);
-                    if (k >= 0 && tot != 0.0f) atomicAdd(&s_g[k][comp], tot);
-                }
+        }
+        // the next set bit of the batch's words, highest first (-1 when none is left)
+        auto next = [&]() -> int {
+            while (!bits && c0 > 0) {
+                c0 -= 32;
+                bits = cbits[(uint32_t)(bs - first + c0) >> 5];
             }
+            if (!bits) return -1;
+            const int hb = 31 - __clz(bits);
+            bits &= ~(1u << hb);
+            return c0 + hb;
+        };
+        while (true) {
+            const int k0 = next(), k1 = next(), k2 = next();
+            const int ne = (k0 >= 0) + (k1 >= 0) + (k2 >= 0);
+            if (ne == 0) break;
+#pragma unroll 1
+            for (int e = 0; e < ne; e++) {
+                const int k = e == 0 ? k0 : (e == 1 ? k1 : k2);
+                const float4 e0 = s_e0[k], e1 = s_e1[k], e2 = s_e2[k], e3 = s_e3[k];
+                const uint32_t lp = (uint32_t)(bs + k - first);
+                float dx;
+                float2 dy;
+                const float2 p = staged_power2(e0, e1, fpx, fpy, &dx, &dy);
+                const float2 G = make_float2(gauss_exp2(p.x), gauss_exp2(p.y));
+                float2 nog;
+                const float2 na = neg_alpha2(e2, G, &nog);  // -alpha
+                const bool u0 = lp < nc0 && !(p.x > 0.0f) && !(na.x > nthr);
+                const bool u1 = lp < nc1 && !(p.y > 0.0f) && !(na.y > nthr);
+                const float2 om = __fadd2_rn(one, na);                 // 1 - alpha
+                const float2 inv = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
+                const float2 gc = __ffma2_rn(g2, make_float2(e3.z, e3.w),
+                                             __ffma2_rn(g1, make_float2(e3.x, e3.y),
+                                                        __fmul2_rn(g0, make_float2(e2.z, e2.w))));
+                const float2 dal = __fmul2_rn(inv, __ffma2_rn(gc, T, ngS));  // dL/dalpha
+                const float2 Tb = __fmul2_rn(T, inv);                        // T before the entry
+                const float2 naT = __fmul2_rn(na, Tb);                       // -alpha T_before
+                const float2 ngS2 = __ffma2_rn(naT, gc, ngS);
+                T = make_float2(u0 ? Tb.x : T.x, u1 ? Tb.y : T.y);
+                ngS = make_float2(u0 ? ngS2.x : ngS.x, u1 ? ngS2.y : ngS.y);
+                // the 0.99 clamp passes no gradient to the opacity or the power
+                const float2 wG = __fmul2_rn(dal, G);
+                const float w0 = (u0 && !(nog.x < -0.99f)) ? wG.x : 0.0f;
+                const float w1 = (u1 && !(nog.y < -0.99f)) ? wG.y : 0.0f;
+                const float2 nt = make_float2(u0 ? naT.x : 0.0f, u1 ? naT.y : 0.0f);
+                const float F = w0 + w1;
+                const float2 b = __fmul2_rn(make_float2(w0, w1), dy);
+                const float m0 = dx * F, m1 = b.x + b.y;
+                const float2 c0g = __fmul2_rn(g0, nt), c1g = __fmul2_rn(g1, nt), c2g = __fmul2_rn(g2, nt);
+                red[9 * e + 0][lane] = m0;
+                red[9 * e + 1][lane] = m1;
+                red[9 * e + 2][lane] = dx * m0;
+                red[9 * e + 3][lane] = dx * m1;
+                red[9 * e + 4][lane] = fmaf(b.x, dy.x, b.y * dy.y);
+                red[9 * e + 5][lane] = F;
+                red[9 * e + 6][lane] = c0g.x + c0g.y;
+                red[9 * e + 7][lane] = c1g.x + c1g.y;
+                red[9 * e + 8][lane] = c2g.x + c2g.y;
+                pairs += (uint32_t)u0 + (uint32_t)u1;
+            }
+            __syncwarp();
+            if (lane < 9 * ne) {
+                const float4* row = reinterpret_cast<const float4*>(red[lane]);
+                float4 acc = row[0];
+#pragma unroll
+                for (int q = 1; q < 8; q++) {
+                    const float4 x = row[q];
+                    acc.x += x.x;
+                    acc.y += x.y;
+                    acc.z += x.z;
+                    acc.w += x.w;
+                }
+                const float tot = (acc.x + acc.y) + (acc.z + acc.w);
+                const int e = lane / 9, comp = lane - 9 * e;
+                const int k = e == 0 ? k0 : (e == 1 ? k1 : k2);
+                if (tot != 0.0f) atomicAdd(&s_g[k][comp], tot);
+            }
+            __syncwarp();
         }
         __syncthreads();
         for (int i = threadIdx.x; i < nb; i += NT) {
             float* dst = reinterpret_cast<float*>(L.gs) + 12 * (size_t)s_j[i];
-            const float4 cn = s_b[i];  // conic A', B', C'
-            const float mx = s_g[i][0], my = s_g[i][1];
+            const float4 cn = s_cn[i];  // conic A', B', C' and opacity
+            const float o = cn.w;
+            const float mx = o * s_g[i][0], my = o * s_g[i][1];
             float gsc[9];
             gsc[0] = -(cn.x * mx + cn.y * my);  // dL/du
             gsc[1] = -(cn.z * my + cn.y * mx);  // dL/dv
-            gsc[2] = -0.5f * s_g[i][2];         // dL/dA'
-            gsc[3] = -s_g[i][3];                // dL/dB'
-            gsc[4] = -0.5f * s_g[i][4];         // dL/dC'
-#pragma unroll
-            for (int c = 5; c < 9; c++) gsc[c] = s_g[i][c];
+            gsc[2] = -0.5f * o * s_g[i][2];     // dL/dA'
+            gsc[3] = -o * s_g[i][3];            // dL/dB'
+            gsc[4] = -0.5f * o * s_g[i][4];     // dL/dC'
+            gsc[5] = s_g[i][5];                 // dL/do
+            gsc[6] = -s_g[i][6];                // dL/d(r, g, b)
+            gsc[7] = -s_g[i][7];
+            gsc[8] = -s_g[i][8];
 #pragma unroll
             for (int c = 0; c < 9; c++)
                 if (gsc[c] != 0.0f) atomicAdd(dst + c, gsc[c]);

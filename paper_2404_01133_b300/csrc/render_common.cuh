@@ -1,6 +1,6 @@
 // Shared pieces of the compositing kernels (stage d of the hot path: Eq. 1, Sec. 3.1, and its
-// backward replay): the per-pair power, the per-warp culling masks, the forward blend and
-// the backward replay of one pixel.
+// backward replay): the per-pair power and exponential, the staged-entry layout and the packed
+// pair arithmetic of a lane's two pixels, and the per-warp culling masks.
 //
 // One CTA per (view, tile), two pixels per thread.  Each round stages `BATCH` projected
 // records of the tile's depth-sorted list in shared memory; a pixel blends with
@@ -54,38 +54,87 @@ __device__ __forceinline__ float gauss_exp2(float p)
     return g;
 }
 
-// p at a lane's two pixels (px, py0) and (px, py1), which share dx, from the entry's staged
-// factors nf (power_factors).
-__device__ __forceinline__ void pair_power2(const float4& a, const float4& nf, float fpx, float fpy0, float fpy1,
-                                            float* pw0, float* pw1, float* dx_out, float* dy0_out, float* dy1_out)
+// ---- a lane's two pixels as packed FP32 pairs --------------------------------------------
+// A lane holds pixels (px, py0) and (px, py0 + 4), so every per-pixel quantity is a pair and
+// one packed FP32x2 instruction updates both.  The pairs that decide skip and stop use explicit
+// IEEE instructions (round to nearest, denormals kept), per component identical to the scalar
+// ones, so both kernels compute the same bits.
+__device__ __forceinline__ unsigned long long pk2(float2 v)
 {
-    const float dx = ieee_sub(a.x, fpx), dy0 = ieee_sub(a.y, fpy0), dy1 = ieee_sub(a.y, fpy1);
-    const float hC = nf.z;                               // -C'/2 log2 e
-    const float ax = ieee_mul(ieee_mul(nf.x, dx), dx);   // -A' dx^2 / 2 log2 e
-    const float nbx = ieee_mul(nf.y, dx);                // -B' dx log2 e
-    *pw0 = ieee_fma(ieee_mul(hC, dy0), dy0, ieee_fma(nbx, dy0, ax));
-    *pw1 = ieee_fma(ieee_mul(hC, dy1), dy1, ieee_fma(nbx, dy1, ax));
-    *dx_out = dx;
-    *dy0_out = dy0;
-    *dy1_out = dy1;
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long r)
+{
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ float2 ieee_sub2(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(r);
+}
+__device__ __forceinline__ float2 ieee_mul2(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(r);
+}
+__device__ __forceinline__ float2 ieee_fma2(float2 a, float2 b, float2 c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
+    return upk2(r);
 }
 
-// Warp sum of 32 values per lane by halving exchanges: at each step a lane keeps half of its
-// values and adds the partner's copy of that half.  On return lane l holds the warp total of
-// v[l] (31 shuffles for 32 sums).
-__device__ __forceinline__ float warp_transpose_sum32(float (&v)[32], int lane)
+// A staged entry of a tile's list, laid out so that the values a packed instruction needs on
+// both pixels sit in aligned register pairs of one 16-byte shared-memory load:
+//   e0 = (v, v, hC, hC)          v: screen y of the centre; hC = -C'/2 log2 e
+//   e1 = (u, hA, hB, -o)         u: screen x; hA = -A'/2 log2 e, hB = -B' log2 e; -opacity
+//   e2 = (-o, -o, r, r)
+//   e3 = (g, g, b, b)            the view-dependent colour
+// Opacity is staged negated: -alpha = max(-0.99, (-o) 2^p) is then exact, T (1 - alpha) is
+// one fused multiply-add fma(-alpha, T, T), and no per-pair negation is needed.
+struct Staged {
+    float4 e0, e1, e2, e3;
+};
+
+__device__ __forceinline__ Staged stage_entry(const float4& a, const float4& conic, const float4& c)
 {
-#pragma unroll
-    for (int o = 16, n = 16; o >= 1; o >>= 1, n >>= 1) {
-        const bool hi = (lane & o) != 0;
-#pragma unroll
-        for (int k = 0; k < n; k++) {
-            const float send = hi ? v[k] : v[k + n];
-            const float keep = hi ? v[k + n] : v[k];
-            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-        }
-    }
-    return v[0];
+    const float4 nf = power_factors(conic);
+    Staged s;
+    s.e0 = make_float4(a.y, a.y, nf.z, nf.z);
+    s.e1 = make_float4(a.x, nf.x, nf.y, -a.z);
+    s.e2 = make_float4(-a.z, -a.z, c.x, c.x);
+    s.e3 = make_float4(c.y, c.y, c.z, c.z);
+    return s;
+}
+
+// p = log2(e) times the power of Eq. 1 at both pixels of a lane from a staged entry, in the
+// operations and order of the oracle's parity analysis: dx = u - px, dy = v - py,
+// p = fma(hC dy, dy, fma(hB dx, dy, (hA dx) dx)).
+__device__ __forceinline__ float2 staged_power2(const float4& e0, const float4& e1, float fpx, float2 fpy, float* dx_out,
+                                                float2* dy_out)
+{
+    const float dx = ieee_sub(e1.x, fpx);
+    const float ax = ieee_mul(ieee_mul(e1.y, dx), dx);
+    const float nbx = ieee_mul(e1.z, dx);
+    const float2 dy = ieee_sub2(make_float2(e0.x, e0.y), fpy);
+    const float2 hcd = ieee_mul2(make_float2(e0.z, e0.w), dy);
+    *dx_out = dx;
+    *dy_out = dy;
+    return ieee_fma2(hcd, dy, ieee_fma2(make_float2(nbx, nbx), dy, make_float2(ax, ax)));
+}
+
+// -alpha at both pixels: max(-0.99, (-o) 2^p), and (-o) 2^p itself (the clamp test reads it).
+__device__ __forceinline__ float2 neg_alpha2(const float4& e2, float2 G, float2* nog)
+{
+    const float2 n = ieee_mul2(make_float2(e2.x, e2.y), G);
+    *nog = n;
+    return make_float2(fmaxf(-0.99f, n.x), fmaxf(-0.99f, n.y));
 }
 
 // Threads of a B x B tile: B*B/2, two pixels each.  Warp w covers the 8 x 8 block at
@@ -149,76 +198,5 @@ __device__ __forceinline__ uint32_t warp_mask(const float4& a, const float4& b, 
     }
     return m;
 }
-
-// Forward blend of one entry into one pixel (Eq. 1 with the 3DGS thresholds).  Written
-// without branches: a warp runs every step for all its lanes anyway, and the predicated form
-// saves the divergence bookkeeping.  A pair that does not blend adds c * 0 (exactly nothing)
-// and keeps T and last.
-struct FwdPixel {
-    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-    uint32_t last = 0, stop_at = 0xffffffffu;
-    bool done = false;
-    __device__ __forceinline__ bool blend(float power, float o, const float4& c, uint32_t pos)
-    {
-        const float alpha = fminf(0.99f, __fmul_rn(o, gauss_exp2(power)));
-        const float Tn = ieee_fma(-alpha, T, T);  // T (1 - alpha), rounded once
-        const bool ok = !done && !(power > 0.0f) && !(alpha < 1.0f / 255.0f);
-        const bool stop = ok && Tn < 1e-4f;
-        const bool use = ok && !stop;
-        const float w = use ? alpha * T : 0.0f;
-        C0 += c.x * w;
-        C1 += c.y * w;
-        C2 += c.z * w;
-        if (stop) {
-            done = true;
-            stop_at = pos;
-        }
-        T = use ? Tn : T;
-        last = use ? pos + 1u : last;
-        return use;
-    }
-};
-
-// Backward replay of one pixel.  The pixel visits its blended entries from the last one
-// (n_contrib) to the first, recovering T before entry i as T_{i+1} / (1 - alpha_i) from the
-// final transmittance.  With g = dL/dP (per channel) and S_i = sum_{m > i} alpha_m T_m c_m
-// + T_end bg, only the scalar gS = g . S_i is needed:
-//   dL/dc_i = g alpha_i T_i,  dL/dalpha_i = T_i (g . c_i) - gS / (1 - alpha_i),
-//   alpha = min(0.99, o G), G = exp(power): dalpha/do = G, dalpha/dpower = o G (not clamped).
-// With dp = dL/dpower, the accumulated values are
-//   m[0..4] = sum dp dx, sum dp dy, sum dp dx^2, sum dp dx dy, sum dp dy^2,
-//   m[5] = dL/do, m[6..8] = dL/d(r, g, b),
-// from which the per-Gaussian factors of the conic give dL/d(u, v, A', B', C') (flush).
-struct BwdPixel {
-    float T = 1.0f, gS = 0.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
-    uint32_t nc = 0;
-    // Predicated like the forward: a pair that did not blend leaves T and gS and adds exact
-    // zeros (selected, never multiplied, so no inf * 0 reaches the sums).  SET writes the
-    // nine sums instead of adding to them (the first pixel of a lane).
-    template <bool SET>
-    __device__ __forceinline__ bool replay(float power, float dx, float dy, float o, const float4& c, uint32_t lp,
-                                           float* m)
-    {
-        const float G = gauss_exp2(power);
-        const float og = __fmul_rn(o, G);
-        const float alpha = fminf(0.99f, og);
-        const bool use = lp < nc && !(power > 0.0f) && !(alpha < 1.0f / 255.0f);
-        const float inv = __fdividef(1.0f, 1.0f - alpha);
-        const float Tb = T * inv;  // transmittance before this entry
-        const float gc = g0 * c.x + g1 * c.y + g2 * c.z;
-        const float dal = gc * Tb - gS * inv;
-        const float aT = alpha * Tb;
-        T = use ? Tb : T;
-        gS = use ? gS + aT * gc : gS;
-        const float aTu = use ? aT : 0.0f;
-        const bool lin = use && !(og > 0.99f);  // the 0.99 clamp passes no gradient
-        const float dp = lin ? dal * og : 0.0f;
-        const float px = dp * dx, py = dp * dy;
-        const float v[9] = {px, py, px * dx, px * dy, py * dy, lin ? dal * G : 0.0f, g0 * aTu, g1 * aTu, g2 * aTu};
-#pragma unroll
-        for (int i = 0; i < 9; i++) m[i] = SET ? v[i] : m[i] + v[i];
-        return use;
-    }
-};
 
 }  // namespace cgs
