@@ -54,9 +54,7 @@ typedef struct cgs_camera {
  * rotation (the covariance), SH features.  With attr_fp16 the non-position attributes are
  * stored in half precision (the transfer variant noted, commented out, after Sec. 3.3.2:
  * position FP32, the other properties FP16; opacity stays with the position here).
- * Original summary follows.
- * Per Gaussian (Sec. 3.1): position, opacity, scale and
- * rotation (the covariance), SH features in R^{3x16} at degree 3.  Detail level l of block
+ * SH features are in R^{3x16} at degree 3.  Detail level l of block
  * b (Sec. 3.3.1/3.3.2) is the index range [level_offset[b*L + l], + level_count[b*L + l]).
  * Level 0 is the finest.  Segments of different blocks must not overlap and must ascend
  * with b, because scene index order breaks depth ties.  A scene without blocks is one
@@ -136,6 +134,27 @@ int64_t cgs_frame_workspace_bytes(int32_t n_views, int32_t width, int32_t height
 int64_t cgs_block_bounds_workspace_bytes(int64_t n);
 int32_t cgs_block_bounds(const cgs_scene* scene, double n_mad, float* d_aabb, void* d_ws, int64_t ws_bytes,
                          void* stream);
+
+/* ---- Scene upload (Sec. 3.1 attributes, Sec. 3.3.2 per-block detail levels) --------------
+ * The library keeps no scene of its own: a cgs_scene describes caller-owned device arrays.
+ * cgs_scene_upload fills one from host arrays in ONE caller-owned device buffer of
+ * cgs_scene_bytes(...) bytes (d_mem, 256-byte aligned, which the caller frees after the last
+ * call that uses the scene): it copies the attributes (layouts as in cgs_scene; scale, quat
+ * and sh in IEEE half when attr_fp16 = 1), the block table level_offset / level_count
+ * [n_blocks][n_levels] and block_cell [n_blocks][4] with one cudaMemcpyAsync each on `stream`
+ * (pageable host memory makes those copies wait for the host), then, for n_mad >= 0, writes
+ * the Eq. 7 block bounds (cgs_block_bounds); for n_mad < 0 the bounds are zero (scenes
+ * rendered with explicit levels or per-view blocks need none).  *out receives the descriptor.
+ * The block table is checked on the host first: every segment within [0, n), and the
+ * blocks' segments ascending and not overlapping (scene order breaks depth ties); a
+ * violation, a null pointer or an invalid size returns CGS_ERR_INVALID_ARGUMENT, a short
+ * buffer CGS_ERR_WORKSPACE_TOO_SMALL, both before any device work.  cgs_scene_bytes returns
+ * -1 for invalid sizes. */
+int64_t cgs_scene_bytes(int64_t n, int32_t sh_degree, int32_t n_blocks, int32_t n_levels, int32_t attr_fp16);
+int32_t cgs_scene_upload(cgs_scene* out, void* d_mem, int64_t mem_bytes, const float* h_mean_opac,
+                         const void* h_scale, const void* h_quat, const void* h_sh, int64_t n, int32_t sh_degree,
+                         int32_t attr_fp16, int32_t n_blocks, int32_t n_levels, const int64_t* h_level_offset,
+                         const int64_t* h_level_count, const float* h_block_cell, double n_mad, void* stream);
 
 /* Block-wise level selection and frustum culling (Sec. 3.3.2) in FP64 for n_views
  * cameras: the corners of a block's box with camera-space z > near_z are projected; the
@@ -233,6 +252,34 @@ int32_t cgs_render_forward_static(const cgs_scene* scene, const cgs_config* cfg,
                                   int32_t width, int32_t height, const int32_t* d_view_block,
                                   const int8_t* d_levels, float* d_image, float* d_final_T,
                                   uint32_t* d_n_contrib, int32_t* d_status, void* stream);
+
+/* ---- Autotuner ------------------------------------------------------------------------------
+ * Picks the tile size and the compositing batch depth of cgs_config for a workload by timing
+ * the real step on the device: for each candidate (tile, batch) in the order
+ *   (16, 256) (16, 128) (16, 64) (16, 32) (8, 64) (8, 32)
+ * one warm-up call and `reps` timed calls (CUDA events on `stream`, median) of
+ * cgs_render_forward (mode CGS_TUNE_FORWARD) or cgs_render_forward + cgs_render_backward_packed
+ * with an upstream gradient of 1/(3 n_views W H) on every pixel (CGS_TUNE_FORWARD_BACKWARD),
+ * over the given scene, cameras, selection (d_view_block / d_levels as in cgs_render_forward)
+ * and frame capacities.  A candidate whose frame reports a device error (a capacity too small
+ * for its tile size) is not eligible.  Writes the fastest choice into inout->tile and
+ * inout->batch (the other fields of *inout are used as given) and, if ms_out is not NULL, the
+ * candidates' median milliseconds into ms_out[CGS_TUNE_CANDIDATES] (-1: not eligible).
+ * d_ws holds cgs_autotune_workspace_bytes(...) bytes of device memory (frames, outputs and
+ * gradient rows of the candidates; its contents are overwritten).  Synchronises `stream`.
+ * With cache_path, a text file of lines "<device name>|<cache_key> <tile> <batch>" is read
+ * first (a hit returns at once, ms_out left at -1) and the choice appended to it.  Returns
+ * CGS_ERR_CAPACITY when no candidate fits, CGS_ERR_INVALID_ARGUMENT for invalid arguments.
+ * cgs_autotune_workspace_bytes returns -1 for invalid sizes. */
+#define CGS_TUNE_CANDIDATES 6
+#define CGS_TUNE_FORWARD 0
+#define CGS_TUNE_FORWARD_BACKWARD 1
+int64_t cgs_autotune_workspace_bytes(int32_t n_views, int32_t width, int32_t height, int32_t n_blocks, int64_t n_cap,
+                                     int64_t k_cap, int32_t sh_degree, int32_t mode);
+int32_t cgs_autotune(const cgs_scene* scene, const cgs_camera* d_cams, int32_t n_views, int32_t width, int32_t height,
+                     const int32_t* d_view_block, const int8_t* d_levels, int64_t n_cap, int64_t k_cap, int32_t mode,
+                     int32_t reps, void* d_ws, int64_t ws_bytes, cgs_config* inout, float* ms_out,
+                     const char* cache_path, const char* cache_key, void* stream);
 
 /* Device address and capacity (elements) of an internal frame array, valid after
  * cgs_render_forward; for parity tests and debugging.  which:
@@ -338,6 +385,15 @@ int32_t cgs_levels_status(const void* d_ws, void* stream);
  * SSIM loss of Eq. 3 is 1 - d_ssim[i].  Asynchronous; n_pairs <= 65535. */
 int32_t cgs_ssim(const float* d_a, int64_t a_stride, const float* d_b, int32_t n_pairs, int32_t channels,
                  int32_t width, int32_t height, float* d_ssim, float* d_map, void* stream);
+
+/* ---- Pose-to-block assignment (Sec. 3.2.2, Eqs. 3-5) ----------------------------------------
+ * For n_poses x n_blocks FP32 SSIM values d_ssim[i][j] (cgs_ssim of pose i's render with every
+ * block against its render without block j) and the block of every pose's camera centre
+ * d_pose_block[i] (cgs_pose_blocks; -1 for none): B1[i][j] = (1 - SSIM) > eps (Eq. 3, FP32),
+ * B2[i][j] = (d_pose_block[i] == j) (Eq. 4), B = B1 or B2 (Eq. 5).  Each of d_b1, d_b2, d_b
+ * (uint8 [n_poses][n_blocks], 0 or 1) may be NULL, not all three.  Asynchronous. */
+int32_t cgs_pose_assign(const float* d_ssim, const int32_t* d_pose_block, int32_t n_poses, int32_t n_blocks,
+                        float eps, uint8_t* d_b1, uint8_t* d_b2, uint8_t* d_b, void* stream);
 
 /* ---- Block partition of a scene (Sec. 3.2.2, Eqs. 2 and 4) --------------------------------
  * Positions are rows of `stride` floats with x, y, z first (stride 4 reads the mean_opac rows

@@ -20,7 +20,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path
 NO_FMA = {"project.cu", "project_bwd.cu", "select.cu", "partition.cu", "levels.cu"}
 FTZ = {"render_bwd.cu"}  # gradient arithmetic only; the decisions it shares with the forward are pinned in PTX
 SOURCES = ["api.cu", "select.cu", "project.cu", "sort.cu", "render.cu", "render_bwd.cu", "project_bwd.cu",
-           "static_ws.cu", "partition.cu", "levels.cu", "ssim.cu", "peaks.cu"]
+           "static_ws.cu", "partition.cu", "levels.cu", "ssim.cu", "peaks.cu", "boundary.cu"]
 
 
 def _nvcc():

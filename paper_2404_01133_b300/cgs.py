@@ -46,6 +46,10 @@ class cgs_config(C.Structure):
 
 CGS_LOD_BLOCK = 0
 CGS_LOD_POINT = 1
+CGS_TUNE_CANDIDATES = 6
+CGS_TUNE_FORWARD = 0
+CGS_TUNE_FORWARD_BACKWARD = 1
+TUNE_ORDER = ((16, 256), (16, 128), (16, 64), (16, 32), (8, 64), (8, 32))
 
 
 class cgs_frame(C.Structure):
@@ -129,6 +133,18 @@ def lib():
         L.cgs_gather_rows.argtypes = [vp, vp, i64, vp, i64, vp]
         L.cgs_debug_exp2.restype = i32
         L.cgs_debug_exp2.argtypes = [vp, i64, vp, vp]
+        L.cgs_scene_bytes.restype = i64
+        L.cgs_scene_bytes.argtypes = [i64, i32, i32, i32, i32]
+        L.cgs_scene_upload.restype = i32
+        L.cgs_scene_upload.argtypes = [P(cgs_scene), vp, i64, vp, vp, vp, vp, i64, i32, i32, i32, i32, vp, vp, vp,
+                                       C.c_double, vp]
+        L.cgs_pose_assign.restype = i32
+        L.cgs_pose_assign.argtypes = [vp, vp, i32, i32, C.c_float, vp, vp, vp, vp]
+        L.cgs_autotune_workspace_bytes.restype = i64
+        L.cgs_autotune_workspace_bytes.argtypes = [i32, i32, i32, i32, i64, i64, i32, i32]
+        L.cgs_autotune.restype = i32
+        L.cgs_autotune.argtypes = [P(cgs_scene), vp, i32, i32, i32, vp, vp, i64, i64, i32, i32, vp, i64,
+                                   P(cgs_config), P(C.c_float), C.c_char_p, C.c_char_p, vp]
         L.cgs_measure_peaks.restype = i32
         L.cgs_measure_peaks.argtypes = [P(C.c_double), i32, vp, i64, vp]
         _lib = L
@@ -367,3 +383,47 @@ def cgs_measure_peaks(d_scratch, stream=None):
     r = (C.c_double * 3)()
     _check(lib().cgs_measure_peaks(r, 3, _ptr(d_scratch), d_scratch.numel(), _stream(stream)), "cgs_measure_peaks")
     return {"fp32_lane_ops_s": r[0], "fp32x2_lane_ops_s": r[1], "ex2_s": r[2]}
+
+
+# ---------------------------------------------------------------------------------------
+# scene upload, pose-to-block decision, autotuner
+# ---------------------------------------------------------------------------------------
+def _host(a):
+    """Host pointer of a contiguous numpy array (kept alive by the caller)."""
+    return None if a is None else a.ctypes.data
+
+
+def cgs_scene_bytes(n, sh_degree, n_blocks, n_levels, attr_fp16=0):
+    return lib().cgs_scene_bytes(n, sh_degree, n_blocks, n_levels, attr_fp16)
+
+
+def cgs_scene_upload(d_mem, mem_bytes, h_mean_opac, h_scale, h_quat, h_sh, n, sh_degree, attr_fp16, h_level_offset,
+                     h_level_count, h_block_cell, n_mad=-1.0, stream=None):
+    """Host numpy arrays in, a cgs_scene over d_mem out."""
+    out = cgs_scene()
+    nb, nl = h_level_offset.shape
+    _check(lib().cgs_scene_upload(C.byref(out), _ptr(d_mem), mem_bytes, _host(h_mean_opac), _host(h_scale),
+                                  _host(h_quat), _host(h_sh), n, sh_degree, attr_fp16, nb, nl, _host(h_level_offset),
+                                  _host(h_level_count), _host(h_block_cell), float(n_mad), _stream(stream)),
+           "cgs_scene_upload")
+    return out
+
+
+def cgs_pose_assign(d_ssim, d_pose_block, n_poses, n_blocks, eps, d_b1=None, d_b2=None, d_b=None, stream=None):
+    return _check(lib().cgs_pose_assign(_ptr(d_ssim), _ptr(d_pose_block), n_poses, n_blocks, float(eps), _ptr(d_b1),
+                                        _ptr(d_b2), _ptr(d_b), _stream(stream)), "cgs_pose_assign")
+
+
+def cgs_autotune_workspace_bytes(n_views, width, height, n_blocks, n_cap, k_cap, sh_degree, mode):
+    return lib().cgs_autotune_workspace_bytes(n_views, width, height, n_blocks, n_cap, k_cap, sh_degree, mode)
+
+
+def cgs_autotune(scene, d_cams, n_views, width, height, d_view_block, d_levels, n_cap, k_cap, mode, reps, d_ws,
+                 ws_bytes, cfg, cache_path=None, cache_key=None, stream=None):
+    """Returns {(tile, batch): median ms or -1}; writes the choice into cfg."""
+    ms = (C.c_float * CGS_TUNE_CANDIDATES)()
+    _check(lib().cgs_autotune(C.byref(scene), _ptr(d_cams), n_views, width, height, _ptr(d_view_block),
+                              _ptr(d_levels), n_cap, k_cap, mode, reps, _ptr(d_ws), ws_bytes, C.byref(cfg), ms,
+                              cache_path.encode() if cache_path else None, cache_key.encode() if cache_key else None,
+                              _stream(stream)), "cgs_autotune")
+    return {c: ms[i] for i, c in enumerate(TUNE_ORDER)}

@@ -95,6 +95,56 @@ class DeviceScene:
         return self.block_aabb
 
 
+class UploadedScene:
+    """A synth-format scene uploaded by the library (cgs_scene_upload) into one device buffer
+    from torch; same interface as DeviceScene for rendering (struct(), n, n_blocks, ...)."""
+
+    def __init__(self, scene, device="cuda", n_mad=-1.0, fp16=False, stream=None):
+        dev = torch.device(device)
+        self.attr_fp16 = 1 if fp16 else 0
+        hdt = np.float16 if fp16 else np.float32
+        self._host = {"mean_opac": np.ascontiguousarray(scene["mean_opac"], np.float32),
+                      "scale": np.ascontiguousarray(scene["scale"], hdt), "quat": np.ascontiguousarray(scene["quat"], hdt),
+                      "sh": np.ascontiguousarray(scene["sh"], hdt),
+                      "level_offset": np.ascontiguousarray(scene["level_offset"], np.int64),
+                      "level_count": np.ascontiguousarray(scene["level_count"], np.int64),
+                      "block_cell": np.ascontiguousarray(scene["block_cell"], np.float32)}
+        h = self._host
+        self.n = int(h["mean_opac"].shape[0])
+        self.sh_degree = int(scene["sh_degree"])
+        self.n_blocks, self.n_levels = h["level_offset"].shape
+        nbytes = _c.cgs_scene_bytes(self.n, self.sh_degree, self.n_blocks, self.n_levels, self.attr_fp16)
+        if nbytes < 0:
+            raise ValueError("invalid scene dimensions")
+        self.mem = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self._s = _c.cgs_scene_upload(self.mem, nbytes, h["mean_opac"], h["scale"], h["quat"], h["sh"], self.n,
+                                      self.sh_degree, self.attr_fp16, h["level_offset"], h["level_count"],
+                                      h["block_cell"], n_mad, stream)
+        torch.cuda.synchronize(dev)  # the host arrays may be released after the copies
+        self.device = dev
+        # tensor views of the uploaded attributes and bounds (inside self.mem)
+        base = self.mem.data_ptr()
+        adt = torch.float16 if fp16 else torch.float32
+        nco = (self.sh_degree + 1) ** 2
+
+        def view(ptr, dtype, shape):
+            off = ptr - base
+            cnt = int(np.prod(shape))
+            elem = torch.tensor([], dtype=dtype).element_size()
+            return self.mem[off:off + cnt * elem].view(dtype).view(shape)
+        sc = self._s
+        self.mean_opac = view(sc.mean_opac, torch.float32, (self.n, 4))
+        self.scale = view(sc.scale, adt, (self.n, 4))
+        self.quat = view(sc.quat, adt, (self.n, 4))
+        self.sh = view(sc.sh, adt, (self.n, nco, 3))
+        self.block_aabb = view(sc.block_aabb, torch.float32, (self.n_blocks, 6))
+
+    def struct(self, attrs=None):
+        if attrs:
+            raise ValueError("an uploaded scene renders its own attributes")
+        return self._s
+
+
 class Frame:
     """Workspace of a batch of equally sized views (device memory from torch)."""
 
@@ -314,6 +364,24 @@ def autotune(run_step, candidates, reps=5, cache_path=None, key=None):
 TUNE_CANDIDATES = [(16, 256), (16, 128), (16, 64), (8, 64), (8, 32)]
 
 
+def autotune_library(dscene, d_cams, width, height, n_cap, k_cap, cfg=None, view_block=None, levels=None,
+                     backward=True, reps=3, cache_path=None, cache_key=None, stream=None):
+    """The library's autotuner (cgs_autotune): times the real step for every (tile, batch)
+    candidate in a workspace from torch and returns (config with the choice, {candidate: ms})."""
+    cfg = cfg or make_config()
+    n_views = d_cams.numel() // 96
+    mode = _c.CGS_TUNE_FORWARD_BACKWARD if backward else _c.CGS_TUNE_FORWARD
+    nbytes = _c.cgs_autotune_workspace_bytes(n_views, width, height, dscene.n_blocks, n_cap, k_cap, dscene.sh_degree,
+                                             mode)
+    if nbytes < 0:
+        raise ValueError("invalid autotune dimensions")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dscene.device)
+    ms = _c.cgs_autotune(dscene.struct(), d_cams, n_views, width, height, view_block, levels, n_cap, k_cap, mode, reps,
+                         ws, nbytes, cfg, cache_path, cache_key, stream)
+    del ws
+    return cfg, ms
+
+
 def partition(pos, pmin, pmax, grid, perm=True, rank=False, stream=None):
     """Block partition of the positions (rows of a float32 device tensor, xyz first): block
     per row, block offsets and (optionally) the stable grouped order.  Returns
@@ -414,9 +482,6 @@ def pose_assign(dscene, cams, pmin, pmax, grid, eps, tile=16, batch=None):
     campos = torch.tensor(np.asarray([c["campos"] for c in cams], np.float32), device=dev)
     pb = torch.empty(P, dtype=torch.int32, device=dev)
     _c.cgs_pose_blocks(campos, P, 3, pmin, pmax, grid, pb)
-    b2 = torch.zeros((P, nb), dtype=torch.bool, device=dev)
-    ok = pb >= 0
-    b2[torch.arange(P, device=dev)[ok], pb[ok].long()] = True
     lv_all = torch.zeros((nb + 1, nb), dtype=torch.int8, device=dev)
     lv_all[torch.arange(1, nb + 1), torch.arange(nb)] = -1
     s_all = torch.empty((P, nb), dtype=torch.float32, device=dev)
@@ -440,5 +505,9 @@ def pose_assign(dscene, cams, pmin, pmax, grid, eps, tile=16, batch=None):
                 img, views = img[1:], views[1:]
             if views:
                 s_all[i, torch.tensor(views, device=dev) - 1] = ssim(full, img)
-    b1 = (1.0 - s_all) > eps
-    return b1, b2, b1 | b2, s_all
+    # Eqs. 3-5 in the library: B1 from the SSIM losses, B2 from the poses' blocks, B = B1 or B2
+    b1u = torch.empty((P, nb), dtype=torch.uint8, device=dev)
+    b2u = torch.empty_like(b1u)
+    bu = torch.empty_like(b1u)
+    _c.cgs_pose_assign(s_all, pb, P, nb, eps, b1u, b2u, bu)
+    return b1u.bool(), b2u.bool(), bu.bool(), s_all

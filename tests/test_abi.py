@@ -97,3 +97,49 @@ def test_partition_host_checks_need_no_device(libcgs):
     assert libcgs.cgs_gather_rows(None, None, 16, None, 0, None) == cgs.CGS_OK             # nothing to move
     assert libcgs.cgs_pose_blocks(1, 4, 3, f3((0, 0, 0)), f3((1, 1, 1)), i3((1, 1, 0)), 1, None) == \
         cgs.CGS_ERR_INVALID_ARGUMENT
+
+
+def test_boundary_entry_points_check_arguments_on_the_host(libcgs):
+    """Scene upload, pose assignment and the autotuner reject invalid sizes, pointers and block
+    tables before any device work (no GPU here)."""
+    import numpy as np
+    from paper_2404_01133_b300 import cgs
+    n, deg, nb, nl = 1000, 3, 4, 3
+    b = cgs.cgs_scene_bytes(n, deg, nb, nl, 0)
+    assert b >= n * (16 + 16 + 16 + 192) and b % 256 == 0
+    assert cgs.cgs_scene_bytes(n, deg, nb, nl, 1) < b                     # half-precision attributes
+    assert cgs.cgs_scene_bytes(n, 4, nb, nl, 0) == -1                     # SH degree above 3
+    assert cgs.cgs_scene_bytes(-1, deg, nb, nl, 0) == -1
+    mo = np.zeros((n, 4), np.float32)
+    sc4 = np.zeros((n, 4), np.float32)
+    sh = np.zeros((n, 16, 3), np.float32)
+    cell = np.zeros((nb, 4), np.float32)
+    cnt = np.full((nb, nl), 100, np.int64)
+    good = np.repeat(np.arange(nb, dtype=np.int64)[:, None] * 250, nl, axis=1)
+    s = cgs.cgs_scene()
+    L = libcgs
+    args = lambda off, count, mem=1 << 20, nbytes=b: (C.byref(s), mem, nbytes, mo.ctypes.data, sc4.ctypes.data,
+                                                       sc4.ctypes.data, sh.ctypes.data, n, deg, 0, nb, nl,
+                                                       off.ctypes.data, count.ctypes.data, cell.ctypes.data, -1.0,
+                                                       None)
+    overlap = good.copy()
+    overlap[2] = 120                                                      # block 2 starts inside block 1
+    assert L.cgs_scene_upload(*args(overlap, cnt)) == cgs.CGS_ERR_INVALID_ARGUMENT
+    beyond = good.copy()
+    beyond[3] = n - 50                                                    # a segment past the last Gaussian
+    assert L.cgs_scene_upload(*args(beyond, cnt)) == cgs.CGS_ERR_INVALID_ARGUMENT
+    assert L.cgs_scene_upload(*args(good, cnt, mem=None)) == cgs.CGS_ERR_INVALID_ARGUMENT
+    assert L.cgs_scene_upload(*args(good, cnt, nbytes=b - 1)) == cgs.CGS_ERR_WORKSPACE_TOO_SMALL
+    # pose assignment: sizes and the three outputs
+    assert L.cgs_pose_assign(None, None, 2, 4, C.c_float(0.05), None, None, None, None) == cgs.CGS_ERR_INVALID_ARGUMENT
+    assert L.cgs_pose_assign(None, None, 0, 4, C.c_float(0.05), 1, None, None, None) == cgs.CGS_OK   # nothing to do
+    assert L.cgs_pose_assign(1, 1, 2, 0, C.c_float(0.05), 1, None, None, None) == cgs.CGS_ERR_INVALID_ARGUMENT
+    # autotuner workspace and arguments
+    wb = cgs.cgs_autotune_workspace_bytes(1, 1920, 1080, 1, 1_000_000, 4_000_000, 3, cgs.CGS_TUNE_FORWARD_BACKWARD)
+    wf = cgs.cgs_autotune_workspace_bytes(1, 1920, 1080, 1, 1_000_000, 4_000_000, 3, cgs.CGS_TUNE_FORWARD)
+    assert wb > wf > cgs.cgs_frame_workspace_bytes(1, 1920, 1080, 16, 1, 1_000_000, 4_000_000)
+    assert cgs.cgs_autotune_workspace_bytes(1, 1920, 1080, 1, 1_000_000, 4_000_000, 3, 7) == -1
+    cfg = cgs.cgs_config()
+    ms = (C.c_float * cgs.CGS_TUNE_CANDIDATES)()
+    assert L.cgs_autotune(None, 1, 1, 64, 64, None, None, 10, 10, 0, 3, 1, 1 << 30, C.byref(cfg), ms, None, None,
+                          None) == cgs.CGS_ERR_INVALID_ARGUMENT
