@@ -335,7 +335,8 @@ def run_ours(args, world, rank, local):
     tgt = tgt_host.to(dev)
     tgt_f32 = torch.from_numpy(synth.target_image(1, W, H))[None].to(dev)
 
-    # autotuner: tile size and batch depth for this workload, timed on the real step
+    # the library's autotuner (cgs_autotune): tile size and batch depth for this workload, timed
+    # on the real forward + backward step
     tune = None
     f32 = torch.float32
     tune_rows = (torch.empty((n, 4), dtype=f32, device=dev), torch.empty((n, 4), dtype=f32, device=dev),
@@ -343,24 +344,11 @@ def run_ours(args, world, rank, local):
                  torch.empty((n,) + tuple(ds.sh.shape[1:]), dtype=f32, device=dev),
                  torch.empty(n, dtype=torch.int64, device=dev))
     if args.tile == 0:
-        tframes = {}
-        l_ = torch.zeros(1, device=dev)
-
-        def run_candidate(tile, batch):
-            if tile not in tframes:
-                f_ = ta.Frame(1, W, H, tile, 1, n, 8_000_000, dev)
-                tframes[tile] = (f_, f_.outputs(), torch.empty((1, 3, H, W), device=dev))
-            f_, (i_, T_, n_), dl_ = tframes[tile]
-            c_ = ta.make_config(tile=tile, batch=batch)
-            cgs.cgs_render_forward(ds.struct(), f_.struct, c_, d_cams, None, None, i_, T_, n_)
-            l_.zero_()
-            cgs.cgs_l1_loss_u8(i_, tgt, i_.numel(), l_, dl_)
-            ta.render_backward_packed(ds, f_, c_, d_cams, dl_, T_, n_, rows=tune_rows)
-
-        best, tune_ms = ta.autotune(run_candidate, ta.TUNE_CANDIDATES, reps=3)
-        tune = {"choice": f"{best[0]}x{best[1]}", "ms": tune_ms}
-        args.tile, args.batch = best
-        del tframes
+        tcfg, tune_ms = ta.autotune_library(ds, d_cams, W, H, n, 8_000_000, reps=5)
+        tune = {"by": "cgs_autotune (forward + packed backward, median of 5)", "choice": f"{tcfg.tile}x{tcfg.batch}",
+                "ms": {f"{t}x{b}": v for (t, b), v in tune_ms.items()}}
+        args.tile, args.batch = tcfg.tile, tcfg.batch
+        torch.cuda.empty_cache()
     cfg = ta.make_config(tile=args.tile, batch=args.batch)
     frame = ta.Frame(1, W, H, args.tile, 1, n, 8_000_000, dev)
     img, T, nc = frame.outputs()
@@ -1102,33 +1090,15 @@ def run_train32(args, world, rank, local, peaks, launches_acc):
             g_.zero_()
         loss.zero_()
 
-    # autotune tile and batch on the first 16 views (two blocks), each tile size with frame
-    # capacities counted for it; a candidate whose frame reports an error is not eligible
+    # the library's autotuner on the first 16 views (two blocks), with the entry capacity the
+    # 8 x 8 tiles need (a candidate whose frame overflows is not eligible)
     tv = list(range(min(16, len(cams))))
     tv_dev = vb_dev[tv].contiguous()
-    tune_frames = {}
-    for tile_ in sorted({t for t, _ in ta.TUNE_CANDIDATES}):
-        s_, e_ = ta.frame_counts(ds, [cams[v] for v in tv], W, H, tile=tile_, view_block=tv_dev)
-        fr_ = ta.Frame(len(tv), W, H, tile_, ds.n_blocks, int(sum(s_) * 1.05) + 1024,
-                       min((1 << 30) - 1, int(sum(e_) * 1.1) + 65536))
-        img_, T_, nc_ = fr_.outputs()
-        tune_frames[tile_] = (fr_, img_, T_, nc_, torch.rand_like(img_), torch.empty_like(img_),
-                              ta.cameras_device([cams[v] for v in tv]))
-    tune_ok = {}
-
-    def run_candidate(tile, batch):
-        fr_, img_, T_, nc_, tg_, dl_, dc_ = tune_frames[tile]
-        c_ = ta.make_config(tile=tile, batch=batch)
-        s_ = ds.struct()
-        cgs.cgs_render_forward(s_, fr_.struct, c_, dc_, tv_dev, None, img_, T_, nc_)
-        cgs.cgs_l1_loss(img_, tg_, img_.numel(), loss, dl_)
-        cgs.cgs_render_backward(s_, fr_.struct, c_, dc_, dl_, T_, nc_, *grads)
-        tune_ok[(tile, batch)] = fr_.status()[0] == cgs.CGS_OK
-
-    _, tune_ms = ta.autotune(run_candidate, ta.TUNE_CANDIDATES, reps=2)
-    ok_ms = {c: tune_ms[f"{c[0]}x{c[1]}"] for c in ta.TUNE_CANDIDATES if tune_ok.get(c)}
-    tile, batch = min(ok_ms, key=ok_ms.get) if ok_ms else (16, 256)
-    del tune_frames
+    s8, e8 = ta.frame_counts(ds, [cams[v] for v in tv], W, H, tile=8, view_block=tv_dev)
+    tcfg, tune_ms = ta.autotune_library(ds, ta.cameras_device([cams[v] for v in tv]), W, H, int(sum(s8) * 1.05) + 1024,
+                                        min((1 << 30) - 1, int(sum(e8) * 1.1) + 65536), view_block=tv_dev, reps=2)
+    tile, batch = tcfg.tile, tcfg.batch
+    ok_ms = {c: v for c, v in tune_ms.items() if v > 0}
     torch.cuda.empty_cache()
     if tile != 16:
         sel, ent = ta.frame_counts(ds, cams, W, H, tile=tile, view_block=vb_dev)
@@ -1199,7 +1169,8 @@ def run_train32(args, world, rank, local, peaks, launches_acc):
                       "tile": tile, "batch": batch, "generation_s": round(t_gen, 1),
                       "gradients": "scene-indexed arrays, cleared inside every timed step",
                       "timing": "CUDA graph of the whole step (all groups), L2 flushed between replays"},
-           "autotune": {"choice": f"{tile}x{batch}", "ms_16_views": tune_ms,
+           "autotune": {"by": "cgs_autotune on the first 16 views (forward + packed backward, median of 2)",
+                        "choice": f"{tile}x{batch}", "ms_16_views": {f"{t}x{b}": v for (t, b), v in tune_ms.items()},
                         "eligible": [f"{t}x{b}" for (t, b) in ok_ms]},
            "batched_ms": t_b, "sequential_ms": t_s, "speedup": t_s / t_b,
            "sequential_mpix_s": world * V * W * H / (t_s * 1e-3) / 1e6,
