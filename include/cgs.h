@@ -238,8 +238,9 @@ int32_t cgs_frame_status(const cgs_frame* frame, int32_t* status, int64_t* count
  *    CGS_ERR_CAPACITY in the device status.
  *  - d_status (device int32, may be NULL) receives the device status of this call as a CGS_*
  *    code, written on `stream` after the render.
- *  - The first call on a device looks up the array's device address on that device (with the
- *    device current); make that first call before any stream capture.
+ *  - Every call looks up the array's device address on the current device (the first lookup
+ *    on a device loads the library there); make the first call on a device before any stream
+ *    capture.  Nothing is cached, so calls after a cudaDeviceReset find the array again.
  *  - Every call uses the same array and clears what must start at zero; calls that overlap
  *    on the GPU (other streams, other host threads) race and must be serialized by the
  *    caller.  d_image etc. stay valid after later calls; the array's contents do not. */

@@ -6,8 +6,6 @@
 // and output buffers, or a process without a tensor library to size and hold a workspace.
 // They pass inputs and outputs; the intermediate state (sorted lists, records, counters)
 // lives in g_static_ws, which every GPU that loads this library keeps until the process exits.
-#include <mutex>
-
 #include "common.cuh"
 
 namespace cgs {
@@ -16,23 +14,16 @@ namespace cgs {
 // device symbol: the device address comes from cudaGetSymbolAddress (static_base).
 static __device__ __align__(256) unsigned char g_static_ws[CGS_STATIC_WORKSPACE_BYTES];
 
-constexpr int MAX_DEVICES = 64;
-static void* g_static_ptr[MAX_DEVICES] = {nullptr};
-static std::mutex g_static_mutex;
-
-// Device address of g_static_ws on the current device, looked up once per device with that
-// device current.  Returns nullptr if the lookup fails.
+// Device address of g_static_ws on the current device, looked up with that device current on
+// every call (nothing is cached, so the address stays right after a device reset reloads the
+// module).  The first lookup on a device loads the library's module there, which is why the
+// first call on a device should come before any stream capture.  Returns nullptr if the
+// lookup fails.
 static void* static_base()
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return nullptr;
-    std::lock_guard<std::mutex> lock(g_static_mutex);
-    if (!g_static_ptr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_static_ws) != cudaSuccess || !p) return nullptr;
-        g_static_ptr[dev] = p;
-    }
-    return g_static_ptr[dev];
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_ws) != cudaSuccess) return nullptr;
+    return p;
 }
 
 // Writes the frame's status as a CGS_* code into *out (device memory).
