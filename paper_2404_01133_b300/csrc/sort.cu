@@ -5,11 +5,12 @@
 //   tile ranges   single-pass scan of the per-tile counts -> [start, end) of every tile
 //   scatter       one thread per entry: a slot in its tile's range (atomic cursor), key
 //                 (FP32 depth bits << 32 | selected index)
-//   tile sort     one CTA per tile: up to 256 keys ranked against each other in shared
-//                 memory (each key's count of smaller keys is its slot); longer tiles go to a
-//                 second kernel: up to 2048 keys a bitonic sort held in registers (shuffles
-//                 within warps, shared memory only for the strides that cross warps), up to
-//                 4096 a bitonic sort in shared memory, beyond that sorted chunks + merge
+//   tile sort     one CTA per tile: up to 128 keys ranked against each other in shared
+//                 memory (each key's count of smaller keys is its slot), up to 256 a bitonic
+//                 sort held in registers; longer tiles go to a second kernel: up to 512 keys the
+//                 register bitonic sort, up to 2048 a stable LSD radix sort in shared memory
+//                 over the 8-bit digits of the depth bits that differ within the tile, equal
+//                 depths then put in index order; beyond that sorted chunks of 2048 + merge
 //                 rounds through global scratch
 //
 // Within a view, a Gaussian appears at most once per tile, so the 64-bit keys of one tile are
@@ -47,26 +48,6 @@ __global__ void __launch_bounds__(256) k_scatter(Layout L)
 }
 
 constexpr int TS_THREADS = 128;
-constexpr int TS_CAP = 2048;  // keys per tile sorted in registers by the long-tile kernel
-constexpr int LT_CAP = 4096;  // keys per chunk of the long-tile kernel
-
-// In-place ascending bitonic sort of s[0, np) (np a power of two) by the threads of a CTA.
-__device__ __forceinline__ void bitonic_smem(unsigned long long* s, int np)
-{
-    for (int size = 2; size <= np; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            __syncthreads();
-            for (int i = threadIdx.x; i < (np >> 1); i += blockDim.x) {
-                const int lo = 2 * i - (i & (stride - 1));
-                const int hi = lo + stride;
-                const bool up = (lo & size) == 0;
-                const unsigned long long a = s[lo], b = s[hi];
-                if ((a > b) == up) { s[lo] = b; s[hi] = a; }
-            }
-        }
-    }
-    __syncthreads();
-}
 
 // Ascending bitonic sort of np = THREADS * E keys held by the CTA in registers: warp w
 // holds keys [32 E w, 32 E (w + 1)), lane l's x[e] being key 32 E w + 32 e + l.  Exchanges
@@ -185,16 +166,139 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(Layout L)
     }
 }
 
-// Tiles longer than RANK_MAX: one CTA per listed tile (persistent over the device list).  Up
-// to TS_CAP keys: bitonic sort held in registers (cta_bitonic).  Longer: chunks of LT_CAP keys
-// sorted in shared memory (the whole tile when it fits), then runs merged pairwise through
-// global scratch (the entry buffer, free after the scatter); with distinct keys, an element's
-// output position is its rank in its own run plus the number of smaller keys in the other
-// run.
-constexpr int TB_THREADS = 256;
-__global__ void __launch_bounds__(TB_THREADS) k_tile_sort_large(Layout L)
+// Stable LSD radix sort of n <= RX_CAP keys (FP32 depth bits << 32 | selected index) held in
+// shared memory a[] by the CTA (RX_THREADS threads, one digit each in the offset scan); b[] is
+// the other buffer.  One pass per 8-bit digit of the depth bits that differ among the keys
+// (bits equal in every key cannot change the order): each warp counts the digits of its
+// contiguous segment (lanes with the same digit found by __match_any_sync, their leader adds
+// the count), the (digit, warp) counts become exclusive offsets in digit-major order, and each
+// warp scatters its segment in order, a key's slot being its warp's running offset for the digit
+// plus the number of earlier lanes of its group with the same digit.  Equal depths are then put
+// in index order (runs of equal depth, rare, sorted by insertion).  Returns the buffer holding
+// the sorted keys.
+constexpr int RX_THREADS = 256;
+constexpr int RX_WARPS = RX_THREADS / 32;
+constexpr int RX_CAP = 2048;
+constexpr int RX_BITONIC = 512;  // up to this many keys the register bitonic sort is faster (measured)
+constexpr size_t RX_SMEM = 2 * RX_CAP * sizeof(unsigned long long) + RX_WARPS * 256 * sizeof(uint32_t);
+
+__device__ unsigned long long* radix_sort_depth(unsigned long long* a, unsigned long long* b, int n,
+                                               uint32_t (*hist)[256], uint32_t* s_scan)
 {
-    __shared__ unsigned long long s[LT_CAP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    uint32_t orv = 0u, andv = 0xffffffffu;
+    for (int i = threadIdx.x; i < n; i += RX_THREADS) {
+        const uint32_t d = (uint32_t)(a[i] >> 32);
+        orv |= d;
+        andv &= d;
+    }
+    orv = __reduce_or_sync(0xffffffffu, orv);
+    andv = __reduce_and_sync(0xffffffffu, andv);
+    if (lane == 0) {
+        s_scan[warp] = orv;
+        s_scan[RX_WARPS + warp] = andv;
+    }
+    __syncthreads();
+    orv = 0u;
+    andv = 0xffffffffu;
+#pragma unroll
+    for (int w = 0; w < RX_WARPS; w++) {
+        orv |= s_scan[w];
+        andv &= s_scan[RX_WARPS + w];
+    }
+    const uint32_t vary = orv ^ andv;
+    __syncthreads();
+    const int seg = (((n + RX_WARPS - 1) / RX_WARPS) + 31) & ~31;
+    const int w0 = warp * seg, w1 = min(n, w0 + seg);
+    for (int shift = 0; shift < 32; shift += 8) {
+        if (((vary >> shift) & 0xffu) == 0u) continue;
+        for (int d = lane; d < 256; d += 32) hist[warp][d] = 0u;
+        __syncwarp();
+        for (int i0 = w0; i0 < w1; i0 += 32) {
+            const int i = i0 + lane;
+            const bool ok = i < w1;
+            const uint32_t d = ok ? ((uint32_t)(a[i] >> 32) >> shift) & 0xffu : 256u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            if (ok && lane == __ffs(peers) - 1) hist[warp][d] += (uint32_t)__popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {
+            const int d = threadIdx.x;  // one digit per thread
+            uint32_t c[RX_WARPS], sum = 0u;
+#pragma unroll
+            for (int w = 0; w < RX_WARPS; w++) {
+                c[w] = hist[w][d];
+                sum += c[w];
+            }
+            uint32_t tot;
+            uint32_t o = block_exclusive_scan<uint32_t>(sum, s_scan, &tot);
+#pragma unroll
+            for (int w = 0; w < RX_WARPS; w++) {
+                hist[w][d] = o;
+                o += c[w];
+            }
+        }
+        __syncthreads();
+        for (int i0 = w0; i0 < w1; i0 += 32) {
+            const int i = i0 + lane;
+            const bool ok = i < w1;
+            const unsigned long long k = ok ? a[i] : 0ull;
+            const uint32_t d = ok ? ((uint32_t)(k >> 32) >> shift) & 0xffu : 256u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const int leader = __ffs(peers) - 1;
+            uint32_t base = 0u;
+            if (ok && lane == leader) base = hist[warp][d];
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (ok) b[base + (uint32_t)__popc(peers & lt)] = k;
+            __syncwarp();
+            if (ok && lane == leader) hist[warp][d] = base + (uint32_t)__popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        unsigned long long* tmp = a;
+        a = b;
+        b = tmp;
+    }
+    // equal depths in index order (the first key of each run of equal depth sorts the run; the
+    // other runs' depths stay where they are while they are sorted)
+    bool tie = false;
+    for (int i = threadIdx.x; i + 1 < n; i += RX_THREADS) tie |= (a[i] >> 32) == (a[i + 1] >> 32);
+    if (__syncthreads_or(tie)) {
+        for (int i = threadIdx.x; i < n; i += RX_THREADS) {
+            const unsigned long long dv = a[i] >> 32;
+            if ((i > 0 && (a[i - 1] >> 32) == dv) || i + 1 >= n || (a[i + 1] >> 32) != dv) continue;
+            int e = i + 1;
+            while (e < n && (a[e] >> 32) == dv) e++;
+            for (int p = i + 1; p < e; p++) {
+                const unsigned long long x = a[p];
+                int q = p - 1;
+                while (q >= i && a[q] > x) {
+                    a[q + 1] = a[q];
+                    q--;
+                }
+                a[q + 1] = x;
+            }
+        }
+        __syncthreads();
+    }
+    return a;
+}
+
+// Tiles longer than RANK_MAX: one CTA per listed tile (persistent over the device list).  Up
+// to RX_BITONIC keys: the bitonic sort held in registers, two keys per thread; up to RX_CAP: the
+// shared-memory radix sort.  Longer: chunks of RX_CAP keys radix-sorted,
+// then runs merged pairwise through global scratch (the entry buffer, free after the scatter);
+// with distinct keys, an element's output position is its rank in its own run plus the number
+// of smaller keys in the other run.
+__global__ void __launch_bounds__(RX_THREADS) k_tile_sort_large(Layout L)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long* sa = reinterpret_cast<unsigned long long*>(smem);
+    unsigned long long* sb = sa + RX_CAP;
+    uint32_t(*hist)[256] = reinterpret_cast<uint32_t(*)[256]>(sb + RX_CAP);
+    __shared__ uint32_t s_scan[33];
     __shared__ uint32_t s_item;
     const uint32_t nbig = L.hdr->n_big;
     while (true) {
@@ -205,27 +309,34 @@ __global__ void __launch_bounds__(TB_THREADS) k_tile_sort_large(Layout L)
         if (item >= nbig) break;
         const uint32_t t = L.big[item];
         const uint32_t st = L.ranges[2 * (size_t)t], n = L.ranges[2 * (size_t)t + 1] - st;
-        if (n <= (uint32_t)TS_CAP) {
-            // listed tiles hold more than 256 keys: two, four or eight keys per thread
-            if (n <= 2u * TB_THREADS) tile_sort_regs<TB_THREADS, 2>(L, s, t, st, n);
-            else if (n <= 4u * TB_THREADS) tile_sort_regs<TB_THREADS, 4>(L, s, t, st, n);
-            else tile_sort_regs<TB_THREADS, 8>(L, s, t, st, n);
+        if (n <= (uint32_t)RX_BITONIC) {
+            tile_sort_regs<RX_THREADS, RX_BITONIC / RX_THREADS>(L, sa, t, st, n);
+            __syncthreads();
+            continue;
+        }
+        if (n <= (uint32_t)RX_CAP) {
+            for (uint32_t i = threadIdx.x; i < n; i += RX_THREADS) sa[i] = L.ekey[st + i];
+            __syncthreads();
+            const unsigned long long* r = radix_sort_depth(sa, sb, (int)n, hist, s_scan);
+            for (uint32_t i = threadIdx.x; i < n; i += RX_THREADS) {
+                L.tval[st + i] = (uint32_t)r[i];
+                L.tkey[st + i] = t;
+            }
             __syncthreads();
             continue;
         }
         unsigned long long* a = L.ekey + st;
         unsigned long long* b = L.eraw + st;
-        for (uint32_t c0 = 0; c0 < n; c0 += LT_CAP) {
-            const int m = (int)min((uint32_t)LT_CAP, n - c0);
-            int np = 2;
-            while (np < m) np <<= 1;
-            for (int i = threadIdx.x; i < np; i += blockDim.x) s[i] = i < m ? a[c0 + i] : ~0ull;
-            bitonic_smem(s, np);
-            for (int i = threadIdx.x; i < m; i += blockDim.x) a[c0 + i] = s[i];
+        for (uint32_t c0 = 0; c0 < n; c0 += RX_CAP) {
+            const int m = (int)min((uint32_t)RX_CAP, n - c0);
+            for (int i = threadIdx.x; i < m; i += RX_THREADS) sa[i] = a[c0 + i];
+            __syncthreads();
+            const unsigned long long* r = radix_sort_depth(sa, sb, m, hist, s_scan);
+            for (int i = threadIdx.x; i < m; i += RX_THREADS) a[c0 + i] = r[i];
             __syncthreads();
         }
-        for (uint32_t width = LT_CAP; width < n; width <<= 1) {
-            for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        for (uint32_t width = RX_CAP; width < n; width <<= 1) {
+            for (uint32_t i = threadIdx.x; i < n; i += RX_THREADS) {
                 const uint32_t base = i - i % (2 * width);
                 const bool in_first = (i - base) < width;
                 const uint32_t a0 = base, a1 = min(base + width, n), b0 = a1, b1 = min(base + 2 * width, n);
@@ -244,7 +355,7 @@ __global__ void __launch_bounds__(TB_THREADS) k_tile_sort_large(Layout L)
             a = b;
             b = tmp;
         }
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        for (uint32_t i = threadIdx.x; i < n; i += RX_THREADS) {
             L.tval[st + i] = (uint32_t)a[i];
             L.tkey[st + i] = t;
         }
@@ -275,8 +386,13 @@ int launch_bin(const Layout& L, int n_sm, cudaStream_t st)
 int launch_tile_sort(const Layout& L, int n_sm, cudaStream_t st)
 {
     const long long vt = (long long)L.V * L.T;
+    static bool smem_set = false;  // the long-tile kernel's dynamic shared memory, set once
+    if (!smem_set) {
+        cudaFuncSetAttribute(k_tile_sort_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RX_SMEM);
+        smem_set = true;
+    }
     k_tile_sort<<<(unsigned)vt, TS_THREADS, 0, st>>>(L);
-    k_tile_sort_large<<<(unsigned)(6 * n_sm), TB_THREADS, 0, st>>>(L);  // six 256-thread CTAs fit an SM
+    k_tile_sort_large<<<(unsigned)(5 * n_sm), RX_THREADS, RX_SMEM, st>>>(L);  // five 40-KB CTAs fit an SM
     return 2;
 }
 

@@ -114,10 +114,10 @@ def test_elongated_and_opaque_gaussians(tile):
     check_against_oracle(sc, cam, g, tile)
 
 
-@pytest.mark.parametrize("n", [2049, 7001])
+@pytest.mark.parametrize("n", [2049, 7001, 9000])
 def test_long_tile_lists_use_the_merge_path(n):
-    """Tiles with more entries than one shared-memory sort holds (2048) are sorted by chunks
-    and merge rounds; keys, values and ranges stay bit-exact."""
+    """Tiles with more entries than one shared-memory radix sort holds (2048) are sorted by
+    chunks and merge rounds; keys, values and ranges stay bit-exact."""
     sc = synth.single_block(synth.random_cube_scene(n, seed=n, sh_degree=0, extent=0.25, log_scale_mu=-2.0))
     cam = synth.small_scene_camera(40, 36, f=60.0, dist=3.0)
     g = gpu_render(sc, [cam])
@@ -126,16 +126,30 @@ def test_long_tile_lists_use_the_merge_path(n):
     assert lens.max() > 2048
 
 
-@pytest.mark.parametrize("n", [1, 31, 32, 33, 128, 129, 255, 256, 257, 2048, 2049, 4096, 4097])
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 128, 129, 255, 256, 257, 512, 513, 2048, 2049, 4096, 4097])
 def test_tile_lengths_at_sort_path_bounds(n):
     """One 16 x 16 tile holding every Gaussian: lengths on both sides of the ranking sort (128
-    keys), the short-tile bitonic sort (256), the long-tile kernel's register sort (2048) and
-    its shared-memory sort (4096, beyond which it merges chunks) stay bit-exact."""
+    keys), the short-tile bitonic sort (256), the long-tile kernel's register bitonic sort (512)
+    and its shared-memory radix sort (2048, beyond which it merges chunks) stay bit-exact."""
     sc = synth.single_block(synth.random_cube_scene(n, seed=100 + n, sh_degree=0, extent=0.2, log_scale_mu=-2.5))
     cam = synth.small_scene_camera(16, 16, f=30.0, dist=3.0)
     g = gpu_render(sc, [cam])
     o, _ = check_against_oracle(sc, cam, g, 16)
     assert o["sort"]["ranges"][0, 1] - o["sort"]["ranges"][0, 0] == n
+
+
+@pytest.mark.parametrize("n", [300, 600, 1500, 5000])
+def test_long_tiles_with_equal_depths_keep_index_order(n):
+    """Long tiles whose Gaussians share depths exactly (four planes facing the camera): the
+    radix sort orders by depth bits, then puts each run of equal depth in index order, across
+    the chunk merges too; bit-exact against the oracle's (depth, index) order."""
+    sc = synth.random_cube_scene(n, seed=7 + n, sh_degree=0, extent=0.2, log_scale_mu=-2.5)
+    sc["mean_opac"][:, 2] = np.random.default_rng(n).choice(np.float32([-0.1, 0.0, 0.05, 0.1]), size=n)
+    sc = synth.single_block(sc)
+    cam = synth.small_scene_camera(16, 16, f=30.0, dist=3.0)
+    g = gpu_render(sc, [cam])
+    o, _ = check_against_oracle(sc, cam, g, 16)
+    assert len(np.unique(o["sort"]["keys"])) == 4   # one tile, four depths: long runs of ties
 
 
 def test_all_culled_view_gives_background():
