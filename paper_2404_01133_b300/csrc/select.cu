@@ -58,6 +58,118 @@ __device__ int lod_level8(const cgs_scene& S, int b, const cgs_camera& c, double
     return lv;
 }
 
+// The same decision in FP32 with a bound on each decided quantity's distance from its FP64
+// value, for the groups where every decision is farther from its threshold than that bound (the
+// FP64 evaluation above decides the rest; *amb is set for the whole group).  Bounds, u = 2^-24
+// (this file is compiled without multiply-add contraction, one rounding per operation):
+//   e = p - c and e2 = (e0^2 + e1^2) + e2^2 have relative error <= 8u (positive terms);
+//   t = ((R0 p0 + R1 p1) + R2 p2) + t0 per row: <= 5u S, S = the sum of the terms' magnitudes
+//   (three product and three sum roundings; the FP64 products of FP32 values are exact);
+//   q = tx / tz: <= (5u Sx + |q| 5u Sz) / (tz - 5u Sz) + u |q|; u_pix = fx q + cx adds
+//   u |fx q| + u |u_pix|; every screen bound is doubled before it is compared.
+__device__ int lod_level8_f32(const cgs_scene& S, int b, const cgs_camera& c, float near_z, double d1, double d2,
+                              bool* amb)
+{
+    const float U = 5.9604645e-8f;
+    const int k = threadIdx.x & 7;
+    const bool active = b >= 0 && b < S.n_blocks && S.level_count[(long long)(b < 0 ? 0 : b) * S.n_levels] > 0;
+    float e2 = INFINITY, xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY, exu = 0.0f, eyv = 0.0f;
+    int front = 0, unsure = 0;
+    if (active) {
+        const float* bb = S.block_aabb + 6 * (long long)b;
+        const float p0 = bb[(k & 1) ? 3 : 0], p1 = bb[(k & 2) ? 4 : 1], p2 = bb[(k & 4) ? 5 : 2];
+        const float e0 = p0 - c.campos[0], ee1 = p1 - c.campos[1], ee2 = p2 - c.campos[2];
+        e2 = (e0 * e0 + ee1 * ee1) + ee2 * ee2;
+        const float tx = ((c.R[0] * p0 + c.R[1] * p1) + c.R[2] * p2) + c.t[0];
+        const float ty = ((c.R[3] * p0 + c.R[4] * p1) + c.R[5] * p2) + c.t[1];
+        const float tz = ((c.R[6] * p0 + c.R[7] * p1) + c.R[8] * p2) + c.t[2];
+        const float ex = 5.0f * U * (((fabsf(c.R[0] * p0) + fabsf(c.R[1] * p1)) + fabsf(c.R[2] * p2)) + fabsf(c.t[0]));
+        const float ey = 5.0f * U * (((fabsf(c.R[3] * p0) + fabsf(c.R[4] * p1)) + fabsf(c.R[5] * p2)) + fabsf(c.t[1]));
+        const float ez = 5.0f * U * (((fabsf(c.R[6] * p0) + fabsf(c.R[7] * p1)) + fabsf(c.R[8] * p2)) + fabsf(c.t[2]));
+        if (tz - ez > near_z) {
+            front = 1;
+            const float q = tx / tz, r = ty / tz;
+            const float dq = (ex + fabsf(q) * ez) / (tz - ez) + U * fabsf(q);
+            const float dr = (ey + fabsf(r) * ez) / (tz - ez) + U * fabsf(r);
+            const float u = c.fx * q + c.cx, v = c.fy * r + c.cy;
+            exu = 2.0f * (fabsf(c.fx) * dq + U * fabsf(c.fx * q) + U * fabsf(u));
+            eyv = 2.0f * (fabsf(c.fy) * dr + U * fabsf(c.fy * r) + U * fabsf(v));
+            xmin = xmax = u;
+            ymin = ymax = v;
+        } else if (!(tz + ez <= near_z)) {
+            unsure = 1;  // the near-plane decision (or a NaN)
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        e2 = fminf(e2, __shfl_xor_sync(0xffffffffu, e2, o, 8));
+        xmin = fminf(xmin, __shfl_xor_sync(0xffffffffu, xmin, o, 8));
+        xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o, 8));
+        ymin = fminf(ymin, __shfl_xor_sync(0xffffffffu, ymin, o, 8));
+        ymax = fmaxf(ymax, __shfl_xor_sync(0xffffffffu, ymax, o, 8));
+        exu = fmaxf(exu, __shfl_xor_sync(0xffffffffu, exu, o, 8));
+        eyv = fmaxf(eyv, __shfl_xor_sync(0xffffffffu, eyv, o, 8));
+        front |= __shfl_xor_sync(0xffffffffu, front, o, 8);
+        unsure |= __shfl_xor_sync(0xffffffffu, unsure, o, 8);
+    }
+    *amb = false;
+    if (!active) return -1;
+    if (unsure) {
+        *amb = true;
+        return -1;
+    }
+    // three-valued comparisons: 1 certainly true, 0 certainly false, -1 too close to tell
+    auto gt = [](float x, float err, float t) { return x - err > t ? 1 : (x + err <= t ? 0 : -1); };
+    auto lt = [](float x, float err, float t) { return x + err < t ? 1 : (x - err >= t ? 0 : -1); };
+    const float Wd = (float)c.width, Hd = (float)c.height;
+    int vis = 0;
+    if (front) {
+        const int t4[4] = {gt(xmax, exu, -0.5f), lt(xmin, exu, Wd - 0.5f), gt(ymax, eyv, -0.5f),
+                           lt(ymin, eyv, Hd - 0.5f)};
+        vis = 1;
+        for (int i = 0; i < 4; i++) {
+            if (t4[i] == 0) { vis = 0; break; }
+            if (t4[i] < 0) vis = -1;
+        }
+    }
+    const float* ce = S.block_cell + 4 * (long long)b;
+    const bool inside = c.campos[0] >= ce[0] && c.campos[0] < ce[1] && c.campos[1] >= ce[2] && c.campos[1] < ce[3];
+    if (!inside) {
+        if (vis < 0) { *amb = true; return -1; }
+        if (vis == 0) return -1;
+    }
+    // level: dmin = sqrt(e2min) against d1, d2 (FP64 sqrt is monotone and correctly rounded)
+    const double e2d = (double)e2;
+    auto less = [&](double d) {
+        const double t = d * d;
+        if (e2d * (1.0 + 16.0 * (double)U) < t * (1.0 - 1e-12)) return 1;
+        if (e2d * (1.0 - 16.0 * (double)U) > t * (1.0 + 1e-12)) return 0;
+        return -1;
+    };
+    int lv;
+    const int c1 = less(d1);
+    if (c1 < 0) { *amb = true; return -1; }
+    if (c1) {
+        lv = 0;
+    } else {
+        const int c2 = less(d2);
+        if (c2 < 0) { *amb = true; return -1; }
+        lv = c2 ? 1 : 2;
+    }
+    if (lv > S.n_levels - 1) lv = S.n_levels - 1;
+    return lv;
+}
+
+// Level of block b for the calling 8-lane group: FP32 where it is certain, FP64 otherwise (all
+// lanes of the warp must call it).
+__device__ int lod_level8_fast(const cgs_scene& S, int b, const cgs_camera& c, double near_z, double d1, double d2)
+{
+    bool amb = false;
+    const int l = lod_level8_f32(S, b, c, (float)near_z, d1, d2, &amb);
+    if (__any_sync(0xffffffffu, amb)) return lod_level8(S, b, c, near_z, d1, d2);
+    return l;
+}
+
 __global__ void k_lod_levels(cgs_scene S, const cgs_camera* __restrict__ cams, int n_views, cgs_config cfg,
                              int8_t* levels)
 {
@@ -67,7 +179,7 @@ __global__ void k_lod_levels(cgs_scene S, const cgs_camera* __restrict__ cams, i
     const int groups = blockDim.x >> 3;
     for (int b0 = 0; b0 < S.n_blocks; b0 += groups) {
         const int b = b0 + (threadIdx.x >> 3);
-        const int l = lod_level8(S, b < S.n_blocks ? b : -1, c, (double)cfg.near_z, cfg.lod_dist[0], cfg.lod_dist[1]);
+        const int l = lod_level8_fast(S, b < S.n_blocks ? b : -1, c, (double)cfg.near_z, cfg.lod_dist[0], cfg.lod_dist[1]);
         if (b < S.n_blocks && (threadIdx.x & 7) == 0) levels[(long long)v * S.n_blocks + b] = (int8_t)l;
     }
 }
@@ -89,6 +201,22 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Layout L, cgs_scene S, c
     const int NB = S.n_blocks, NL = S.n_levels;
     int8_t* lev = L.levels + (long long)v * NB;
     const int b0 = blockIdx.x * SEL_BLOCKS;
+    // this CTA's blocks: level, and the chosen level's count and offset (a view of at most
+    // SEL_BLOCKS blocks is handled by one CTA, whose second phase reads them from here)
+    __shared__ int s_lv[SEL_BLOCKS];
+    __shared__ long long s_cnt[SEL_BLOCKS], s_off[SEL_BLOCKS];
+    auto keep = [&](int b, int l) {
+        long long cnt = 0, off = 0;
+        if (l >= 0) {
+            cnt = S.level_count[(long long)b * NL + l];
+            off = S.level_offset[(long long)b * NL + l];
+            if (cnt <= 0) l = -1;
+        }
+        lev[b] = (int8_t)l;
+        s_lv[b - b0] = l;
+        s_cnt[b - b0] = cnt;
+        s_off[b - b0] = off;
+    };
     if (levels_in || view_block) {
         const int b = b0 + (int)threadIdx.x;
         if (threadIdx.x < SEL_BLOCKS && b < NB) {
@@ -100,23 +228,20 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Layout L, cgs_scene S, c
             } else {
                 l = (b == view_block[v]) ? 0 : -1;
             }
-            if (l >= 0 && S.level_count[(long long)b * NL + l] <= 0) l = -1;
-            lev[b] = (int8_t)l;
+            keep(b, l);
         }
     } else if (L.lod_mode == CGS_LOD_POINT) {
         // point-wise baseline: every non-empty block at its finest level; k_project applies the
         // per-Gaussian distance test
         const int b = b0 + (int)threadIdx.x;
-        if (threadIdx.x < SEL_BLOCKS && b < NB) lev[b] = S.level_count[(long long)b * NL] > 0 ? 0 : -1;
+        if (threadIdx.x < SEL_BLOCKS && b < NB) keep(b, 0);
     } else {
         const cgs_camera c = cams[v];
         const int b = b0 + (int)(threadIdx.x >> 3);
-        int l = lod_level8(S, b < NB ? b : -1, c, (double)cfg.near_z, cfg.lod_dist[0], cfg.lod_dist[1]);
-        if (b < NB && (threadIdx.x & 7) == 0) {
-            if (l >= 0 && S.level_count[(long long)b * NL + l] <= 0) l = -1;
-            lev[b] = (int8_t)l;
-        }
+        const int l = lod_level8_fast(S, b < NB ? b : -1, c, (double)cfg.near_z, cfg.lod_dist[0], cfg.lod_dist[1]);
+        if (b < NB && (threadIdx.x & 7) == 0) keep(b, l);
     }
+    const bool one_cta = gridDim.x == 1;
     __shared__ bool s_last;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -130,7 +255,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Layout L, cgs_scene S, c
     }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
+    if (!one_cta) __threadfence();
     // phase 2: the ordered segment list, one CTA-wide exclusive scan per chunk of blocks of the
     // packed pair (selected count << 0 | Gaussian count << SEG_BITS); the levels written by the
     // other CTAs are read past L1
@@ -143,15 +268,16 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Layout L, cgs_scene S, c
     long long* so = L.seg_off + (long long)v * NB;
     for (int c0 = 0; c0 < NB; c0 += blockDim.x) {
         const int b = c0 + threadIdx.x;
-        const int l = b < NB ? (int)__ldcg(lev + b) : -1;
-        const unsigned long long cnt = l >= 0 ? (unsigned long long)S.level_count[(long long)b * NL + l] : 0ull;
+        const int l = b < NB ? (one_cta ? s_lv[b] : (int)__ldcg(lev + b)) : -1;
+        const unsigned long long cnt =
+            l >= 0 ? (unsigned long long)(one_cta ? s_cnt[b] : S.level_count[(long long)b * NL + l]) : 0ull;
         const unsigned long long x = l >= 0 ? (1ull | (cnt << SEG_BITS)) : 0ull;
         unsigned long long tot;
         const unsigned long long ex = s_carry + block_exclusive_scan<unsigned long long>(x, wb, &tot);
         if (l >= 0) {
             const int sidx = (int)(ex & ((1ull << SEG_BITS) - 1));
             const unsigned long long acc = ex >> SEG_BITS;
-            so[sidx] = S.level_offset[(long long)b * NL + l];
+            so[sidx] = one_cta ? s_off[b] : S.level_offset[(long long)b * NL + l];
             L.seg_blk[(long long)v * NB + sidx] = b;
             sb[sidx] = (uint32_t)(acc < 0xffffffffull ? acc : 0xffffffffull);
         }
@@ -175,9 +301,21 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Layout L, cgs_scene S, c
     }
     __syncthreads();
     if (!s_last) return;
+    const int V = L.V;
+    if (V == 1) {  // one view: its count is the total
+        if (threadIdx.x == 0) {
+            const unsigned long long total = s_carry >> SEG_BITS;
+            L.view_base[0] = 0u;
+            L.view_base[1] = (uint32_t)(total < 0xffffffffull ? total : 0xffffffffull);
+            L.hdr->n_sel_raw = total;
+            const unsigned long long cap = (unsigned long long)L.n_cap;
+            L.hdr->n_sel = (uint32_t)(total < cap ? total : cap);
+            if (total > cap) latch(L.hdr, ST_CAPACITY);
+        }
+        return;
+    }
     __threadfence();
     // exclusive prefix of the per-view counts; total capped at the frame capacity
-    const int V = L.V;
     const int per = (V + blockDim.x - 1) / blockDim.x;
     const int v0 = threadIdx.x * per;
     const volatile uint32_t* vc = L.view_cnt;
