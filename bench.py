@@ -64,10 +64,12 @@ OPS_FWD_BLEND = 6
 OPS_BWD_EVAL = 17
 OPS_BWD_GRAD = 28
 
-# DRAM bytes (read + write) per launch of a kernel of the headline workload, from one ncu
-# capture of the current build (the summary committed beside the kernel profiles); a kernel
-# absent here reports traffic null.  An entry is removed when its kernel changes.
-NCU_TRAFFIC_BYTES = {}
+# DRAM bytes (read + write) per launch of a kernel of the headline workload at 16 x 16 tiles and
+# batch 128, from one ncu capture of the current build (the summary committed beside the kernel
+# profiles: DRAM bytes per second times the launch's duration); a kernel absent here reports
+# traffic null.  An entry is removed when its kernel changes.
+NCU_TRAFFIC_BYTES = {"render": 15.325e6, "render_bwd": 67.159e6, "project": 73.995e6, "project_bwd": 72.779e6,
+                     "loss": 31.151e6}
 
 
 def parse_args():
@@ -463,7 +465,7 @@ def run_ours(args, world, rank, local):
     i_fwd = ideal_ms(work, peaks, fwd_keys)
     dom = max(work, key=lambda k_: stage_ms.get(k_, 0.0))
     roof = roofline(dom, stage_ms, work, peaks, KERNEL_NAMES[dom],
-                    NCU_TRAFFIC_BYTES.get(dom) if args.tile == 16 else None)
+                    NCU_TRAFFIC_BYTES.get(dom) if (args.tile, args.batch) == (16, 128) else None)
     strict = {"render": pairs_b * (OPS_FWD_EVAL + OPS_FWD_BLEND) / (stage_ms["render"] * 1e-3) / 1e12 / peaks["fp32_tops"],
               "render_bwd": pairs_b * (OPS_BWD_EVAL + OPS_BWD_GRAD) / (stage_ms["render_bwd"] * 1e-3) / 1e12
               / peaks["fp32_tops"]}
@@ -968,7 +970,7 @@ def run_lod_workloads(args, world, rank, local, peaks, launches_acc):
     clk = clocks.stop()
     mean = lambda k: float(np.mean([r[k]["fps"] for r in rows]))
     worst = min(rows, key=lambda r: r["lod"]["fps"])
-    wdom = max(worst["lod"]["_stage_ms"], key=worst["lod"]["_stage_ms"].get)
+    wdom = max(worst["lod"]["_work"], key=lambda k_: worst["lod"]["_stage_ms"].get(k_, 0.0))
     roof = roofline(wdom, worst["lod"]["_stage_ms"], worst["lod"]["_work"], peaks, KERNEL_NAMES[wdom])
     roof["frame"] = f"block-LoD frame at {worst['height_m']:g} m (the sweep's slowest)"
     for r in rows:
@@ -1026,7 +1028,7 @@ def run_lod_workloads(args, world, rank, local, peaks, launches_acc):
         status.append(cgs.cgs_status_string(s_))
         counts += np.asarray(c_, np.int64)
     work = stage_work(counts, 0, n_tiles * V, W * H * V, sc["sh_degree"])
-    qdom = max(per_frame_stage, key=per_frame_stage.get)
+    qdom = max(work, key=lambda k_: per_frame_stage.get(k_, 0.0))
     qroof = roofline(qdom, per_frame_stage, work, peaks, KERNEL_NAMES[qdom])
     qroof["frame"] = "the 64 poses' batched frames together (work and time summed over the frames)"
     queue = {"metric": "LoD pose queue FPS, batched vs sequential (64 poses, 20M Gaussians, 1080p)",
@@ -1139,7 +1141,7 @@ def run_train32(args, world, rank, local, peaks, launches_acc):
     n_tiles = ((W + tile - 1) // tile) * ((H + tile - 1) // tile) * V
     work = stage_work(counts, sum_nc, n_tiles, W * H * V, sc["sh_degree"], backward=True, loss_bytes=12,
                       packed=False)
-    dom = max(per_step_stage, key=per_step_stage.get)
+    dom = max(work, key=lambda k_: per_step_stage.get(k_, 0.0))
     roof = roofline(dom, per_step_stage, work, peaks, KERNEL_NAMES[dom])
     roof["frame"] = "the batched step's frames together (work and time summed over the frames)"
     del parts
