@@ -985,7 +985,7 @@ def run_lod_workloads(args, world, rank, local, peaks, launches_acc):
            "mean_fps": {"lod": mean("lod"), "pointwise_lod": mean("pointwise"), "no_lod_level0": mean("level0")},
            "per_height": rows, "roofline": roof, "clocks": clk,
            "paper_context": "53.7 FPS block LoD, 30.3 point-wise, 21.6 no LoD on MatrixCity (unnamed GPU, width "
-                            "1600; Table 4 and the LoD experiments)"}
+                            "1600; Tables 2 and 5)"}
 
     # ---- lodqueue: 64 poses -----------------------------------------------------------------
     qcams = synth.lod_pose_queue(sc["side"])
