@@ -27,7 +27,9 @@
  * for finite-difference pins, liboracle_f64).  The key path -- everything that turns
  * floating point into an integer the GPU must reproduce (near/degenerate culls, radius,
  * tile rect, depth bits) -- is always evaluated in FP32 by project_one_f.  Compositing
- * decisions (skip, stop) are taken in REAL.
+ * decisions (skip, stop) are taken in REAL.  The falloff exp(power) is the exponential
+ * rounded once to REAL (the FP64 exponential, then one rounding): the paper fixes no
+ * precision for it, and a correctly rounded value is the plain definition.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -368,7 +370,10 @@ static int64_t pixel_walk(const int64_t* list, int64_t len, REAL px, REAL py, co
         }
         if (power > 0) { if (hash) *hash = fnv(*hash, 1); continue; }
         REAL o = mean_opac[4 * g + 3];
-        REAL G = exp(power);
+        /* G = exp(power) correctly rounded to REAL: the FP64 exponential, rounded once (in the
+         * FP32 build its result is the nearest float to e^power except where e^power lies
+         * within an FP64 rounding error of a float rounding boundary) */
+        REAL G = (REAL)exp((double)power);
         REAL og = o * G;
         if (amb && fabs((double)og - 1.0 / 255.0) <= 2.0 * ea * (double)og) *amb = 1;
         REAL alpha = og < (REAL)0.99 ? og : (REAL)0.99;
@@ -791,7 +796,7 @@ int64_t orc_concat(int32_t n_blocks, int32_t n_levels, const int64_t* level_offs
     return m;
 }
 
-/* Point-wise level selection, the baseline Sec. 3.3.2 compares against (Table 4): each
+/* Point-wise level selection, the baseline Sec. 3.3.2 compares against (Table 5): each
  * Gaussian takes the level of its own distance to the camera centre (FP32,
  * dist = sqrt((dx*dx + dy*dy) + dz*dz), level 0 if dist < d1, 1 if < d2, else 2, clamped)
  * and is kept iff its rank in its block's finest level is below that level's count (levels
