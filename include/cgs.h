@@ -89,12 +89,19 @@ typedef struct cgs_config {
                             1 if dmin < d2, else 2 */
     int32_t lod_mode;    /* when the renderer selects levels itself (no d_levels, no
                             d_view_block): CGS_LOD_BLOCK or CGS_LOD_POINT */
-    int32_t _pad2;
+    int32_t exact;       /* 0: the fast compositing path.  1: the parity build of the
+                            compositing kernels (forward and backward): each pair's power,
+                            falloff and alpha in the operations and order of Eq. 1's plain
+                            per-pixel loop, e^power rounded once to FP32 from the FP64
+                            exponential, transmittance T (1 - alpha) and colour C + c alpha T
+                            with two roundings each; slow (one FP64 exponential per pair),
+                            for parity checks.  Not available for cgs_render_forward_hits
+                            (CGS_ERR_UNSUPPORTED). */
 } cgs_config;
 
 /* Level selection modes.
  * CGS_LOD_BLOCK: the paper's block-wise selection (Sec. 3.3.2, cgs_lod_select).
- * CGS_LOD_POINT: the point-wise baseline the paper compares against (Sec. 3.3.2, Table 4):
+ * CGS_LOD_POINT: the point-wise baseline the paper compares against (Sec. 3.3.2; Table 5, the LoD-strategy ablation):
  *   every non-empty block takes part without block culling; a Gaussian of block b at rank r
  *   in the block's finest level (levels are nested prefixes) is rendered iff
  *   r < level_count[b][l], l = 0 if dist < d1, 1 if dist < d2, else 2 (clamped), with

@@ -41,7 +41,7 @@ class cgs_scene(C.Structure):
 
 class cgs_config(C.Structure):
     _fields_ = [("tile", C.c_int32), ("batch", C.c_int32), ("near_z", C.c_float), ("bg", C.c_float * 3),
-                ("lod_dist", C.c_double * 2), ("lod_mode", C.c_int32), ("_pad2", C.c_int32)]
+                ("lod_dist", C.c_double * 2), ("lod_mode", C.c_int32), ("exact", C.c_int32)]
 
 
 CGS_LOD_BLOCK = 0

@@ -18,7 +18,7 @@ namespace cgs {
 //
 // With HITS, every blend is also counted per scene Gaussian: one atomic add per (warp, entry)
 // of the number of the warp's pixels that blended it (L.hits, indexed by scene index).
-template <int B, int BATCH, bool HITS>
+template <int B, int BATCH, bool HITS, bool EXACT>
 __global__ void __launch_bounds__(B * B / 2, B == 16 ? 8 : 32) k_render_fwd(Layout L, const uint32_t* __restrict__ tval, float bg0,
                                                           float bg1, float bg2, float* __restrict__ image,
                                                           float* __restrict__ final_T, uint32_t* __restrict__ n_contrib)
@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 8 : 32) k_render_fwd(Layo
     __shared__ float4 s_e0[BATCH], s_e1[BATCH], s_e2[BATCH], s_e3[BATCH];
     __shared__ uint32_t s_m[BATCH];
     __shared__ uint32_t s_g[HITS ? BATCH : 1];
+    __shared__ float4 s_cn[EXACT ? BATCH : 1];  // parity build: conic A', B', C' and opacity
     const int v = blockIdx.z;
     const int tile = blockIdx.y * L.tiles_x + blockIdx.x;
     const uint2 rg = reinterpret_cast<const uint2*>(L.ranges)[(size_t)v * L.T + tile];
@@ -63,6 +64,7 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 8 : 32) k_render_fwd(Layo
                 s_e3[i] = se.e3;
                 m = warp_mask<B>(a, b, c.w, tx0, ty0);
                 if (HITS) s_g[i] = L.gidx[j];
+                if (EXACT) s_cn[i] = make_float4(b.x, b.y, b.z, a.z);
             }
             s_m[i] = m;
         }
@@ -79,25 +81,52 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 8 : 32) k_render_fwd(Layo
                 const int k = c0 + kk;
                 const float4 e0 = s_e0[k], e1 = s_e1[k], e2 = s_e2[k], e3 = s_e3[k];
                 const uint32_t pos = start - rg.x + (uint32_t)k;
-                float dx;
-                float2 dy;
-                const float2 p = staged_power2(e0, e1, fpx, fpy, &dx, &dy);
-                const float2 G = make_float2(gauss_exp2(p.x), gauss_exp2(p.y));
-                float2 nog;
-                const float2 na = neg_alpha2(e2, G, &nog);  // -alpha
-                const float2 Tn = ieee_fma2(na, T, T);      // T (1 - alpha), rounded once
+                float2 p, na, Tn;  // power (times log2 e in the fast path), -alpha, T (1 - alpha)
+                if constexpr (EXACT) {
+                    const float4 cn = s_cn[k];
+                    p = make_float2(exact_power(cn, e1.x, e0.x, fpx, fpy.x), exact_power(cn, e1.x, e0.x, fpx, fpy.y));
+                    const float a0 = exact_alpha(exact_og(cn.w, p.x)), a1 = exact_alpha(exact_og(cn.w, p.y));
+                    na = make_float2(-a0, -a1);
+                    Tn = make_float2(ieee_mul(T.x, ieee_sub(1.0f, a0)), ieee_mul(T.y, ieee_sub(1.0f, a1)));
+                } else {
+                    float dx;
+                    float2 dy;
+                    p = staged_power2(e0, e1, fpx, fpy, &dx, &dy);
+                    const float2 G = make_float2(gauss_exp2(p.x), gauss_exp2(p.y));
+                    float2 nog;
+                    na = neg_alpha2(e2, G, &nog);  // -alpha
+                    Tn = ieee_fma2(na, T, T);      // T (1 - alpha), rounded once
+                }
                 const bool ok0 = !done0 && !(p.x > 0.0f) && !(na.x > nthr);
                 const bool ok1 = !done1 && !(p.y > 0.0f) && !(na.y > nthr);
                 const bool st0 = ok0 && Tn.x < 1e-4f, st1 = ok1 && Tn.y < 1e-4f;
                 const bool b0 = ok0 && !st0, b1 = ok1 && !st1;
-                // -alpha where the pixel blends, 0 where it does not: then T (1 - alpha) and the
-                // colour weight alpha T come out of the packed FMA pipe (fma(0, T, T) = T exactly)
-                const float2 nab = make_float2(b0 ? na.x : 0.0f, b1 ? na.y : 0.0f);
-                const float2 w = __fmul2_rn(nab, T);        // -alpha T, or 0
-                NC0 = __ffma2_rn(make_float2(e2.z, e2.w), w, NC0);
-                NC1 = __ffma2_rn(make_float2(e3.x, e3.y), w, NC1);
-                NC2 = __ffma2_rn(make_float2(e3.z, e3.w), w, NC2);
-                T = ieee_fma2(nab, T, T);
+                if constexpr (EXACT) {
+                    // the colour sums C + c (alpha T), positive in this build
+                    if (b0) {
+                        const float w = ieee_mul(-na.x, T.x);
+                        NC0.x = ieee_add(NC0.x, ieee_mul(e2.z, w));
+                        NC1.x = ieee_add(NC1.x, ieee_mul(e3.x, w));
+                        NC2.x = ieee_add(NC2.x, ieee_mul(e3.z, w));
+                        T.x = Tn.x;
+                    }
+                    if (b1) {
+                        const float w = ieee_mul(-na.y, T.y);
+                        NC0.y = ieee_add(NC0.y, ieee_mul(e2.w, w));
+                        NC1.y = ieee_add(NC1.y, ieee_mul(e3.y, w));
+                        NC2.y = ieee_add(NC2.y, ieee_mul(e3.w, w));
+                        T.y = Tn.y;
+                    }
+                } else {
+                    // -alpha where the pixel blends, 0 where it does not: then T (1 - alpha) and the
+                    // colour weight alpha T come out of the packed FMA pipe (fma(0, T, T) = T exactly)
+                    const float2 nab = make_float2(b0 ? na.x : 0.0f, b1 ? na.y : 0.0f);
+                    const float2 w = __fmul2_rn(nab, T);        // -alpha T, or 0
+                    NC0 = __ffma2_rn(make_float2(e2.z, e2.w), w, NC0);
+                    NC1 = __ffma2_rn(make_float2(e3.x, e3.y), w, NC1);
+                    NC2 = __ffma2_rn(make_float2(e3.z, e3.w), w, NC2);
+                    T = ieee_fma2(nab, T, T);
+                }
                 last0 = b0 ? pos + 1u : last0;
                 last1 = b1 ? pos + 1u : last1;
                 stop0 = st0 ? pos : stop0;
@@ -118,6 +147,13 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 8 : 32) k_render_fwd(Layo
         }
     }
     const size_t HW = (size_t)L.W * L.H;
+    if constexpr (EXACT) {
+        // C + T bg as the plain loop forms it; stored negated to share the writes below
+        NC0 = make_float2(-ieee_add(NC0.x, ieee_mul(T.x, bg0)), -ieee_add(NC0.y, ieee_mul(T.y, bg0)));
+        NC1 = make_float2(-ieee_add(NC1.x, ieee_mul(T.x, bg1)), -ieee_add(NC1.y, ieee_mul(T.y, bg1)));
+        NC2 = make_float2(-ieee_add(NC2.x, ieee_mul(T.x, bg2)), -ieee_add(NC2.y, ieee_mul(T.y, bg2)));
+        bg0 = bg1 = bg2 = 0.0f;
+    }
     if (in0) {
         const size_t pix = (size_t)py0 * L.W + px;
         image[(3 * (size_t)v + 0) * HW + pix] = T.x * bg0 - NC0.x;
@@ -150,14 +186,17 @@ static void fwd_launch(const Layout& L, const uint32_t* tval, const cgs_config& 
                        cudaStream_t st)
 {
     dim3 grid(L.tiles_x, L.tiles_y, L.V);
-    if (L.hits)
-        k_render_fwd<B, BATCH, true><<<grid, B * B / 2, 0, st>>>(L, tval, c.bg[0], c.bg[1], c.bg[2], img, T, nc);
+    if (c.exact)
+        k_render_fwd<B, BATCH, false, true><<<grid, B * B / 2, 0, st>>>(L, tval, c.bg[0], c.bg[1], c.bg[2], img, T, nc);
+    else if (L.hits)
+        k_render_fwd<B, BATCH, true, false><<<grid, B * B / 2, 0, st>>>(L, tval, c.bg[0], c.bg[1], c.bg[2], img, T, nc);
     else
-        k_render_fwd<B, BATCH, false><<<grid, B * B / 2, 0, st>>>(L, tval, c.bg[0], c.bg[1], c.bg[2], img, T, nc);
+        k_render_fwd<B, BATCH, false, false><<<grid, B * B / 2, 0, st>>>(L, tval, c.bg[0], c.bg[1], c.bg[2], img, T, nc);
 }
 bool launch_render_fwd(const Layout& L, const cgs_config& c, float* img, float* T, uint32_t* nc, cudaStream_t st)
 {
     const uint32_t* tv = L.tval;
+    if (c.exact && L.hits) return false;  // hit counting has no parity build
     if (L.B == 16) {
         switch (c.batch) {
             case 32: fwd_launch<16, 32>(L, tv, c, img, T, nc, st); return true;

@@ -26,7 +26,7 @@ namespace cgs {
 // T_before = T / (1 - alpha); dL/dalpha = (T (g . c) - gS) / (1 - alpha), dL/dc = g alpha
 // T_before; then T = T_before and gS += alpha T_before (g . c).  The running sum is kept
 // negated (ngS = -gS) and alpha enters as -alpha, so no step negates anything.
-template <int B, int BATCH>
+template <int B, int BATCH, bool EXACT>
 __global__ void __launch_bounds__(B * B / 2, B == 16 ? 6 : 24) k_render_bwd(Layout L, const uint32_t* __restrict__ tval, float bg0,
                                                           float bg1, float bg2, const float* __restrict__ dL_dimg,
                                                           const float* __restrict__ final_T,
@@ -141,10 +141,20 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 6 : 24) k_render_bwd(Layo
                 const uint32_t lp = (uint32_t)(bs + k - first);
                 float dx;
                 float2 dy;
-                const float2 p = staged_power2(e0, e1, fpx, fpy, &dx, &dy);
-                const float2 G = make_float2(gauss_exp2(p.x), gauss_exp2(p.y));
-                float2 nog;
-                const float2 na = neg_alpha2(e2, G, &nog);  // -alpha
+                float2 p = staged_power2(e0, e1, fpx, fpy, &dx, &dy);
+                float2 G, nog, na;  // falloff, -o G, -alpha
+                if constexpr (EXACT) {
+                    // the parity build's decisions: power, G and alpha as the forward took them
+                    const float4 cn = s_cn[k];
+                    p = make_float2(exact_power(cn, e1.x, e0.x, fpx, fpy.x), exact_power(cn, e1.x, e0.x, fpx, fpy.y));
+                    G = make_float2(__double2float_rn(exp((double)p.x)), __double2float_rn(exp((double)p.y)));
+                    const float og0 = ieee_mul(cn.w, G.x), og1 = ieee_mul(cn.w, G.y);
+                    nog = make_float2(-og0, -og1);
+                    na = make_float2(-exact_alpha(og0), -exact_alpha(og1));
+                } else {
+                    G = make_float2(gauss_exp2(p.x), gauss_exp2(p.y));
+                    na = neg_alpha2(e2, G, &nog);
+                }
                 const bool u0 = lp < nc0 && !(p.x > 0.0f) && !(na.x > nthr);
                 const bool u1 = lp < nc1 && !(p.y > 0.0f) && !(na.y > nthr);
                 const float2 om = __fadd2_rn(one, na);                 // 1 - alpha
@@ -227,7 +237,10 @@ static void bwd_launch(const Layout& L, const uint32_t* tval, const cgs_config& 
                        const uint32_t* nc, cudaStream_t st)
 {
     dim3 grid(L.tiles_x, L.tiles_y, L.V);
-    k_render_bwd<B, BATCH><<<grid, B * B / 2, 0, st>>>(L, tval, c.bg[0], c.bg[1], c.bg[2], dimg, T, nc);
+    if (c.exact)
+        k_render_bwd<B, BATCH, true><<<grid, B * B / 2, 0, st>>>(L, tval, c.bg[0], c.bg[1], c.bg[2], dimg, T, nc);
+    else
+        k_render_bwd<B, BATCH, false><<<grid, B * B / 2, 0, st>>>(L, tval, c.bg[0], c.bg[1], c.bg[2], dimg, T, nc);
 }
 
 bool launch_render_bwd(const Layout& L, const cgs_config& c, const float* dimg, const float* T, const uint32_t* nc,

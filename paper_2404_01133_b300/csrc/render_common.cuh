@@ -22,6 +22,12 @@ __device__ __forceinline__ float ieee_sub(float a, float b)
     asm("sub.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
     return r;
 }
+__device__ __forceinline__ float ieee_add(float a, float b)
+{
+    float r;
+    asm("add.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
 __device__ __forceinline__ float ieee_mul(float a, float b)
 {
     float r;
@@ -136,6 +142,28 @@ __device__ __forceinline__ float2 neg_alpha2(const float4& e2, float2 G, float2*
     *nog = n;
     return make_float2(fmaxf(-0.99f, n.x), fmaxf(-0.99f, n.y));
 }
+
+// ---- the parity build (cgs_config.exact) -------------------------------------------------
+// The decisions of Eq. 1 in the operations and order of the plain per-pixel loop: with
+// dx = u - px, dy = v - py, power = -0.5 ((A' dx) dx + (C' dy) dy) - (B' dx) dy, every
+// operation rounded once; G = e^power rounded once to FP32 (the FP64 exponential, then one
+// rounding); alpha = min(0.99, o G) (o G when o G < 0.99, else 0.99).  The transmittance then
+// follows T (1 - alpha) and the colour C + c (alpha T), two roundings each.  One FP64
+// exponential per pair: slow on this part, meant for parity checks.
+__device__ __forceinline__ float exact_power(const float4& cn, float u, float v, float px, float py)
+{
+    const float dx = ieee_sub(u, px), dy = ieee_sub(v, py);
+    const float s = ieee_add(ieee_mul(ieee_mul(cn.x, dx), dx), ieee_mul(ieee_mul(cn.z, dy), dy));
+    return ieee_sub(ieee_mul(-0.5f, s), ieee_mul(ieee_mul(cn.y, dx), dy));
+}
+
+// o G with G = e^p rounded once to FP32.
+__device__ __forceinline__ float exact_og(float o, float p)
+{
+    return ieee_mul(o, __double2float_rn(exp((double)p)));
+}
+
+__device__ __forceinline__ float exact_alpha(float og) { return og < 0.99f ? og : 0.99f; }
 
 // Threads of a B x B tile: B*B/2, two pixels each.  Warp w covers the 8 x 8 block at
 // ((w % (B/8)) * 8, (w / (B/8)) * 8); lane l takes pixels (l & 7, l >> 3) and (l & 7, (l >> 3) + 4).

@@ -35,9 +35,12 @@ def cameras_device(cams, device="cuda"):
     return cameras_host(cams).to(device, non_blocking=False)
 
 
-def make_config(tile=16, batch=None, near_z=0.2, bg=(0.0, 0.0, 0.0), lod_dist=(200.0, 600.0), lod_mode=0):
+def make_config(tile=16, batch=None, near_z=0.2, bg=(0.0, 0.0, 0.0), lod_dist=(200.0, 600.0), lod_mode=0,
+                exact=False):
+    """exact=True selects the compositing kernels' parity build (cgs_config.exact)."""
     c = _c.cgs_config()
     c.lod_mode = lod_mode
+    c.exact = 1 if exact else 0
     c.tile = tile
     c.batch = batch if batch is not None else (256 if tile == 16 else 64)
     c.near_z = near_z

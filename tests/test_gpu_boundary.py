@@ -84,8 +84,9 @@ def test_autotune_times_every_candidate_and_caches(tmp_path):
     assert set(ms) == set(cgs.TUNE_ORDER)
     assert all(v > 0 for v in ms.values())                          # all fit this frame
     assert (cfg.tile, cfg.batch) == min(ms, key=ms.get)
-    # the chosen configuration renders as any other (tile and batch never change results)
-    o = oracle.render(sc, cams[0])
+    # the chosen configuration renders as the oracle at its tile size (the batch depth never
+    # changes results; the tile size does, through the 3-sigma truncation of each tile list)
+    o = oracle.render(sc, cams[0], oracle.make_config(tile=cfg.tile))
     fr = ta.Frame(1, W, H, cfg.tile, 1, ds.n, 64 * ds.n)
     img, T, nc = ta.render_forward(ds, fr, cfg, d_cams)
     torch.cuda.synchronize()
