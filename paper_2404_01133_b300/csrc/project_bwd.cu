@@ -1,6 +1,6 @@
-// Backward of the projection and colour (differentiable rendering, Sec. 3.1): chains the
-// per-Gaussian screen-space gradients (u, v, conic, opacity, rgb) accumulated by the
-// compositing backward to the scene attributes.  Discrete decisions pass no gradient: the
+// Backward of the projection and colour (differentiable rendering, Sec. 3.1): turns the
+// per-Gaussian pixel moments accumulated by the compositing backward into the screen-space
+// gradients (u, v, conic, opacity, rgb) and chains them to the scene attributes.  Discrete decisions pass no gradient: the
 // guard-band clamp zeroes the clamped coordinate's direct term, the colour clamp masks its
 // channel, and the quaternion gradient goes through the normalisation.  Compiled with
 // -fmad=false like the forward projection, so the recomputed clamp decisions match it.
@@ -175,7 +175,8 @@ __global__ void __launch_bounds__(PB_THREADS, 6) k_project_bwd(Layout L, cgs_sce
             const float4 mo = __ldg(reinterpret_cast<const float4*>(S.mean_opac) + g);
             const float m[3] = {mo.x, mo.y, mo.z};
             if (colour_role) {
-                const float grgb[3] = {gb.z, gb.w, gc4.x};
+                // the accumulated colour moments are the negated colour gradient
+                const float grgb[3] = {-gb.z, -gb.w, -gc4.x};
                 float Yg[48];
                 colour_grad<DEG>(m, c, S, g, grgb, Yg, gm);
                 float* gsh = g_sh + (PACKED ? (long long)r : g) * (long long)(nc * 3);
@@ -205,8 +206,15 @@ __global__ void __launch_bounds__(PB_THREADS, 6) k_project_bwd(Layout L, cgs_sce
                 float s[3], q[4];
                 load_scale_quat(S, g, s, q);
                 Proj p;
-                if (project_one(m, s, q, c, near_z, p) == 0)
-                    geometry_chain(p, c, ga.x, ga.y, ga.z, ga.w, gb.x, s, gm, gsv, gqn);
+                if (project_one(m, s, q, c, near_z, p) == 0) {
+                    // the pixel moments of w = dL/do (m0..m4 in ga.xyzw, gb.x): dL/dpower = o w
+                    // and power = -A'/2 dx^2 - B' dx dy - C'/2 dy^2 with dx = u - px
+                    const float o = mo.w;
+                    const float mx = o * ga.x, my = o * ga.y;
+                    const float gu = -(p.conic[0] * mx + p.conic[1] * my);
+                    const float gv = -(p.conic[2] * my + p.conic[1] * mx);
+                    geometry_chain(p, c, gu, gv, -0.5f * o * ga.z, -o * ga.w, -0.5f * o * gb.x, s, gm, gsv, gqn);
+                }
                 const long long row = PACKED ? (long long)r : g;
                 const float4 x_sc = make_float4(gsv[0], gsv[1], gsv[2], 0.0f);
                 const float4 x_q = make_float4(gqn[0], gqn[1], gqn[2], gqn[3]);

@@ -11,15 +11,17 @@ namespace cgs {
 // in the forward (the forward's contribution bits), last first.  Per entry, a lane replays its
 // two pixels as packed pairs and reduces them to nine values:
 //   w = dL/do of a pixel (dalpha/do = G when the 0.99 clamp is inactive, else 0); since
-//   dL/dpower = o w, the power moments are kept as moments of w and multiplied by o once per
-//   (tile, Gaussian):  m0 = sum w dx, m1 = sum w dy, m2 = sum w dx^2, m3 = sum w dx dy,
-//   m4 = sum w dy^2, m5 = sum w;  m6..m8 = sum (-alpha T) dL/d(r, g, b)  (negated colour
-//   gradient, the staged opacity being -o).
+//   dL/dpower = o w, the power moments are kept as moments of w:  m0 = sum w dx,
+//   m1 = sum w dy, m2 = sum w dx^2, m3 = sum w dx dy, m4 = sum w dy^2, m5 = sum w;
+//   m6..m8 = sum (-alpha T) dL/d(r, g, b)  (negated colour gradient, the staged opacity
+//   being -o).
 // The two pixels of a lane share dx, so m0 = dx m5, m2 = dx m0, m3 = dx m1.  Up to three
 // entries' 27 values go through a per-warp shared-memory transpose (row = value, column =
-// lane; lane r then sums row r with eight 16-byte loads), are added in shared memory per
-// entry, turned into dL/d(u, v, conic, o, rgb) with the entry's conic and opacity, and added
-// once per (tile, Gaussian) to the global accumulator.
+// lane; lane r then sums row r with eight 16-byte loads), and lane 9 e + c adds the warp's sum
+// of m_c for entry e to the Gaussian's row of the global accumulator (one vector of 27 atomic
+// adds per three entries).  The moments are linear in the pixels, so the projection backward
+// turns their totals into dL/d(u, v, conic, o, rgb) once per Gaussian, with its conic and
+// opacity: no per-tile flush, no shared accumulator, no barrier after the replay.
 //
 // Replay of one pixel: from its final transmittance T and gS = dL/dP . S, S the colour behind
 // the current entry (initially T_final bg), entry i with alpha = min(0.99, o G) recovers
@@ -35,9 +37,9 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 6 : 24) k_render_bwd(Layo
     constexpr int NT = B * B / 2;
     constexpr int NW = B * B / 64;
     constexpr int RS = 36;  // transpose row stride: 32 lanes + 4, conflict-free 16-byte row reads
-    __shared__ float4 s_e0[BATCH], s_e1[BATCH], s_e2[BATCH], s_e3[BATCH], s_cn[BATCH];
+    __shared__ float4 s_e0[BATCH], s_e1[BATCH], s_e2[BATCH], s_e3[BATCH];
+    __shared__ float4 s_cn[EXACT ? BATCH : 1];  // parity build: conic A', B', C' and opacity
     __shared__ uint32_t s_j[BATCH];
-    __shared__ float s_g[BATCH][9];
     __shared__ __align__(16) float s_red[NW][27][RS];
     __shared__ uint32_t s_maxnc;
     const int v = blockIdx.z;
@@ -106,9 +108,8 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 6 : 24) k_render_bwd(Layo
             s_e1[i] = se.e1;
             s_e2[i] = se.e2;
             s_e3[i] = se.e3;
-            s_cn[i] = make_float4(cb.x, cb.y, cb.z, a.z);
+            if (EXACT) s_cn[i] = make_float4(cb.x, cb.y, cb.z, a.z);
         }
-        for (int i = threadIdx.x; i < 9 * BATCH; i += NT) (&s_g[0][0])[i] = 0.0f;
         __syncthreads();
         const int kmax = (int)min((long long)nb, (long long)wmax - (bs - first));  // entries k < kmax
         // this warp's set bits of the batch, highest first, across its 32-entry chunks
@@ -134,8 +135,11 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 6 : 24) k_render_bwd(Layo
             const int k0 = next(), k1 = next(), k2 = next();
             const int ne = (k0 >= 0) + (k1 >= 0) + (k2 >= 0);
             if (ne == 0) break;
-#pragma unroll 1
-            for (int e = 0; e < ne; e++) {
+            // unrolled: the three entries' falloff and gradient arithmetic is independent apart
+            // from the per-pixel T and gS chain, so the scheduler can overlap it
+#pragma unroll
+            for (int e = 0; e < 3; e++) {
+                if (e >= ne) break;
                 const int k = e == 0 ? k0 : (e == 1 ? k1 : k2);
                 const float4 e0 = s_e0[k], e1 = s_e1[k], e2 = s_e2[k], e3 = s_e3[k];
                 const uint32_t lp = (uint32_t)(bs + k - first);
@@ -203,29 +207,9 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 6 : 24) k_render_bwd(Layo
                 const float tot = (acc.x + acc.y) + (acc.z + acc.w);
                 const int e = lane / 9, comp = lane - 9 * e;
                 const int k = e == 0 ? k0 : (e == 1 ? k1 : k2);
-                if (tot != 0.0f) atomicAdd(&s_g[k][comp], tot);
+                if (tot != 0.0f) atomicAdd(reinterpret_cast<float*>(L.gs) + 12 * (size_t)s_j[k] + comp, tot);
             }
             __syncwarp();
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < nb; i += NT) {
-            float* dst = reinterpret_cast<float*>(L.gs) + 12 * (size_t)s_j[i];
-            const float4 cn = s_cn[i];  // conic A', B', C' and opacity
-            const float o = cn.w;
-            const float mx = o * s_g[i][0], my = o * s_g[i][1];
-            float gsc[9];
-            gsc[0] = -(cn.x * mx + cn.y * my);  // dL/du
-            gsc[1] = -(cn.z * my + cn.y * mx);  // dL/dv
-            gsc[2] = -0.5f * o * s_g[i][2];     // dL/dA'
-            gsc[3] = -o * s_g[i][3];            // dL/dB'
-            gsc[4] = -0.5f * o * s_g[i][4];     // dL/dC'
-            gsc[5] = s_g[i][5];                 // dL/do
-            gsc[6] = -s_g[i][6];                // dL/d(r, g, b)
-            gsc[7] = -s_g[i][7];
-            gsc[8] = -s_g[i][8];
-#pragma unroll
-            for (int c = 0; c < 9; c++)
-                if (gsc[c] != 0.0f) atomicAdd(dst + c, gsc[c]);
         }
     }
     const uint32_t ws = __reduce_add_sync(0xffffffffu, pairs);
