@@ -29,7 +29,7 @@ namespace cgs {
 // T_before; then T = T_before and gS += alpha T_before (g . c).  The running sum is kept
 // negated (ngS = -gS) and alpha enters as -alpha, so no step negates anything.
 template <int B, int BATCH, bool EXACT>
-__global__ void __launch_bounds__(B * B / 2, B == 16 ? 6 : 24) k_render_bwd(Layout L, const uint32_t* __restrict__ tval, float bg0,
+__global__ void __launch_bounds__(B * B / 2, B == 16 ? 7 : 28) k_render_bwd(Layout L, const uint32_t* __restrict__ tval, float bg0,
                                                           float bg1, float bg2, const float* __restrict__ dL_dimg,
                                                           const float* __restrict__ final_T,
                                                           const uint32_t* __restrict__ n_contrib)
