@@ -195,16 +195,17 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 7 : 28) k_render_bwd(Layo
             __syncwarp();
             if (lane < 9 * ne) {
                 const float4* row = reinterpret_cast<const float4*>(red[lane]);
-                float4 acc = row[0];
+                // the row's 32 values as two packed pairs of running sums
+                const float4 r0 = row[0];
+                float2 ax = make_float2(r0.x, r0.y), az = make_float2(r0.z, r0.w);
 #pragma unroll
                 for (int q = 1; q < 8; q++) {
                     const float4 x = row[q];
-                    acc.x += x.x;
-                    acc.y += x.y;
-                    acc.z += x.z;
-                    acc.w += x.w;
+                    ax = __fadd2_rn(ax, make_float2(x.x, x.y));
+                    az = __fadd2_rn(az, make_float2(x.z, x.w));
                 }
-                const float tot = (acc.x + acc.y) + (acc.z + acc.w);
+                const float2 s2 = __fadd2_rn(ax, az);
+                const float tot = s2.x + s2.y;
                 const int e = lane / 9, comp = lane - 9 * e;
                 const int k = e == 0 ? k0 : (e == 1 ? k1 : k2);
                 if (tot != 0.0f) atomicAdd(reinterpret_cast<float*>(L.gs) + 12 * (size_t)s_j[k] + comp, tot);

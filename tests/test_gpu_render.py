@@ -126,7 +126,7 @@ def test_long_tile_lists_use_the_merge_path(n):
     assert lens.max() > 2048
 
 
-@pytest.mark.parametrize("n", [1, 31, 32, 33, 128, 129, 255, 256, 257, 512, 513, 2048, 2049, 4096, 4097])
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 64, 65, 128, 129, 255, 256, 257, 512, 513, 2048, 2049, 4096, 4097])
 def test_tile_lengths_at_sort_path_bounds(n):
     """One 16 x 16 tile holding every Gaussian: lengths on both sides of the ranking sort (128
     keys), the short-tile bitonic sort (256), the long-tile kernel's register bitonic sort (512)
