@@ -10,7 +10,11 @@
  *    pointers owned by the caller.  No entry point of this header allocates or frees
  *    device memory or keeps a pointer after it returns.
  *  - Every call only enqueues work on `stream` (a cudaStream_t; NULL = legacy default
- *    stream) and returns; only cgs_frame_status synchronizes.
+ *    stream) and returns; only cgs_frame_status synchronizes.  A forward runs its long-tile
+ *    sort on a side stream that the library keeps per host thread and device, forked from
+ *    `stream` after the entries are binned and joined back into it before compositing: the
+ *    work still starts after everything enqueued on `stream` before the call and ends before
+ *    anything enqueued after it, also under stream capture.
  *  - The return value is CGS_OK or the code of a failed host-side argument check or
  *    launch.  Conditions found on the device (capacity overflow, a bounded inter-block
  *    wait that gave up) are latched in the frame's device status word and reported by

@@ -273,7 +273,9 @@ static int32_t render_forward(const cgs_scene* scene, const cgs_frame* frame, co
     }
     {
         StageScope s(CGS_STAGE_SORT, st);
-        counted(launch_tile_sort(L, n_sm, st));
+        const int n = launch_tile_sort(L, n_sm, st);
+        if (n < 0) return CGS_ERR_CUDA;
+        counted(n);
     }
     {
         StageScope s(CGS_STAGE_RENDER, st);

@@ -7,7 +7,8 @@
 //                 (FP32 depth bits << 32 | selected index)
 //   tile sort     one CTA per tile: up to 128 keys ranked against each other in shared
 //                 memory (each key's count of smaller keys is its slot), up to 256 a bitonic
-//                 sort held in registers; longer tiles go to a second kernel: up to 512 keys the
+//                 sort held in registers; longer tiles (listed by the range scan) go to a
+//                 second kernel, run on a side stream beside the first: up to 512 keys the
 //                 register bitonic sort, up to 2048 a stable LSD radix sort in shared memory
 //                 over the 8-bit digits of the depth bits that differ within the tile, equal
 //                 depths then put in index order; beyond that sorted chunks of 2048 + merge
@@ -22,7 +23,11 @@
 
 namespace cgs {
 
-// [start, end) of every (view, tile) from the per-tile counts.
+constexpr int TS_THREADS = 128;
+constexpr int RANK_MAX = 2 * TS_THREADS;  // keys per tile sorted by the short-tile kernel
+
+// [start, end) of every (view, tile) from the per-tile counts; tiles longer than RANK_MAX are
+// listed for the long-tile kernel here, so that kernel can run beside the short-tile one.
 struct TileRangeOp {
     Layout L;
     __device__ long long count() const { return (long long)L.V * L.T; }
@@ -31,6 +36,7 @@ struct TileRangeOp {
     {
         L.ranges[2 * t] = (uint32_t)e;
         L.ranges[2 * t + 1] = (uint32_t)(e + x);
+        if (x > (uint32_t)RANK_MAX) L.big[atomicAdd(&L.hdr->n_big, 1u)] = (uint32_t)t;
     }
     __device__ void finish(unsigned long long total) const { (void)total; }
 };
@@ -46,8 +52,6 @@ __global__ void __launch_bounds__(256) k_scatter(Layout L)
         L.ekey[slot] = ((unsigned long long)(uint32_t)L.pkey[j] << 32) | j;
     }
 }
-
-constexpr int TS_THREADS = 128;
 
 // Ascending bitonic sort of np = THREADS * E keys held by the CTA in registers: warp w
 // holds keys [32 E w, 32 E (w + 1)), lane l's x[e] being key 32 E w + 32 e + l.  Exchanges
@@ -129,24 +133,19 @@ __device__ __forceinline__ void tile_sort_regs(const Layout& L, unsigned long lo
     }
 }
 
-constexpr int RANK_MAX = 2 * TS_THREADS;  // keys per tile sorted by this kernel
 constexpr int RANK_ONLY = TS_THREADS;     // up to this many keys by ranking, above by a bitonic sort
 
 // One CTA per (view, tile).  Up to RANK_ONLY keys: every thread ranks one key against all keys
 // of the tile in shared memory (keys are distinct, so the rank is the output slot; n^2
 // comparisons); up to RANK_MAX keys: a bitonic sort of 256 keys held two per thread (n log^2 n,
-// fewer operations above about 128 keys); longer tiles are listed for the long-tile kernel,
-// kept apart so the common short tiles run at full occupancy.
+// fewer operations above about 128 keys); longer tiles (listed by the range scan) are left to
+// the long-tile kernel, kept apart so the common short tiles run at full occupancy.
 __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(Layout L)
 {
     __shared__ unsigned long long s[RANK_MAX];
     const uint32_t t = blockIdx.x;
     const uint32_t st = L.ranges[2 * (size_t)t], n = L.ranges[2 * (size_t)t + 1] - st;
-    if (n == 0) return;
-    if (n > (uint32_t)RANK_MAX) {
-        if (threadIdx.x == 0) L.big[atomicAdd(&L.hdr->n_big, 1u)] = t;
-        return;
-    }
+    if (n == 0 || n > (uint32_t)RANK_MAX) return;  // longer tiles: listed by the range scan
     if (n > (uint32_t)RANK_ONLY) {
         tile_sort_regs<TS_THREADS, 2>(L, s, t, st, n);
         return;
@@ -382,17 +381,60 @@ int launch_bin(const Layout& L, int n_sm, cudaStream_t st)
     return 2;
 }
 
-// Per-tile sort (register, shared-memory and long-tile paths).
+// A second stream and two events, per host thread and device, on which the long-tile sort runs
+// beside the short-tile sort (fork after the scatter, join before the compositing).  Created on
+// first use outside a stream capture; until then the two kernels run one after the other.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    bool ok = false, tried = false;
+};
+
+static SideStream* side_stream(cudaStream_t st)
+{
+    constexpr int MAX_DEV = 64;
+    static thread_local SideStream side[MAX_DEV];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return nullptr;
+    SideStream& x = side[dev];
+    if (!x.tried) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+        x.tried = true;
+        // relaxed for this thread while creating, so a capture running on another thread's
+        // stream is not disturbed
+        cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+        cudaThreadExchangeStreamCaptureMode(&mode);
+        x.ok = cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking) == cudaSuccess &&
+               cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming) == cudaSuccess;
+        cudaThreadExchangeStreamCaptureMode(&mode);
+    }
+    return x.ok ? &x : nullptr;
+}
+
+// Per-tile sort (register, shared-memory and long-tile paths).  Returns the number of kernels
+// launched, or -1 if the fork or join of the side stream failed.
 int launch_tile_sort(const Layout& L, int n_sm, cudaStream_t st)
 {
     const long long vt = (long long)L.V * L.T;
-    static bool smem_set = false;  // the long-tile kernel's dynamic shared memory, set once
-    if (!smem_set) {
+    static bool smem_set[64] = {};  // the long-tile kernel's dynamic shared memory, set once per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !smem_set[dev]) {
         cudaFuncSetAttribute(k_tile_sort_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RX_SMEM);
-        smem_set = true;
+        smem_set[dev] = true;
+    }
+    SideStream* sd = side_stream(st);
+    if (sd && cudaEventRecord(sd->fork, st) == cudaSuccess && cudaStreamWaitEvent(sd->s, sd->fork, 0) == cudaSuccess) {
+        k_tile_sort_large<<<(unsigned)(5 * n_sm), RX_THREADS, RX_SMEM, sd->s>>>(L);  // five 40-KB CTAs fit an SM
+        k_tile_sort<<<(unsigned)vt, TS_THREADS, 0, st>>>(L);
+        if (cudaEventRecord(sd->join, sd->s) != cudaSuccess || cudaStreamWaitEvent(st, sd->join, 0) != cudaSuccess)
+            return -1;
+        return 2;
     }
     k_tile_sort<<<(unsigned)vt, TS_THREADS, 0, st>>>(L);
-    k_tile_sort_large<<<(unsigned)(5 * n_sm), RX_THREADS, RX_SMEM, st>>>(L);  // five 40-KB CTAs fit an SM
+    k_tile_sort_large<<<(unsigned)(5 * n_sm), RX_THREADS, RX_SMEM, st>>>(L);
     return 2;
 }
 
