@@ -91,17 +91,17 @@ __device__ __forceinline__ void prefetch_rows(const cgs_scene& S, long long g)
 //            (warp ballots and shuffles, then the warp totals in shared memory) and reserves a
 //            range of the visible list and of the entry buffer with one atomic add each; the
 //            whole CTA then emits the round's (tile << 32 | j) entries: thread t takes entries
-//            t, t + 256, ..., finds the owning Gaussian by a binary search over the round's
+//            t, t + 128, ..., finds the owning Gaussian by a binary search over the round's
 //            exclusive offsets in shared memory, and counts the tile.  A round of large
 //            Gaussians (hundreds of tiles each, near the camera) is spread over all warps.
 // The order of the visible list and of the entries depends on the order in which CTAs
 // reserve their ranges; nothing downstream depends on it (entries are sorted per tile by
 // (depth, index), the backward works per Gaussian).  DEG is the scene's SH degree.
-constexpr int PROJ_THREADS = 256;
+constexpr int PROJ_THREADS = 128;
 constexpr int PROJ_WARPS = PROJ_THREADS / 32;
 constexpr int PROJ_ITEMS = 2;  // selected Gaussians per thread in phase 1
 constexpr int PROJ_STEP = PROJ_THREADS * PROJ_ITEMS;
-constexpr int PROJ_CTAS_PER_SM = 5;  // latency-bound: registers capped so five CTAs fit an SM
+constexpr int PROJ_CTAS_PER_SM = 10;  // latency-bound: registers capped so ten CTAs fit an SM
 
 template <int DEG>
 __global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM)
