@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 7 : 28) k_render_bwd(Layo
     __shared__ float4 s_e0[BATCH], s_e1[BATCH], s_e2[BATCH], s_e3[BATCH];
     __shared__ float4 s_cn[EXACT ? BATCH : 1];  // parity build: conic A', B', C' and opacity
     __shared__ uint32_t s_j[BATCH];
+    __shared__ uint8_t s_pos[NW][BATCH];  // per warp: the batch positions it visits, highest first
     __shared__ __align__(16) float s_red[NW][27][RS];
     __shared__ uint32_t s_maxnc;
     const int v = blockIdx.z;
@@ -112,29 +113,31 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 7 : 28) k_render_bwd(Layo
         }
         __syncthreads();
         const int kmax = (int)min((long long)nb, (long long)wmax - (bs - first));  // entries k < kmax
-        // this warp's set bits of the batch, highest first, across its 32-entry chunks
-        int c0 = (kmax - 1) & ~31;
-        uint32_t bits = 0;
+        // this warp's set bits of the batch as a list of positions, highest first: lane c holds
+        // the contribution word of the batch's chunk c, and each chunk's set bits (taken highest
+        // first, one per lane) are placed by a ballot
+        uint8_t* pos = s_pos[warp];
+        int cnt = 0;
         if (kmax > 0) {
-            bits = cbits[(uint32_t)(bs - first + c0) >> 5];
-            const int avail = kmax - c0;
-            if (avail < 32) bits &= (1u << avail) - 1u;
-        }
-        // the next set bit of the batch's words, highest first (-1 when none is left)
-        auto next = [&]() -> int {
-            while (!bits && c0 > 0) {
-                c0 -= 32;
-                bits = cbits[(uint32_t)(bs - first + c0) >> 5];
+            const int nwords = (kmax + 31) >> 5;
+            uint32_t word = 0;
+            if (lane < nwords) {
+                word = cbits[(uint32_t)(bs - first) / 32u + (uint32_t)lane];
+                const int avail = kmax - 32 * lane;
+                if (avail < 32) word &= (1u << avail) - 1u;
             }
-            if (!bits) return -1;
-            const int hb = 31 - __clz(bits);
-            bits &= ~(1u << hb);
-            return c0 + hb;
-        };
-        while (true) {
-            const int k0 = next(), k1 = next(), k2 = next();
-            const int ne = (k0 >= 0) + (k1 >= 0) + (k2 >= 0);
-            if (ne == 0) break;
+            for (int c = nwords - 1; c >= 0; c--) {
+                const uint32_t bits = __shfl_sync(0xffffffffu, word, c);
+                const bool set = ((bits >> (31 - lane)) & 1u) != 0u;
+                const uint32_t ball = __ballot_sync(0xffffffffu, set);
+                if (set) pos[cnt + __popc(ball & lanemask_lt())] = (uint8_t)(32 * c + 31 - lane);
+                cnt += __popc(ball);
+            }
+            __syncwarp();
+        }
+        for (int gi = 0; gi < cnt; gi += 3) {
+            const int ne = min(3, cnt - gi);
+            const int k0 = pos[gi], k1 = ne > 1 ? (int)pos[gi + 1] : -1, k2 = ne > 2 ? (int)pos[gi + 2] : -1;
             // unrolled: the three entries' falloff and gradient arithmetic is independent apart
             // from the per-pixel T and gS chain, so the scheduler can overlap it
 #pragma unroll
