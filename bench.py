@@ -68,8 +68,7 @@ OPS_BWD_GRAD = 28
 # batch 128, from one ncu capture of the current build (the summary committed beside the kernel
 # profiles: DRAM bytes per second times the launch's duration); a kernel absent here reports
 # traffic null.  An entry is removed when its kernel changes.
-NCU_TRAFFIC_BYTES = {"render": 15.401e6, "render_bwd": 67.030e6, "project": 74.186e6, "project_bwd": 72.990e6,
-                     "loss": 31.151e6}
+NCU_TRAFFIC_BYTES = {"render": 15.401e6, "project": 74.186e6, "project_bwd": 72.990e6}
 
 
 def parse_args():
@@ -253,10 +252,12 @@ def device_peaks(dev, index):
             "sm_count": sm, "nominal_fp32_tops": sm * 128 * mhz * 1e6 / 1e12, "clocks_during_peaks": c}
 
 
-def stage_work(counts, sum_nc, n_tiles, pixels, deg, backward=False, loss_bytes=9, packed=True):
+def stage_work(counts, sum_nc, n_tiles, pixels, deg, backward=False, loss_bytes=None, packed=True):
     """Algorithmic work per launch of every stage of a frame: (bound, amount), HBM bytes or
     FP32 operations.  counts: the frame counters (selected, visible, entries, evaluated
-    pairs, contributing pairs); sum_nc: the sum of n_contrib over the frame's pixels."""
+    pairs, contributing pairs); sum_nc: the sum of n_contrib over the frame's pixels.
+    loss_bytes None: the L1 loss runs inside the compositing backward (its image and target
+    reads overlap that kernel's arithmetic and get no term of their own)."""
     n_sel, n_vis, k, pf, pb = (int(x) for x in counts[:5])
     nco = (deg + 1) ** 2
     w = {
@@ -279,8 +280,10 @@ def stage_work(counts, sum_nc, n_tiles, pixels, deg, backward=False, loss_bytes=
         # form) and clear the screen-space gradients
         w["project_bwd"] = ("hbm", n_vis * ((4 + 8 + 4 + 48 + 16 + 16 + 16 + 12 * nco) +
                                             (16 + 16 + 16 + 12 * nco + (8 if packed else 0) + 48)))
-        # L1: image read (4 B), target read (1 B 8-bit, 4 B FP32), gradient written (4 B)
-        w["loss"] = ("hbm", pixels * 3 * loss_bytes)
+        # a separate L1 kernel: image read (4 B), target read (1 B 8-bit, 4 B FP32), gradient
+        # written (4 B)
+        if loss_bytes is not None:
+            w["loss"] = ("hbm", pixels * 3 * loss_bytes)
     return w
 
 
@@ -355,7 +358,6 @@ def run_ours(args, world, rank, local):
     frame = ta.Frame(1, W, H, args.tile, 1, n, 8_000_000, dev)
     img, T, nc = frame.outputs()
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
-    dL = torch.empty_like(img)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     st = torch.cuda.current_stream(dev)
     s_struct = ds.struct()
@@ -375,8 +377,7 @@ def run_ours(args, world, rank, local):
         cur = torch.cuda.current_stream().cuda_stream
         cgs.cgs_render_forward(s_struct, frame.struct, cfg, cam_buf, None, None, img, T, nc, cur)
         loss.zero_()
-        cgs.cgs_l1_loss_u8(img, tgt_buf, img.numel(), loss, dL, cur)
-        cgs.cgs_render_backward_packed(s_struct, frame.struct, cfg, cam_buf, dL, T, nc, *rows, cur)
+        cgs.cgs_render_backward_l1(s_struct, frame.struct, cfg, cam_buf, img, tgt_buf, 1, T, nc, loss, *rows, cur)
 
     def step(fwd_only=False):
         # the current stream at call time (the capture stream while a CUDA graph is recorded)
@@ -385,16 +386,14 @@ def run_ours(args, world, rank, local):
         if fwd_only:
             return
         loss.zero_()
-        cgs.cgs_l1_loss_u8(img, tgt, img.numel(), loss, dL, cur)
-        cgs.cgs_render_backward_packed(s_struct, frame.struct, cfg, d_cams, dL, T, nc, *rows, cur)
+        cgs.cgs_render_backward_l1(s_struct, frame.struct, cfg, d_cams, img, tgt, 1, T, nc, loss, *rows, cur)
 
     def step_f32_target():
         # the same step with an FP32 target image (U[0,1]), 4 bytes per target value
         cur = torch.cuda.current_stream().cuda_stream
         cgs.cgs_render_forward(s_struct, frame.struct, cfg, d_cams, None, None, img, T, nc, cur)
         loss.zero_()
-        cgs.cgs_l1_loss(img, tgt_f32, img.numel(), loss, dL, cur)
-        cgs.cgs_render_backward_packed(s_struct, frame.struct, cfg, d_cams, dL, T, nc, *rows, cur)
+        cgs.cgs_render_backward_l1(s_struct, frame.struct, cfg, d_cams, img, tgt_f32, 0, T, nc, loss, *rows, cur)
 
     def step_dense():
         # the scene-indexed form: gradients added into arrays laid out like the scene, which
@@ -403,8 +402,7 @@ def run_ours(args, world, rank, local):
         grad_flat.zero_()
         cgs.cgs_render_forward(s_struct, frame.struct, cfg, d_cams, None, None, img, T, nc, cur)
         loss.zero_()
-        cgs.cgs_l1_loss_u8(img, tgt, img.numel(), loss, dL, cur)
-        cgs.cgs_render_backward(s_struct, frame.struct, cfg, d_cams, dL, T, nc, *grads, cur)
+        cgs.cgs_render_backward_l1(s_struct, frame.struct, cfg, d_cams, img, tgt, 1, T, nc, loss, *grads, None, cur)
 
     for _ in range(args.warmup):
         step()
@@ -459,7 +457,7 @@ def run_ours(args, world, rank, local):
     fwd_value = whole_job_mpix_s(world, pix, fwd_ms)
     n_sel, n_vis, k_ent, pairs_f, pairs_b = counts[:5]
     n_tiles = ((W + args.tile - 1) // args.tile) * ((H + args.tile - 1) // args.tile)
-    work = stage_work(counts, sum_nc, n_tiles, pix, sc["sh_degree"], backward=True, loss_bytes=9)
+    work = stage_work(counts, sum_nc, n_tiles, pix, sc["sh_degree"], backward=True)
     fwd_keys = ("project", "duplicate", "sort", "render")
     i_ms = ideal_ms(work, peaks)
     i_fwd = ideal_ms(work, peaks, fwd_keys)
@@ -480,7 +478,8 @@ def run_ours(args, world, rank, local):
                    "l2": "flushed between timed steps (256 MB write)",
                    "gradients": "packed rows per visible Gaussian, written in full by every step; the loss "
                                 "accumulator cleared inside the step; nothing cleared between steps",
-                   "target": "8-bit RGB image, channel t stands for t/255"},
+                   "target": "8-bit RGB image, channel t stands for t/255",
+                   "loss": "L1, mean |img - target|, formed inside the compositing backward (cgs_render_backward_l1)"},
         "fwd_mpix_s": fwd_value, "fwd_ms": fwd_ms, "fps_fwd_bwd": 1e3 / step_ms, "fps_fwd": 1e3 / fwd_ms,
         "gaussians_per_s": world * n / (step_ms * 1e-3),
         "stage_ms": {k_: round(v, 4) for k_, v in stage_ms.items()},
@@ -544,7 +543,6 @@ def run_batched_compare(args, ds, sc, cfg, st, flush, world, synth, ta, cgs):
     d_cams = ta.cameras_device(cams)
     img, T, nc = frame.outputs()
     tgt = torch.rand((V, 3, H, W), device=ds.device)
-    dL = torch.empty_like(img)
     loss = torch.zeros(1, device=ds.device)
     s_struct = ds.struct()
 
@@ -561,22 +559,20 @@ def run_batched_compare(args, ds, sc, cfg, st, flush, world, synth, ta, cgs):
         cur = torch.cuda.current_stream().cuda_stream
         cgs.cgs_render_forward(s_struct, frame.struct, cfg, d_cams, None, None, img, T, nc, cur)
         loss.zero_()
-        cgs.cgs_l1_loss(img, tgt, img.numel(), loss, dL, cur)
-        cgs.cgs_render_backward_packed(s_struct, frame.struct, cfg, d_cams, dL, T, nc, *rows, cur)
+        cgs.cgs_render_backward_l1(s_struct, frame.struct, cfg, d_cams, img, tgt, 0, T, nc, loss, *rows, cur)
 
     f1 = ta.Frame(1, W, H, cfg.tile, ds.n_blocks, max(sel) + 1024, min((1 << 30) - 1, max(ent) * 2 + 65536))
     d1 = [ta.cameras_device([c]) for c in cams]
     i1, T1, n1 = f1.outputs()
-    dL1 = torch.empty_like(i1)
     rows1 = [packed_rows(f1.n_cap) for _ in range(V)]  # one set of rows per view, as the batched frame has
+    tgt_v = [tgt[v:v + 1].contiguous() for v in range(V)]
 
     def sequential():
         cur = torch.cuda.current_stream().cuda_stream
         loss.zero_()
         for v in range(V):
             cgs.cgs_render_forward(s_struct, f1.struct, cfg, d1[v], None, None, i1, T1, n1, cur)
-            cgs.cgs_l1_loss(i1, tgt[v:v + 1].contiguous(), i1.numel(), loss, dL1, cur)
-            cgs.cgs_render_backward_packed(s_struct, f1.struct, cfg, d1[v], dL1, T1, n1, *rows1[v], cur)
+            cgs.cgs_render_backward_l1(s_struct, f1.struct, cfg, d1[v], i1, tgt_v[v], 0, T1, n1, loss, *rows1[v], cur)
     g_b = ta.capture(batched, warmup=1)
     g_s = ta.capture(sequential, warmup=1)
     k = max(3, args.steps // 2)
@@ -602,7 +598,6 @@ def run_fp16_compare(args, sc, cfg, d_cams, tgt, ds32, st, flush, world, ta, cgs
     for name, ds in (("fp32", ds32), ("fp16", ds16)):
         frame = ta.Frame(1, W, H, cfg.tile, 1, ds.n, 8_000_000, ds.device)
         img, T, nc = frame.outputs()
-        dL = torch.empty_like(img)
         loss = torch.zeros(1, device=ds.device)
         f32, cap = torch.float32, ds.n
         rows = (torch.empty((cap, 4), dtype=f32, device=ds.device), torch.empty((cap, 4), dtype=f32, device=ds.device),
@@ -615,8 +610,7 @@ def run_fp16_compare(args, sc, cfg, d_cams, tgt, ds32, st, flush, world, ta, cgs
             cur = torch.cuda.current_stream().cuda_stream
             cgs.cgs_render_forward(s_struct, frame.struct, cfg, d_cams, None, None, img, T, nc, cur)
             loss.zero_()
-            cgs.cgs_l1_loss_u8(img, tgt, img.numel(), loss, dL, cur)
-            cgs.cgs_render_backward_packed(s_struct, frame.struct, cfg, d_cams, dL, T, nc, *rows, cur)
+            cgs.cgs_render_backward_l1(s_struct, frame.struct, cfg, d_cams, img, tgt, 1, T, nc, loss, *rows, cur)
 
         for _ in range(2):
             one()
@@ -1111,17 +1105,15 @@ def run_train32(args, world, rank, local, peaks, launches_acc):
         fr = ta.Frame(len(views), W, H, tile, ds.n_blocks, n_cap, min((1 << 30) - 1, k_cap))
         img, T, nc = fr.outputs()
         tgt = torch.rand_like(img)
-        parts.append((fr, ta.cameras_device([cams[v] for v in views]), vb_dev[views].contiguous(), img, T, nc, tgt,
-                      torch.empty_like(img)))
+        parts.append((fr, ta.cameras_device([cams[v] for v in views]), vb_dev[views].contiguous(), img, T, nc, tgt))
 
     def batched_all():
         cur = torch.cuda.current_stream().cuda_stream
         s_struct = ds.struct()
         clear()
-        for fr, dc, vbd, img, T, nc, tgt, dL in parts:
+        for fr, dc, vbd, img, T, nc, tgt in parts:
             cgs.cgs_render_forward(s_struct, fr.struct, cfg, dc, vbd, None, img, T, nc, cur)
-            cgs.cgs_l1_loss(img, tgt, img.numel(), loss, dL, cur)
-            cgs.cgs_render_backward(s_struct, fr.struct, cfg, dc, dL, T, nc, *grads, cur)
+            cgs.cgs_render_backward_l1(s_struct, fr.struct, cfg, dc, img, tgt, 0, T, nc, loss, *grads, None, cur)
     clocks = ClockSampler(local).start()
     ms_b, l_b = _graph_ms(batched_all, max(2, args.steps // 4), flush, world)
     clk = clocks.stop()
@@ -1139,7 +1131,7 @@ def run_train32(args, world, rank, local, peaks, launches_acc):
         sum_nc += int(p[5].to(torch.int64).sum().item())
     V = len(cams)
     n_tiles = ((W + tile - 1) // tile) * ((H + tile - 1) // tile) * V
-    work = stage_work(counts, sum_nc, n_tiles, W * H * V, sc["sh_degree"], backward=True, loss_bytes=12,
+    work = stage_work(counts, sum_nc, n_tiles, W * H * V, sc["sh_degree"], backward=True,
                       packed=False)
     dom = max(work, key=lambda k_: per_step_stage.get(k_, 0.0))
     roof = roofline(dom, per_step_stage, work, peaks, KERNEL_NAMES[dom])
@@ -1150,7 +1142,6 @@ def run_train32(args, world, rank, local, peaks, launches_acc):
                   min((1 << 30) - 1, int(max(ent) * 1.05) + 65536))
     i1, T1, n1 = f1.outputs()
     t1 = torch.rand_like(i1)
-    dL1 = torch.empty_like(i1)
     d1 = [ta.cameras_device([c]) for c in cams]
 
     def seq_all():
@@ -1159,8 +1150,7 @@ def run_train32(args, world, rank, local, peaks, launches_acc):
         clear()
         for v in range(len(cams)):
             cgs.cgs_render_forward(s_struct, f1.struct, cfg, d1[v], vb_dev[v:v + 1], None, i1, T1, n1, cur)
-            cgs.cgs_l1_loss(i1, t1, i1.numel(), loss, dL1, cur)
-            cgs.cgs_render_backward(s_struct, f1.struct, cfg, d1[v], dL1, T1, n1, *grads, cur)
+            cgs.cgs_render_backward_l1(s_struct, f1.struct, cfg, d1[v], i1, t1, 0, T1, n1, loss, *grads, None, cur)
     ms_s, l_s = _graph_ms(seq_all, max(2, args.steps // 4), flush, world)
     launches_acc[0] += l_s
     t_s = max_over_ranks(sum(ms_s) / len(ms_s), world)

@@ -216,6 +216,23 @@ int32_t cgs_render_backward_packed(const cgs_scene* scene, const cgs_frame* fram
                                    const uint32_t* d_n_contrib, float* d_g_mean_opac, float* d_g_scale,
                                    float* d_g_quat, float* d_g_sh, int64_t* d_g_index, void* stream);
 
+/* The L1 loss and the backward in one pass (Sec. 3.2.3's L1 term, Sec. 3.1's differentiable
+ * rendering): equivalent to cgs_l1_loss (target_u8 = 0: d_target is float) or cgs_l1_loss_u8
+ * (target_u8 = 1: d_target is uint8_t, t standing for t / 255) over the frame's whole image,
+ * count = n_views * 3 * height * width, followed by cgs_render_backward (d_g_index = NULL:
+ * gradients ADDED into scene-indexed arrays) or cgs_render_backward_packed (d_g_index != NULL:
+ * rows WRITTEN), without the gradient image: the compositing backward forms each pixel's
+ * dL/dimage = sign(img - target) / count from d_image (the forward's output, [n_views][3][H][W])
+ * and d_target (same layout) where it reads it.  ADDS mean |img - target| into *d_loss (atomic
+ * adds, so the summation order is not fixed).  The per-pixel gradient equals cgs_l1_loss's bit
+ * for bit.  CGS_ERR_UNSUPPORTED for the parity configuration (cfg->exact); other errors as
+ * cgs_render_backward. */
+int32_t cgs_render_backward_l1(const cgs_scene* scene, const cgs_frame* frame, const cgs_config* cfg,
+                               const cgs_camera* d_cams, const float* d_image, const void* d_target,
+                               int32_t target_u8, const float* d_final_T, const uint32_t* d_n_contrib,
+                               float* d_loss, float* d_g_mean_opac, float* d_g_scale, float* d_g_quat,
+                               float* d_g_sh, int64_t* d_g_index, void* stream);
+
 /* L1 photometric loss (the L1 term of the training loss, Sec. 3.2.3) over `count` values:
  * ADDS mean|img - target| into *d_loss and writes d_grad = sign(img - target) / count
  * (sign(0) = 0). */

@@ -91,6 +91,9 @@ def lib():
         L.cgs_render_backward_packed.restype = i32
         L.cgs_render_backward_packed.argtypes = [P(cgs_scene), P(cgs_frame), P(cgs_config), vp, vp, vp, vp, vp, vp,
                                                  vp, vp, vp, vp]
+        L.cgs_render_backward_l1.restype = i32
+        L.cgs_render_backward_l1.argtypes = [P(cgs_scene), P(cgs_frame), P(cgs_config), vp, vp, vp, i32, vp, vp, vp,
+                                             vp, vp, vp, vp, vp, vp]
         L.cgs_l1_loss.restype = i32
         L.cgs_l1_loss.argtypes = [vp, vp, i64, vp, vp, vp]
         L.cgs_l1_loss_u8.restype = i32
@@ -237,6 +240,15 @@ def cgs_render_backward_packed(scene, frame, cfg, d_cams, d_dL_dimage, d_final_T
                                                    _ptr(d_g_mean_opac), _ptr(d_g_scale), _ptr(d_g_quat),
                                                    _ptr(d_g_sh), _ptr(d_g_index), _stream(stream)),
                   "cgs_render_backward_packed")
+
+
+def cgs_render_backward_l1(scene, frame, cfg, d_cams, d_image, d_target, target_u8, d_final_T, d_n_contrib,
+                           d_loss, d_g_mean_opac, d_g_scale, d_g_quat, d_g_sh, d_g_index=None, stream=None):
+    return _check(lib().cgs_render_backward_l1(C.byref(scene), C.byref(frame), C.byref(cfg), _ptr(d_cams),
+                                               _ptr(d_image), _ptr(d_target), int(target_u8), _ptr(d_final_T),
+                                               _ptr(d_n_contrib), _ptr(d_loss), _ptr(d_g_mean_opac),
+                                               _ptr(d_g_scale), _ptr(d_g_quat), _ptr(d_g_sh), _ptr(d_g_index),
+                                               _stream(stream)), "cgs_render_backward_l1")
 
 
 def cgs_l1_loss(d_img, d_target, count, d_loss, d_grad, stream=None):

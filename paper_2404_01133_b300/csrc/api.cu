@@ -17,7 +17,7 @@ int launch_bin(const Layout& L, int n_sm, cudaStream_t st);
 int launch_tile_sort(const Layout& L, int n_sm, cudaStream_t st);
 bool launch_render_fwd(const Layout& L, const cgs_config& c, float* img, float* T, uint32_t* nc, cudaStream_t st);
 bool launch_render_bwd(const Layout& L, const cgs_config& c, const float* dimg, const float* T, const uint32_t* nc,
-                       cudaStream_t st);
+                       const L1In* l1, cudaStream_t st);
 void launch_project_bwd(const Layout& L, const cgs_scene& S, const cgs_camera* cams, float near_z, float* g_mo,
                         float* g_sc, float* g_q, float* g_sh, long long* g_index, int n_sm, cudaStream_t st);
 void launch_l1(const float* img, const float* tgt, long long n, float* loss, float* grad, int n_sm, cudaStream_t st);
@@ -99,7 +99,6 @@ static bool make_layout(const cgs_frame* f, Layout* L, size_t* bytes)
     l.hdr = c.take<Header>(1);
     l.scan_lb = c.take<unsigned long long>(scan_tiles_vt);
     l.tcnt = c.take<uint32_t>(vt);
-    l.tcur = c.take<uint32_t>(vt);
     l.sel_done = c.take<uint32_t>(l.V);
     l.zero_bytes = c.off;
     l.ranges = c.take<uint32_t>(2 * vt);
@@ -303,23 +302,26 @@ int32_t cgs_render_forward_hits(const cgs_scene* scene, const cgs_frame* frame, 
                           d_hits, stream);
 }
 
+// l1 == NULL: dL/dimage from d_dL_dimage; else the fused L1 loss (d_dL_dimage unused).
 static int32_t render_backward(const cgs_scene* scene, const cgs_frame* frame, const cgs_config* cfg,
                                const cgs_camera* d_cams, const float* d_dL_dimage, const float* d_final_T,
                                const uint32_t* d_n_contrib, float* d_g_mean_opac, float* d_g_scale, float* d_g_quat,
-                               float* d_g_sh, int64_t* d_g_index, void* stream)
+                               float* d_g_sh, int64_t* d_g_index, const L1In* l1, void* stream)
 {
     Layout L;
     size_t bytes = 0;
     if (!make_layout(frame, &L, &bytes) || !frame->ws) return CGS_ERR_INVALID_ARGUMENT;
     if ((size_t)frame->ws_bytes < bytes) return CGS_ERR_WORKSPACE_TOO_SMALL;
     if (!scene_ok(scene) || scene->n_blocks != frame->n_blocks || !config_ok(cfg, frame->tile) || !d_cams ||
-        !d_dL_dimage || !d_final_T || !d_n_contrib || !d_g_mean_opac || !d_g_scale || !d_g_quat || !d_g_sh)
+        (!l1 && !d_dL_dimage) || !d_final_T || !d_n_contrib || !d_g_mean_opac || !d_g_scale || !d_g_quat ||
+        !d_g_sh)
         return CGS_ERR_INVALID_ARGUMENT;
+    if (l1 && cfg->exact) return CGS_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     const int n_sm = sm_count();
     {
         StageScope s(CGS_STAGE_RENDER_BWD, st);
-        if (!launch_render_bwd(L, *cfg, d_dL_dimage, d_final_T, d_n_contrib, st)) return CGS_ERR_UNSUPPORTED;
+        if (!launch_render_bwd(L, *cfg, d_dL_dimage, d_final_T, d_n_contrib, l1, st)) return CGS_ERR_UNSUPPORTED;
         counted(1);
     }
     {
@@ -337,7 +339,7 @@ int32_t cgs_render_backward(const cgs_scene* scene, const cgs_frame* frame, cons
                             float* d_g_sh, void* stream)
 {
     return render_backward(scene, frame, cfg, d_cams, d_dL_dimage, d_final_T, d_n_contrib, d_g_mean_opac, d_g_scale,
-                           d_g_quat, d_g_sh, nullptr, stream);
+                           d_g_quat, d_g_sh, nullptr, nullptr, stream);
 }
 
 int32_t cgs_render_backward_packed(const cgs_scene* scene, const cgs_frame* frame, const cgs_config* cfg,
@@ -347,7 +349,27 @@ int32_t cgs_render_backward_packed(const cgs_scene* scene, const cgs_frame* fram
 {
     if (!d_g_index) return CGS_ERR_INVALID_ARGUMENT;
     return render_backward(scene, frame, cfg, d_cams, d_dL_dimage, d_final_T, d_n_contrib, d_g_mean_opac, d_g_scale,
-                           d_g_quat, d_g_sh, d_g_index, stream);
+                           d_g_quat, d_g_sh, d_g_index, nullptr, stream);
+}
+
+int32_t cgs_render_backward_l1(const cgs_scene* scene, const cgs_frame* frame, const cgs_config* cfg,
+                               const cgs_camera* d_cams, const float* d_image, const void* d_target,
+                               int32_t target_u8, const float* d_final_T, const uint32_t* d_n_contrib,
+                               float* d_loss, float* d_g_mean_opac, float* d_g_scale, float* d_g_quat,
+                               float* d_g_sh, int64_t* d_g_index, void* stream)
+{
+    if (!frame || !d_image || !d_target || !d_loss || (target_u8 != 0 && target_u8 != 1) || frame->n_views < 1 ||
+        frame->width < 1 || frame->height < 1)
+        return CGS_ERR_INVALID_ARGUMENT;
+    const long long count = 3LL * frame->n_views * frame->width * frame->height;
+    L1In l1;
+    l1.img = d_image;
+    l1.tgt = d_target;
+    l1.loss = d_loss;
+    l1.inv = 1.0f / (float)count;  // the FP32 quotient cgs_l1_loss forms on the device
+    l1.u8 = target_u8;
+    return render_backward(scene, frame, cfg, d_cams, nullptr, d_final_T, d_n_contrib, d_g_mean_opac, d_g_scale,
+                           d_g_quat, d_g_sh, d_g_index, &l1, stream);
 }
 
 int32_t cgs_l1_loss(const float* d_img, const float* d_target, int64_t count, float* d_loss, float* d_grad,

@@ -46,7 +46,6 @@ struct Layout {
     unsigned long long* scan_lb; // [scan tiles of V*T] look-back words of the tile-range scan
     uint32_t* tcnt;              // [V * T] entries per tile
     uint32_t* sel_done;          // [V] CTAs of the view that finished the selection's first phase
-    uint32_t* tcur;              // [V * T] scatter cursors
     // not zeroed
     uint32_t* ranges;            // [V * T][2] [start, end) of every tile's entries
     uint32_t* view_base;         // [V + 1] exclusive prefix of per-view selected counts
@@ -67,7 +66,8 @@ struct Layout {
     unsigned long long* eraw;    // [k_cap] tile << 32 | j per entry; later scratch of the long-tile sort
     unsigned long long* ekey;    // [k_cap] depth bits << 32 | j, scattered into tile ranges
     uint32_t* tval;              // [k_cap] selected index per entry, (tile, depth, index) order
-    uint32_t* tkey;              // [k_cap] tile id per entry, same order
+    uint32_t* tkey;              // [k_cap] tile id per entry, same order; before the sort, the
+                                 // entry's rank within its tile (projection -> scatter)
     uint32_t* big;               // [V * T] tiles for the long-tile sort
     float4* gs;                  // [n_cap][3] screen-space gradients (du dv dA dB | dC do dr dg | db - - -)
     uint32_t* hits;              // optional [scene n]: pixels blending each scene Gaussian (added to)
@@ -76,6 +76,18 @@ struct Layout {
     size_t zero_bytes;           // bytes to clear from hdr
     long long n_cap, k_cap;
     int V, W, H, B, tiles_x, tiles_y, T, NB;
+};
+
+// The L1 photometric loss (Sec. 3.2.3) folded into the compositing backward: each pixel's
+// dL/dimage = sign(img - target) / count comes from the rendered image and the target where the
+// backward reads it, so no gradient image is written or read, and mean |img - target| is added
+// to *loss (one atomic add per CTA).  inv = 1 / count as the FP32 quotient 1.0f / (float)count.
+struct L1In {
+    const float* img;  // rendered image [V][3][H][W]
+    const void* tgt;   // target, same layout: float, or uint8_t channel t standing for t / 255
+    float* loss;
+    float inv;
+    int u8;            // target element type: 1 = uint8_t, 0 = float
 };
 
 // ---------------------------------------------------------------------------------------

@@ -7,6 +7,35 @@
 
 namespace cgs {
 
+// A target value of the fused L1 loss, as stored: FP32 (LOSS = 2), or the 8-bit channel value
+// (LOSS = 1) mapped through the shared t / 255 table later.
+template <int LOSS>
+__device__ __forceinline__ float l1_target(const void* tgt, size_t i)
+{
+    if constexpr (LOSS == 1) return (float)static_cast<const uint8_t*>(tgt)[i];
+    else return static_cast<const float*>(tgt)[i];
+}
+
+// *g holds the image value on entry and the L1 gradient sign(img - target) inv on return
+// (0 where they are equal or either is NaN); returns |img - target|.  Explicit IEEE subtract
+// and non-flushing compares, as in cgs_l1_loss.
+template <int LOSS>
+__device__ __forceinline__ float l1_grad(float* g, float t, const float* tab, float inv)
+{
+    const float tv = LOSS == 1 ? tab[(int)t] : t;
+    const float d = ieee_sub(*g, tv);
+    float r;
+    asm("{\n\t.reg .pred gt, lt;\n\t"
+        "setp.gt.f32 gt, %1, 0f00000000;\n\t"
+        "setp.lt.f32 lt, %1, 0f00000000;\n\t"
+        "selp.f32 %0, %2, 0f00000000, gt;\n\t"
+        "@lt mov.f32 %0, %3;\n\t}"
+        : "=f"(r)
+        : "f"(d), "f"(inv), "f"(-inv));
+    *g = r;
+    return fabsf(d);
+}
+
 // Backward.  A warp visits exactly the entries that blended into at least one of its pixels
 // in the forward (the forward's contribution bits), last first.  Per entry, a lane replays its
 // two pixels as packed pairs and reduces them to nine values:
@@ -28,11 +57,17 @@ namespace cgs {
 // T_before = T / (1 - alpha); dL/dalpha = (T (g . c) - gS) / (1 - alpha), dL/dc = g alpha
 // T_before; then T = T_before and gS += alpha T_before (g . c).  The running sum is kept
 // negated (ngS = -gS) and alpha enters as -alpha, so no step negates anything.
-template <int B, int BATCH, bool EXACT>
+//
+// LOSS = 0: dL/dimage is read from dL_dimg.  LOSS = 1 (8-bit target) or 2 (FP32 target): it is
+// the L1 gradient sign(img - target) / count (L1In), formed here from l1.img and l1.tgt, and the
+// CTA's share of mean |img - target| goes to *l1.loss; dL_dimg is not read.  The difference and
+// both sign tests are explicit IEEE instructions, so this file's flush-to-zero leaves the
+// gradient bit-identical to cgs_l1_loss's.
+template <int B, int BATCH, bool EXACT, int LOSS>
 __global__ void __launch_bounds__(B * B / 2, B == 16 ? 7 : 28) k_render_bwd(Layout L, const uint32_t* __restrict__ tval, float bg0,
                                                           float bg1, float bg2, const float* __restrict__ dL_dimg,
                                                           const float* __restrict__ final_T,
-                                                          const uint32_t* __restrict__ n_contrib)
+                                                          const uint32_t* __restrict__ n_contrib, L1In l1)
 {
     constexpr int NT = B * B / 2;
     constexpr int NW = B * B / 64;
@@ -43,6 +78,8 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 7 : 28) k_render_bwd(Layo
     __shared__ uint8_t s_pos[NW][BATCH];  // per warp: the batch positions it visits, highest first
     __shared__ __align__(16) float s_red[NW][27][RS];
     __shared__ uint32_t s_maxnc;
+    __shared__ float s_tab[LOSS == 1 ? 256 : 1];  // t / 255 for an 8-bit target, correctly rounded
+    __shared__ float s_lw[LOSS ? NW : 1];         // per-warp sums of |img - target|
     const int v = blockIdx.z;
     const int tile = blockIdx.y * L.tiles_x + blockIdx.x;
     const uint2 rg = reinterpret_cast<const uint2*>(L.ranges)[(size_t)v * L.T + tile];
@@ -58,29 +95,70 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 7 : 28) k_render_bwd(Layo
     const size_t HW = (size_t)L.W * L.H;
     float2 T = make_float2(1.0f, 1.0f), g0 = make_float2(0.0f, 0.0f), g1 = g0, g2 = g0;
     uint32_t nc0 = 0, nc1 = 0;
+    // with LOSS: the image values in g*, the target values (raw) in t*, turned into the
+    // gradient after the first barrier (the 8-bit table is built before it)
+    float2 t0 = g0, t1 = g0, t2 = g0;
     if (in0) {
         const size_t pix = (size_t)py0 * L.W + px;
         T.x = final_T[(size_t)v * HW + pix];
         nc0 = n_contrib[(size_t)v * HW + pix];
-        g0.x = dL_dimg[(3 * (size_t)v + 0) * HW + pix];
-        g1.x = dL_dimg[(3 * (size_t)v + 1) * HW + pix];
-        g2.x = dL_dimg[(3 * (size_t)v + 2) * HW + pix];
+        const float* src = LOSS ? l1.img : dL_dimg;
+        g0.x = src[(3 * (size_t)v + 0) * HW + pix];
+        g1.x = src[(3 * (size_t)v + 1) * HW + pix];
+        g2.x = src[(3 * (size_t)v + 2) * HW + pix];
+        if constexpr (LOSS) {
+            t0.x = l1_target<LOSS>(l1.tgt, (3 * (size_t)v + 0) * HW + pix);
+            t1.x = l1_target<LOSS>(l1.tgt, (3 * (size_t)v + 1) * HW + pix);
+            t2.x = l1_target<LOSS>(l1.tgt, (3 * (size_t)v + 2) * HW + pix);
+        }
     }
     if (in1) {
         const size_t pix = (size_t)py1 * L.W + px;
         T.y = final_T[(size_t)v * HW + pix];
         nc1 = n_contrib[(size_t)v * HW + pix];
-        g0.y = dL_dimg[(3 * (size_t)v + 0) * HW + pix];
-        g1.y = dL_dimg[(3 * (size_t)v + 1) * HW + pix];
-        g2.y = dL_dimg[(3 * (size_t)v + 2) * HW + pix];
+        const float* src = LOSS ? l1.img : dL_dimg;
+        g0.y = src[(3 * (size_t)v + 0) * HW + pix];
+        g1.y = src[(3 * (size_t)v + 1) * HW + pix];
+        g2.y = src[(3 * (size_t)v + 2) * HW + pix];
+        if constexpr (LOSS) {
+            t0.y = l1_target<LOSS>(l1.tgt, (3 * (size_t)v + 0) * HW + pix);
+            t1.y = l1_target<LOSS>(l1.tgt, (3 * (size_t)v + 1) * HW + pix);
+            t2.y = l1_target<LOSS>(l1.tgt, (3 * (size_t)v + 2) * HW + pix);
+        }
+    }
+    if (threadIdx.x == 0) s_maxnc = 0;
+    if constexpr (LOSS == 1)
+        for (int i = threadIdx.x; i < 256; i += NT) s_tab[i] = __fdiv_rn((float)i, 255.0f);
+    __syncthreads();
+    if constexpr (LOSS) {
+        float acc = 0.0f;
+        if (in0) {
+            acc += l1_grad<LOSS>(&g0.x, t0.x, s_tab, l1.inv);
+            acc += l1_grad<LOSS>(&g1.x, t1.x, s_tab, l1.inv);
+            acc += l1_grad<LOSS>(&g2.x, t2.x, s_tab, l1.inv);
+        }
+        if (in1) {
+            acc += l1_grad<LOSS>(&g0.y, t0.y, s_tab, l1.inv);
+            acc += l1_grad<LOSS>(&g1.y, t1.y, s_tab, l1.inv);
+            acc += l1_grad<LOSS>(&g2.y, t2.y, s_tab, l1.inv);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) s_lw[warp] = acc;
     }
     float2 ngS = make_float2(-(T.x * (g0.x * bg0 + g1.x * bg1 + g2.x * bg2)),
                              -(T.y * (g0.y * bg0 + g1.y * bg1 + g2.y * bg2)));
-    if (threadIdx.x == 0) s_maxnc = 0;
-    __syncthreads();
     const uint32_t mnc = max(nc0, nc1);
     if (mnc) atomicMax(&s_maxnc, mnc);
     __syncthreads();
+    if constexpr (LOSS) {
+        if (threadIdx.x == 0) {
+            float t = 0.0f;
+#pragma unroll
+            for (int w = 0; w < NW; w++) t += s_lw[w];
+            if (t != 0.0f) atomicAdd(l1.loss, t * l1.inv);
+        }
+    }
     const long long first = rg.x;
     // n_contrib never exceeds the tile's list length; clamp so a mismatched buffer cannot
     // move the replay outside this tile's entries
@@ -222,30 +300,39 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 7 : 28) k_render_bwd(Layo
 
 template <int B, int BATCH>
 static void bwd_launch(const Layout& L, const uint32_t* tval, const cgs_config& c, const float* dimg, const float* T,
-                       const uint32_t* nc, cudaStream_t st)
+                       const uint32_t* nc, const L1In* l1, cudaStream_t st)
 {
     dim3 grid(L.tiles_x, L.tiles_y, L.V);
+    const L1In none{};
+    const float b0 = c.bg[0], b1 = c.bg[1], b2 = c.bg[2];
     if (c.exact)
-        k_render_bwd<B, BATCH, true><<<grid, B * B / 2, 0, st>>>(L, tval, c.bg[0], c.bg[1], c.bg[2], dimg, T, nc);
+        k_render_bwd<B, BATCH, true, 0><<<grid, B * B / 2, 0, st>>>(L, tval, b0, b1, b2, dimg, T, nc, none);
+    else if (!l1)
+        k_render_bwd<B, BATCH, false, 0><<<grid, B * B / 2, 0, st>>>(L, tval, b0, b1, b2, dimg, T, nc, none);
+    else if (l1->u8)
+        k_render_bwd<B, BATCH, false, 1><<<grid, B * B / 2, 0, st>>>(L, tval, b0, b1, b2, nullptr, T, nc, *l1);
     else
-        k_render_bwd<B, BATCH, false><<<grid, B * B / 2, 0, st>>>(L, tval, c.bg[0], c.bg[1], c.bg[2], dimg, T, nc);
+        k_render_bwd<B, BATCH, false, 2><<<grid, B * B / 2, 0, st>>>(L, tval, b0, b1, b2, nullptr, T, nc, *l1);
 }
 
+// l1 != NULL: the L1 loss and its gradient are formed inside the kernel (dimg unused); not
+// built for the parity configuration (cgs_config.exact), which then returns false.
 bool launch_render_bwd(const Layout& L, const cgs_config& c, const float* dimg, const float* T, const uint32_t* nc,
-                       cudaStream_t st)
+                       const L1In* l1, cudaStream_t st)
 {
     const uint32_t* tv = L.tval;
+    if (l1 && c.exact) return false;
     if (L.B == 16) {
         switch (c.batch) {
-            case 32: bwd_launch<16, 32>(L, tv, c, dimg, T, nc, st); return true;
-            case 64: bwd_launch<16, 64>(L, tv, c, dimg, T, nc, st); return true;
-            case 128: bwd_launch<16, 128>(L, tv, c, dimg, T, nc, st); return true;
-            case 256: bwd_launch<16, 256>(L, tv, c, dimg, T, nc, st); return true;
+            case 32: bwd_launch<16, 32>(L, tv, c, dimg, T, nc, l1, st); return true;
+            case 64: bwd_launch<16, 64>(L, tv, c, dimg, T, nc, l1, st); return true;
+            case 128: bwd_launch<16, 128>(L, tv, c, dimg, T, nc, l1, st); return true;
+            case 256: bwd_launch<16, 256>(L, tv, c, dimg, T, nc, l1, st); return true;
         }
     } else if (L.B == 8) {
         switch (c.batch) {
-            case 32: bwd_launch<8, 32>(L, tv, c, dimg, T, nc, st); return true;
-            case 64: bwd_launch<8, 64>(L, tv, c, dimg, T, nc, st); return true;
+            case 32: bwd_launch<8, 32>(L, tv, c, dimg, T, nc, l1, st); return true;
+            case 64: bwd_launch<8, 64>(L, tv, c, dimg, T, nc, l1, st); return true;
         }
     }
     return false;

@@ -250,6 +250,30 @@ class RenderFn(torch.autograd.Function):
         return grads + (None, None, None, None, None, None)
 
 
+def render_backward_l1(dscene, frame, cfg, d_cams, img, target, final_T, n_contrib, grads=None, rows=None,
+                       attrs=None, stream=None):
+    """L1 loss and backward in one pass (cgs_render_backward_l1): returns (loss, gradients).  With
+    `rows` (or neither `grads` nor `rows`) the gradients are packed rows as render_backward_packed
+    returns them; with `grads` they are added into those scene-indexed arrays."""
+    loss = torch.zeros(1, dtype=torch.float32, device=img.device)
+    u8 = 1 if target.dtype == torch.uint8 else 0
+    if grads is not None:
+        g_mo, g_sc, g_q, g_sh = grads
+        _c.cgs_render_backward_l1(dscene.struct(attrs), frame.struct, cfg, d_cams, img, target.contiguous(), u8,
+                                  final_T, n_contrib, loss, g_mo, g_sc, g_q, g_sh, None, stream)
+        return loss, grads
+    if rows is None:
+        f32, dev, cap = torch.float32, dscene.device, frame.n_cap
+        rows = (torch.empty((cap, 4), dtype=f32, device=dev), torch.empty((cap, 4), dtype=f32, device=dev),
+                torch.empty((cap, 4), dtype=f32, device=dev),
+                torch.empty((cap,) + tuple(dscene.sh.shape[1:]), dtype=f32, device=dev),
+                torch.empty(cap, dtype=torch.int64, device=dev))
+    g_mo, g_sc, g_q, g_sh, g_idx = rows
+    _c.cgs_render_backward_l1(dscene.struct(attrs), frame.struct, cfg, d_cams, img, target.contiguous(), u8,
+                              final_T, n_contrib, loss, g_mo, g_sc, g_q, g_sh, g_idx, stream)
+    return loss, rows
+
+
 def l1_loss(img, target, stream=None):
     """L1 loss and its gradient; target is float32, or uint8 (t stands for t / 255)."""
     loss = torch.zeros(1, dtype=torch.float32, device=img.device)
