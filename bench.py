@@ -68,7 +68,7 @@ OPS_BWD_GRAD = 28
 # batch 128, from one ncu capture of the current build (the summary committed beside the kernel
 # profiles: DRAM bytes per second times the launch's duration); a kernel absent here reports
 # traffic null.  An entry is removed when its kernel changes.
-NCU_TRAFFIC_BYTES = {"render": 15.401e6, "project": 74.186e6, "project_bwd": 72.990e6}
+NCU_TRAFFIC_BYTES = {"render": 15.401e6, "render_bwd": 74.597e6, "project": 74.186e6, "project_bwd": 72.990e6}
 
 
 def parse_args():
@@ -92,6 +92,8 @@ def parse_args():
     ap.add_argument("--lod-batch", type=int, default=128,
                     help="compositing batch depth of the LoD workloads (128 measured best over the height sweep)")
     ap.add_argument("--train-scale", type=float, default=1.0, help="scales the Gaussian counts of train32")
+    ap.add_argument("--train-tile", type=int, default=0, help="train32 tile size (16 or 8); 0 = autotune")
+    ap.add_argument("--train-batch", type=int, default=64, help="train32 batch depth with --train-tile")
     return ap.parse_args()
 
 
@@ -1094,6 +1096,8 @@ def run_train32(args, world, rank, local, peaks, launches_acc):
     tcfg, tune_ms = ta.autotune_library(ds, ta.cameras_device([cams[v] for v in tv]), W, H, int(sum(s8) * 1.05) + 1024,
                                         min((1 << 30) - 1, int(sum(e8) * 1.1) + 65536), view_block=tv_dev, reps=2)
     tile, batch = tcfg.tile, tcfg.batch
+    if args.train_tile:
+        tile, batch = args.train_tile, args.train_batch
     ok_ms = {c: v for c, v in tune_ms.items() if v > 0}
     torch.cuda.empty_cache()
     if tile != 16:

@@ -99,6 +99,7 @@ static bool make_layout(const cgs_frame* f, Layout* L, size_t* bytes)
     l.hdr = c.take<Header>(1);
     l.scan_lb = c.take<unsigned long long>(scan_tiles_vt);
     l.tcnt = c.take<uint32_t>(vt);
+    l.tcur = c.take<uint32_t>(vt);
     l.sel_done = c.take<uint32_t>(l.V);
     l.zero_bytes = c.off;
     l.ranges = c.take<uint32_t>(2 * vt);

@@ -45,6 +45,7 @@ struct Layout {
     // zeroed at every forward (one memset from hdr over zero_bytes)
     unsigned long long* scan_lb; // [scan tiles of V*T] look-back words of the tile-range scan
     uint32_t* tcnt;              // [V * T] entries per tile
+    uint32_t* tcur;              // [V * T] scatter cursors
     uint32_t* sel_done;          // [V] CTAs of the view that finished the selection's first phase
     // not zeroed
     uint32_t* ranges;            // [V * T][2] [start, end) of every tile's entries
@@ -66,8 +67,7 @@ struct Layout {
     unsigned long long* eraw;    // [k_cap] tile << 32 | j per entry; later scratch of the long-tile sort
     unsigned long long* ekey;    // [k_cap] depth bits << 32 | j, scattered into tile ranges
     uint32_t* tval;              // [k_cap] selected index per entry, (tile, depth, index) order
-    uint32_t* tkey;              // [k_cap] tile id per entry, same order; before the sort, the
-                                 // entry's rank within its tile (projection -> scatter)
+    uint32_t* tkey;              // [k_cap] tile id per entry, same order
     uint32_t* big;               // [V * T] tiles for the long-tile sort
     float4* gs;                  // [n_cap][3] screen-space gradients (du dv dA dB | dC do dr dg | db - - -)
     uint32_t* hits;              // optional [scene n]: pixels blending each scene Gaussian (added to)

@@ -92,8 +92,7 @@ __device__ __forceinline__ void prefetch_rows(const cgs_scene& S, long long g)
 //            range of the visible list and of the entry buffer with one atomic add each; the
 //            whole CTA then emits the round's (tile << 32 | j) entries: thread t takes entries
 //            t, t + 128, ..., finds the owning Gaussian by a binary search over the round's
-//            exclusive offsets in shared memory, and counts the tile (the count before the
-//            increment is the entry's rank within its tile).  A round of large
+//            exclusive offsets in shared memory, and counts the tile.  A round of large
 //            Gaussians (hundreds of tiles each, near the camera) is spread over all warps.
 // The order of the visible list and of the entries depends on the order in which CTAs
 // reserve their ranges; nothing downstream depends on it (entries are sorted per tile by
@@ -103,7 +102,6 @@ constexpr int PROJ_WARPS = PROJ_THREADS / 32;
 constexpr int PROJ_ITEMS = 2;  // selected Gaussians per thread in phase 1
 constexpr int PROJ_STEP = PROJ_THREADS * PROJ_ITEMS;
 constexpr int PROJ_CTAS_PER_SM = 10;  // latency-bound: registers capped so ten CTAs fit an SM
-constexpr int PROJ_EMIT = 4;          // entries a thread emits per pass of phase 3
 
 template <int DEG>
 __global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM)
@@ -262,43 +260,22 @@ __global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM)
             s_ry[threadIdx.x] = ry;
             __syncthreads();
             const uint32_t rtot = s_rtot;
-            // PROJ_EMIT entries per thread and pass (t, t + 128, ...): their count atomics return
-            // together instead of one round trip per entry
-            for (uint32_t i0 = threadIdx.x; i0 < rtot; i0 += PROJ_EMIT * PROJ_THREADS) {
-                uint32_t et[PROJ_EMIT], ej[PROJ_EMIT], er[PROJ_EMIT];
+            for (uint32_t idx = threadIdx.x; idx < rtot; idx += PROJ_THREADS) {
+                // owner: the last slot o with s_ex[o] <= idx (a slot with no entries shares its
+                // successor's offset and is never the last such slot)
+                int o = 0;
 #pragma unroll
-                for (int e = 0; e < PROJ_EMIT; e++) {
-                    const uint32_t idx = i0 + (uint32_t)(e * PROJ_THREADS);
-                    et[e] = 0xffffffffu;  // no entry (a tile id is below V * T < 2^32 - 1)
-                    ej[e] = 0;
-                    if (idx < rtot && s_ebase + idx < cap) {
-                        // owner: the last slot o with s_ex[o] <= idx (a slot with no entries
-                        // shares its successor's offset and is never the last such slot)
-                        int o = 0;
-#pragma unroll
-                        for (int step = PROJ_THREADS / 2; step >= 1; step >>= 1)
-                            if (s_ex[o + step] <= idx) o += step;
-                        const uint32_t orx = s_rx[o], ory = s_ry[o];
-                        const uint32_t tx0 = orx & 0xffffu, ty0 = orx >> 16, w = (ory & 0xffffu) - tx0;
-                        const uint32_t local = idx - s_ex[o];
-                        et[e] = (uint32_t)s_ev[o] * (uint32_t)L.T + (ty0 + local / w) * (uint32_t)L.tiles_x +
-                                (tx0 + local % w);
-                        ej[e] = s_ej[o];
-                    }
-                }
-                // the count's old value is the entry's rank among its tile's entries (in arrival
-                // order): its slot in the tile's range, which the scatter reads from tkey (free
-                // until the per-tile sort writes it)
-#pragma unroll
-                for (int e = 0; e < PROJ_EMIT; e++)
-                    if (et[e] != 0xffffffffu) er[e] = atomicAdd(&L.tcnt[et[e]], 1u);
-#pragma unroll
-                for (int e = 0; e < PROJ_EMIT; e++) {
-                    if (et[e] != 0xffffffffu) {
-                        const unsigned long long k = s_ebase + i0 + (uint32_t)(e * PROJ_THREADS);
-                        L.eraw[k] = ((unsigned long long)et[e] << 32) | ej[e];
-                        L.tkey[k] = er[e];
-                    }
+                for (int step = PROJ_THREADS / 2; step >= 1; step >>= 1)
+                    if (s_ex[o + step] <= idx) o += step;
+                const unsigned long long k = s_ebase + idx;
+                if (k < cap) {
+                    const uint32_t orx = s_rx[o], ory = s_ry[o];
+                    const uint32_t tx0 = orx & 0xffffu, ty0 = orx >> 16, w = (ory & 0xffffu) - tx0;
+                    const uint32_t local = idx - s_ex[o];
+                    const uint32_t t = (uint32_t)s_ev[o] * (uint32_t)L.T + (ty0 + local / w) * (uint32_t)L.tiles_x +
+                                       (tx0 + local % w);
+                    L.eraw[k] = ((unsigned long long)t << 32) | s_ej[o];
+                    atomicAdd(&L.tcnt[t], 1u);
                 }
             }
             __syncthreads();

@@ -3,9 +3,8 @@
 // ties to the lower index).
 //
 //   tile ranges   single-pass scan of the per-tile counts -> [start, end) of every tile
-//   scatter       one thread per entry: a slot in its tile's range (the range start plus the
-//                 rank the projection's per-tile count gave the entry), key (FP32 depth bits
-//                 << 32 | selected index)
+//   scatter       one thread per entry: a slot in its tile's range (atomic cursor), key
+//                 (FP32 depth bits << 32 | selected index)
 //   tile sort     one CTA per tile: up to 128 keys ranked against each other in shared
 //                 memory (each key's count of smaller keys is its slot), up to 256 a bitonic
 //                 sort held in registers; longer tiles (listed by the range scan) go to a
@@ -42,15 +41,14 @@ struct TileRangeOp {
     __device__ void finish(unsigned long long total) const { (void)total; }
 };
 
-// One thread per entry: its slot inside its tile's range (the range start plus the rank the
-// projection's tile count gave it, in tkey) and the (depth bits, index) key.
+// One thread per entry: a slot inside its tile's range and the (depth bits, index) key.
 __global__ void __launch_bounds__(256) k_scatter(Layout L)
 {
     const long long n = entries_kept(L);
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         const unsigned long long w = L.eraw[k];
         const uint32_t t = (uint32_t)(w >> 32), j = (uint32_t)w;
-        const uint32_t slot = L.ranges[2 * (size_t)t] + L.tkey[k];
+        const uint32_t slot = L.ranges[2 * (size_t)t] + atomicAdd(&L.tcur[t], 1u);
         L.ekey[slot] = ((unsigned long long)(uint32_t)L.pkey[j] << 32) | j;
     }
 }
