@@ -374,12 +374,13 @@ def run_ours(args, world, rank, local):
     # written in full every step, so nothing is cleared outside the timed region
     rows = tune_rows
 
-    def step_with(tgt_buf, cam_buf):
+    def step_with(tgt_buf, cam_buf, loss_buf):
         # the same step reading the target image and the camera from the given device buffers
+        # and accumulating the loss into loss_buf
         cur = torch.cuda.current_stream().cuda_stream
         cgs.cgs_render_forward(s_struct, frame.struct, cfg, cam_buf, None, None, img, T, nc, cur)
-        loss.zero_()
-        cgs.cgs_render_backward_l1(s_struct, frame.struct, cfg, cam_buf, img, tgt_buf, 1, T, nc, loss, *rows, cur)
+        loss_buf.zero_()
+        cgs.cgs_render_backward_l1(s_struct, frame.struct, cfg, cam_buf, img, tgt_buf, 1, T, nc, loss_buf, *rows, cur)
 
     def step(fwd_only=False):
         # the current stream at call time (the capture stream while a CUDA graph is recorded)
@@ -634,47 +635,57 @@ def run_fp16_compare(args, sc, cfg, d_cams, tgt, ds32, st, flush, world, ta, cgs
 def run_e2e(args, frame, cams, tgt_host, step_with, loss, st, world):
     """The training step end to end through the public API with its per-step inputs on the
     HOST: every step copies its camera and its target image from pinned host memory, runs
-    forward + L1 + backward, and reads the loss back; the Gaussian parameters (the model) stay
-    resident, as weights do in training.  Copies run on a second stream into two alternating
-    buffers, so step i+1's copy overlaps step i's kernels; every copy is inside the timed
-    region."""
+    forward + L1 + backward, and reads the loss back into pinned host memory; the Gaussian
+    parameters (the model) stay resident, as weights do in training.  Copies run on a second
+    stream with two alternating sets of buffers (target, camera, loss): step i+1's inputs
+    arrive while step i's kernels run, and step i's loss is read back on that stream after
+    step i, so the compute stream goes straight on to step i+1.  Every copy is inside the timed
+    region, which ends when the last loss has reached the host."""
     import torch
     from paper_2404_01133_b300 import torch_api as ta
     cam_host = ta.cameras_host(cams[:1])
     bufs = [(torch.empty(tgt_host.shape, dtype=tgt_host.dtype, device="cuda"),
-             torch.empty(cam_host.shape, dtype=cam_host.dtype, device="cuda")) for _ in range(2)]
+             torch.empty(cam_host.shape, dtype=cam_host.dtype, device="cuda"),
+             torch.zeros(1, dtype=torch.float32, device="cuda")) for _ in range(2)]
     cs = torch.cuda.Stream()
-    ready = [torch.cuda.Event() for _ in range(2)]
-    free = [torch.cuda.Event() for _ in range(2)]
+    ready = [torch.cuda.Event() for _ in range(2)]   # set b's inputs are on the device
+    done = [torch.cuda.Event() for _ in range(2)]    # the step that used set b has finished
     k = max(3, min(args.steps, 20))
     loss_host = torch.empty(k, dtype=torch.float32).pin_memory()
     h2d = tgt_host.numel() * tgt_host.element_size() + cam_host.numel()
 
     def copy_in(i):
         b = i % 2
-        cs.wait_event(free[b])      # the buffer's previous step has finished with it
+        cs.wait_event(done[b])      # the set's previous step has finished with it (and its loss was read)
         with torch.cuda.stream(cs):
             bufs[b][0].copy_(tgt_host, non_blocking=True)
             bufs[b][1].copy_(cam_host, non_blocking=True)
         ready[b].record(cs)
 
-    for tb, cb in bufs:  # valid inputs before the capture's warm-up call runs on them
+    def read_loss(i):
+        b = i % 2
+        cs.wait_event(done[b])
+        with torch.cuda.stream(cs):
+            loss_host[i:i + 1].copy_(bufs[b][2], non_blocking=True)
+
+    for tb, cb, _ in bufs:  # valid inputs before the capture's warm-up call runs on them
         tb.copy_(tgt_host)
         cb.copy_(cam_host)
     torch.cuda.synchronize()
-    # the kernels of one step, captured once per input buffer (the public capture helper)
-    graphs = [ta.capture(lambda b=b: step_with(bufs[b][0], bufs[b][1]), warmup=1) for b in range(2)]
+    # the kernels of one step, captured once per buffer set (the public capture helper)
+    graphs = [ta.capture(lambda b=b: step_with(bufs[b][0], bufs[b][1], bufs[b][2]), warmup=1) for b in range(2)]
 
     def run(k_):
         copy_in(0)
         for i in range(k_):
-            if i + 1 < k_:
-                copy_in(i + 1)
             b = i % 2
             st.wait_event(ready[b])
             graphs[b].replay()
-            free[b].record(st)
-            loss_host[i:i + 1].copy_(loss, non_blocking=True)
+            done[b].record(st)
+            if i + 1 < k_:
+                copy_in(i + 1)      # waits only for step i - 1: overlaps step i
+            read_loss(i)            # after step i, before set b's next inputs
+        st.wait_stream(cs)
 
     run(2)
     torch.cuda.synchronize()
@@ -688,8 +699,11 @@ def run_e2e(args, frame, cams, tgt_host, step_with, loss, st, world):
     W, H = frame.width, frame.height
     return {"value": world * W * H / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4,
-            "inputs": "per step: camera + target image (pinned host, copy stream overlapped); model resident",
-            "step": "CUDA graph replay per input buffer"}
+            "inputs": "per step: camera + target image (pinned host); model resident",
+            "pipelining": "copy stream with two buffer sets: inputs of step i+1 and the loss of step i "
+                          "move while step i+1 / step i run; the timed region ends after the last loss "
+                          "reached pinned host memory",
+            "step": "CUDA graph replay per buffer set"}
 
 
 def run_e2e_scene_upload(args, ds, frame, sc, tgt_host, tgt_dev, step, loss, st, world):

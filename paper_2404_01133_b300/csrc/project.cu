@@ -134,9 +134,11 @@ __global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM)
                 locate(L, j, &v, &g);
                 L.gidx[j] = (uint32_t)g;
                 const cgs_camera& c = cams[v];
+                // the scale row is read with the position, not after the near-plane test: one
+                // round trip instead of two for the Gaussians in front of the camera
                 const float4 mo = __ldg(mo4 + g);
+                const float sm0 = load_max_scale(S, g);
                 const float m[3] = {mo.x, mo.y, mo.z};
-                // near-plane test first, so culled Gaussians never read scale or rotation
                 const float tz = ((c.R[6] * m[0] + c.R[7] * m[1]) + c.R[8] * m[2]) + c.t[2];
                 bool keep = tz > near_z;
                 if (keep && L.lod_mode == CGS_LOD_POINT) {
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM)
                     keep = (long long)rank < S.level_count[(long long)blk * S.n_levels + lv];
                 }
                 if (keep) {
-                    const float sm = load_max_scale(S, g);
+                    const float sm = sm0;
                     const float tx = ((c.R[0] * m[0] + c.R[1] * m[1]) + c.R[2] * m[2]) + c.t[0];
                     const float ty = ((c.R[3] * m[0] + c.R[4] * m[1]) + c.R[5] * m[2]) + c.t[1];
                     keep = !surely_off_screen(sm, c, tx, ty, tz, L.W, L.H);

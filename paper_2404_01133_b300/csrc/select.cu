@@ -72,12 +72,26 @@ __device__ int lod_level8_f32(const cgs_scene& S, int b, const cgs_camera& c, fl
 {
     const float U = 5.9604645e-8f;
     const int k = threadIdx.x & 7;
-    const bool active = b >= 0 && b < S.n_blocks && S.level_count[(long long)(b < 0 ? 0 : b) * S.n_levels] > 0;
+    // every value of the block read up front (no load waits on another): its level-0 count,
+    // this lane's corner and the ground cell
+    const bool inrange = b >= 0 && b < S.n_blocks;
+    const long long bq = inrange ? b : 0;
+    const long long cnt0 = inrange ? S.level_count[bq * S.n_levels] : 0;
+    float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, ce[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (inrange && S.block_aabb) {
+        const float* bb = S.block_aabb + 6 * bq;
+        p0 = bb[(k & 1) ? 3 : 0];
+        p1 = bb[(k & 2) ? 4 : 1];
+        p2 = bb[(k & 4) ? 5 : 2];
+    }
+    if (inrange && S.block_cell) {
+        const float* cp = S.block_cell + 4 * bq;
+        ce[0] = cp[0]; ce[1] = cp[1]; ce[2] = cp[2]; ce[3] = cp[3];
+    }
+    const bool active = inrange && cnt0 > 0;
     float e2 = INFINITY, xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY, exu = 0.0f, eyv = 0.0f;
     int front = 0, unsure = 0;
     if (active) {
-        const float* bb = S.block_aabb + 6 * (long long)b;
-        const float p0 = bb[(k & 1) ? 3 : 0], p1 = bb[(k & 2) ? 4 : 1], p2 = bb[(k & 4) ? 5 : 2];
         const float e0 = p0 - c.campos[0], ee1 = p1 - c.campos[1], ee2 = p2 - c.campos[2];
         e2 = (e0 * e0 + ee1 * ee1) + ee2 * ee2;
         const float tx = ((c.R[0] * p0 + c.R[1] * p1) + c.R[2] * p2) + c.t[0];
@@ -132,7 +146,6 @@ __device__ int lod_level8_f32(const cgs_scene& S, int b, const cgs_camera& c, fl
             if (t4[i] < 0) vis = -1;
         }
     }
-    const float* ce = S.block_cell + 4 * (long long)b;
     const bool inside = c.campos[0] >= ce[0] && c.campos[0] < ce[1] && c.campos[1] >= ce[2] && c.campos[1] < ce[3];
     if (!inside) {
         if (vis < 0) { *amb = true; return -1; }
@@ -238,8 +251,30 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Layout L, cgs_scene S, c
     } else {
         const cgs_camera c = cams[v];
         const int b = b0 + (int)(threadIdx.x >> 3);
-        const int l = lod_level8_fast(S, b < NB ? b : -1, c, (double)cfg.near_z, cfg.lod_dist[0], cfg.lod_dist[1]);
-        if (b < NB && (threadIdx.x & 7) == 0) keep(b, l);
+        // the counts and offsets of the three levels the LoD can choose, fetched together with
+        // the block's bounds instead of after the level is known
+        const bool lead = b < NB && (threadIdx.x & 7) == 0;
+        long long pc[3] = {0, 0, 0}, po[3] = {0, 0, 0};
+        if (lead) {
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                if (q < NL) {
+                    pc[q] = S.level_count[(long long)b * NL + q];
+                    po[q] = S.level_offset[(long long)b * NL + q];
+                }
+            }
+        }
+        int l = lod_level8_fast(S, b < NB ? b : -1, c, (double)cfg.near_z, cfg.lod_dist[0], cfg.lod_dist[1]);
+        if (lead) {
+            // l <= min(2, NL - 1)
+            const long long cnt = l >= 0 ? (l == 0 ? pc[0] : (l == 1 ? pc[1] : pc[2])) : 0;
+            const long long off = l >= 0 ? (l == 0 ? po[0] : (l == 1 ? po[1] : po[2])) : 0;
+            if (l >= 0 && cnt <= 0) l = -1;
+            lev[b] = (int8_t)l;
+            s_lv[b - b0] = l;
+            s_cnt[b - b0] = l >= 0 ? cnt : 0;
+            s_off[b - b0] = l >= 0 ? off : 0;
+        }
     }
     const bool one_cta = gridDim.x == 1;
     __shared__ bool s_last;
