@@ -136,13 +136,18 @@ __device__ __forceinline__ void tile_sort_regs(const Layout& L, unsigned long lo
 constexpr int RANK_ONLY = TS_THREADS;     // up to this many keys by ranking, above by a bitonic sort
 
 // One CTA per (view, tile).  Up to RANK_ONLY keys: every thread ranks one key against all keys
-// of the tile in shared memory (keys are distinct, so the rank is the output slot; n^2
-// comparisons); up to RANK_MAX keys: a bitonic sort of 256 keys held two per thread (n log^2 n,
-// fewer operations above about 128 keys); longer tiles (listed by the range scan) are left to
-// the long-tile kernel, kept apart so the common short tiles run at full occupancy.
+// of the tile in shared memory (n^2 comparisons): first by its 32-bit depth alone (the count of
+// strictly smaller depths, four depths per 16-byte load), then, only for a key whose depth
+// another key shares (found by counting keys per rank), by index among the equal depths, so
+// the rank is the key's slot in (depth, index) order.  Up to RANK_MAX keys: a bitonic sort of
+// 256 keys held two per thread (n log^2 n, fewer operations above about 128 keys); longer tiles
+// (listed by the range scan) are left to the long-tile kernel, kept apart so the common short
+// tiles run at full occupancy.
 __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(Layout L)
 {
     __shared__ unsigned long long s[RANK_MAX];
+    __shared__ __align__(16) uint32_t s_d[RANK_ONLY];  // depth bits
+    __shared__ uint32_t s_j[RANK_ONLY], s_c[RANK_ONLY];  // indices; keys per depth rank
     const uint32_t t = blockIdx.x;
     const uint32_t st = L.ranges[2 * (size_t)t], n = L.ranges[2 * (size_t)t + 1] - st;
     if (n == 0 || n > (uint32_t)RANK_MAX) return;  // longer tiles: listed by the range scan
@@ -152,14 +157,34 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(Layout L)
     }
     {
         const uint32_t i = threadIdx.x;
+        const uint32_t n4 = (n + 3u) >> 2;
         const unsigned long long key = i < n ? L.ekey[st + i] : ~0ull;
-        if (i < n) s[i] = key;
+        const uint32_t d = (uint32_t)(key >> 32), j = (uint32_t)key;
+        if (i < n) {
+            s_d[i] = d;
+            s_j[i] = j;
+            s_c[i] = 0u;
+        } else if (i < 4u * n4) {
+            s_d[i] = 0xffffffffu;  // padding: above every depth (positive finite FP32 bits)
+        }
+        __syncthreads();
+        uint32_t r = 0;
+        if (i < n) {
+            const uint4* d4 = reinterpret_cast<const uint4*>(s_d);
+#pragma unroll 4
+            for (uint32_t m = 0; m < n4; m++) {
+                const uint4 q = d4[m];
+                r += (uint32_t)(q.x < d) + (uint32_t)(q.y < d) + (uint32_t)(q.z < d) + (uint32_t)(q.w < d);
+            }
+            atomicAdd(&s_c[r], 1u);  // keys of equal depth share r
+        }
         __syncthreads();
         if (i < n) {
-            uint32_t r = 0;
-#pragma unroll 4
-            for (uint32_t m = 0; m < n; m++) r += s[m] < key;
-            L.tval[st + r] = (uint32_t)key;
+            if (s_c[r] > 1u) {
+                // equal depths (rare): ordered by index among themselves
+                for (uint32_t m = 0; m < n; m++) r += (uint32_t)(s_d[m] == d && s_j[m] < j);
+            }
+            L.tval[st + r] = j;
             L.tkey[st + r] = t;
         }
     }

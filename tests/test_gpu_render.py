@@ -152,6 +152,21 @@ def test_long_tiles_with_equal_depths_keep_index_order(n):
     assert len(np.unique(o["sort"]["keys"])) == 4   # one tile, four depths: long runs of ties
 
 
+@pytest.mark.parametrize("n", [5, 40, 100, 128, 200])
+def test_short_tiles_with_equal_depths_keep_index_order(n):
+    """Tiles of up to 256 keys whose Gaussians share depths exactly (four planes facing the
+    camera): the ranking path orders by depth bits first and puts keys of equal depth in index
+    order, the register bitonic path compares whole keys; bit-exact against the oracle."""
+    sc = synth.random_cube_scene(n, seed=11 + n, sh_degree=0, extent=0.2, log_scale_mu=-2.5)
+    sc["mean_opac"][:, 2] = np.random.default_rng(n + 1).choice(np.float32([-0.1, 0.0, 0.05, 0.1]), size=n)
+    sc = synth.single_block(sc)
+    cam = synth.small_scene_camera(16, 16, f=30.0, dist=3.0)
+    g = gpu_render(sc, [cam])
+    o, _ = check_against_oracle(sc, cam, g, 16)
+    keys = o["sort"]["keys"]   # (tile, depth bits) of every entry: one tile here
+    assert len(keys) == n and len(np.unique(keys)) < n   # ties present
+
+
 def test_all_culled_view_gives_background():
     sc, cams = synth.workload_small()
     cam = synth.camera_from_rt(np.diag([-1.0, 1.0, -1.0]), [0.0, 0.0, -10.0], 150, 150, 63.5, 63.5, 128, 128)
