@@ -83,7 +83,9 @@ __device__ __forceinline__ void prefetch_rows(const cgs_scene& S, long long g)
 //   phase 1  PROJ_ITEMS Gaussians per thread: scene index, near plane, the point-wise level
 //            test, the cheap off-screen bound; the survivors are queued in shared memory
 //   phase 2  in rounds of one queued Gaussian per thread (dense warps, so the full projection
-//            is not run by warps whose lanes are mostly culled): covariance,
+//            is not run by warps whose lanes are mostly culled; survivors of several steps are
+//            queued until a full round is there, so a step whose few survivors would fill a
+//            fraction of a round runs no phase 2 at all): covariance,
 //            radius, tile rect; for the visible ones the projected record (screen-space part
 //            and the view-dependent SH colour, Sec. 3.1, its coefficients read as they are
 //            used), the rect and the (view, depth) sort key
@@ -112,18 +114,22 @@ __global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM)
     __shared__ uint32_t s_ex[PROJ_THREADS], s_ej[PROJ_THREADS], s_rx[PROJ_THREADS], s_ry[PROJ_THREADS];
     __shared__ int s_ev[PROJ_THREADS];
     __shared__ unsigned long long s_ebase;
-    __shared__ uint32_t s_qj[PROJ_STEP];
-    __shared__ int s_qv[PROJ_STEP];
-    __shared__ long long s_qg[PROJ_STEP];
+    // the queue of phase-1 survivors: a remainder of fewer than PROJ_THREADS from earlier steps
+    // plus one step's survivors
+    constexpr int QCAP = PROJ_STEP + PROJ_THREADS;
+    __shared__ uint32_t s_qj[QCAP];
+    __shared__ int s_qv[QCAP];
+    __shared__ long long s_qg[QCAP];
     const uint32_t n = L.hdr->n_sel;
     const float4* __restrict__ mo4 = reinterpret_cast<const float4*>(S.mean_opac);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const unsigned long long cap = (unsigned long long)L.k_cap;
+    if (threadIdx.x == 0) s_nq = 0;
+    __syncthreads();
     for (uint32_t base = blockIdx.x * PROJ_STEP; base < n; base += gridDim.x * PROJ_STEP) {
-        // phase 1
-        if (threadIdx.x == 0) s_nq = 0;
-        __syncthreads();
+        const bool last_step = base + gridDim.x * PROJ_STEP >= n;  // this CTA's final step (uniform)
+        // phase 1: survivors appended to the queue
 #pragma unroll 1
         for (int u = 0; u < PROJ_ITEMS; u++) {
             const uint32_t j = base + (uint32_t)(u * PROJ_THREADS) + threadIdx.x;
@@ -177,12 +183,15 @@ __global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM)
         }
         __syncthreads();
         const uint32_t nq = s_nq;
-        __syncthreads();  // every thread has read nq before the next step resets it
-        for (uint32_t q0 = 0; q0 < nq; q0 += PROJ_THREADS) {
+        // phase 2 runs full rounds only; the rest waits in the queue for the next step's
+        // survivors (all of it in the CTA's last step)
+        const uint32_t nproc = last_step ? nq : (nq / PROJ_THREADS) * PROJ_THREADS;
+        __syncthreads();  // every thread has read nq before the queue is compacted below
+        for (uint32_t q0 = 0; q0 < nproc; q0 += PROJ_THREADS) {
             // phase 2
             uint32_t tt = 0, rx = 0, ry = 0, j = 0;
             int v = 0;
-            if (q0 + threadIdx.x < nq) {
+            if (q0 + threadIdx.x < nproc) {
                 const uint32_t qi = q0 + threadIdx.x;
                 j = s_qj[qi];
                 v = s_qv[qi];
@@ -282,6 +291,28 @@ __global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM)
             }
             __syncthreads();
         }
+        // the unprocessed remainder (fewer than PROJ_THREADS) moves to the front of the queue;
+        // its rows are fetched into L2 for the next step's first round
+        if (nproc > 0 && nproc < nq) {
+            const uint32_t rem = nq - nproc;
+            uint32_t qj = 0;
+            int qv = 0;
+            long long qg = 0;
+            if (threadIdx.x < rem) {
+                qj = s_qj[nproc + threadIdx.x];
+                qv = s_qv[nproc + threadIdx.x];
+                qg = s_qg[nproc + threadIdx.x];
+            }
+            __syncthreads();
+            if (threadIdx.x < rem) {
+                s_qj[threadIdx.x] = qj;
+                s_qv[threadIdx.x] = qv;
+                s_qg[threadIdx.x] = qg;
+                prefetch_rows<DEG>(S, qg);
+            }
+        }
+        if (threadIdx.x == 0) s_nq = nq - nproc;
+        __syncthreads();
     }
 }
 
