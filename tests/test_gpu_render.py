@@ -242,6 +242,33 @@ def test_lod_selection_bit_exact(dist):
     assert (got == -1).any() and (got >= 0).any()
 
 
+def test_one_view_selection_matches_oracle():
+    """One view of a four-block scene: the selected list the renderer builds (the scene index
+    of every selected Gaussian, in segment order), its count and the view prefix equal the
+    oracle's LoD selection and concatenation, for cameras that cull blocks, use every level and
+    mix levels in one frame; one mixed frame is rendered in full."""
+    sc = lod_scene(n=20000, grid=2)
+    aabb = oracle.block_bounds(sc, 4.0)
+    cams = lod_cameras(sc["side"])
+    seen, mixed = set(), None
+    for cam in cams:
+        lev = np.asarray(oracle.lod_select(sc, aabb, cam)).ravel()
+        idx = np.asarray(oracle.concat(sc, lev), np.int64)
+        g = gpu_render(sc, [cam], n_mad=4.0)
+        assert g["status"] == 0
+        assert g["counts"][0] == len(idx)
+        gidx = g["frame"].buffer(cgs.BUF_SCENE_INDEX, torch.int32, count=len(idx)).cpu().numpy()
+        np.testing.assert_array_equal(gidx.astype(np.int64), idx)
+        vb = g["frame"].buffer(cgs.BUF_VIEW_BASE, torch.int32, count=2).cpu().numpy()
+        assert list(vb) == [0, len(idx)]
+        seen.update(int(x) for x in lev)
+        if mixed is None and len(set(int(x) for x in lev if x >= 0)) > 1:
+            mixed = (cam, idx)
+    assert seen == {-1, 0, 1, 2} and mixed is not None
+    cam, idx = mixed
+    check_against_oracle(sc, cam, gpu_render(sc, [cam], n_mad=4.0), 16, idx=idx)
+
+
 def test_lod_render_matches_oracle_on_concatenated_selection():
     sc = lod_scene()
     aabb = oracle.block_bounds(sc, 4.0)
