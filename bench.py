@@ -357,7 +357,9 @@ def run_ours(args, world, rank, local):
         args.tile, args.batch = tcfg.tile, tcfg.batch
         torch.cuda.empty_cache()
     cfg = ta.make_config(tile=args.tile, batch=args.batch)
-    frame = ta.Frame(1, W, H, args.tile, 1, n, 8_000_000, dev)
+    # the timed steps leave out the compositing backward's diagnostic count of contributing
+    # pairs (CGS_FRAME_NO_PAIR_COUNT); one counting step after the timing supplies it
+    frame = ta.Frame(1, W, H, args.tile, 1, n, 8_000_000, dev, count_pairs=False)
     img, T, nc = frame.outputs()
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -447,8 +449,12 @@ def run_ours(args, world, rank, local):
         ms_fwd, _ = timed_fn(lambda: step(fwd_only=True), args.steps, st, flush, world)
         ms_f32t, _ = timed_fn(step_f32_target, max(3, args.steps // 2), st, flush, world)
         ms_dense, _ = timed_fn(step_dense, max(3, args.steps // 2), st, flush, world)
-    step()  # one full step so the frame's counters hold both the forward and the backward
+    # one full step with every counter on, so the frame's counters hold both the forward and the
+    # backward (the work counts of the roofline)
+    frame.struct.flags = 0
+    step()
     status, counts = frame.status()
+    frame.struct.flags = cgs.CGS_FRAME_NO_PAIR_COUNT
     if status != cgs.CGS_OK:
         raise RuntimeError(f"frame status: {cgs.cgs_status_string(status)}")
     sum_nc = int(nc.to(torch.int64).sum().item())
@@ -482,7 +488,9 @@ def run_ours(args, world, rank, local):
                    "gradients": "packed rows per visible Gaussian, written in full by every step; the loss "
                                 "accumulator cleared inside the step; nothing cleared between steps",
                    "target": "8-bit RGB image, channel t stands for t/255",
-                   "loss": "L1, mean |img - target|, formed inside the compositing backward (cgs_render_backward_l1)"},
+                   "loss": "L1, mean |img - target|, formed inside the compositing backward (cgs_render_backward_l1)",
+                   "counters": "timed steps without the backward's diagnostic pair count (CGS_FRAME_NO_PAIR_COUNT); "
+                               "the work counts come from one counting step of the same frame"},
         "fwd_mpix_s": fwd_value, "fwd_ms": fwd_ms, "fps_fwd_bwd": 1e3 / step_ms, "fps_fwd": 1e3 / fwd_ms,
         "gaussians_per_s": world * n / (step_ms * 1e-3),
         "stage_ms": {k_: round(v, 4) for k_, v in stage_ms.items()},
@@ -542,7 +550,7 @@ def run_batched_compare(args, ds, sc, cfg, st, flush, world, synth, ta, cgs):
     sel, ent = ta.frame_counts(ds, cams, W, H, tile=cfg.tile)
     n_cap = int(sum(sel) * 1.05) + 1024
     k_cap = min((1 << 30) - 1, int(sum(ent) * 1.1) + 65536)
-    frame = ta.Frame(V, W, H, cfg.tile, ds.n_blocks, n_cap, k_cap)
+    frame = ta.Frame(V, W, H, cfg.tile, ds.n_blocks, n_cap, k_cap, count_pairs=False)
     d_cams = ta.cameras_device(cams)
     img, T, nc = frame.outputs()
     tgt = torch.rand((V, 3, H, W), device=ds.device)
@@ -564,7 +572,8 @@ def run_batched_compare(args, ds, sc, cfg, st, flush, world, synth, ta, cgs):
         loss.zero_()
         cgs.cgs_render_backward_l1(s_struct, frame.struct, cfg, d_cams, img, tgt, 0, T, nc, loss, *rows, cur)
 
-    f1 = ta.Frame(1, W, H, cfg.tile, ds.n_blocks, max(sel) + 1024, min((1 << 30) - 1, max(ent) * 2 + 65536))
+    f1 = ta.Frame(1, W, H, cfg.tile, ds.n_blocks, max(sel) + 1024, min((1 << 30) - 1, max(ent) * 2 + 65536),
+                  count_pairs=False)
     d1 = [ta.cameras_device([c]) for c in cams]
     i1, T1, n1 = f1.outputs()
     rows1 = [packed_rows(f1.n_cap) for _ in range(V)]  # one set of rows per view, as the batched frame has
@@ -599,7 +608,7 @@ def run_fp16_compare(args, sc, cfg, d_cams, tgt, ds32, st, flush, world, ta, cgs
     W, H = 1920, 1080
     res = {}
     for name, ds in (("fp32", ds32), ("fp16", ds16)):
-        frame = ta.Frame(1, W, H, cfg.tile, 1, ds.n, 8_000_000, ds.device)
+        frame = ta.Frame(1, W, H, cfg.tile, 1, ds.n, 8_000_000, ds.device, count_pairs=False)
         img, T, nc = frame.outputs()
         loss = torch.zeros(1, device=ds.device)
         f32, cap = torch.float32, ds.n

@@ -44,6 +44,7 @@ class cgs_config(C.Structure):
                 ("lod_dist", C.c_double * 2), ("lod_mode", C.c_int32), ("exact", C.c_int32)]
 
 
+CGS_FRAME_NO_PAIR_COUNT = 1
 CGS_LOD_BLOCK = 0
 CGS_LOD_POINT = 1
 CGS_TUNE_CANDIDATES = 6
@@ -54,7 +55,7 @@ TUNE_ORDER = ((16, 256), (16, 128), (16, 64), (16, 32), (8, 64), (8, 32))
 
 class cgs_frame(C.Structure):
     _fields_ = [("ws", C.c_void_p), ("ws_bytes", C.c_int64), ("n_views", C.c_int32), ("width", C.c_int32),
-                ("height", C.c_int32), ("tile", C.c_int32), ("n_blocks", C.c_int32), ("_pad", C.c_int32),
+                ("height", C.c_int32), ("tile", C.c_int32), ("n_blocks", C.c_int32), ("flags", C.c_int32),
                 ("n_cap", C.c_int64), ("k_cap", C.c_int64)]
 
 

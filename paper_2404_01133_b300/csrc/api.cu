@@ -74,7 +74,8 @@ struct Carver {
 // Fills L from the frame dimensions; returns false if they are invalid.
 static bool make_layout(const cgs_frame* f, Layout* L, size_t* bytes)
 {
-    if (!f || f->n_views < 1 || f->n_views > 65535 || f->width < 1 || f->height < 1 ||
+    if (!f || (f->flags & ~CGS_FRAME_NO_PAIR_COUNT) != 0 || f->n_views < 1 || f->n_views > 65535 || f->width < 1 ||
+        f->height < 1 ||
         (f->tile != 16 && f->tile != 8) || f->n_blocks < 1 || f->n_cap < 1 || f->n_cap >= (1ll << 31) ||
         f->k_cap < 1 || f->k_cap >= (1ll << 30))
         return false;
@@ -127,6 +128,7 @@ static bool make_layout(const cgs_frame* f, Layout* L, size_t* bytes)
     l.cbits_words = (long long)nw * (l.k_cap / 32 + vt + 1);
     l.cbits = c.take<uint32_t>(l.cbits_words);
     l.hits = nullptr;
+    l.count_pairs = (f->flags & CGS_FRAME_NO_PAIR_COUNT) ? 0 : 1;
     *L = l;
     *bytes = c.off;
     return true;

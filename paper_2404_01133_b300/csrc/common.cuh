@@ -74,6 +74,7 @@ struct Layout {
     uint32_t* cbits;             // per (tile, warp): bit p set when entry p blends into any of the warp's pixels
     long long cbits_words;
     size_t zero_bytes;           // bytes to clear from hdr
+    int count_pairs;             // the compositing backward counts its contributing pairs
     long long n_cap, k_cap;
     int V, W, H, B, tiles_x, tiles_y, T, NB;
 };

@@ -63,7 +63,9 @@ __device__ __forceinline__ float l1_grad(float* g, float t, const float* tab, fl
 // CTA's share of mean |img - target| goes to *l1.loss; dL_dimg is not read.  The difference and
 // both sign tests are explicit IEEE instructions, so this file's flush-to-zero leaves the
 // gradient bit-identical to cgs_l1_loss's.
-template <int B, int BATCH, bool EXACT, int LOSS>
+//
+// COUNT: the contributing pairs replayed are counted into the frame header (a diagnostic).
+template <int B, int BATCH, bool EXACT, int LOSS, bool COUNT>
 __global__ void __launch_bounds__(B * B / 2, B == 16 ? 7 : 28) k_render_bwd(Layout L, const uint32_t* __restrict__ tval, float bg0,
                                                           float bg1, float bg2, const float* __restrict__ dL_dimg,
                                                           const float* __restrict__ final_T,
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 7 : 28) k_render_bwd(Layo
                 red[9 * e + 6][lane] = c0g.x + c0g.y;
                 red[9 * e + 7][lane] = c1g.x + c1g.y;
                 red[9 * e + 8][lane] = c2g.x + c2g.y;
-                pairs += (uint32_t)u0 + (uint32_t)u1;
+                if constexpr (COUNT) pairs += (uint32_t)u0 + (uint32_t)u1;
             }
             __syncwarp();
             if (lane < 9 * ne) {
@@ -294,8 +296,10 @@ __global__ void __launch_bounds__(B * B / 2, B == 16 ? 7 : 28) k_render_bwd(Layo
             __syncwarp();
         }
     }
-    const uint32_t ws = __reduce_add_sync(0xffffffffu, pairs);
-    if (lane == 0 && ws) atomicAdd(&L.hdr->pairs_bwd, (unsigned long long)ws);
+    if constexpr (COUNT) {
+        const uint32_t ws = __reduce_add_sync(0xffffffffu, pairs);
+        if (lane == 0 && ws) atomicAdd(&L.hdr->pairs_bwd, (unsigned long long)ws);
+    }
 }
 
 template <int B, int BATCH>
@@ -305,14 +309,18 @@ static void bwd_launch(const Layout& L, const uint32_t* tval, const cgs_config& 
     dim3 grid(L.tiles_x, L.tiles_y, L.V);
     const L1In none{};
     const float b0 = c.bg[0], b1 = c.bg[1], b2 = c.bg[2];
-    if (c.exact)
-        k_render_bwd<B, BATCH, true, 0><<<grid, B * B / 2, 0, st>>>(L, tval, b0, b1, b2, dimg, T, nc, none);
-    else if (!l1)
-        k_render_bwd<B, BATCH, false, 0><<<grid, B * B / 2, 0, st>>>(L, tval, b0, b1, b2, dimg, T, nc, none);
-    else if (l1->u8)
-        k_render_bwd<B, BATCH, false, 1><<<grid, B * B / 2, 0, st>>>(L, tval, b0, b1, b2, nullptr, T, nc, *l1);
-    else
-        k_render_bwd<B, BATCH, false, 2><<<grid, B * B / 2, 0, st>>>(L, tval, b0, b1, b2, nullptr, T, nc, *l1);
+    const int NT = B * B / 2;
+    if (c.exact) {
+        k_render_bwd<B, BATCH, true, 0, true><<<grid, NT, 0, st>>>(L, tval, b0, b1, b2, dimg, T, nc, none);
+    } else if (L.count_pairs) {
+        if (!l1) k_render_bwd<B, BATCH, false, 0, true><<<grid, NT, 0, st>>>(L, tval, b0, b1, b2, dimg, T, nc, none);
+        else if (l1->u8) k_render_bwd<B, BATCH, false, 1, true><<<grid, NT, 0, st>>>(L, tval, b0, b1, b2, nullptr, T, nc, *l1);
+        else k_render_bwd<B, BATCH, false, 2, true><<<grid, NT, 0, st>>>(L, tval, b0, b1, b2, nullptr, T, nc, *l1);
+    } else {
+        if (!l1) k_render_bwd<B, BATCH, false, 0, false><<<grid, NT, 0, st>>>(L, tval, b0, b1, b2, dimg, T, nc, none);
+        else if (l1->u8) k_render_bwd<B, BATCH, false, 1, false><<<grid, NT, 0, st>>>(L, tval, b0, b1, b2, nullptr, T, nc, *l1);
+        else k_render_bwd<B, BATCH, false, 2, false><<<grid, NT, 0, st>>>(L, tval, b0, b1, b2, nullptr, T, nc, *l1);
+    }
 }
 
 // l1 != NULL: the L1 loss and its gradient are formed inside the kernel (dimg unused); not

@@ -55,7 +55,7 @@ extern "C" int32_t cgs_render_forward_static(const cgs_scene* scene, const cgs_c
     f.height = height;
     f.tile = cfg->tile;
     f.n_blocks = scene->n_blocks;
-    f._pad = 0;
+    f.flags = 0;
     f.n_cap = scene->n > 0 ? scene->n : 1;
     f.k_cap = CGS_STATIC_MAX_ENTRIES;
     const int64_t need = cgs_frame_workspace_bytes(1, width, height, cfg->tile, scene->n_blocks, f.n_cap, f.k_cap);

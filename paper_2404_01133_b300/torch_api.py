@@ -151,7 +151,7 @@ class UploadedScene:
 class Frame:
     """Workspace of a batch of equally sized views (device memory from torch)."""
 
-    def __init__(self, n_views, width, height, tile, n_blocks, n_cap, k_cap, device="cuda"):
+    def __init__(self, n_views, width, height, tile, n_blocks, n_cap, k_cap, device="cuda", count_pairs=True):
         nbytes = _c.cgs_frame_workspace_bytes(n_views, width, height, tile, n_blocks, n_cap, k_cap)
         if nbytes <= 0:
             raise ValueError("invalid frame dimensions")
@@ -161,6 +161,7 @@ class Frame:
         f.ws_bytes = nbytes
         f.n_views, f.width, f.height, f.tile, f.n_blocks = n_views, width, height, tile, n_blocks
         f.n_cap, f.k_cap = n_cap, k_cap
+        f.flags = 0 if count_pairs else _c.CGS_FRAME_NO_PAIR_COUNT
         self.struct = f
         self.n_views, self.width, self.height, self.tile = n_views, width, height, tile
         self.n_cap, self.k_cap = n_cap, k_cap

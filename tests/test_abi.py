@@ -54,6 +54,13 @@ def test_host_argument_checks_need_no_device(libcgs):
     assert libcgs.cgs_render_forward(C.byref(s), C.byref(f), C.byref(c), None, None, None, None, None, None,
                                      None) == cgs.CGS_ERR_INVALID_ARGUMENT
     assert libcgs.cgs_l1_loss(None, None, 10, None, None, None) == cgs.CGS_ERR_INVALID_ARGUMENT
+    # a frame with an unknown flag is rejected before any CUDA call
+    f2 = cgs.cgs_frame()
+    f2.ws, f2.ws_bytes = 256, 1 << 30
+    f2.n_views, f2.width, f2.height, f2.tile, f2.n_blocks, f2.n_cap, f2.k_cap = 1, 64, 64, 16, 1, 100, 1000
+    f2.flags = 2
+    st, cnt = C.c_int32(0), (C.c_int64 * 8)()
+    assert libcgs.cgs_frame_status(C.byref(f2), C.byref(st), cnt, None) == cgs.CGS_ERR_INVALID_ARGUMENT
     assert cgs.cgs_status_string(cgs.CGS_ERR_CAPACITY).startswith("capacity")
     assert cgs.cgs_version() == 1
 

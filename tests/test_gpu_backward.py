@@ -114,6 +114,30 @@ def test_backward_twice_accumulates_and_state_resets():
         np.testing.assert_allclose(a[k], b[k], rtol=1e-4, atol=1e-5 * np.abs(a[k]).max())
 
 
+def test_backward_without_the_pair_count_gives_the_same_gradients():
+    """A frame flagged CGS_FRAME_NO_PAIR_COUNT: the backward's gradients are those of the
+    counting backward (up to the order of its atomic additions) and the contributing-pair
+    count is left out, in a backward of an existing frame and in a fresh forward + backward."""
+    sc = synth.single_block(synth.random_cube_scene(600, seed=23, sh_degree=3, log_scale_mu=-2.4))
+    cam = synth.small_scene_camera(80, 64, f=70.0, dist=3.0)
+    g = gpu_render(sc, [cam])
+    w = np.random.default_rng(4).normal(size=(3, 64, 80)).astype(np.float32)
+    a = gpu_grads(g, w)
+    pairs = g["frame"].status()[1][4]
+    assert pairs > 0
+    g["frame"].struct.flags = cgs.CGS_FRAME_NO_PAIR_COUNT
+    b = gpu_grads(g, w)
+    assert g["frame"].status()[1][4] == pairs        # not counted again
+    for k in a:
+        np.testing.assert_allclose(b[k], a[k], rtol=1e-4, atol=1e-5 * np.abs(a[k]).max())
+    ta.render_forward(g["ds"], g["frame"], g["cfg"], g["cams"], out=(g["image"], g["final_T"], g["n_contrib"]))
+    c = gpu_grads(g, w)
+    st, counts = g["frame"].status()
+    assert st == 0 and counts[4] == 0 and counts[3] > 0
+    for k in a:
+        np.testing.assert_allclose(c[k], a[k], rtol=1e-4, atol=1e-5 * np.abs(a[k]).max())
+
+
 def test_l1_loss_kernel():
     rng = np.random.default_rng(5)
     img = rng.uniform(size=(3, 50, 70)).astype(np.float32)
