@@ -148,10 +148,15 @@ __global__ void __launch_bounds__(PB_THREADS, 6) k_project_bwd(Layout L, cgs_sce
     const bool colour_role = threadIdx.x >= PB_PER_CTA;
     const uint32_t li = threadIdx.x - (colour_role ? PB_PER_CTA : 0);
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (uint32_t r0 = blockIdx.x * PB_PER_CTA; r0 < n; r0 += gridDim.x * PB_PER_CTA) {
+    const uint32_t stride = gridDim.x * PB_PER_CTA;
+    for (uint32_t r0 = blockIdx.x * PB_PER_CTA; r0 < n; r0 += stride) {
         const uint32_t r = r0 + li;
         const bool valid = r < n;
         const uint32_t j = valid ? vis[r] : 0u;
+        // the visible-list slot of this thread's next Gaussian, read now and used at the end of
+        // the iteration to fetch that Gaussian's rows into L2
+        const bool more = r + stride < n;
+        const uint32_t jn = more ? vis[r + stride] : 0u;
         float4 ga = z4, gb = z4, gc4 = z4;
         if (valid) {
             ga = L.gs[3 * (size_t)j];
@@ -235,14 +240,34 @@ __global__ void __launch_bounds__(PB_THREADS, 6) k_project_bwd(Layout L, cgs_sce
                 reinterpret_cast<float4*>(g_mo)[r] =
                     make_float4(gm[0] + s_cm[0][li], gm[1] + s_cm[1][li], gm[2] + s_cm[2][li], gb.y);
         }
+        if (more) {
+            // the next Gaussian's rows into L2: the accumulator row and the attribute rows this
+            // role reads
+            const long long gn = L.gidx[jn];
+            const char* acc = reinterpret_cast<const char*>(L.gs + 3 * (size_t)jn);
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(acc));
+            if (colour_role) {
+                const size_t row = (size_t)(nc * 3) * (S.attr_fp16 ? 2u : 4u);
+                const char* q = reinterpret_cast<const char*>(S.sh) + (size_t)gn * row;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
+                if (row > 64) asm volatile("prefetch.global.L2 [%0];" ::"l"(q + row - 1));
+            } else {
+                const size_t ab = S.attr_fp16 ? 8u : 16u;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char*>(S.mean_opac) + 16 * (size_t)gn));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char*>(S.scale) + ab * (size_t)gn));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char*>(S.quat) + ab * (size_t)gn));
+            }
+        }
     }
 }
 
 void launch_project_bwd(const Layout& L, const cgs_scene& S, const cgs_camera* cams, float near_z, float* g_mo,
                         float* g_sc, float* g_q, float* g_sh, long long* g_index, int n_sm, cudaStream_t st)
 {
+    // one wave of resident CTAs (six per SM); each loops over the visible list, fetching its
+    // next Gaussian's rows into L2 while it works on the current one
     long long want = (L.n_cap + PB_PER_CTA - 1) / PB_PER_CTA;
-    long long grid = want < (long long)n_sm * 16 ? want : (long long)n_sm * 16;
+    long long grid = want < (long long)n_sm * 6 ? want : (long long)n_sm * 6;
     if (grid < 1) grid = 1;
     const unsigned gr = (unsigned)grid;
 #define CGS_PB_LAUNCH(D)                                                                                  \
