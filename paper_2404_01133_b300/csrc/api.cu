@@ -94,16 +94,20 @@ static bool make_layout(const cgs_frame* f, Layout* L, size_t* bytes)
     l.n_cap = f->n_cap;
     l.k_cap = f->k_cap;
     const long long vt = (long long)l.V * l.T;
-    const long long scan_tiles_vt = (vt + SCAN_TILE - 1) / SCAN_TILE;
+    l.tsub_sh = vt <= TSUB_MAX_TILES ? 2 : 0;
+    static_assert(TSUB == 4, "tsub_sh is log2 of TSUB");
+    const long long vts = vt << l.tsub_sh;
+    const long long scan_tiles_vt = (vts + SCAN_TILE - 1) / SCAN_TILE;
 
     Carver c{(char*)f->ws, 0};
     l.hdr = c.take<Header>(1);
     l.scan_lb = c.take<unsigned long long>(scan_tiles_vt);
-    l.tcnt = c.take<uint32_t>(vt);
-    l.tcur = c.take<uint32_t>(vt);
+    l.tcnt = c.take<uint32_t>(vts);
+    l.tcur = c.take<uint32_t>(vts);
     l.sel_done = c.take<uint32_t>(l.V);
     l.zero_bytes = c.off;
     l.ranges = c.take<uint32_t>(2 * vt);
+    l.ssub = c.take<uint32_t>(vts);
     l.view_base = c.take<uint32_t>(l.V + 1);
     l.view_cnt = c.take<uint32_t>(l.V);
     l.n_seg = c.take<uint32_t>(l.V);

@@ -32,6 +32,14 @@ struct Header {
     uint32_t ctr[N_CTR];
 };
 
+// A frame of at most TSUB_MAX_TILES (view, tile) pairs counts, ranges and scatters each tile's
+// entries in TSUB sub-ranges (an entry's is the low bits of its selected index), so the
+// scatter's cursors see a TSUB-th of a tile's entries each (the sub-ranges of a tile are
+// contiguous and make up its range); larger frames, whose counters already spread over many
+// tiles, keep one range per tile (Layout::tsub_sh).
+constexpr int TSUB = 4;
+constexpr long long TSUB_MAX_TILES = 65536;
+
 // Polls of a look-back flag before a kernel gives up and latches ST_SPIN.
 constexpr int SPIN_LIMIT = 1 << 22;
 
@@ -44,11 +52,13 @@ struct Layout {
     Header* hdr;
     // zeroed at every forward (one memset from hdr over zero_bytes)
     unsigned long long* scan_lb; // [scan tiles of V*T] look-back words of the tile-range scan
-    uint32_t* tcnt;              // [V * T] entries per tile
-    uint32_t* tcur;              // [V * T] scatter cursors
+    uint32_t* tcnt;              // [V * T][1 << tsub_sh] entries per tile and sub-range
+    uint32_t* tcur;              // [V * T][1 << tsub_sh] scatter cursors
     uint32_t* sel_done;          // [V] CTAs of the view that finished the selection's first phase
     // not zeroed
     uint32_t* ranges;            // [V * T][2] [start, end) of every tile's entries
+    uint32_t* ssub;              // [V * T][1 << tsub_sh] start of every sub-range
+    int tsub_sh;                 // log2 of the sub-ranges per tile: 2 (TSUB) or 0
     uint32_t* view_base;         // [V + 1] exclusive prefix of per-view selected counts
     uint32_t* view_cnt;          // [V] selected count per view
     uint32_t* n_seg;             // [V]

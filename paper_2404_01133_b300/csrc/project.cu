@@ -94,7 +94,8 @@ __device__ __forceinline__ void prefetch_rows(const cgs_scene& S, long long g)
 //            range of the visible list and of the entry buffer with one atomic add each; the
 //            whole CTA then emits the round's (tile << 32 | j) entries: thread t takes entries
 //            t, t + 128, ..., finds the owning Gaussian by a binary search over the round's
-//            exclusive offsets in shared memory, and counts the tile.  A round of large
+//            exclusive offsets in shared memory, and counts the tile (in the sub-range of the
+//            entry's index).  A round of large
 //            Gaussians (hundreds of tiles each, near the camera) is spread over all warps.
 // The order of the visible list and of the entries depends on the order in which CTAs
 // reserve their ranges; nothing downstream depends on it (entries are sorted per tile by
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(PROJ_THREADS, PROJ_CTAS_PER_SM)
                     const uint32_t t = (uint32_t)s_ev[o] * (uint32_t)L.T + (ty0 + local / w) * (uint32_t)L.tiles_x +
                                        (tx0 + local % w);
                     L.eraw[k] = ((unsigned long long)t << 32) | s_ej[o];
-                    atomicAdd(&L.tcnt[t], 1u);
+                    atomicAdd(&L.tcnt[((size_t)t << L.tsub_sh) + (s_ej[o] & ((1u << L.tsub_sh) - 1u))], 1u);
                 }
             }
             __syncthreads();

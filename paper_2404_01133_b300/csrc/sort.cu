@@ -3,7 +3,8 @@
 // ties to the lower index).
 //
 //   tile ranges   single-pass scan of the per-tile counts -> [start, end) of every tile
-//   scatter       one thread per entry: a slot in its tile's range (atomic cursor), key
+//   scatter       one thread per entry: a slot in its tile's range (an atomic cursor of one of
+//                 the tile's sub-ranges, chosen by the entry's index), key
 //                 (FP32 depth bits << 32 | selected index)
 //   tile sort     one CTA per tile: up to 128 keys ranked against each other in shared
 //                 memory (each key's count of smaller keys is its slot), up to 256 a bitonic
@@ -26,20 +27,30 @@ namespace cgs {
 constexpr int TS_THREADS = 128;
 constexpr int RANK_MAX = 2 * TS_THREADS;  // keys per tile sorted by the short-tile kernel
 
-// [start, end) of every (view, tile) from the per-tile counts; tiles longer than RANK_MAX are
-// listed for the long-tile kernel here, so that kernel can run beside the short-tile one.
+// The start of every (view, tile, sub-range) and the [start, end) of every (view, tile) from the
+// per-sub-range counts; tiles longer than RANK_MAX are listed for the long-tile kernel here, so
+// that kernel can run beside the short-tile one.  A tile's counts are consecutive items of one
+// scanning thread (its SCAN_IPT items start at a multiple of SCAN_IPT, which the sub-range count
+// divides), stored in order, so the thread reads back the tile's start at its last sub-range.
 struct TileRangeOp {
     Layout L;
-    __device__ long long count() const { return (long long)L.V * L.T; }
-    __device__ uint32_t load(long long t) const { return L.tcnt[t]; }
-    __device__ void store(long long t, unsigned long long e, uint32_t x) const
+    __device__ long long count() const { return ((long long)L.V * L.T) << L.tsub_sh; }
+    __device__ uint32_t load(long long i) const { return L.tcnt[i]; }
+    __device__ void store(long long i, unsigned long long e, uint32_t x) const
     {
-        L.ranges[2 * t] = (uint32_t)e;
-        L.ranges[2 * t + 1] = (uint32_t)(e + x);
-        if (x > (uint32_t)RANK_MAX) L.big[atomicAdd(&L.hdr->n_big, 1u)] = (uint32_t)t;
+        const long long t = i >> L.tsub_sh;
+        const int sub = (int)(i - (t << L.tsub_sh)), last = (1 << L.tsub_sh) - 1;
+        L.ssub[i] = (uint32_t)e;
+        if (sub == 0) L.ranges[2 * t] = (uint32_t)e;
+        if (sub == last) {
+            const uint32_t end = (uint32_t)(e + x);
+            L.ranges[2 * t + 1] = end;
+            if (end - L.ranges[2 * t] > (uint32_t)RANK_MAX) L.big[atomicAdd(&L.hdr->n_big, 1u)] = (uint32_t)t;
+        }
     }
     __device__ void finish(unsigned long long total) const { (void)total; }
 };
+static_assert(SCAN_IPT % TSUB == 0, "a tile's sub-ranges are scanned by one thread");
 
 // One thread per entry: a slot inside its tile's range and the (depth bits, index) key.
 __global__ void __launch_bounds__(256) k_scatter(Layout L)
@@ -48,7 +59,8 @@ __global__ void __launch_bounds__(256) k_scatter(Layout L)
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         const unsigned long long w = L.eraw[k];
         const uint32_t t = (uint32_t)(w >> 32), j = (uint32_t)w;
-        const uint32_t slot = L.ranges[2 * (size_t)t] + atomicAdd(&L.tcur[t], 1u);
+        const size_t q = ((size_t)t << L.tsub_sh) + (j & ((1u << L.tsub_sh) - 1u));
+        const uint32_t slot = L.ssub[q] + atomicAdd(&L.tcur[q], 1u);
         L.ekey[slot] = ((unsigned long long)(uint32_t)L.pkey[j] << 32) | j;
     }
 }
@@ -400,7 +412,7 @@ int launch_bin(const Layout& L, int n_sm, cudaStream_t st)
 {
     const long long vt = (long long)L.V * L.T;
     TileRangeOp op{L};
-    k_scan<TileRangeOp><<<(unsigned)grid_for(vt, SCAN_TILE, n_sm, 8), SCAN_THREADS, 0, st>>>(
+    k_scan<TileRangeOp><<<(unsigned)grid_for(vt << L.tsub_sh, SCAN_TILE, n_sm, 8), SCAN_THREADS, 0, st>>>(
         op, L.scan_lb, L.hdr->ctr + CTR_SCAN_RANGES, L.hdr);
     k_scatter<<<(unsigned)grid_for(L.k_cap, 256, n_sm, 16), 256, 0, st>>>(L);
     return 2;
