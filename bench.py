@@ -68,7 +68,7 @@ OPS_BWD_GRAD = 28
 # batch 128, from one ncu capture of the current build (the summary committed beside the kernel
 # profiles: DRAM bytes per second times the launch's duration); a kernel absent here reports
 # traffic null.  An entry is removed when its kernel changes.
-NCU_TRAFFIC_BYTES = {"render": 15.401e6, "render_bwd": 74.580e6, "project": 79.418e6, "project_bwd": 73.001e6}
+NCU_TRAFFIC_BYTES = {"render": 15.401e6, "render_bwd": 74.580e6, "project_bwd": 73.001e6}
 
 
 def parse_args():
